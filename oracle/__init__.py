@@ -1,0 +1,198 @@
+"""FP64 CPU oracle for the explicit finite-difference step (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg
+may import this package.  The GPU library never imports it and it imports
+nothing of the GPU library: the two share no code.
+
+The arithmetic lives in ``sp_oracle.c`` (plain C, OpenMP over rows, FP64,
+compiled with ``-ffp-contract=off``); this module compiles it and wraps it for
+numpy arrays.  See the C file's header for the equations (SymPhas 2.0, Eq.
+(model-a), Eq. (model-b), Gray-Scott in Pearson's form), the stencils and the
+fixed evaluation order.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sp_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+AC, CH, GS = 0, 1, 2
+S1, S2, S3, S4, S5, S6 = range(6)
+STENCIL_DIMS = {S1: 2, S2: 2, S3: 2, S4: 3, S5: 3, S6: 3}
+STENCIL_RADIUS = {S1: 1, S2: 1, S3: 2, S4: 1, S5: 1, S6: 2}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so next to its source (gcc, no GPU needed)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off",
+               "-fno-fast-math", "-o", _LIB + ".tmp", _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def lib():
+    """The loaded oracle library.  ``SP_ORACLE_LIB`` names another build of the same
+    source (used by the mutation test, which plants mistakes in a copy)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = os.environ.get("SP_ORACLE_LIB")
+            if not path:
+                path = build()
+            L = ctypes.CDLL(path)
+            i64, dbl, ptr, u64 = ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_uint64
+            c_int = ctypes.c_int
+            L.or_num_threads.restype = c_int
+            L.or_stencil_q.restype = c_int
+            L.or_stencil_q.argtypes = [c_int]
+            L.or_stencil_sum.argtypes = [c_int, i64, i64, i64, ptr, ptr]
+            L.or_laplacian.argtypes = [c_int, i64, i64, i64, dbl, ptr, ptr]
+            L.or_chemical_potential.argtypes = [c_int, i64, i64, i64, dbl, ptr, ptr, ptr]
+            L.or_step.argtypes = [c_int, c_int, i64, i64, i64, dbl, dbl, ptr, ptr, ptr, i64]
+            L.or_splitmix64_nth.restype = u64
+            L.or_splitmix64_nth.argtypes = [u64, u64]
+            L.or_u01.restype = dbl
+            L.or_u01.argtypes = [u64, u64]
+            L.or_initial_condition.argtypes = [c_int, c_int, i64, i64, i64, u64, dbl, dbl, i64, i64, ptr, ptr]
+            L.or_sum.restype = dbl
+            L.or_sum.argtypes = [ptr, i64]
+            L.or_mass.restype = dbl
+            L.or_mass.argtypes = [c_int, i64, i64, i64, dbl, ptr]
+            L.or_free_energy.restype = dbl
+            L.or_free_energy.argtypes = [c_int, i64, i64, i64, dbl, dbl, dbl, ptr]
+            L.or_rel_l2.restype = dbl
+            L.or_rel_l2.argtypes = [ptr, ptr, i64]
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a
+
+
+def _shape3(a: np.ndarray, dims: int):
+    """numpy shape (ny, nx) or (nz, ny, nx) -> (nx, ny, nz)."""
+    if dims == 2:
+        ny, nx = a.shape
+        return nx, ny, 1
+    nz, ny, nx = a.shape
+    return nx, ny, nz
+
+
+def params(c1=1.0, c2=1.0, kappa=1.0, Du=0.16, Dv=0.08, F=0.035, k=0.065) -> np.ndarray:
+    """Parameter vector in the oracle's order: c1, c2, kappa, Du, Dv, F, k."""
+    return np.array([c1, c2, kappa, Du, Dv, F, k], dtype=np.float64)
+
+
+def num_threads() -> int:
+    return lib().or_num_threads()
+
+
+def stencil_q(st: int) -> int:
+    return lib().or_stencil_q(st)
+
+
+def stencil_sum(st: int, f) -> np.ndarray:
+    f = _f64(f)
+    out = np.empty_like(f)
+    nx, ny, nz = _shape3(f, STENCIL_DIMS[st])
+    if lib().or_stencil_sum(st, nx, ny, nz, _p(f), _p(out)):
+        raise ValueError("or_stencil_sum: bad arguments")
+    return out
+
+
+def laplacian(st: int, f, h: float = 1.0) -> np.ndarray:
+    f = _f64(f)
+    out = np.empty_like(f)
+    nx, ny, nz = _shape3(f, STENCIL_DIMS[st])
+    if lib().or_laplacian(st, nx, ny, nz, h, _p(f), _p(out)):
+        raise ValueError("or_laplacian: bad arguments")
+    return out
+
+
+def chemical_potential(st: int, f, h: float = 1.0, prm=None) -> np.ndarray:
+    f = _f64(f)
+    prm = params() if prm is None else _f64(prm)
+    out = np.empty_like(f)
+    nx, ny, nz = _shape3(f, STENCIL_DIMS[st])
+    if lib().or_chemical_potential(st, nx, ny, nz, h, _p(prm), _p(f), _p(out)):
+        raise ValueError("or_chemical_potential: bad arguments")
+    return out
+
+
+def step(model: int, st: int, u, v=None, *, h: float = 1.0, dt: float, prm=None, nsteps: int = 1):
+    """Return the fields after ``nsteps`` forward-Euler steps (copies; inputs untouched)."""
+    u = np.array(u, dtype=np.float64, copy=True, order="C")
+    vv = None if v is None else np.array(v, dtype=np.float64, copy=True, order="C")
+    prm = params() if prm is None else _f64(prm)
+    nx, ny, nz = _shape3(u, STENCIL_DIMS[st])
+    rc = lib().or_step(model, st, nx, ny, nz, h, dt, _p(prm), _p(u),
+                       None if vv is None else _p(vv), int(nsteps))
+    if rc:
+        raise ValueError("or_step: bad arguments or out of memory")
+    return u if model != GS else (u, vv)
+
+
+def splitmix64_nth(seed: int, n: int) -> int:
+    return int(lib().or_splitmix64_nth(seed, n))
+
+
+def u01(seed: int, n: int) -> float:
+    return float(lib().or_u01(seed, n))
+
+
+def initial_condition(model: int, shape, *, seed: int, mean: float = 0.0, amp: float = 0.01,
+                      patches: int = 0, patch: int = 0):
+    """Seeded initial fields; ``shape`` is (ny, nx) or (nz, ny, nx)."""
+    dims = len(shape)
+    u = np.empty(shape, dtype=np.float64)
+    v = np.empty(shape, dtype=np.float64) if model == GS else None
+    nx, ny, nz = _shape3(u, dims)
+    rc = lib().or_initial_condition(model, dims, nx, ny, nz, seed, mean, amp, patches, patch,
+                                    _p(u), None if v is None else _p(v))
+    if rc:
+        raise ValueError("or_initial_condition: bad arguments")
+    return u if model != GS else (u, v)
+
+
+def kahan_sum(f) -> float:
+    f = _f64(f).ravel()
+    return lib().or_sum(_p(f), f.size)
+
+
+def mass(f, h: float = 1.0) -> float:
+    f = _f64(f)
+    dims = f.ndim
+    nx, ny, nz = _shape3(f, dims)
+    return lib().or_mass(dims, nx, ny, nz, h, _p(f))
+
+
+def free_energy(f, h: float = 1.0, c1: float = 1.0, c2: float = 1.0) -> float:
+    f = _f64(f)
+    dims = f.ndim
+    nx, ny, nz = _shape3(f, dims)
+    return lib().or_free_energy(dims, nx, ny, nz, h, c1, c2, _p(f))
+
+
+def rel_l2(a, b) -> float:
+    a = _f64(a).ravel()
+    b = _f64(b).ravel()
+    assert a.size == b.size
+    return lib().or_rel_l2(_p(a), _p(b), a.size)

@@ -1,0 +1,434 @@
+/*
+ * sp_oracle.c -- plain FP64 CPU oracle for the explicit finite-difference time
+ * step of phase-field and reaction-diffusion models on periodic regular grids
+ * (SymPhas 2.0, arXiv 2511.10508: Model A Eq. (model-a), Model B Eq. (model-b),
+ * the periodic benchmark protocol of Sec. "Benchmarks"; Gray-Scott in Pearson's
+ * two-field form, which the paper names in its Introduction).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the GPU library includes, links or
+ * calls this file, and this file uses nothing of the GPU library; the two share
+ * no code.  Only the tests, the package smoke check and the benchmark's CPU
+ * baseline leg load it.
+ *
+ * Plain on purpose: every time step is a loop over all grid points that reads
+ * its neighbours through a periodic wrap; Cahn-Hilliard stores the chemical
+ * potential of every point in a full array before the outer Laplacian.  There
+ * is no blocking, no fusion across steps and no reordering beyond the fixed
+ * evaluation order written below (which the GPU FP64 path also follows, so
+ * FP64 results can be compared bit for bit).
+ *
+ * Layout: a field is an array of nx*ny*nz doubles, index (z*ny + y)*nx + x,
+ * x fastest; 2D grids have nz == 1.
+ *
+ * Readings of the paper (it prints no stencil coefficients, no integrator and
+ * no Gray-Scott equations):
+ *  - forward Euler: phi' = phi + dt * RHS;
+ *  - Laplacian stencils, written as integer weights over a denominator q,
+ *    L_h f = (1/(q h^2)) * sum_s w_s f(x+s):
+ *      S1 2D 5-point            q=1  : centre -4, faces 1
+ *      S2 2D 9-point isotropic  q=6  : centre -20, faces 4, corners 1
+ *      S3 2D 4th-order cross    q=12 : centre -60, +-1: 16, +-2: -1 (per axis)
+ *      S4 3D 7-point            q=1  : centre -6, faces 1
+ *      S5 3D 27-point isotropic q=30 : centre -128, faces 14, edges 3, corners 1
+ *      S6 3D 4th-order cross    q=12 : centre -90, +-1: 16, +-2: -1 (per axis)
+ *    (the paper derives stencils from polynomial interpolation, Sec.
+ *    "Compile-Time Stencil Generation"; the isotropic S2/S5 choice and the
+ *    4th-order cross are readings, pinned by tests against Taylor moments and
+ *    exact Fourier symbols);
+ *  - Cahn-Hilliard with kappa on the inner Laplacian, both Laplacians by the
+ *    same stencil, composed (L_h applied to mu), not a direct biharmonic;
+ *  - Gray-Scott, both fields read from the old time level:
+ *      du/dt = Du lap u - u v^2 + F (1 - u)
+ *      dv/dt = Dv lap v + u v^2 - (F + k) v.
+ *
+ * Fixed evaluation order (the FP64 parity contract), per point:
+ *   class sums of neighbours as written in stencil_sum(), then
+ *   S = fma(w_centre, f0, <weighted class sums>);
+ *   q_h2 = (q*h)*h;
+ *   Allen-Cahn:    rhs = fma(p, fma(-c2, p*p, c1), (1/q_h2)*S);  p' = fma(dt, rhs, p)
+ *   Cahn-Hilliard: mu  = fma(p, fma(c2, p*p, -c1), -((kappa/q_h2)*S(p)))
+ *                  p'  = fma(dt/q_h2, S(mu), p)
+ *   Gray-Scott:    uvv = (u*v)*v
+ *                  ru  = fma(F, 1-u, fma(Du/q_h2, S(u), -uvv))
+ *                  rv  = fma(-(F+k), v, fma(Dv/q_h2, S(v), uvv))
+ *                  u'  = fma(dt, ru, u);  v' = fma(dt, rv, v)
+ * Compile with -ffp-contract=off so that no other multiply-add is fused.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { OR_S1 = 0, OR_S2 = 1, OR_S3 = 2, OR_S4 = 3, OR_S5 = 4, OR_S6 = 5 };
+enum { OR_AC = 0, OR_CH = 1, OR_GS = 2 };
+/* parameter vector: c1, c2, kappa, Du, Dv, F, k */
+enum { P_C1 = 0, P_C2, P_KAPPA, P_DU, P_DV, P_F, P_K, P_COUNT };
+
+#define OR_MAXR 2
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+int or_stencil_dims(int st) { return (st >= OR_S4) ? 3 : 2; }
+int or_stencil_radius(int st) { return (st == OR_S3 || st == OR_S6) ? 2 : 1; }
+int or_stencil_q(int st) {
+    switch (st) {
+    case OR_S1: return 1;
+    case OR_S2: return 6;
+    case OR_S3: return 12;
+    case OR_S4: return 1;
+    case OR_S5: return 30;
+    case OR_S6: return 12;
+    }
+    return 0;
+}
+
+/* Periodic neighbour tables: w[a][(d+R)*n + i] = (i + d) mod n for |d| <= R. */
+typedef struct {
+    int64_t n[3];
+    int64_t *w[3];
+} grid_t;
+
+static int grid_init(grid_t *g, int64_t nx, int64_t ny, int64_t nz) {
+    g->n[0] = nx; g->n[1] = ny; g->n[2] = nz;
+    for (int a = 0; a < 3; a++) {
+        int64_t n = g->n[a];
+        g->w[a] = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * OR_MAXR + 1) * (size_t)n);
+        if (!g->w[a]) return -1;
+        for (int d = -OR_MAXR; d <= OR_MAXR; d++)
+            for (int64_t i = 0; i < n; i++) {
+                int64_t r = (i + d) % n;
+                if (r < 0) r += n;
+                g->w[a][(d + OR_MAXR) * n + i] = r;
+            }
+    }
+    return 0;
+}
+
+static void grid_free(grid_t *g) {
+    for (int a = 0; a < 3; a++) free(g->w[a]);
+}
+
+static inline double at(const double *f, const grid_t *g, int64_t x, int64_t y, int64_t z,
+                        int dx, int dy, int dz) {
+    int64_t xx = g->w[0][(dx + OR_MAXR) * g->n[0] + x];
+    int64_t yy = g->w[1][(dy + OR_MAXR) * g->n[1] + y];
+    int64_t zz = g->w[2][(dz + OR_MAXR) * g->n[2] + z];
+    return f[(zz * g->n[1] + yy) * g->n[0] + xx];
+}
+
+/* Unscaled weighted neighbour sum S = sum_s w_s f(x+s), in the fixed order. */
+static double stencil_sum(int st, const double *f, const grid_t *g, int64_t x, int64_t y, int64_t z) {
+#define P(dx, dy, dz) at(f, g, x, y, z, dx, dy, dz)
+    switch (st) {
+    case OR_S1: {
+        double C = (P(-1, 0, 0) + P(1, 0, 0)) + (P(0, -1, 0) + P(0, 1, 0));
+        return fma(-4.0, P(0, 0, 0), C);
+    }
+    case OR_S2: {
+        double C = (P(-1, 0, 0) + P(1, 0, 0)) + (P(0, -1, 0) + P(0, 1, 0));
+        double D = (P(-1, -1, 0) + P(1, -1, 0)) + (P(-1, 1, 0) + P(1, 1, 0));
+        return fma(-20.0, P(0, 0, 0), fma(4.0, C, D));
+    }
+    case OR_S3: {
+        double F1 = (P(-1, 0, 0) + P(1, 0, 0)) + (P(0, -1, 0) + P(0, 1, 0));
+        double F2 = (P(-2, 0, 0) + P(2, 0, 0)) + (P(0, -2, 0) + P(0, 2, 0));
+        return fma(-60.0, P(0, 0, 0), fma(16.0, F1, -F2));
+    }
+    case OR_S4: {
+        double F = ((P(-1, 0, 0) + P(1, 0, 0)) + (P(0, -1, 0) + P(0, 1, 0))) + (P(0, 0, -1) + P(0, 0, 1));
+        return fma(-6.0, P(0, 0, 0), F);
+    }
+    case OR_S5: {
+        /* in-plane cross and diagonal sums of the planes dz = -1, 0, 1 */
+        double Cm = (P(-1, 0, -1) + P(1, 0, -1)) + (P(0, -1, -1) + P(0, 1, -1));
+        double C0 = (P(-1, 0, 0) + P(1, 0, 0)) + (P(0, -1, 0) + P(0, 1, 0));
+        double Cp = (P(-1, 0, 1) + P(1, 0, 1)) + (P(0, -1, 1) + P(0, 1, 1));
+        double Dm = (P(-1, -1, -1) + P(1, -1, -1)) + (P(-1, 1, -1) + P(1, 1, -1));
+        double D0 = (P(-1, -1, 0) + P(1, -1, 0)) + (P(-1, 1, 0) + P(1, 1, 0));
+        double Dp = (P(-1, -1, 1) + P(1, -1, 1)) + (P(-1, 1, 1) + P(1, 1, 1));
+        double F = C0 + (P(0, 0, -1) + P(0, 0, 1)); /* 6 faces   */
+        double E = D0 + (Cm + Cp);                  /* 12 edges  */
+        double K = Dm + Dp;                         /* 8 corners */
+        return fma(-128.0, P(0, 0, 0), fma(14.0, F, fma(3.0, E, K)));
+    }
+    case OR_S6: {
+        double F1 = ((P(-1, 0, 0) + P(1, 0, 0)) + (P(0, -1, 0) + P(0, 1, 0))) + (P(0, 0, -1) + P(0, 0, 1));
+        double F2 = ((P(-2, 0, 0) + P(2, 0, 0)) + (P(0, -2, 0) + P(0, 2, 0))) + (P(0, 0, -2) + P(0, 0, 2));
+        return fma(-90.0, P(0, 0, 0), fma(16.0, F1, -F2));
+    }
+    }
+#undef P
+    return NAN;
+}
+
+static int check_grid(int st, int64_t nx, int64_t ny, int64_t nz) {
+    if (st < OR_S1 || st > OR_S6) return -1;
+    if (nx < 1 || ny < 1 || nz < 1) return -1;
+    if (or_stencil_dims(st) == 2 && nz != 1) return -1;
+    return 0;
+}
+
+/* out = S (unscaled weighted sum) at every point. */
+int or_stencil_sum(int st, int64_t nx, int64_t ny, int64_t nz, const double *f, double *out) {
+    grid_t g;
+    if (check_grid(st, nx, ny, nz) || grid_init(&g, nx, ny, nz)) return -1;
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int64_t z = 0; z < nz; z++)
+        for (int64_t y = 0; y < ny; y++)
+            for (int64_t x = 0; x < nx; x++)
+                out[(z * ny + y) * nx + x] = stencil_sum(st, f, &g, x, y, z);
+    grid_free(&g);
+    return 0;
+}
+
+/* out = L_h f = S / (q h^2) at every point. */
+int or_laplacian(int st, int64_t nx, int64_t ny, int64_t nz, double h, const double *f, double *out) {
+    if (or_stencil_sum(st, nx, ny, nz, f, out)) return -1;
+    const double s = 1.0 / (((double)or_stencil_q(st) * h) * h);
+    const int64_t n = nx * ny * nz;
+    for (int64_t i = 0; i < n; i++) out[i] = s * out[i];
+    return 0;
+}
+
+/* Cahn-Hilliard chemical potential mu = c2 p^3 - c1 p - kappa L_h p at every point. */
+static void ch_mu(int st, const grid_t *g, const double *p, double *mu, double kq, double c1, double c2) {
+    const int64_t nx = g->n[0], ny = g->n[1], nz = g->n[2];
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int64_t z = 0; z < nz; z++)
+        for (int64_t y = 0; y < ny; y++)
+            for (int64_t x = 0; x < nx; x++) {
+                const int64_t i = (z * ny + y) * nx + x;
+                const double pi = p[i];
+                const double S = stencil_sum(st, p, g, x, y, z);
+                mu[i] = fma(pi, fma(c2, pi * pi, -c1), -(kq * S));
+            }
+}
+
+int or_chemical_potential(int st, int64_t nx, int64_t ny, int64_t nz, double h, const double *prm,
+                          const double *p, double *mu) {
+    grid_t g;
+    if (check_grid(st, nx, ny, nz) || grid_init(&g, nx, ny, nz)) return -1;
+    const double q_h2 = ((double)or_stencil_q(st) * h) * h;
+    ch_mu(st, &g, p, mu, prm[P_KAPPA] / q_h2, prm[P_C1], prm[P_C2]);
+    grid_free(&g);
+    return 0;
+}
+
+/*
+ * Advance nsteps forward-Euler steps in place.  u is the only field of
+ * Allen-Cahn / Cahn-Hilliard; Gray-Scott has u and v.  prm = {c1, c2, kappa,
+ * Du, Dv, F, k}.  Returns 0, or -1 on bad arguments / allocation failure.
+ */
+int or_step(int model, int st, int64_t nx, int64_t ny, int64_t nz, double h, double dt,
+            const double *prm, double *u, double *v, int64_t nsteps) {
+    grid_t g;
+    if (check_grid(st, nx, ny, nz) || model < OR_AC || model > OR_GS || nsteps < 0) return -1;
+    if (model == OR_GS && !v) return -1;
+    if (grid_init(&g, nx, ny, nz)) return -1;
+    const int64_t n = nx * ny * nz;
+    const double q_h2 = ((double)or_stencil_q(st) * h) * h;
+    const double c1 = prm[P_C1], c2 = prm[P_C2];
+    double *un = (double *)malloc(sizeof(double) * (size_t)n);
+    double *vn = (model == OR_GS) ? (double *)malloc(sizeof(double) * (size_t)n) : NULL;
+    double *mu = (model == OR_CH) ? (double *)malloc(sizeof(double) * (size_t)n) : NULL;
+    if (!un || (model == OR_GS && !vn) || (model == OR_CH && !mu)) {
+        free(un); free(vn); free(mu); grid_free(&g);
+        return -1;
+    }
+    double *uc = u, *vc = v;
+    for (int64_t s = 0; s < nsteps; s++) {
+        if (model == OR_AC) {
+            const double sAC = 1.0 / q_h2;
+#pragma omp parallel for collapse(2) schedule(static)
+            for (int64_t z = 0; z < nz; z++)
+                for (int64_t y = 0; y < ny; y++)
+                    for (int64_t x = 0; x < nx; x++) {
+                        const int64_t i = (z * ny + y) * nx + x;
+                        const double p = uc[i];
+                        const double S = stencil_sum(st, uc, &g, x, y, z);
+                        const double rhs = fma(p, fma(-c2, p * p, c1), sAC * S);
+                        un[i] = fma(dt, rhs, p);
+                    }
+        } else if (model == OR_CH) {
+            ch_mu(st, &g, uc, mu, prm[P_KAPPA] / q_h2, c1, c2);
+            const double dq = dt / q_h2;
+#pragma omp parallel for collapse(2) schedule(static)
+            for (int64_t z = 0; z < nz; z++)
+                for (int64_t y = 0; y < ny; y++)
+                    for (int64_t x = 0; x < nx; x++) {
+                        const int64_t i = (z * ny + y) * nx + x;
+                        un[i] = fma(dq, stencil_sum(st, mu, &g, x, y, z), uc[i]);
+                    }
+        } else {
+            const double duq = prm[P_DU] / q_h2, dvq = prm[P_DV] / q_h2;
+            const double F = prm[P_F], Fk = prm[P_F] + prm[P_K];
+#pragma omp parallel for collapse(2) schedule(static)
+            for (int64_t z = 0; z < nz; z++)
+                for (int64_t y = 0; y < ny; y++)
+                    for (int64_t x = 0; x < nx; x++) {
+                        const int64_t i = (z * ny + y) * nx + x;
+                        const double a = uc[i], b = vc[i];
+                        const double uvv = (a * b) * b;
+                        const double ru = fma(F, 1.0 - a, fma(duq, stencil_sum(st, uc, &g, x, y, z), -uvv));
+                        const double rv = fma(-Fk, b, fma(dvq, stencil_sum(st, vc, &g, x, y, z), uvv));
+                        un[i] = fma(dt, ru, a);
+                        vn[i] = fma(dt, rv, b);
+                    }
+        }
+        /* ping-pong: the new level becomes current */
+        double *t = uc; uc = un; un = t;
+        if (model == OR_GS) { t = vc; vc = vn; vn = t; }
+    }
+    if (uc != u) { memcpy(u, uc, sizeof(double) * (size_t)n); un = uc; }
+    if (model == OR_GS && vc != v) { memcpy(v, vc, sizeof(double) * (size_t)n); vn = vc; }
+    free(un); free(vn); free(mu);
+    grid_free(&g);
+    return 0;
+}
+
+/* ---------------------------------------------------------------- IC ---- */
+
+/*
+ * n-th output (n = 0, 1, ...) of SplitMix64 seeded with `seed` (Steele, Lea and
+ * Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014): the
+ * state after n+1 calls is seed + (n+1)*gamma, and the output is the state
+ * passed through the 64-bit finaliser below.
+ */
+uint64_t or_splitmix64_nth(uint64_t seed, uint64_t n) {
+    uint64_t z = seed + (n + 1u) * UINT64_C(0x9E3779B97F4A7C15);
+    z = (z ^ (z >> 30)) * UINT64_C(0xBF58476D1CE4E5B9);
+    z = (z ^ (z >> 27)) * UINT64_C(0x94D049BB133111EB);
+    return z ^ (z >> 31);
+}
+
+/* Uniform double in [0, 1): the top 53 bits of the n-th output. */
+double or_u01(uint64_t seed, uint64_t n) {
+    return (double)(or_splitmix64_nth(seed, n) >> 11) * 0x1.0p-53;
+}
+
+/*
+ * Seeded initial condition (the paper starts from "uniformly distributed random
+ * noise", Sec. "Benchmarks").  With N = nx*ny*nz points:
+ *  - Allen-Cahn / Cahn-Hilliard: u_i = mean + amp*(2 U(i) - 1), U(n) = or_u01(seed, n).
+ *  - Gray-Scott: u = 1, v = 0 everywhere, then `patches` square (2D) or cubic (3D)
+ *    patches of side `patch` set u = 0.5, v = 0.25.  Patch p has lower corner
+ *    c_a - patch/2 on axis a, with c_a = splitmix64_nth(seed, 2N + 3p + a) mod n_a,
+ *    and wraps periodically.  Then u_i += amp*(2U(i)-1), v_i += amp*(2U(N+i)-1)
+ *    (each written as base + amp*(2U-1)).
+ * dims selects 2D (nz must be 1) or 3D.
+ */
+int or_initial_condition(int model, int dims, int64_t nx, int64_t ny, int64_t nz, uint64_t seed,
+                         double mean, double amp, int64_t patches, int64_t patch, double *u, double *v) {
+    if (nx < 1 || ny < 1 || nz < 1 || (dims == 2 && nz != 1) || (dims != 2 && dims != 3)) return -1;
+    const int64_t N = nx * ny * nz;
+    if (model == OR_AC || model == OR_CH) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < N; i++) u[i] = mean + amp * (2.0 * or_u01(seed, (uint64_t)i) - 1.0);
+        return 0;
+    }
+    if (model != OR_GS || !v || patches < 0 || patch < 0) return -1;
+    if (patch > nx || patch > ny || (dims == 3 && patch > nz)) return -1;
+    int64_t *lo = (int64_t *)malloc(sizeof(int64_t) * 3 * (size_t)(patches > 0 ? patches : 1));
+    if (!lo) return -1;
+    for (int64_t p = 0; p < patches; p++) {
+        const int64_t nn[3] = {nx, ny, nz};
+        for (int a = 0; a < 3; a++) {
+            int64_t c = (int64_t)(or_splitmix64_nth(seed, (uint64_t)(2 * N + 3 * p + a)) % (uint64_t)nn[a]);
+            int64_t l = (c - patch / 2) % nn[a];
+            if (l < 0) l += nn[a];
+            lo[3 * p + a] = l;
+        }
+    }
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int64_t z = 0; z < nz; z++)
+        for (int64_t y = 0; y < ny; y++)
+            for (int64_t x = 0; x < nx; x++) {
+                const int64_t i = (z * ny + y) * nx + x;
+                double bu = 1.0, bv = 0.0;
+                for (int64_t p = 0; p < patches; p++) {
+                    int64_t ox = (x - lo[3 * p + 0]) % nx; if (ox < 0) ox += nx;
+                    int64_t oy = (y - lo[3 * p + 1]) % ny; if (oy < 0) oy += ny;
+                    int64_t oz = 0;
+                    if (dims == 3) { oz = (z - lo[3 * p + 2]) % nz; if (oz < 0) oz += nz; }
+                    if (ox < patch && oy < patch && oz < (dims == 3 ? patch : 1)) { bu = 0.5; bv = 0.25; }
+                }
+                u[i] = bu + amp * (2.0 * or_u01(seed, (uint64_t)i) - 1.0);
+                v[i] = bv + amp * (2.0 * or_u01(seed, (uint64_t)(N + i)) - 1.0);
+            }
+    free(lo);
+    return 0;
+}
+
+/* -------------------------------------------------------- reductions ---- */
+
+/* Neumaier-compensated sum, sequential in index order. */
+double or_sum(const double *f, int64_t n) {
+    double s = 0.0, c = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        const double x = f[i];
+        const double t = s + x;
+        if (fabs(s) >= fabs(x)) c += (s - t) + x;
+        else c += (x - t) + s;
+        s = t;
+    }
+    return s + c;
+}
+
+static double cell_volume(int dims, double h) { return dims == 3 ? (h * h) * h : h * h; }
+
+/* Mass M = h^d * sum_i phi_i. */
+double or_mass(int dims, int64_t nx, int64_t ny, int64_t nz, double h, const double *f) {
+    return cell_volume(dims, h) * or_sum(f, nx * ny * nz);
+}
+
+/*
+ * Discrete Landau free energy (the LANDAU_FE density of Models A/B, whose
+ * functional derivative gives Eq. (model-a) and Eq. (model-b)):
+ *   F_h = h^d sum_i [ 1/2 sum_axes ((phi_{i+e} - phi_i)/h)^2 - c1/2 phi^2 + c2/4 phi^4 ]
+ * with forward differences (a reading: the paper gives no discrete gradient).
+ */
+double or_free_energy(int dims, int64_t nx, int64_t ny, int64_t nz, double h, double c1, double c2,
+                      const double *f) {
+    const int64_t n = nx * ny * nz;
+    double *e = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!e) return NAN;
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int64_t z = 0; z < nz; z++)
+        for (int64_t y = 0; y < ny; y++)
+            for (int64_t x = 0; x < nx; x++) {
+                const int64_t i = (z * ny + y) * nx + x;
+                const double p = f[i];
+                const double gx = (f[(z * ny + y) * nx + (x + 1) % nx] - p) / h;
+                const double gy = (f[(z * ny + (y + 1) % ny) * nx + x] - p) / h;
+                double g2 = gx * gx + gy * gy;
+                if (dims == 3) {
+                    const double gz = (f[(((z + 1) % nz) * ny + y) * nx + x] - p) / h;
+                    g2 += gz * gz;
+                }
+                const double p2 = p * p;
+                e[i] = 0.5 * g2 - 0.5 * c1 * p2 + 0.25 * c2 * p2 * p2;
+            }
+    const double r = cell_volume(dims, h) * or_sum(e, n);
+    free(e);
+    return r;
+}
+
+/* Relative L2 distance ||a - b|| / ||b|| (plain, with compensated sums). */
+double or_rel_l2(const double *a, const double *b, int64_t n) {
+    double *d = (double *)malloc(sizeof(double) * (size_t)n);
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!d || !r) { free(d); free(r); return NAN; }
+    for (int64_t i = 0; i < n; i++) { d[i] = (a[i] - b[i]) * (a[i] - b[i]); r[i] = b[i] * b[i]; }
+    const double num = or_sum(d, n), den = or_sum(r, n);
+    free(d); free(r);
+    return den > 0 ? sqrt(num / den) : sqrt(num);
+}
