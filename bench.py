@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the fused explicit time step on one GB300.
+
+Default workload: 2D Cahn-Hilliard (Model B, Eq. (model-b)), 4096 x 4096
+periodic grid, FP64, h = 1, dt = 0.01, kappa = c1 = c2 = 1, 5-point Laplacian,
+seeded uniform noise of +-0.01.  One benchmark step = SUB forward-Euler time
+steps of the whole grid plus one FP64 mass reduction (the mass-drift check).
+
+Prints one JSON line (rank 0).  `value` is GLUPS (grid points x time steps /
+s / 1e9) with the fields resident in HBM, timed with CUDA events on the
+launching stream; `e2e` is the same metric through the C ABI with host
+buffers: every step writes the field from pinned host memory, steps, reduces
+and reads the field back.  `--impl reference` times the FP64 CPU oracle on the
+host cores instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# name -> (model, dims, shape (numpy order), dt, stencil, dtype, sub-steps per bench step)
+WORKLOADS = {
+    "ch2d-4096-f64-lap5": (1, 2, (4096, 4096), 0.01, 0, 0, 100),
+    "ch2d-4096-f64-lap9x4": (1, 2, (4096, 4096), 0.01, 2, 0, 100),
+    "ch2d-4096-f32-lap5": (1, 2, (4096, 4096), 0.01, 0, 1, 100),
+    "ac2d-256-f64-lap5": (0, 2, (256, 256), 0.05, 0, 0, 1000),
+    "gs2d-32768-f32-lap5": (2, 2, (32768, 32768), 1.0, 0, 1, 10),
+    "gs2d-32768-f64-lap5": (2, 2, (32768, 32768), 1.0, 0, 0, 2),
+    "ch3d-1024-f32-lap7": (1, 3, (1024, 1024, 1024), 0.005, 3, 1, 5),
+    "ch3d-1024-bf16-lap7": (1, 3, (1024, 1024, 1024), 0.005, 3, 2, 5),
+    "ch3d-1024-f64-lap7": (1, 3, (1024, 1024, 1024), 0.005, 3, 0, 2),
+    "ch3d-1024-f32-lap27": (1, 3, (1024, 1024, 1024), 0.005, 4, 1, 5),
+    "ch3d-1024-f64-lap27": (1, 3, (1024, 1024, 1024), 0.005, 4, 0, 2),
+}
+DEFAULT = "ch2d-4096-f64-lap5"
+MODEL_NAME = {0: "Allen-Cahn", 1: "Cahn-Hilliard", 2: "Gray-Scott"}
+STENCIL_NAME = {0: "5-point", 1: "9-point box", 2: "4th-order 9-point cross", 3: "7-point", 4: "27-point",
+                5: "4th-order 13-point cross"}
+DTYPE_NAME = {0: "f64", 1: "f32", 2: "bf16-storage/f32"}
+ESIZE = {0: 8, 1: 4, 2: 2}
+
+# FP64 operations per stencil application with the fixed evaluation order and
+# reuse of row/plane partial sums where the order permits it.
+STENCIL_OPS = {0: 4, 1: 6, 2: 8, 3: 6, 4: 12, 5: 12}
+
+
+def fp64_ops_per_lup(model: int, st: int) -> int:
+    s = STENCIL_OPS[st]
+    return {0: s + 5, 1: 2 * s + 5, 2: 2 * s + 9}[model]
+
+
+def hbm_bytes_per_lup(model: int, dtype: int) -> int:
+    nf = 2 if model == 2 else 1
+    return 2 * nf * ESIZE[dtype]
+
+
+def load_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+# FP64 pipe: 152 SMs x 2 FP64 operations / clock x 2070 MHz (max SM clock).
+FP64_PEAK_GOPS = 152 * 2 * 2.070
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_rate(model, dims, shape, dt, st, budget_s=12.0, max_steps=64):
+    """FP64 oracle GLUPS on the host cores over a bounded sample of the workload."""
+    import numpy as np
+
+    import oracle as O
+
+    prm = O.params()
+    npts = int(np.prod(shape))
+    if model == 2:
+        u, v = O.initial_condition(O.GS, shape, seed=2, amp=0.01, patches=64, patch=20)
+    else:
+        u = O.initial_condition(model, shape, seed=1, amp=0.01)
+        v = None
+    t0 = time.perf_counter()
+    O.step(model, st, u, v, dt=dt, prm=prm, nsteps=1) if model == 2 else O.step(model, st, u, dt=dt, prm=prm, nsteps=1)
+    t1 = time.perf_counter() - t0
+    n = int(max(1, min(max_steps, budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    if model == 2:
+        O.step(model, st, u, v, dt=dt, prm=prm, nsteps=n)
+    else:
+        O.step(model, st, u, dt=dt, prm=prm, nsteps=n)
+    el = time.perf_counter() - t0
+    return {"value": npts * n / el / 1e9, "unit": "GLUPS", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{n} FP64 oracle time steps of the full {'x'.join(map(str, shape[::-1]))} grid "
+                      f"({el:.1f} s, OpenMP)"}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    model, dims, shape, dt, st, dtype, sub = WORKLOADS[args.workload]
+    import numpy as np
+
+    import oracle as O
+
+    npts = int(np.prod(shape))
+    prm = O.params()
+    if model == 2:
+        u, v = O.initial_condition(O.GS, shape, seed=2, amp=0.01, patches=64, patch=20)
+    else:
+        u, v = O.initial_condition(model, shape, seed=1, amp=0.01), None
+    # one reference step = a bounded sample: `per` oracle time steps of the full grid
+    t0 = time.perf_counter()
+    O.step(model, st, u, v, dt=dt, prm=prm, nsteps=1) if model == 2 else O.step(model, st, u, dt=dt, prm=prm, nsteps=1)
+    t1 = time.perf_counter() - t0
+    total_budget = 120.0
+    per = int(max(1, min(sub, total_budget / max(t1, 1e-6) / max(1, args.steps + args.warmup))))
+    for _ in range(args.warmup):
+        O.step(model, st, u, v, dt=dt, prm=prm, nsteps=per) if model == 2 else O.step(model, st, u, dt=dt, prm=prm, nsteps=per)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.step(model, st, u, v, dt=dt, prm=prm, nsteps=per) if model == 2 else O.step(model, st, u, dt=dt, prm=prm, nsteps=per)
+    el = time.perf_counter() - t0
+    val = npts * per * args.steps / el / 1e9
+    line = {"impl": "reference", "metric": "GLUPS", "value": val, "unit": "GLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded uniform noise)", "config": workload_config(args.workload),
+            "e2e": {"value": val, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "cpu_baseline": {"value": val, "unit": "GLUPS", "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"each step = {per} FP64 oracle time steps of the full grid"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(name):
+    model, dims, shape, dt, st, dtype, sub = WORKLOADS[name]
+    return {"workload": f"{MODEL_NAME[model]} {dims}D {'x'.join(map(str, shape[::-1]))} {DTYPE_NAME[dtype]}, "
+                        f"{STENCIL_NAME[st]} Laplacian, dt={dt}, h=1, periodic",
+            "model": MODEL_NAME[model], "grid": list(shape[::-1]), "stencil": STENCIL_NAME[st],
+            "storage": DTYPE_NAME[dtype], "time_steps_per_bench_step": sub,
+            "l2": "inputs larger than L2 (ping-pong field buffers exceed the 126 MB L2)"
+            if int(__import__("numpy").prod(shape)) * ESIZE[dtype] * 2 > 126e6 else "L2-resident (small grid)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2511_10508_gb300 as sp
+
+    model, dims, shape, dt, st, dtype, sub = WORKLOADS[args.workload]
+    npts = int(np.prod(shape))
+    kw = dict(stencil=st, dtype=dtype, seed=1 + rank, ic_amp=0.01)
+    if model == 2:
+        kw.update(seed=2 + rank, gs_patches=64, gs_patch=20)
+    sim = sp.Simulation(model, shape, dt=dt, **kw)
+    stream = torch.cuda.Stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    def bench_step():
+        sim.step(sub, stream=stream)
+        sim.reduce(sp.MASS, stream=stream)
+
+    # warm-up
+    for _ in range(args.warmup):
+        bench_step()
+    barrier()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 2)]
+    with ClockSampler(local) as clocks:
+        barrier()
+        ev[0].record(stream)
+        for i in range(args.steps):
+            ev[2 * i + 1].record(stream)
+            sim.step(sub, stream=stream)
+            ev[2 * i + 2].record(stream)
+            sim.reduce(sp.MASS, stream=stream)
+        ev[-1].record(stream)
+        barrier()
+    total_ms = ev[0].elapsed_time(ev[-1])
+    step_ms = sum(ev[2 * i + 1].elapsed_time(ev[2 * i + 2]) for i in range(args.steps))
+    if world > 1:
+        t = torch.tensor([total_ms, step_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms, step_ms = float(t[0]), float(t[1])
+    lups = npts * sub * args.steps
+    value = world * lups / (total_ms * 1e-3) / 1e9
+    launch_ms = step_ms / (args.steps * sub)  # average duration of one step-kernel launch
+
+    peaks = load_peaks()
+    if dtype == 0:
+        ops = fp64_ops_per_lup(model, st)
+        achieved = ops * npts / (launch_ms * 1e-3) / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "FP64 Gop/s",
+                "frac": achieved / FP64_PEAK_GOPS, "traffic": None,
+                "note": f"{ops} FP64 ops/LUP (fixed evaluation order); peak = 152 SMs x 2 FP64 ops/clk x 2.07 GHz; "
+                        f"HBM side {hbm_bytes_per_lup(model, dtype) * npts / (launch_ms * 1e-3) / 1e9:.0f} GB/s"}
+    else:
+        bpl = hbm_bytes_per_lup(model, dtype)
+        achieved = bpl * npts / (launch_ms * 1e-3) / 1e9
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "note": f"{bpl} algorithmic bytes/LUP; peak = measured copy bandwidth"
+                                         + ("" if "hbm_gbs" in peaks else " (fallback)")}
+
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+        host_out = torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+        host_in[...] = sim.read(0, stream=stream)
+        host_v = None
+        if model == 2:
+            host_v = torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+            host_v[...] = sim.read(1, stream=stream)
+        e2e_steps = max(1, min(args.steps, 5))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            sim.write(0, host_in, stream=stream)
+            if model == 2:
+                sim.write(1, host_v, stream=stream)
+            sim.step(sub, stream=stream)
+            sim.reduce(sp.MASS, stream=stream)
+            host_out[...] = 0
+            N = sp._native
+            N.check(N.lib().sp_read(sim.handle, 0, host_out.ctypes.data, host_out.nbytes, 1,
+                                    stream.cuda_stream), "sp_read")
+        barrier()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], dtype=torch.float64, device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t[0])
+        nf = 2 if model == 2 else 1
+        e2e = {"value": world * npts * sub * e2e_steps / el / 1e9, "unit": "GLUPS",
+               "h2d_bytes_per_step": npts * 8 * nf, "d2h_bytes_per_step": npts * 8 + 8, "steps": e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_rate(model, dims, shape, dt, st)
+
+    launches_per_step = sub + 2
+    line = {"metric": "GLUPS", "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {0: "f64", 1: "f32", 2: "bf16"}[dtype],
+            "data": "synthetic (seeded uniform noise, generated on device)",
+            "config": dict(workload_config(args.workload), parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clocks.summary(), "gpu_launches": launches_per_step * args.steps,
+            "kernel_ms_per_time_step": launch_ms}
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,181 @@
+/*
+ * sp.h -- C ABI of the GB300 (sm_103a) explicit finite-difference stepper for
+ * phase-field and reaction-diffusion models on periodic regular grids.
+ *
+ * Method: SymPhas 2.0 (arXiv 2511.10508).  Each time step is one fused pass of
+ *   - a finite-difference Laplacian (stencils from polynomial interpolation,
+ *     Sec. "Compile-Time Stencil Generation"),
+ *   - the pointwise reaction / chemical-potential term of the model
+ *     (Model A, Eq. (model-a); Model B, Eq. (model-b); Gray-Scott, which the
+ *     paper names in its Introduction, in Pearson's two-field form), and
+ *   - the forward-Euler update,
+ * on a periodic grid (Sec. "Benchmarks": periodic boundaries, seeded uniform
+ * noise start).  Fields stay resident on the device; host transfers happen only
+ * on explicit read/write (Sec. "CUDA Implementation").
+ *
+ * Conventions for every call:
+ *  - Return value: SP_OK (0) or one of the sp_status codes; sp_last_error()
+ *    gives a message for the calling thread's last failing call.
+ *  - Grid shape: shape[0] = nx, shape[1] = ny, shape[2] = nz (nz = 1 in 2D).
+ *    Fields are row-major with x fastest: index (z*ny + y)*nx + x.  One field
+ *    (phi) for Allen-Cahn / Cahn-Hilliard, two (u = field 0, v = field 1) for
+ *    Gray-Scott; structure of arrays.
+ *  - Streams: `stream` is a cudaStream_t passed as void*.  NULL selects the
+ *    simulation's own stream.  Device work is enqueued asynchronously on that
+ *    stream, except where a call says it synchronises.
+ *  - Ownership: the library owns every device buffer it allocates and frees it
+ *    in sp_destroy / sp_server_destroy.  The caller owns every host buffer.
+ *  - Thread safety: one handle must not be used from two threads at once;
+ *    different handles are independent.
+ */
+#ifndef SP_H
+#define SP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- enums -- */
+
+typedef enum sp_status {
+    SP_OK = 0,
+    SP_EINVAL = 1,      /* bad argument: shape, model, stencil/dims mismatch, sizes */
+    SP_EUNSTABLE = 2,   /* dt above the forward-Euler stability bound */
+    SP_ENOMEM = 3,      /* device or host allocation failed */
+    SP_EBUDGET = 4,     /* request larger than the server's HBM budget */
+    SP_ECUDA = 5,       /* a CUDA runtime call failed (message in sp_last_error) */
+    SP_ETIMEOUT = 6,    /* a bounded device-side wait expired */
+    SP_EBUSY = 7,       /* resource busy (e.g. server queue full) */
+    SP_PENDING = 8,     /* sp_poll: request not finished yet */
+    SP_ENOTFOUND = 9    /* unknown ticket */
+} sp_status;
+
+typedef enum sp_model {
+    SP_ALLEN_CAHN = 0,     /* Model A, Eq. (model-a): dphi/dt = lap phi + c1 phi - c2 phi^3 */
+    SP_CAHN_HILLIARD = 1,  /* Model B, Eq. (model-b): dphi/dt = lap(c2 phi^3 - c1 phi - kappa lap phi) */
+    SP_GRAY_SCOTT = 2      /* du/dt = Du lap u - u v^2 + F(1-u); dv/dt = Dv lap v + u v^2 - (F+k) v */
+} sp_model;
+
+/* Laplacian stencils (integer weights over a denominator q; L f = sum w f / (q h^2)). */
+typedef enum sp_stencil {
+    SP_LAP_DEFAULT = -1,   /* 5-point in 2D, 7-point in 3D */
+    SP_LAP_5 = 0,          /* 2D, q=1:  centre -4, faces 1 */
+    SP_LAP_9BOX = 1,       /* 2D, q=6:  centre -20, faces 4, corners 1 (isotropic) */
+    SP_LAP_9CROSS4 = 2,    /* 2D, q=12: centre -60, +-1: 16, +-2: -1 per axis (4th order) */
+    SP_LAP_7 = 3,          /* 3D, q=1:  centre -6, faces 1 */
+    SP_LAP_27 = 4,         /* 3D, q=30: centre -128, faces 14, edges 3, corners 1 (isotropic) */
+    SP_LAP_13CROSS4 = 5    /* 3D, q=12: centre -90, +-1: 16, +-2: -1 per axis (4th order) */
+} sp_stencil;
+
+/* Storage / arithmetic precision of the fields. */
+typedef enum sp_dtype {
+    SP_F64 = 0,            /* FP64 storage and arithmetic (bitwise-reproducible order) */
+    SP_F32 = 1,            /* FP32 storage and arithmetic */
+    SP_BF16_F32 = 2        /* BF16 storage, FP32 arithmetic (convert on load/store) */
+} sp_dtype;
+
+typedef enum sp_ic_kind {
+    SP_IC_NOISE = 0,       /* AC/CH: mean + amp*(2U-1); GS: u=1,v=0, patches, then noise */
+    SP_IC_CONSTANT = 1     /* every field = ic_mean (GS: u = ic_mean, v = 0) */
+} sp_ic_kind;
+
+typedef enum sp_reduce_what {
+    SP_MASS = 0,           /* h^d * sum phi (field 0), compensated FP64 */
+    SP_FREE_ENERGY = 1,    /* h^d sum [1/2 |grad+ phi|^2 - c1/2 phi^2 + c2/4 phi^4] (field 0) */
+    SP_SUM_U = 2,          /* sum of field 0 (no h^d) */
+    SP_SUM_V = 3,          /* sum of field 1 (Gray-Scott) */
+    SP_MIN_U = 4,          /* minimum of field 0 */
+    SP_MAX_U = 5,          /* maximum of field 0 */
+    SP_SUMSQ_U = 6         /* sum of squares of field 0 */
+} sp_reduce_what;
+
+/* ----------------------------------------------------------- parameters -- */
+
+typedef struct sp_params {
+    double c1, c2, kappa;  /* Allen-Cahn / Cahn-Hilliard coefficients (defaults 1) */
+    double Du, Dv, F, k;   /* Gray-Scott coefficients */
+    int stencil;           /* sp_stencil */
+    int dtype;             /* sp_dtype */
+    uint64_t seed;         /* initial-condition seed */
+    int ic_kind;           /* sp_ic_kind */
+    double ic_mean, ic_amp;/* noise mean and half-width */
+    int gs_patches;        /* Gray-Scott: number of seeded patches */
+    int gs_patch;          /* Gray-Scott: patch side (points) */
+    int steps_per_launch;  /* time steps fused per kernel launch (temporal blocking);
+                              0 = the library's choice, 1 = none */
+    int flags;             /* reserved, must be 0 */
+} sp_params;
+
+/* Fill *p with the defaults: c1 = c2 = kappa = 1; Du = 0.16, Dv = 0.08, F = 0.035,
+ * k = 0.065; default stencil of `dims`; FP64; seed 0; noise IC with mean 0 and
+ * amp 0.01 (Gray-Scott: 64 patches of side 20); steps_per_launch 0. */
+void sp_params_default(int model, int dims, sp_params *p);
+
+/*
+ * Forward-Euler stability check, host only (no device needed).  The growth
+ * factor of the linearisation about |phi| = 1 (Gray-Scott: the diffusion part
+ * plus the largest reaction rate) must satisfy dt * max|sigma| <= 2.
+ * *factor (may be NULL) receives dt * max|sigma|.  Returns SP_OK when stable,
+ * SP_EUNSTABLE when not, SP_EINVAL for bad arguments.
+ */
+int sp_check_stability(int model, int dims, double h, double dt, const sp_params *p, double *factor);
+
+/* ------------------------------------------------------- one simulation -- */
+
+typedef struct sp_sim sp_sim;
+
+/*
+ * Create a simulation on the current CUDA device: validates the arguments,
+ * checks stability (SP_EUNSTABLE), allocates two device buffers per field (the
+ * current and the next time level; 2 f words per point, Table 2 of the paper
+ * with f0 = 0 because the chemical potential stays on chip) plus a small
+ * reduction scratch, and writes the seeded initial condition on the device.
+ * Synchronises before returning.  *out receives the handle.
+ */
+int sp_create(int model, int dims, const int64_t shape[3], double h, double dt,
+              const sp_params *p, sp_sim **out);
+
+/* Advance nsteps forward-Euler steps; asynchronous on `stream`. */
+int sp_step(sp_sim *sim, int64_t nsteps, void *stream);
+
+/*
+ * Copy field `field` (0 = phi/u, 1 = v) of the current time level to host
+ * memory.  as_f64 != 0 converts to FP64 (exact widening for FP32/BF16);
+ * otherwise the storage type is copied.  `bytes` must equal N * element size.
+ * Synchronises `stream` before returning.
+ */
+int sp_read(sp_sim *sim, int field, void *host_dst, size_t bytes, int as_f64, void *stream);
+
+/*
+ * Overwrite field `field` of the current time level from host memory (FP64
+ * when is_f64 != 0, rounded to nearest into the storage type; otherwise the
+ * storage type).  Synchronises `stream` before returning.
+ */
+int sp_write(sp_sim *sim, int field, const void *host_src, size_t bytes, int is_f64, void *stream);
+
+/* Reduce the current time level (sp_reduce_what) into *out (FP64).  Synchronises. */
+int sp_reduce(sp_sim *sim, int what, double *out, void *stream);
+
+/* Device pointer of field `field` at the current time level (storage type).
+ * Valid until the next sp_step / sp_destroy. */
+int sp_field_devptr(sp_sim *sim, int field, void **dptr);
+
+/* Number of time steps taken since creation. */
+int sp_steps_taken(const sp_sim *sim, int64_t *steps);
+
+/* Release all device memory of the simulation (synchronises its stream). */
+int sp_destroy(sp_sim *sim);
+
+/* Message of the calling thread's last failing call ("" if none). */
+const char *sp_last_error(void);
+
+/* Library version, e.g. 100 for 0.1.0. */
+int sp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SP_H */

@@ -1,0 +1,151 @@
+"""GB300 (sm_103a) explicit finite-difference stepper for phase-field and
+reaction-diffusion models on periodic grids (SymPhas 2.0, arXiv 2511.10508).
+
+The Python layer only marshals arguments into ``libsp.so`` (``include/sp.h``);
+fields live in device memory and every step runs in the library's CUDA
+kernels.  Streams may be torch CUDA streams (``torch.cuda.Stream``) or raw
+``cudaStream_t`` integers.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native as N
+from ._native import (ALLEN_CAHN, BF16_F32, CAHN_HILLIARD, F32, F64, FREE_ENERGY, GRAY_SCOTT, IC_CONSTANT,
+                      IC_NOISE, LAP_5, LAP_7, LAP_9BOX, LAP_9CROSS4, LAP_13CROSS4, LAP_27, LAP_DEFAULT, MASS,
+                      MAX_U, MIN_U, SUM_U, SUM_V, SUMSQ_U, SpError)
+
+__all__ = ["Simulation", "params", "check_stability", "SpError", "ALLEN_CAHN", "CAHN_HILLIARD", "GRAY_SCOTT",
+           "LAP_5", "LAP_9BOX", "LAP_9CROSS4", "LAP_7", "LAP_27", "LAP_13CROSS4", "LAP_DEFAULT", "F64", "F32",
+           "BF16_F32", "IC_NOISE", "IC_CONSTANT", "MASS", "FREE_ENERGY", "SUM_U", "SUM_V", "MIN_U", "MAX_U",
+           "SUMSQ_U"]
+
+_STORAGE = {F64: np.float64, F32: np.float32, BF16_F32: np.uint16}
+
+
+def params(model: int, dims: int, **kw) -> N.sp_params:
+    """sp_params with the library defaults, overridden by keyword arguments."""
+    p = N.sp_params()
+    N.lib().sp_params_default(model, dims, ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(f"sp_params has no field {k!r}")
+        setattr(p, k, v)
+    return p
+
+
+def check_stability(model: int, dims: int, h: float, dt: float, prm: N.sp_params | None = None):
+    """(stable, dt*max|sigma|) from the library's host-only check."""
+    prm = prm if prm is not None else params(model, dims)
+    f = ctypes.c_double(0.0)
+    rc = N.lib().sp_check_stability(model, dims, h, dt, ctypes.byref(prm), ctypes.byref(f))
+    if rc not in (N.SP_OK, N.SP_EUNSTABLE):
+        raise SpError(rc, "sp_check_stability")
+    return rc == N.SP_OK, f.value
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+class Simulation:
+    """One resident grid.  ``shape`` is numpy order: (ny, nx) or (nz, ny, nx)."""
+
+    def __init__(self, model: int, shape, *, h: float = 1.0, dt: float, prm: N.sp_params | None = None, **kw):
+        self.model = model
+        self.shape = tuple(int(s) for s in shape)
+        self.dims = len(self.shape)
+        self.prm = prm if prm is not None else params(model, self.dims, **kw)
+        xyz = (ctypes.c_int64 * 3)(*(list(self.shape[::-1]) + [1] * (3 - self.dims)))
+        h_ = ctypes.c_void_p()
+        N.check(N.lib().sp_create(model, self.dims, xyz, h, dt, ctypes.byref(self.prm), ctypes.byref(h_)),
+                "sp_create")
+        self._h = h_
+        self.nfields = 2 if model == GRAY_SCOTT else 1
+        self.dtype = self.prm.dtype
+
+    # -- lifecycle
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            N.lib().sp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- calls
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def step(self, n: int = 1, stream=None) -> None:
+        N.check(N.lib().sp_step(self._h, int(n), _stream_ptr(stream)), "sp_step")
+
+    def read(self, field: int = 0, as_f64: bool = True, stream=None) -> np.ndarray:
+        dt = np.float64 if as_f64 else _STORAGE[self.dtype]
+        out = np.empty(self.shape, dtype=dt)
+        N.check(N.lib().sp_read(self._h, field, out.ctypes.data, out.nbytes, int(as_f64), _stream_ptr(stream)),
+                "sp_read")
+        return out
+
+    def write(self, field: int, values, stream=None) -> None:
+        arr = np.ascontiguousarray(values)
+        is_f64 = arr.dtype == np.float64
+        if not is_f64 and arr.dtype != _STORAGE[self.dtype]:
+            raise TypeError(f"write expects float64 or the storage dtype, got {arr.dtype}")
+        if arr.shape != self.shape:
+            raise ValueError(f"shape {arr.shape} != {self.shape}")
+        N.check(N.lib().sp_write(self._h, field, arr.ctypes.data, arr.nbytes, int(is_f64), _stream_ptr(stream)),
+                "sp_write")
+
+    def reduce(self, what: int, stream=None) -> float:
+        out = ctypes.c_double(0.0)
+        N.check(N.lib().sp_reduce(self._h, what, ctypes.byref(out), _stream_ptr(stream)), "sp_reduce")
+        return out.value
+
+    def devptr(self, field: int = 0) -> int:
+        p = ctypes.c_void_p()
+        N.check(N.lib().sp_field_devptr(self._h, field, ctypes.byref(p)), "sp_field_devptr")
+        return int(p.value)
+
+    @property
+    def steps_taken(self) -> int:
+        s = ctypes.c_int64(0)
+        N.check(N.lib().sp_steps_taken(self._h, ctypes.byref(s)), "sp_steps_taken")
+        return s.value
+
+    def field_tensor(self, field: int = 0):
+        """Zero-copy torch view of the current level (valid until the next step)."""
+        import torch
+
+        tdt = {F64: torch.float64, F32: torch.float32, BF16_F32: torch.bfloat16}[self.dtype]
+        esize = {F64: 8, F32: 4, BF16_F32: 2}[self.dtype]
+        strides = []
+        acc = 1
+        for s in reversed(self.shape):
+            strides.append(acc * esize)
+            acc *= s
+        typestr = {F64: "<f8", F32: "<f4", BF16_F32: "<u2"}[self.dtype]
+
+        class _CAI:
+            __cuda_array_interface__ = {"shape": self.shape, "typestr": typestr,
+                                        "data": (self.devptr(field), False), "version": 2,
+                                        "strides": tuple(reversed(strides))}
+
+        t = torch.as_tensor(_CAI(), device="cuda")
+        return t.view(tdt) if self.dtype == BF16_F32 else t

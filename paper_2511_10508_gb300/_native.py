@@ -1,0 +1,86 @@
+"""ctypes binding of ``include/sp.h`` (argument marshalling only).
+
+Every computation runs in ``libsp.so``'s CUDA kernels.  If the library is
+missing this module raises ImportError: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsp.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "sp.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'` "
+                      "(nvcc, sm_103a). There is no CPU fallback.")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# enums (mirrors sp.h)
+SP_OK, SP_EINVAL, SP_EUNSTABLE, SP_ENOMEM, SP_EBUDGET, SP_ECUDA, SP_ETIMEOUT, SP_EBUSY, SP_PENDING, SP_ENOTFOUND = range(10)
+ALLEN_CAHN, CAHN_HILLIARD, GRAY_SCOTT = 0, 1, 2
+LAP_DEFAULT, LAP_5, LAP_9BOX, LAP_9CROSS4, LAP_7, LAP_27, LAP_13CROSS4 = -1, 0, 1, 2, 3, 4, 5
+F64, F32, BF16_F32 = 0, 1, 2
+IC_NOISE, IC_CONSTANT = 0, 1
+MASS, FREE_ENERGY, SUM_U, SUM_V, MIN_U, MAX_U, SUMSQ_U = range(7)
+
+
+class sp_params(ctypes.Structure):
+    _fields_ = [("c1", ctypes.c_double), ("c2", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("Du", ctypes.c_double), ("Dv", ctypes.c_double), ("F", ctypes.c_double), ("k", ctypes.c_double),
+                ("stencil", ctypes.c_int), ("dtype", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("ic_kind", ctypes.c_int), ("ic_mean", ctypes.c_double), ("ic_amp", ctypes.c_double),
+                ("gs_patches", ctypes.c_int), ("gs_patch", ctypes.c_int),
+                ("steps_per_launch", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_P = ctypes.POINTER
+
+_SIGS = {
+    "sp_params_default": (None, [ctypes.c_int, ctypes.c_int, _P(sp_params)]),
+    "sp_check_stability": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                          _P(sp_params), _P(ctypes.c_double)]),
+    "sp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P(_i64), ctypes.c_double, ctypes.c_double,
+                                 _P(sp_params), _P(_vp)]),
+    "sp_step": (ctypes.c_int, [_vp, _i64, _vp]),
+    "sp_read": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_int, _vp]),
+    "sp_write": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_int, _vp]),
+    "sp_reduce": (ctypes.c_int, [_vp, ctypes.c_int, _P(ctypes.c_double), _vp]),
+    "sp_field_devptr": (ctypes.c_int, [_vp, ctypes.c_int, _P(_vp)]),
+    "sp_steps_taken": (ctypes.c_int, [_vp, _P(_i64)]),
+    "sp_destroy": (ctypes.c_int, [_vp]),
+    "sp_last_error": (ctypes.c_char_p, []),
+    "sp_version": (ctypes.c_int, []),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def header_functions(path: str = HEADER) -> list[str]:
+    """Names of the functions that ``include/sp.h`` declares."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sp_[a-z0-9_]+)\s*\(", text)))
+
+
+class SpError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib.sp_last_error().decode(errors="replace")
+        super().__init__(f"{where} failed with status {code}: {msg}")
+        self.code = code
+
+
+def check(code: int, where: str) -> None:
+    if code != SP_OK:
+        raise SpError(code, where)
+
+
+def lib() -> ctypes.CDLL:
+    return _lib

@@ -1,0 +1,202 @@
+// sp_common.cuh -- device-side building blocks shared by the step, initial-
+// condition and reduction kernels: stencil tables, the per-model arithmetic in
+// a fixed evaluation order, storage/compute type traits and vector loads.
+//
+// Method: SymPhas 2.0 (arXiv 2511.10508), Model A Eq. (model-a), Model B
+// Eq. (model-b), periodic finite-difference stencils (Sec. "Compile-Time
+// Stencil Generation"); Gray-Scott in Pearson's two-field form.
+//
+// Fixed evaluation order.  The whole library is compiled with --fmad=false, so
+// a*b+c is never contracted; every fused multiply-add below is explicit.  The
+// FP64 kernels evaluate exactly these expressions, so FP64 results are
+// reproducible bit for bit by any implementation that follows the same order:
+//   stencil sum S (integer weights w over denominator q):
+//     S1  C = (f[-1,0]+f[1,0]) + (f[0,-1]+f[0,1]);           S = fma(-4, f0, C)
+//     S2  D = (f[-1,-1]+f[1,-1]) + (f[-1,1]+f[1,1]);          S = fma(-20, f0, fma(4, C, D))
+//     S3  F2 = (f[-2,0]+f[2,0]) + (f[0,-2]+f[0,2]);           S = fma(-60, f0, fma(16, C, -F2))
+//     S4  F = C0 + (f[0,0,-1]+f[0,0,1]);                       S = fma(-6, f0, F)
+//     S5  Cz, Dz = in-plane cross / diagonal sums of plane z;
+//         F = C0 + (f[0,0,-1]+f[0,0,1]); E = D0 + (C- + C+); K = D- + D+
+//                                                              S = fma(-128, f0, fma(14, F, fma(3, E, K)))
+//     S6  F1 = F of S4; F2 = ((f[-2,0,0]+f[2,0,0]) + (f[0,-2,0]+f[0,2,0])) + (f[0,0,-2]+f[0,0,2])
+//                                                              S = fma(-90, f0, fma(16, F1, -F2))
+//   with q_h2 = (q*h)*h (host):
+//     Allen-Cahn:    p' = fma(dt, fma(p, fma(-c2, p*p, c1), (1/q_h2)*S(p)), p)
+//     Cahn-Hilliard: mu = fma(p, fma(c2, p*p, -c1), -((kappa/q_h2)*S(p)));  p' = fma(dt/q_h2, S(mu), p)
+//     Gray-Scott:    uvv = (u*v)*v
+//                    u' = fma(dt, fma(F, 1-u, fma(Du/q_h2, S(u), -uvv)), u)
+//                    v' = fma(dt, fma(-(F+k), v, fma(Dv/q_h2, S(v), uvv)), v)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace sp {
+
+enum Model : int { AC = 0, CH = 1, GS = 2 };
+enum Stencil : int { L5 = 0, L9BOX = 1, L9X4 = 2, L7 = 3, L27 = 4, L13X4 = 5 };
+
+template <int ST> struct StencilInfo;
+template <> struct StencilInfo<L5>    { static constexpr int dims = 2, r = 1, q = 1; };
+template <> struct StencilInfo<L9BOX> { static constexpr int dims = 2, r = 1, q = 6; };
+template <> struct StencilInfo<L9X4>  { static constexpr int dims = 2, r = 2, q = 12; };
+template <> struct StencilInfo<L7>    { static constexpr int dims = 3, r = 1, q = 1; };
+template <> struct StencilInfo<L27>   { static constexpr int dims = 3, r = 1, q = 30; };
+template <> struct StencilInfo<L13X4> { static constexpr int dims = 3, r = 2, q = 12; };
+
+// ------------------------------------------------------------ precision --
+
+typedef __nv_bfloat16 bf16;
+
+template <typename T> struct Cmp { typedef T type; };
+template <> struct Cmp<bf16> { typedef float type; };
+
+__device__ __forceinline__ double to_c(double x) { return x; }
+__device__ __forceinline__ float to_c(float x) { return x; }
+__device__ __forceinline__ float to_c(bf16 x) { return __bfloat162float(x); }
+
+template <typename T> __device__ __forceinline__ T from_c(typename Cmp<T>::type x);
+template <> __device__ __forceinline__ double from_c<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_c<float>(float x) { return x; }
+template <> __device__ __forceinline__ bf16 from_c<bf16>(float x) { return __float2bfloat16_rn(x); }
+
+__device__ __forceinline__ double FMA(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float FMA(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// ------------------------------------------------------- vector access --
+
+template <int BYTES> struct VecT;
+template <> struct VecT<2> { typedef unsigned short type; };
+template <> struct VecT<4> { typedef unsigned int type; };
+template <> struct VecT<8> { typedef uint2 type; };
+template <> struct VecT<16> { typedef uint4 type; };
+
+// Load V consecutive elements (16- or 8-byte aligned) and widen to C.
+template <typename T, int V>
+__device__ __forceinline__ void load_vec(const T *__restrict__ p, typename Cmp<T>::type (&out)[V]) {
+    typedef typename VecT<V * sizeof(T)>::type W;
+    union { W w; T t[V]; } u;
+    u.w = __ldg(reinterpret_cast<const W *>(p));
+#pragma unroll
+    for (int i = 0; i < V; ++i) out[i] = to_c(u.t[i]);
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void store_vec(T *__restrict__ p, const typename Cmp<T>::type (&in)[V]) {
+    typedef typename VecT<V * sizeof(T)>::type W;
+    union { W w; T t[V]; } u;
+#pragma unroll
+    for (int i = 0; i < V; ++i) u.t[i] = from_c<T>(in[i]);
+    *reinterpret_cast<W *>(p) = u.w;
+}
+
+template <typename T>
+__device__ __forceinline__ typename Cmp<T>::type load_one(const T *__restrict__ p) { return to_c(__ldg(p)); }
+
+// Periodic wrap of an index that may lie anywhere (small grids: several periods).
+__device__ __forceinline__ int wrap_slow(int i, int n) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+__device__ __forceinline__ int wrap_idx(int i, int n) {
+    return ((unsigned)i < (unsigned)n) ? i : wrap_slow(i, n);
+}
+
+// ------------------------------------------------------------ stencils --
+
+// Unscaled weighted neighbour sum S in the fixed order.  P(dx, dy, dz) returns
+// the neighbour value at that offset (2D stencils use dz = 0 only).
+template <int ST, typename C, typename Acc>
+__device__ __forceinline__ C stencil_sum(const Acc &P) {
+    if constexpr (ST == L5) {
+        const C Cs = (P(-1, 0, 0) + P(1, 0, 0)) + (P(0, -1, 0) + P(0, 1, 0));
+        return FMA(C(-4), P(0, 0, 0), Cs);
+    } else if constexpr (ST == L9BOX) {
+        const C Cs = (P(-1, 0, 0) + P(1, 0, 0)) + (P(0, -1, 0) + P(0, 1, 0));
+        const C D = (P(-1, -1, 0) + P(1, -1, 0)) + (P(-1, 1, 0) + P(1, 1, 0));
+        return FMA(C(-20), P(0, 0, 0), FMA(C(4), Cs, D));
+    } else if constexpr (ST == L9X4) {
+        const C F1 = (P(-1, 0, 0) + P(1, 0, 0)) + (P(0, -1, 0) + P(0, 1, 0));
+        const C F2 = (P(-2, 0, 0) + P(2, 0, 0)) + (P(0, -2, 0) + P(0, 2, 0));
+        return FMA(C(-60), P(0, 0, 0), FMA(C(16), F1, -F2));
+    } else if constexpr (ST == L7) {
+        const C F = ((P(-1, 0, 0) + P(1, 0, 0)) + (P(0, -1, 0) + P(0, 1, 0))) + (P(0, 0, -1) + P(0, 0, 1));
+        return FMA(C(-6), P(0, 0, 0), F);
+    } else if constexpr (ST == L27) {
+        const C Cm = (P(-1, 0, -1) + P(1, 0, -1)) + (P(0, -1, -1) + P(0, 1, -1));
+        const C C0 = (P(-1, 0, 0) + P(1, 0, 0)) + (P(0, -1, 0) + P(0, 1, 0));
+        const C Cp = (P(-1, 0, 1) + P(1, 0, 1)) + (P(0, -1, 1) + P(0, 1, 1));
+        const C Dm = (P(-1, -1, -1) + P(1, -1, -1)) + (P(-1, 1, -1) + P(1, 1, -1));
+        const C D0 = (P(-1, -1, 0) + P(1, -1, 0)) + (P(-1, 1, 0) + P(1, 1, 0));
+        const C Dp = (P(-1, -1, 1) + P(1, -1, 1)) + (P(-1, 1, 1) + P(1, 1, 1));
+        const C F = C0 + (P(0, 0, -1) + P(0, 0, 1));
+        const C E = D0 + (Cm + Cp);
+        const C K = Dm + Dp;
+        return FMA(C(-128), P(0, 0, 0), FMA(C(14), F, FMA(C(3), E, K)));
+    } else {  // L13X4
+        const C F1 = ((P(-1, 0, 0) + P(1, 0, 0)) + (P(0, -1, 0) + P(0, 1, 0))) + (P(0, 0, -1) + P(0, 0, 1));
+        const C F2 = ((P(-2, 0, 0) + P(2, 0, 0)) + (P(0, -2, 0) + P(0, 2, 0))) + (P(0, 0, -2) + P(0, 0, 2));
+        return FMA(C(-90), P(0, 0, 0), FMA(C(16), F1, -F2));
+    }
+}
+
+// ------------------------------------------------------ model constants --
+
+// Host-computed coefficients (see the header comment); narrowed to C on use.
+struct StepConsts {
+    double c1, c2;   // reaction coefficients
+    double sAC;      // 1 / q_h2                (Allen-Cahn Laplacian scale)
+    double kq;       // kappa / q_h2            (Cahn-Hilliard inner)
+    double dq;       // dt / q_h2               (Cahn-Hilliard outer, folded with dt)
+    double duq, dvq; // Du / q_h2, Dv / q_h2    (Gray-Scott)
+    double F, Fk;    // F, F + k
+    double dt;
+};
+
+template <typename C> struct ConstsC {
+    C c1, c2, sAC, kq, dq, duq, dvq, F, Fk, dt;
+    __device__ __forceinline__ explicit ConstsC(const StepConsts &k)
+        : c1(C(k.c1)), c2(C(k.c2)), sAC(C(k.sAC)), kq(C(k.kq)), dq(C(k.dq)), duq(C(k.duq)),
+          dvq(C(k.dvq)), F(C(k.F)), Fk(C(k.Fk)), dt(C(k.dt)) {}
+};
+
+// Allen-Cahn update of one point from its value and stencil sum.
+template <typename C>
+__device__ __forceinline__ C ac_update(C p, C S, const ConstsC<C> &k) {
+    const C rhs = FMA(p, FMA(-k.c2, p * p, k.c1), k.sAC * S);
+    return FMA(k.dt, rhs, p);
+}
+
+// Cahn-Hilliard chemical potential of one point.
+template <typename C>
+__device__ __forceinline__ C ch_mu(C p, C S, const ConstsC<C> &k) {
+    return FMA(p, FMA(k.c2, p * p, -k.c1), -(k.kq * S));
+}
+
+// Cahn-Hilliard update from the stencil sum of mu.
+template <typename C>
+__device__ __forceinline__ C ch_update(C p, C Smu, const ConstsC<C> &k) {
+    return FMA(k.dq, Smu, p);
+}
+
+// Gray-Scott update of (u, v) from values and stencil sums.
+template <typename C>
+__device__ __forceinline__ void gs_update(C u, C v, C Su, C Sv, const ConstsC<C> &k, C &un, C &vn) {
+    const C uvv = (u * v) * v;
+    const C ru = FMA(k.F, C(1) - u, FMA(k.duq, Su, -uvv));
+    const C rv = FMA(-k.Fk, v, FMA(k.dvq, Sv, uvv));
+    un = FMA(k.dt, ru, u);
+    vn = FMA(k.dt, rv, v);
+}
+
+// ------------------------------------------------------- launch records --
+
+struct StepArgs {
+    const void *in0, *in1;   // current level (field 0, field 1)
+    void *out0, *out1;       // next level
+    int nx, ny, nz;
+    StepConsts k;
+};
+
+}  // namespace sp

@@ -1,0 +1,159 @@
+// sp_reduce.cu -- FP64 reductions over a resident field: mass, discrete Landau
+// free energy, sums, sum of squares, min and max.
+//
+// Mass M = h^d sum phi (conserved by Model B, Eq. (model-b)); free energy
+// F_h = h^d sum [1/2 sum_axes ((phi_{i+e} - phi_i)/h)^2 - c1/2 phi^2 + c2/4 phi^4],
+// the Landau density whose functional derivative (Eq. (2) of the paper, first-
+// order case) gives Models A and B, with forward differences.
+//
+// Two passes, deterministic for a fixed grid size: every thread keeps a
+// Neumaier-compensated (sum, correction) pair over a grid-stride range; warps
+// combine pairs with shuffles, blocks through shared memory, and each block
+// writes its pair to a scratch array; a single block then combines the block
+// pairs in index order and writes the scaled result.
+#include "sp_internal.h"
+
+namespace sp {
+
+__device__ __forceinline__ void neu_add(double &s, double &c, double x) {
+    const double t = s + x;
+    c += (fabs(s) >= fabs(x)) ? ((s - t) + x) : ((x - t) + s);
+    s = t;
+}
+
+__device__ __forceinline__ void neu_merge(double &s, double &c, double s2, double c2) {
+    neu_add(s, c, s2);
+    c += c2;
+}
+
+template <int WHAT>
+__device__ __forceinline__ void combine(double &s, double &c, double s2, double c2) {
+    if constexpr (WHAT == SP_MIN_U) s = fmin(s, s2);
+    else if constexpr (WHAT == SP_MAX_U) s = fmax(s, s2);
+    else neu_merge(s, c, s2, c2);
+}
+
+template <int WHAT>
+__device__ __forceinline__ void block_combine(double &s, double &c) {
+    __shared__ double ws[32], wc[32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double s2 = __shfl_down_sync(0xffffffffu, s, off);
+        const double c2 = __shfl_down_sync(0xffffffffu, c, off);
+        combine<WHAT>(s, c, s2, c2);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) { ws[warp] = s; wc[warp] = c; }
+    __syncthreads();
+    if (warp == 0) {
+        s = lane < nw ? ws[lane] : ((WHAT == SP_MIN_U) ? INFINITY : (WHAT == SP_MAX_U ? -INFINITY : 0.0));
+        c = lane < nw ? wc[lane] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double s2 = __shfl_down_sync(0xffffffffu, s, off);
+            const double c2 = __shfl_down_sync(0xffffffffu, c, off);
+            combine<WHAT>(s, c, s2, c2);
+        }
+    }
+}
+
+template <typename T, int WHAT>
+__global__ void __launch_bounds__(kReduceThreads)
+reduce_partial_kernel(const T *__restrict__ f, int nx, int ny, int nz, int dims, double h, double c1,
+                      double c2, double *__restrict__ partials) {
+    const uint64_t N = (uint64_t)nx * ny * nz;
+    double s = (WHAT == SP_MIN_U) ? INFINITY : (WHAT == SP_MAX_U ? -INFINITY : 0.0), c = 0.0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const double p = (double)to_c(f[i]);
+        if constexpr (WHAT == SP_MIN_U) {
+            s = fmin(s, p);
+        } else if constexpr (WHAT == SP_MAX_U) {
+            s = fmax(s, p);
+        } else if constexpr (WHAT == SP_SUMSQ_U) {
+            neu_add(s, c, p * p);
+        } else if constexpr (WHAT == SP_FREE_ENERGY) {
+            const int x = (int)(i % (uint64_t)nx);
+            const int y = (int)((i / (uint64_t)nx) % (uint64_t)ny);
+            const uint64_t row = i - (uint64_t)x;
+            const uint64_t zbase = row - (uint64_t)y * nx;
+            const double px = (double)to_c(f[row + (x + 1 == nx ? 0 : x + 1)]);
+            const double py = (double)to_c(f[zbase + (uint64_t)(y + 1 == ny ? 0 : y + 1) * nx + x]);
+            const double gx = (px - p) / h;
+            const double gy = (py - p) / h;
+            double g2 = gx * gx + gy * gy;
+            if (dims == 3) {
+                const int z = (int)(i / ((uint64_t)nx * ny));
+                const uint64_t plane = (uint64_t)nx * ny;
+                const double pz = (double)to_c(f[(uint64_t)(z + 1 == nz ? 0 : z + 1) * plane + (i - (uint64_t)z * plane)]);
+                const double gz = (pz - p) / h;
+                g2 = g2 + gz * gz;
+            }
+            const double p2 = p * p;
+            neu_add(s, c, 0.5 * g2 - 0.5 * c1 * p2 + 0.25 * c2 * p2 * p2);
+        } else {
+            neu_add(s, c, p);
+        }
+    }
+    block_combine<WHAT>(s, c);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = s;
+        partials[2 * blockIdx.x + 1] = c;
+    }
+}
+
+template <int WHAT>
+__global__ void __launch_bounds__(kReduceThreads)
+reduce_final_kernel(const double *__restrict__ partials, int nblocks, double scale, double *__restrict__ out) {
+    double s = (WHAT == SP_MIN_U) ? INFINITY : (WHAT == SP_MAX_U ? -INFINITY : 0.0), c = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) combine<WHAT>(s, c, partials[2 * b], partials[2 * b + 1]);
+    block_combine<WHAT>(s, c);
+    if (threadIdx.x == 0) {
+        if constexpr (WHAT == SP_MIN_U || WHAT == SP_MAX_U) out[0] = s;
+        else out[0] = scale * (s + c);
+    }
+}
+
+template <typename T, int WHAT>
+static cudaError_t launch_reduce_t(const void *f, const ReduceGeom &g, double *partials, int nblocks,
+                                   double *out, cudaStream_t s) {
+    const double scale = (WHAT == SP_MASS || WHAT == SP_FREE_ENERGY) ? g.cell_volume : 1.0;
+    reduce_partial_kernel<T, WHAT><<<nblocks, kReduceThreads, 0, s>>>(
+        static_cast<const T *>(f), g.nx, g.ny, g.nz, g.dims, g.h, g.c1, g.c2, partials);
+    reduce_final_kernel<WHAT><<<1, kReduceThreads, 0, s>>>(partials, nblocks, scale, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_reduce_dt(int what, const void *f, const ReduceGeom &g, double *partials, int nblocks,
+                                    double *out, cudaStream_t s) {
+    switch (what) {
+    case SP_MASS: return launch_reduce_t<T, SP_MASS>(f, g, partials, nblocks, out, s);
+    case SP_FREE_ENERGY: return launch_reduce_t<T, SP_FREE_ENERGY>(f, g, partials, nblocks, out, s);
+    case SP_SUM_U:
+    case SP_SUM_V: return launch_reduce_t<T, SP_SUM_U>(f, g, partials, nblocks, out, s);
+    case SP_MIN_U: return launch_reduce_t<T, SP_MIN_U>(f, g, partials, nblocks, out, s);
+    case SP_MAX_U: return launch_reduce_t<T, SP_MAX_U>(f, g, partials, nblocks, out, s);
+    case SP_SUMSQ_U: return launch_reduce_t<T, SP_SUMSQ_U>(f, g, partials, nblocks, out, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int reduce_blocks(uint64_t N, int n_sm) {
+    const uint64_t want = (N + kReduceThreads - 1) / kReduceThreads;
+    const uint64_t cap = (uint64_t)n_sm * kReduceBlocksPerSM;
+    const uint64_t b = want < cap ? want : cap;
+    return (int)(b > 0 ? b : 1);
+}
+
+cudaError_t launch_reduce(int dtype, int what, const void *f, const ReduceGeom &g, double *partials,
+                          int nblocks, double *out, cudaStream_t s) {
+    switch (dtype) {
+    case SP_F64: return launch_reduce_dt<double>(what, f, g, partials, nblocks, out, s);
+    case SP_F32: return launch_reduce_dt<float>(what, f, g, partials, nblocks, out, s);
+    default: return launch_reduce_dt<bf16>(what, f, g, partials, nblocks, out, s);
+    }
+}
+
+}  // namespace sp

@@ -1,0 +1,444 @@
+// sp_runtime.cu -- the C ABI of include/sp.h: simulation handles, argument
+// validation, the forward-Euler stability check, device buffers, initial
+// conditions, stepping, host transfers and reductions.
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "sp_internal.h"
+
+using namespace sp;
+
+// --------------------------------------------------------------- errors --
+
+static thread_local std::string g_last_error;
+
+static int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define SP_CUDA(call)                                                                        \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) return fail(SP_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+extern "C" const char *sp_last_error(void) { return g_last_error.c_str(); }
+extern "C" int sp_version(void) { return 100; }
+
+// ---------------------------------------------------- stencil metadata --
+
+static int stencil_dims(int st) { return st >= SP_LAP_7 ? 3 : 2; }
+static int stencil_q(int st) {
+    static const int q[6] = {1, 6, 12, 1, 30, 12};
+    return q[st];
+}
+// max over theta of the symbol lambda(theta) (eigenvalue of -h^2 L_h)
+static double stencil_lambda_max(int st) {
+    static const double lm[6] = {8.0, 16.0 / 3.0, 32.0 / 3.0, 12.0, 92.0 / 15.0, 16.0};
+    return lm[st];
+}
+
+static int resolve_stencil(int st, int dims) {
+    if (st == SP_LAP_DEFAULT) return dims == 2 ? SP_LAP_5 : SP_LAP_7;
+    return st;
+}
+
+extern "C" void sp_params_default(int model, int dims, sp_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->c1 = 1.0;
+    p->c2 = 1.0;
+    p->kappa = 1.0;
+    p->Du = 0.16;
+    p->Dv = 0.08;
+    p->F = 0.035;
+    p->k = 0.065;
+    p->stencil = dims == 3 ? SP_LAP_7 : SP_LAP_5;
+    p->dtype = SP_F64;
+    p->seed = 0;
+    p->ic_kind = SP_IC_NOISE;
+    p->ic_mean = 0.0;
+    p->ic_amp = 0.01;
+    p->gs_patches = model == SP_GRAY_SCOTT ? 64 : 0;
+    p->gs_patch = model == SP_GRAY_SCOTT ? 20 : 0;
+    p->steps_per_launch = 0;
+    p->flags = 0;
+}
+
+static bool is_finite(double x) { return std::isfinite(x); }
+
+// Largest |sigma| of the linearised update over the stencil's spectrum, where
+// sigma is the growth rate of a Fourier mode:
+//   Allen-Cahn:    sigma = -lam + a,            a in {c1 - 3 c2 (|phi| = 1), c1 (phi = 0)}
+//   Cahn-Hilliard: sigma = -lam (kappa lam + a), a in {3 c2 - c1, -c1}
+//   Gray-Scott:    about (u, v) = (1, 0): sigma_u = -Du lam - F, sigma_v = -Dv lam - (F + k)
+// with lam in [0, lambda_max / h^2].  Forward Euler is stable when dt*max|sigma| <= 2.
+static double max_growth(int model, int st, double h, const sp_params &p) {
+    const double lam = stencil_lambda_max(st) / (h * h);
+    double m = 0.0;
+    if (model == SP_ALLEN_CAHN) {
+        const double as[2] = {p.c1 - 3.0 * p.c2, p.c1};
+        for (double a : as) m = std::fmax(m, std::fmax(std::fabs(a), std::fabs(-lam + a)));
+    } else if (model == SP_CAHN_HILLIARD) {
+        const double as[2] = {3.0 * p.c2 - p.c1, -p.c1};
+        for (double a : as) {
+            m = std::fmax(m, std::fabs(lam * (p.kappa * lam + a)));
+            if (p.kappa > 0) {
+                const double ls = -a / (2.0 * p.kappa);
+                if (ls > 0 && ls < lam) m = std::fmax(m, std::fabs(ls * (p.kappa * ls + a)));
+            }
+        }
+    } else {
+        m = std::fmax(std::fabs(p.Du * lam + p.F), std::fabs(p.Dv * lam + p.F + p.k));
+    }
+    return m;
+}
+
+static int validate_params(int model, int dims, double h, double dt, const sp_params &p, int *st_out) {
+    if (model < SP_ALLEN_CAHN || model > SP_GRAY_SCOTT) return fail(SP_EINVAL, "unknown model %d", model);
+    if (dims != 2 && dims != 3) return fail(SP_EINVAL, "dims must be 2 or 3 (got %d)", dims);
+    const int st = resolve_stencil(p.stencil, dims);
+    if (st < SP_LAP_5 || st > SP_LAP_13CROSS4) return fail(SP_EINVAL, "unknown stencil %d", p.stencil);
+    if (stencil_dims(st) != dims) return fail(SP_EINVAL, "stencil %d is %dD but the grid is %dD", st, stencil_dims(st), dims);
+    if (!(is_finite(h) && h > 0)) return fail(SP_EINVAL, "h must be finite and > 0");
+    if (!(is_finite(dt) && dt > 0)) return fail(SP_EINVAL, "dt must be finite and > 0");
+    const double vals[7] = {p.c1, p.c2, p.kappa, p.Du, p.Dv, p.F, p.k};
+    for (double v : vals)
+        if (!is_finite(v)) return fail(SP_EINVAL, "non-finite model coefficient");
+    if (p.dtype < SP_F64 || p.dtype > SP_BF16_F32) return fail(SP_EINVAL, "unknown dtype %d", p.dtype);
+    if (p.flags != 0) return fail(SP_EINVAL, "flags must be 0");
+    if (p.steps_per_launch < 0) return fail(SP_EINVAL, "steps_per_launch must be >= 0");
+    if (p.ic_kind != SP_IC_NOISE && p.ic_kind != SP_IC_CONSTANT) return fail(SP_EINVAL, "unknown ic_kind %d", p.ic_kind);
+    if (!is_finite(p.ic_mean) || !is_finite(p.ic_amp)) return fail(SP_EINVAL, "non-finite ic_mean/ic_amp");
+    *st_out = st;
+    return SP_OK;
+}
+
+extern "C" int sp_check_stability(int model, int dims, double h, double dt, const sp_params *p, double *factor) {
+    if (!p) return fail(SP_EINVAL, "params is NULL");
+    int st;
+    if (int rc = validate_params(model, dims, h, dt, *p, &st)) return rc;
+    const double f = dt * max_growth(model, st, h, *p);
+    if (factor) *factor = f;
+    if (!(f <= 2.0)) return fail(SP_EUNSTABLE, "dt*max|sigma| = %.6g > 2: forward Euler is unstable", f);
+    return SP_OK;
+}
+
+// ---------------------------------------------------------- the handle --
+
+struct sp_sim {
+    int model, dims, stencil, dtype, nf;
+    int nx, ny, nz;
+    uint64_t N;
+    double h, dt;
+    sp_params p;
+    size_t esize;
+    void *f[2][2];        // [level][field]
+    int cur;              // current level
+    int64_t steps;
+    cudaStream_t stream;  // library-owned stream
+    double *d_partials;   // reduction scratch: 2 doubles per block, then the result
+    int nred;
+    double *h_out;        // pinned host scalar
+    double *d_stage;      // FP64 staging for converted transfers (lazy)
+    size_t stage_elems;
+    StepConsts k;
+    int device, n_sm;
+};
+
+static size_t dtype_size(int dt) { return dt == SP_F64 ? 8 : (dt == SP_F32 ? 4 : 2); }
+
+static StepConsts make_consts(const sp_sim &s) {
+    StepConsts k;
+    const double q_h2 = ((double)stencil_q(s.stencil) * s.h) * s.h;
+    k.c1 = s.p.c1;
+    k.c2 = s.p.c2;
+    k.sAC = 1.0 / q_h2;
+    k.kq = s.p.kappa / q_h2;
+    k.dq = s.dt / q_h2;
+    k.duq = s.p.Du / q_h2;
+    k.dvq = s.p.Dv / q_h2;
+    k.F = s.p.F;
+    k.Fk = s.p.F + s.p.k;
+    k.dt = s.dt;
+    return k;
+}
+
+static void release(sp_sim *s) {
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (int l = 0; l < 2; ++l)
+        for (int f = 0; f < 2; ++f)
+            if (s->f[l][f]) cudaFree(s->f[l][f]);
+    if (s->d_partials) cudaFree(s->d_partials);
+    if (s->d_stage) cudaFree(s->d_stage);
+    if (s->h_out) cudaFreeHost(s->h_out);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+extern "C" int sp_create(int model, int dims, const int64_t shape[3], double h, double dt, const sp_params *p,
+                         sp_sim **out) {
+    if (!out) return fail(SP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!shape) return fail(SP_EINVAL, "shape is NULL");
+    sp_params prm;
+    if (p) prm = *p;
+    else sp_params_default(model, dims, &prm);
+    int st;
+    if (int rc = validate_params(model, dims, h, dt, prm, &st)) return rc;
+    const int64_t nx = shape[0], ny = shape[1], nz = dims == 2 ? 1 : shape[2];
+    if (dims == 2 && !(shape[2] == 0 || shape[2] == 1)) return fail(SP_EINVAL, "2D grid needs shape[2] in {0, 1}");
+    if (nx < 1 || ny < 1 || nz < 1) return fail(SP_EINVAL, "grid sides must be >= 1");
+    if (nx > INT_MAX || ny > INT_MAX || nz > INT_MAX) return fail(SP_EINVAL, "grid side too large");
+    if (dims == 3 && nx * ny > (int64_t)INT_MAX) return fail(SP_EINVAL, "3D plane nx*ny must be < 2^31");
+    if (model == SP_GRAY_SCOTT && prm.ic_kind == SP_IC_NOISE) {
+        if (prm.gs_patches < 0 || prm.gs_patches > kMaxPatches)
+            return fail(SP_EINVAL, "gs_patches must be in [0, %d]", kMaxPatches);
+        if (prm.gs_patch < 0 || prm.gs_patch > nx || prm.gs_patch > ny || (dims == 3 && prm.gs_patch > nz))
+            return fail(SP_EINVAL, "gs_patch must be in [0, min side]");
+    }
+    double factor = 0;
+    if (int rc = sp_check_stability(model, dims, h, dt, &prm, &factor)) return rc;
+
+    sp_sim *s = new (std::nothrow) sp_sim();
+    if (!s) return fail(SP_ENOMEM, "host allocation failed");
+    std::memset(s, 0, sizeof *s);
+    s->model = model;
+    s->dims = dims;
+    s->stencil = st;
+    s->dtype = prm.dtype;
+    s->nf = model == SP_GRAY_SCOTT ? 2 : 1;
+    s->nx = (int)nx;
+    s->ny = (int)ny;
+    s->nz = (int)nz;
+    s->N = (uint64_t)nx * ny * nz;
+    s->h = h;
+    s->dt = dt;
+    s->p = prm;
+    s->p.stencil = st;
+    s->esize = dtype_size(prm.dtype);
+    s->k = make_consts(*s);
+
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, s->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        release(s);
+        return fail(SP_ECUDA, "device setup: %s", cudaGetErrorString(e));
+    }
+    const size_t bytes = s->N * s->esize;
+    for (int l = 0; l < 2; ++l)
+        for (int f = 0; f < s->nf; ++f) {
+            e = cudaMalloc(&s->f[l][f], bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                release(s);
+                return fail(SP_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+            }
+        }
+    s->nred = reduce_blocks(s->N, s->n_sm);
+    e = cudaMalloc(&s->d_partials, sizeof(double) * (2 * (size_t)s->nred + 1));
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_out, sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        release(s);
+        return fail(SP_ENOMEM, "scratch allocation failed: %s", cudaGetErrorString(e));
+    }
+    e = launch_ic(s->dtype, s->f[0][0], s->nf > 1 ? s->f[0][1] : nullptr, model, dims, s->nx, s->ny, s->nz,
+                  prm.seed, prm.ic_kind, prm.ic_mean, prm.ic_amp, prm.gs_patches, prm.gs_patch, s->stream, s->n_sm);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        release(s);
+        return fail(SP_ECUDA, "initial condition: %s", cudaGetErrorString(e));
+    }
+    *out = s;
+    return SP_OK;
+}
+
+static cudaStream_t pick(sp_sim *s, void *stream) { return stream ? (cudaStream_t)stream : s->stream; }
+
+static cudaError_t launch_one_step(sp_sim *s, cudaStream_t st) {
+    StepArgs a;
+    a.in0 = s->f[s->cur][0];
+    a.in1 = s->nf > 1 ? s->f[s->cur][1] : s->f[s->cur][0];
+    a.out0 = s->f[1 - s->cur][0];
+    a.out1 = s->nf > 1 ? s->f[1 - s->cur][1] : s->f[1 - s->cur][0];
+    a.nx = s->nx;
+    a.ny = s->ny;
+    a.nz = s->nz;
+    a.k = s->k;
+    switch (s->dtype) {
+    case SP_F64: return launch_step_f64(s->model, s->stencil, a, st, s->n_sm);
+    case SP_F32: return launch_step_f32(s->model, s->stencil, a, st, s->n_sm);
+    default: return launch_step_bf16(s->model, s->stencil, a, st, s->n_sm);
+    }
+}
+
+extern "C" int sp_step(sp_sim *s, int64_t nsteps, void *stream) {
+    if (!s) return fail(SP_EINVAL, "sim is NULL");
+    if (nsteps < 0) return fail(SP_EINVAL, "nsteps must be >= 0");
+    const cudaStream_t st = pick(s, stream);
+    for (int64_t i = 0; i < nsteps; ++i) {
+        SP_CUDA(launch_one_step(s, st));
+        s->cur ^= 1;
+        s->steps += 1;
+    }
+    return SP_OK;
+}
+
+static int check_field(const sp_sim *s, int field) {
+    if (field < 0 || field >= s->nf) return fail(SP_EINVAL, "field %d out of range (model has %d)", field, s->nf);
+    return SP_OK;
+}
+
+static int ensure_stage(sp_sim *s) {
+    if (s->d_stage) return SP_OK;
+    const size_t want = s->N < ((size_t)1 << 22) ? (size_t)s->N : ((size_t)1 << 22);  // <= 32 MiB
+    cudaError_t e = cudaMalloc(&s->d_stage, want * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        s->d_stage = nullptr;
+        return fail(SP_ENOMEM, "staging allocation failed: %s", cudaGetErrorString(e));
+    }
+    s->stage_elems = want;
+    return SP_OK;
+}
+
+extern "C" int sp_read(sp_sim *s, int field, void *host_dst, size_t bytes, int as_f64, void *stream) {
+    if (!s || !host_dst) return fail(SP_EINVAL, "NULL argument");
+    if (int rc = check_field(s, field)) return rc;
+    const bool conv = as_f64 && s->dtype != SP_F64;
+    const size_t want = s->N * (as_f64 ? sizeof(double) : s->esize);
+    if (bytes != want) return fail(SP_EINVAL, "bytes = %zu, expected %zu", bytes, want);
+    const cudaStream_t st = pick(s, stream);
+    const void *src = s->f[s->cur][field];
+    if (!conv) {
+        SP_CUDA(cudaMemcpyAsync(host_dst, src, bytes, cudaMemcpyDeviceToHost, st));
+    } else {
+        if (int rc = ensure_stage(s)) return rc;
+        for (uint64_t off = 0; off < s->N; off += s->stage_elems) {
+            const uint64_t n = (s->N - off) < s->stage_elems ? (s->N - off) : s->stage_elems;
+            SP_CUDA(launch_convert_to_f64(s->dtype, (const char *)src + off * s->esize, s->d_stage, n, st));
+            SP_CUDA(cudaMemcpyAsync((double *)host_dst + off, s->d_stage, n * sizeof(double),
+                                    cudaMemcpyDeviceToHost, st));
+        }
+    }
+    SP_CUDA(cudaStreamSynchronize(st));
+    return SP_OK;
+}
+
+extern "C" int sp_write(sp_sim *s, int field, const void *host_src, size_t bytes, int is_f64, void *stream) {
+    if (!s || !host_src) return fail(SP_EINVAL, "NULL argument");
+    if (int rc = check_field(s, field)) return rc;
+    const bool conv = is_f64 && s->dtype != SP_F64;
+    const size_t want = s->N * (is_f64 ? sizeof(double) : s->esize);
+    if (bytes != want) return fail(SP_EINVAL, "bytes = %zu, expected %zu", bytes, want);
+    const cudaStream_t st = pick(s, stream);
+    void *dst = s->f[s->cur][field];
+    if (!conv) {
+        SP_CUDA(cudaMemcpyAsync(dst, host_src, bytes, cudaMemcpyHostToDevice, st));
+    } else {
+        if (int rc = ensure_stage(s)) return rc;
+        for (uint64_t off = 0; off < s->N; off += s->stage_elems) {
+            const uint64_t n = (s->N - off) < s->stage_elems ? (s->N - off) : s->stage_elems;
+            SP_CUDA(cudaMemcpyAsync(s->d_stage, (const double *)host_src + off, n * sizeof(double),
+                                    cudaMemcpyHostToDevice, st));
+            SP_CUDA(launch_convert_from_f64(s->dtype, s->d_stage, (char *)dst + off * s->esize, n, st));
+        }
+    }
+    SP_CUDA(cudaStreamSynchronize(st));
+    return SP_OK;
+}
+
+extern "C" int sp_reduce(sp_sim *s, int what, double *out, void *stream) {
+    if (!s || !out) return fail(SP_EINVAL, "NULL argument");
+    if (what < SP_MASS || what > SP_SUMSQ_U) return fail(SP_EINVAL, "unknown reduction %d", what);
+    if (what == SP_SUM_V && s->nf < 2) return fail(SP_EINVAL, "SP_SUM_V needs the Gray-Scott model");
+    const int field = what == SP_SUM_V ? 1 : 0;
+    ReduceGeom g;
+    g.nx = s->nx;
+    g.ny = s->ny;
+    g.nz = s->nz;
+    g.dims = s->dims;
+    g.h = s->h;
+    g.cell_volume = s->dims == 3 ? (s->h * s->h) * s->h : s->h * s->h;
+    g.c1 = s->p.c1;
+    g.c2 = s->p.c2;
+    const cudaStream_t st = pick(s, stream);
+    double *d_out = s->d_partials + 2 * (size_t)s->nred;
+    SP_CUDA(launch_reduce(s->dtype, what, s->f[s->cur][field], g, s->d_partials, s->nred, d_out, st));
+    SP_CUDA(cudaMemcpyAsync(s->h_out, d_out, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SP_CUDA(cudaStreamSynchronize(st));
+    *out = *s->h_out;
+    return SP_OK;
+}
+
+extern "C" int sp_field_devptr(sp_sim *s, int field, void **dptr) {
+    if (!s || !dptr) return fail(SP_EINVAL, "NULL argument");
+    if (int rc = check_field(s, field)) return rc;
+    *dptr = s->f[s->cur][field];
+    return SP_OK;
+}
+
+extern "C" int sp_steps_taken(const sp_sim *s, int64_t *steps) {
+    if (!s || !steps) return fail(SP_EINVAL, "NULL argument");
+    *steps = s->steps;
+    return SP_OK;
+}
+
+extern "C" int sp_destroy(sp_sim *s) {
+    if (!s) return SP_OK;
+    release(s);
+    return SP_OK;
+}
+
+// ---------------------------------------------------- conversion kernels --
+
+namespace sp {
+
+template <typename T>
+__global__ void from_f64_kernel(const double *__restrict__ src, T *__restrict__ dst, uint64_t n) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        if constexpr (sizeof(T) == 4) dst[i] = __double2float_rn(src[i]);
+        else dst[i] = __double2bfloat16(src[i]);
+    }
+}
+
+template <typename T>
+__global__ void to_f64_kernel(const T *__restrict__ src, double *__restrict__ dst, uint64_t n) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        dst[i] = (double)to_c(src[i]);
+}
+
+static int conv_blocks(uint64_t n) {
+    const uint64_t b = (n + 255) / 256;
+    return (int)(b < 4096 ? (b ? b : 1) : 4096);
+}
+
+cudaError_t launch_convert_from_f64(int dtype, const double *src, void *dst, uint64_t n, cudaStream_t s) {
+    if (dtype == SP_F32) from_f64_kernel<float><<<conv_blocks(n), 256, 0, s>>>(src, (float *)dst, n);
+    else from_f64_kernel<bf16><<<conv_blocks(n), 256, 0, s>>>(src, (bf16 *)dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_to_f64(int dtype, const void *src, double *dst, uint64_t n, cudaStream_t s) {
+    if (dtype == SP_F32) to_f64_kernel<float><<<conv_blocks(n), 256, 0, s>>>((const float *)src, dst, n);
+    else to_f64_kernel<bf16><<<conv_blocks(n), 256, 0, s>>>((const bf16 *)src, dst, n);
+    return cudaGetLastError();
+}
+
+}  // namespace sp

@@ -18,3 +18,9 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+# Under pytest-xdist every worker would start a full OpenMP team for the oracle;
+# keep one thread per worker so the workers do not oversubscribe the cores.
+if os.environ.get("PYTEST_XDIST_WORKER"):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")

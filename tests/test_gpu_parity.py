@@ -1,0 +1,248 @@
+"""GPU path (through the C ABI) against the FP64 oracle.
+
+FP64: the kernels evaluate the same expressions in the same order as the
+oracle, with no contraction, so fields must be equal bit for bit.
+FP32 / BF16-storage: compared with the FP64 oracle started from the same
+(rounded) initial field; the bounds are stated per test.
+Grids are ragged (sides not multiples of the tile) and span several tiles and
+several slabs along the streamed axis.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+MODELS = {0: "AC", 1: "CH", 2: "GS"}
+DT = {0: 0.05, 1: 0.005, 2: 0.5}
+DT3 = {0: 0.05, 1: 0.002, 2: 0.25}
+
+
+@pytest.fixture(scope="module")
+def sp():
+    import __graft_entry__
+
+    __graft_entry__._load_builder().build()
+    import paper_2511_10508_gb300 as sp
+
+    return sp
+
+
+def make(sp, model, shape, st, dtype=0, dt=None, **kw):
+    dims = len(shape)
+    dt = dt if dt is not None else (DT if dims == 2 else DT3)[model]
+    base = dict(stencil=st, dtype=dtype, seed=kw.pop("seed", 12345))
+    if model == 2:
+        base.update(gs_patches=kw.pop("gs_patches", 6), gs_patch=kw.pop("gs_patch", 5), ic_amp=kw.pop("ic_amp", 0.01))
+    else:
+        base.update(ic_amp=kw.pop("ic_amp", 0.5))
+    base.update(kw)
+    return sp.Simulation(model, shape, dt=dt, **base), dt
+
+
+def oracle_ic(model, shape, prm):
+    if model == 2:
+        return O.initial_condition(O.GS, shape, seed=prm.seed, amp=prm.ic_amp, patches=prm.gs_patches,
+                                   patch=prm.gs_patch)
+    return O.initial_condition(model, shape, seed=prm.seed, mean=prm.ic_mean, amp=prm.ic_amp)
+
+
+def oparams(prm):
+    return O.params(c1=prm.c1, c2=prm.c2, kappa=prm.kappa, Du=prm.Du, Dv=prm.Dv, F=prm.F, k=prm.k)
+
+
+CASES_2D = [(m, s) for m in (0, 1, 2) for s in (0, 1, 2)]
+CASES_3D = [(m, s) for m in (0, 1, 2) for s in (3, 4, 5)]
+
+
+@pytest.mark.parametrize("model,st", CASES_2D + CASES_3D)
+def test_fp64_bitwise(sp, model, st):
+    dims = O.STENCIL_DIMS[st]
+    shape = (70, 301) if dims == 2 else (37, 45, 70)
+    sim, dt = make(sp, model, shape, st)
+    with sim:
+        ic = oracle_ic(model, shape, sim.prm)
+        u0 = sim.read(0)
+        if model == 2:
+            assert np.array_equal(u0, ic[0]) and np.array_equal(sim.read(1), ic[1])
+        else:
+            assert np.array_equal(u0, ic)
+        n = 9
+        sim.step(n)
+        assert sim.steps_taken == n
+        if model == 2:
+            ru, rv = O.step(O.GS, st, ic[0], ic[1], dt=dt, prm=oparams(sim.prm), nsteps=n)
+            gu, gv = sim.read(0), sim.read(1)
+            assert np.array_equal(gu, ru), np.abs(gu - ru).max()
+            assert np.array_equal(gv, rv), np.abs(gv - rv).max()
+        else:
+            ref = O.step(model, st, ic, dt=dt, prm=oparams(sim.prm), nsteps=n)
+            g = sim.read(0)
+            assert np.array_equal(g, ref), np.abs(g - ref).max()
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (3, 5), (2, 7), (5, 1), (33, 257), (1, 1, 1), (2, 3, 5), (3, 1, 4),
+                                   (40, 33, 65)])
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_fp64_bitwise_small_and_degenerate(sp, shape, model):
+    """Sides smaller than the stencil radius (neighbours wrap several times), a
+    single point, and sides one past a tile boundary."""
+    dims = len(shape)
+    for st in ((0, 2) if dims == 2 else (3, 5)):
+        kw = dict(gs_patches=1, gs_patch=1) if model == 2 else {}
+        sim, dt = make(sp, model, shape, st, **kw)
+        with sim:
+            ic = oracle_ic(model, shape, sim.prm)
+            sim.step(5)
+            if model == 2:
+                ru, rv = O.step(O.GS, st, ic[0], ic[1], dt=dt, prm=oparams(sim.prm), nsteps=5)
+                assert np.array_equal(sim.read(0), ru) and np.array_equal(sim.read(1), rv)
+            else:
+                ref = O.step(model, st, ic, dt=dt, prm=oparams(sim.prm), nsteps=5)
+                assert np.array_equal(sim.read(0), ref)
+
+
+def test_fp64_long_slab_streaming(sp):
+    """A tall grid is split into several slabs along the streamed axis; the slab
+    seams must be invisible (bitwise) over many steps."""
+    for model, st, shape in [(1, 0, (1500, 300)), (1, 2, (900, 257)), (1, 3, (200, 40, 70)), (2, 4, (150, 33, 66))]:
+        sim, dt = make(sp, model, shape, st)
+        with sim:
+            ic = oracle_ic(model, shape, sim.prm)
+            sim.step(12)
+            if model == 2:
+                ru, rv = O.step(O.GS, st, ic[0], ic[1], dt=dt, prm=oparams(sim.prm), nsteps=12)
+                assert np.array_equal(sim.read(0), ru) and np.array_equal(sim.read(1), rv)
+            else:
+                ref = O.step(model, st, ic, dt=dt, prm=oparams(sim.prm), nsteps=12)
+                assert np.array_equal(sim.read(0), ref)
+
+
+# FP32 arithmetic: per-step relative rounding ~6e-8; over these short runs the
+# relative L2 error against the FP64 oracle stays below 1e-5.
+# BF16 storage: every store rounds to 8 significant bits (relative 2^-9); the
+# error after a few steps is of that order, bounded here by 1e-2.
+TOL = {1: 1e-5, 2: 1e-2}
+
+
+@pytest.mark.parametrize("dtype", [1, 2])
+@pytest.mark.parametrize("model,st", [(0, 0), (1, 0), (1, 2), (2, 0), (0, 3), (1, 3), (1, 4), (2, 3), (1, 5)])
+def test_reduced_precision_against_fp64_oracle(sp, dtype, model, st):
+    dims = O.STENCIL_DIMS[st]
+    shape = (60, 1100) if dims == 2 else (36, 40, 72)
+    sim, dt = make(sp, model, shape, st, dtype=dtype)
+    with sim:
+        u0 = sim.read(0)  # the rounded initial field, widened exactly
+        ic = oracle_ic(model, shape, sim.prm)
+        first = ic[0] if model == 2 else ic
+        # initial condition: the FP64 value rounded once to the storage type
+        ulp = 2.0 ** -24 if dtype == 1 else 2.0 ** -8
+        assert np.all(np.abs(u0 - first) <= ulp * np.abs(first) + 1e-300)
+        n = 10
+        if model == 2:
+            v0 = sim.read(1)
+            ru, rv = O.step(O.GS, st, u0, v0, dt=dt, prm=oparams(sim.prm), nsteps=n)
+            sim.step(n)
+            eu, ev = O.rel_l2(sim.read(0), ru), O.rel_l2(sim.read(1), rv)
+            assert eu < TOL[dtype] and ev < TOL[dtype], (eu, ev)
+        else:
+            ref = O.step(model, st, u0, dt=dt, prm=oparams(sim.prm), nsteps=n)
+            sim.step(n)
+            e = O.rel_l2(sim.read(0), ref)
+            assert e < TOL[dtype], e
+
+
+@pytest.mark.parametrize("dtype", [0, 1, 2])
+def test_reductions(sp, dtype):
+    for model, shape, st in [(1, (70, 301), 0), (0, (37, 45, 70), 3), (2, (64, 96), 0)]:
+        sim, dt = make(sp, model, shape, st, dtype=dtype)
+        with sim:
+            sim.step(3)
+            u = sim.read(0)
+            scale = np.abs(u).sum() + 1.0
+            assert abs(sim.reduce(sp.MASS) - O.mass(u)) <= 1e-13 * scale
+            assert abs(sim.reduce(sp.SUM_U) - O.kahan_sum(u)) <= 1e-13 * scale
+            assert abs(sim.reduce(sp.SUMSQ_U) - O.kahan_sum(u * u)) <= 1e-13 * (u * u).sum()
+            assert sim.reduce(sp.MIN_U) == u.min() and sim.reduce(sp.MAX_U) == u.max()
+            fe = O.free_energy(u, h=1.0, c1=sim.prm.c1, c2=sim.prm.c2)
+            assert abs(sim.reduce(sp.FREE_ENERGY) - fe) <= 1e-12 * (abs(fe) + scale)
+            if model == 2:
+                v = sim.read(1)
+                assert abs(sim.reduce(sp.SUM_V) - O.kahan_sum(v)) <= 1e-13 * (np.abs(v).sum() + 1)
+
+
+def test_reductions_with_h(sp):
+    """Cell volume h^d and the 1/h of the gradient enter mass and free energy."""
+    shape = (48, 80)
+    with sp.Simulation(sp.CAHN_HILLIARD, shape, h=0.7, dt=0.001, seed=4, ic_amp=0.3) as sim:
+        u = sim.read(0)
+        assert abs(sim.reduce(sp.MASS) - O.mass(u, h=0.7)) <= 1e-13 * np.abs(u).sum()
+        fe = O.free_energy(u, h=0.7)
+        assert abs(sim.reduce(sp.FREE_ENERGY) - fe) <= 1e-12 * abs(fe)
+
+
+def test_write_read_roundtrip_and_resume(sp):
+    """sp_write + sp_read round-trip bit for bit (FP64) and resuming from a written
+    state equals continuing the run (checkpoint / resume)."""
+    shape = (50, 130)
+    with sp.Simulation(sp.CAHN_HILLIARD, shape, dt=0.005, seed=8, ic_amp=0.4) as a, \
+            sp.Simulation(sp.CAHN_HILLIARD, shape, dt=0.005, seed=99, ic_amp=0.4) as b:
+        a.step(6)
+        snap = a.read(0)
+        b.write(0, snap)
+        assert np.array_equal(b.read(0), snap)
+        a.step(7)
+        b.step(7)
+        assert np.array_equal(a.read(0), b.read(0))
+
+
+@pytest.mark.parametrize("dtype", [1, 2])
+def test_write_rounds_to_storage(sp, dtype):
+    shape = (16, 40)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(shape)
+    with sp.Simulation(sp.ALLEN_CAHN, shape, dt=0.01, dtype=dtype) as s:
+        s.write(0, x)
+        y = s.read(0)
+        if dtype == 1:
+            assert np.array_equal(y, x.astype(np.float32).astype(np.float64))
+        else:
+            assert np.all(np.abs(y - x) <= 2.0 ** -9 * np.abs(x))
+        raw = s.read(0, as_f64=False)
+        assert raw.dtype == (np.float32 if dtype == 1 else np.uint16)
+
+
+def test_periodic_shift_equivariance_gpu(sp):
+    shape = (64, 96)
+    rng = np.random.default_rng(1)
+    x = rng.uniform(-0.5, 0.5, shape)
+    with sp.Simulation(sp.CAHN_HILLIARD, shape, dt=0.005, stencil=sp.LAP_9CROSS4) as a, \
+            sp.Simulation(sp.CAHN_HILLIARD, shape, dt=0.005, stencil=sp.LAP_9CROSS4) as b:
+        a.write(0, x)
+        b.write(0, np.roll(x, (5, -17), (0, 1)))
+        a.step(10)
+        b.step(10)
+        assert np.array_equal(np.roll(a.read(0), (5, -17), (0, 1)), b.read(0))
+
+
+def test_torch_stream_and_zero_copy_view(sp):
+    torch = pytest.importorskip("torch")
+    shape = (40, 300)
+    s = torch.cuda.Stream()
+    with sp.Simulation(sp.ALLEN_CAHN, shape, dt=0.05, seed=2, ic_amp=0.1) as sim:
+        ic = O.initial_condition(O.AC, shape, seed=2, amp=0.1)
+        sim.step(4, stream=s)
+        s.synchronize()
+        t = sim.field_tensor(0)
+        ref = O.step(O.AC, O.S1, ic, dt=0.05, nsteps=4)
+        assert np.array_equal(t.cpu().numpy(), ref)
+
+
+def test_mass_conservation_cahn_hilliard_gpu(sp):
+    with sp.Simulation(sp.CAHN_HILLIARD, (256, 256), dt=0.01, seed=1, ic_amp=0.01) as sim:
+        m0 = sim.reduce(sp.MASS)
+        sim.step(500)
+        m1 = sim.reduce(sp.MASS)
+        u = sim.read(0)
+        assert abs(m1 - m0) <= 500 * 1e-15 * u.size * np.abs(u).max()
