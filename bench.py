@@ -133,7 +133,7 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_rate(model, dims, shape, dt, st, budget_s=12.0, max_steps=64):
+def oracle_rate(model, dims, shape, dt, st, budget_s=15.0, max_steps=2000):
     """FP64 oracle GLUPS on the host cores over a bounded sample of the workload."""
     import numpy as np
 
@@ -220,7 +220,7 @@ def workload_config(name):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))

@@ -197,6 +197,15 @@ def test_write_read_roundtrip_and_resume(sp):
         assert np.array_equal(a.read(0), b.read(0))
 
 
+def bf16_round(x):
+    """Round FP64 values to the nearest BF16 value (ties to even), exactly: a BF16
+    number is m * 2^(e-7) with an integer significand m in [128, 256)."""
+    x = np.asarray(x, dtype=np.float64)
+    e = np.floor(np.log2(np.abs(np.where(x == 0, 1.0, x))))
+    scale = np.exp2(e - 7)
+    return np.where(x == 0, 0.0, np.round(x / scale) * scale)
+
+
 @pytest.mark.parametrize("dtype", [1, 2])
 def test_write_rounds_to_storage(sp, dtype):
     shape = (16, 40)
@@ -208,7 +217,7 @@ def test_write_rounds_to_storage(sp, dtype):
         if dtype == 1:
             assert np.array_equal(y, x.astype(np.float32).astype(np.float64))
         else:
-            assert np.all(np.abs(y - x) <= 2.0 ** -9 * np.abs(x))
+            assert np.array_equal(y, bf16_round(x))
         raw = s.read(0, as_f64=False)
         assert raw.dtype == (np.float32 if dtype == 1 else np.uint16)
 
