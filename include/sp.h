@@ -50,7 +50,8 @@ typedef enum sp_status {
     SP_ETIMEOUT = 6,    /* a bounded device-side wait expired */
     SP_EBUSY = 7,       /* resource busy (e.g. server queue full) */
     SP_PENDING = 8,     /* sp_poll: request not finished yet */
-    SP_ENOTFOUND = 9    /* unknown ticket */
+    SP_ENOTFOUND = 9,   /* unknown ticket */
+    SP_ETOOLARGE = 10   /* request exceeds a fixed-size limit (see sp_reduce_field_noalloc) */
 } sp_status;
 
 typedef enum sp_model {
@@ -158,6 +159,33 @@ int sp_write(sp_sim *sim, int field, const void *host_src, size_t bytes, int is_
 
 /* Reduce the current time level (sp_reduce_what) into *out (FP64).  Synchronises. */
 int sp_reduce(sp_sim *sim, int what, double *out, void *stream);
+
+/*
+ * Reduce a field that the caller owns, allocating nothing.  The paper has no
+ * counterpart; this exists for callers that cannot allocate device memory when
+ * they need a diagnostic: an application whose memory pool already holds
+ * nearly all of HBM, a latency-critical loop in which cudaMalloc/cudaFree
+ * would stall or synchronise the device, or code that keeps its fields in its
+ * own allocator.  Same reductions as sp_reduce (except SP_SUM_V: pass the v
+ * field with SP_SUM_U), same kernels and, on the same device, the same result.
+ *   what:   SP_MASS, SP_FREE_ENERGY, SP_SUM_U, SP_MIN_U, SP_MAX_U or SP_SUMSQ_U
+ *   dtype:  storage type of `field` (sp_dtype)
+ *   field:  device pointer, nx*ny*nz elements, x fastest; only read
+ *   dims, shape, h: grid as in sp_create; c1, c2 enter SP_FREE_ENERGY only
+ *   out:    host pointer receiving the FP64 result
+ *   stream: cudaStream_t (NULL = the legacy default stream); the call
+ *           synchronises it before returning.
+ * Block partials live in a fixed device array of the library (room for 512
+ * partials, 8 KiB, held on every GPU that loads the library until exit); a
+ * grid needing more partials than that fails with SP_ETOOLARGE.  The array is
+ * shared by all calls and keeps the last call's contents; calls that overlap
+ * on the GPU race on it.  The first call on a device looks up the array's
+ * device address: make it before any stream capture.  No cudaMalloc, cudaFree
+ * or allocating routine is called; on failure only the status code is
+ * returned and sp_last_error() is not updated.
+ */
+int sp_reduce_field_noalloc(int what, int dtype, const void *field, int dims, const int64_t shape[3], double h,
+                            double c1, double c2, double *out, void *stream);
 
 /* Device pointer of field `field` at the current time level (storage type).
  * Valid until the next sp_step / sp_destroy. */
