@@ -32,6 +32,13 @@ WORKLOADS = {
     "ch2d-4096-f64-lap5": (1, 2, (4096, 4096), 0.01, 0, 0, 100),
     "ch2d-4096-f64-lap9x4": (1, 2, (4096, 4096), 0.01, 2, 0, 100),
     "ch2d-4096-f32-lap5": (1, 2, (4096, 4096), 0.01, 0, 1, 100),
+    "ch2d-16384-f32-lap5": (1, 2, (16384, 16384), 0.01, 0, 1, 20),
+    "ch2d-16384-bf16-lap5": (1, 2, (16384, 16384), 0.01, 0, 2, 20),
+    "ch2d-16384-f32-lap9x4": (1, 2, (16384, 16384), 0.01, 2, 1, 20),
+    "gs2d-32768-bf16-lap5": (2, 2, (32768, 32768), 1.0, 0, 2, 10),
+    "gs2d-8192-f32-lap5": (2, 2, (8192, 8192), 1.0, 0, 1, 10),
+    "ch2d-8192-f32-lap5": (1, 2, (8192, 8192), 0.01, 0, 1, 10),
+    "ch3d-384-f32-lap7": (1, 3, (384, 384, 384), 0.005, 3, 1, 10),
     "ac2d-256-f64-lap5": (0, 2, (256, 256), 0.05, 0, 0, 1000),
     "gs2d-32768-f32-lap5": (2, 2, (32768, 32768), 1.0, 0, 1, 10),
     "gs2d-32768-f64-lap5": (2, 2, (32768, 32768), 1.0, 0, 0, 2),

@@ -94,6 +94,18 @@ __device__ __forceinline__ void store_vec(T *__restrict__ p, const typename Cmp<
 template <typename T>
 __device__ __forceinline__ typename Cmp<T>::type load_one(const T *__restrict__ p) { return to_c(__ldg(p)); }
 
+// Asynchronous 16-byte global -> shared copy (both addresses 16-byte aligned),
+// committed as one group per call site; completion is awaited by the issuing
+// thread with cp_async_wait<N> (at most N groups still pending).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // Periodic wrap of an index that may lie anywhere (small grids: several periods).
 __device__ __forceinline__ int wrap_slow(int i, int n) {
     int r = i % n;
@@ -154,11 +166,23 @@ struct StepConsts {
     double dt;
 };
 
-template <typename C> struct ConstsC {
-    C c1, c2, sAC, kq, dq, duq, dvq, F, Fk, dt;
-    __device__ __forceinline__ explicit ConstsC(const StepConsts &k)
-        : c1(C(k.c1)), c2(C(k.c2)), sAC(C(k.sAC)), kq(C(k.kq)), dq(C(k.dq)), duq(C(k.duq)),
-          dvq(C(k.dvq)), F(C(k.F)), Fk(C(k.Fk)), dt(C(k.dt)) {}
+// The same coefficients rounded once to FP32 on the host, so that FP32/BF16
+// kernels contain no FP64 instruction (a double->float conversion runs on the
+// FP64 pipe, which the compiler may re-run inside loops).
+struct StepConstsF {
+    float c1, c2, sAC, kq, dq, duq, dvq, F, Fk, dt;
+};
+
+template <typename C> struct ConstsC;
+template <> struct ConstsC<double> {
+    double c1, c2, sAC, kq, dq, duq, dvq, F, Fk, dt;
+    __device__ __forceinline__ ConstsC(const StepConsts &k, const StepConstsF &)
+        : c1(k.c1), c2(k.c2), sAC(k.sAC), kq(k.kq), dq(k.dq), duq(k.duq), dvq(k.dvq), F(k.F), Fk(k.Fk), dt(k.dt) {}
+};
+template <> struct ConstsC<float> {
+    float c1, c2, sAC, kq, dq, duq, dvq, F, Fk, dt;
+    __device__ __forceinline__ ConstsC(const StepConsts &, const StepConstsF &k)
+        : c1(k.c1), c2(k.c2), sAC(k.sAC), kq(k.kq), dq(k.dq), duq(k.duq), dvq(k.dvq), F(k.F), Fk(k.Fk), dt(k.dt) {}
 };
 
 // Allen-Cahn update of one point from its value and stencil sum.
@@ -196,7 +220,8 @@ struct StepArgs {
     const void *in0, *in1;   // current level (field 0, field 1)
     void *out0, *out1;       // next level
     int nx, ny, nz;
-    StepConsts k;
+    StepConsts k;            // FP64 coefficients
+    StepConstsF kf;          // the same, rounded to FP32
 };
 
 }  // namespace sp

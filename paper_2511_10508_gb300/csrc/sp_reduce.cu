@@ -7,10 +7,11 @@
 // order case) gives Models A and B, with forward differences.
 //
 // Two passes, deterministic for a fixed grid size: every thread keeps a
-// Neumaier-compensated (sum, correction) pair over a grid-stride range; warps
-// combine pairs with shuffles, blocks through shared memory, and each block
-// writes its pair to a scratch array; a single block then combines the block
-// pairs in index order and writes the scaled result.
+// Neumaier-compensated (sum, correction) pair over a grid-stride range (fed
+// with FP64 sums of 16-value blocks); warps combine pairs with shuffles,
+// blocks through shared memory, and each block writes its pair to a scratch
+// array; a single block then combines the block pairs in index order and
+// writes the scaled result.
 #include "sp_internal.h"
 
 namespace sp {
@@ -58,43 +59,92 @@ __device__ __forceinline__ void block_combine(double &s, double &c) {
     }
 }
 
+// Point value of a plain reduction (sum, mass, sum of squares) in FP64.
+template <int WHAT> __device__ __forceinline__ double point_value(double p) {
+    if constexpr (WHAT == SP_SUMSQ_U) return p * p;
+    else return p;
+}
+
+// Free-energy density at linear index i (forward differences, periodic).
+template <typename T>
+__device__ __forceinline__ double fe_density(const T *__restrict__ f, uint64_t i, int nx, int ny, int nz, int dims,
+                                             double h, double c1, double c2) {
+    const double p = (double)to_c(f[i]);
+    const int x = (int)(i % (uint64_t)nx);
+    const int y = (int)((i / (uint64_t)nx) % (uint64_t)ny);
+    const uint64_t row = i - (uint64_t)x;
+    const uint64_t zbase = row - (uint64_t)y * nx;
+    const double px = (double)to_c(f[row + (x + 1 == nx ? 0 : x + 1)]);
+    const double py = (double)to_c(f[zbase + (uint64_t)(y + 1 == ny ? 0 : y + 1) * nx + x]);
+    const double gx = (px - p) / h;
+    const double gy = (py - p) / h;
+    double g2 = gx * gx + gy * gy;
+    if (dims == 3) {
+        const int z = (int)(i / ((uint64_t)nx * ny));
+        const uint64_t plane = (uint64_t)nx * ny;
+        const double pz = (double)to_c(f[(uint64_t)(z + 1 == nz ? 0 : z + 1) * plane + (i - (uint64_t)z * plane)]);
+        const double gz = (pz - p) / h;
+        g2 = g2 + gz * gz;
+    }
+    const double p2 = p * p;
+    return 0.5 * g2 - 0.5 * c1 * p2 + 0.25 * c2 * p2 * p2;
+}
+
+// Block partials.  Sums: each thread reads 16-byte vectors in a grid-stride
+// loop, adds every kBlockVecs vectors (16 values for FP32) with plain FP64
+// additions and folds that block sum into its Neumaier pair, so the FP64 pipe
+// (slow on this part) sees ~2 operations per value instead of ~7; the error
+// bound becomes u|S| + 15u sum|x| per thread instead of u|S|.  Min / max run in
+// the compute type.  The free energy keeps a per-point Neumaier update.
 template <typename T, int WHAT>
 __global__ void __launch_bounds__(kReduceThreads)
 reduce_partial_kernel(const T *__restrict__ f, int nx, int ny, int nz, int dims, double h, double c1,
                       double c2, double *__restrict__ partials) {
+    typedef typename Cmp<T>::type C;
+    constexpr int VE = 16 / sizeof(T);       // values per vector
+    constexpr int kBlockVecs = (16 + VE - 1) / VE;
     const uint64_t N = (uint64_t)nx * ny * nz;
     double s = (WHAT == SP_MIN_U) ? INFINITY : (WHAT == SP_MAX_U ? -INFINITY : 0.0), c = 0.0;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-        const double p = (double)to_c(f[i]);
-        if constexpr (WHAT == SP_MIN_U) {
-            s = fmin(s, p);
-        } else if constexpr (WHAT == SP_MAX_U) {
-            s = fmax(s, p);
-        } else if constexpr (WHAT == SP_SUMSQ_U) {
-            neu_add(s, c, p * p);
-        } else if constexpr (WHAT == SP_FREE_ENERGY) {
-            const int x = (int)(i % (uint64_t)nx);
-            const int y = (int)((i / (uint64_t)nx) % (uint64_t)ny);
-            const uint64_t row = i - (uint64_t)x;
-            const uint64_t zbase = row - (uint64_t)y * nx;
-            const double px = (double)to_c(f[row + (x + 1 == nx ? 0 : x + 1)]);
-            const double py = (double)to_c(f[zbase + (uint64_t)(y + 1 == ny ? 0 : y + 1) * nx + x]);
-            const double gx = (px - p) / h;
-            const double gy = (py - p) / h;
-            double g2 = gx * gx + gy * gy;
-            if (dims == 3) {
-                const int z = (int)(i / ((uint64_t)nx * ny));
-                const uint64_t plane = (uint64_t)nx * ny;
-                const double pz = (double)to_c(f[(uint64_t)(z + 1 == nz ? 0 : z + 1) * plane + (i - (uint64_t)z * plane)]);
-                const double gz = (pz - p) / h;
-                g2 = g2 + gz * gz;
+    if constexpr (WHAT == SP_FREE_ENERGY) {
+        for (uint64_t i = tid; i < N; i += stride) neu_add(s, c, fe_density(f, i, nx, ny, nz, dims, h, c1, c2));
+    } else {
+        // vector part when the base is 16-byte aligned (library buffers always are;
+        // a caller's pointer may not be), then the scalar tail
+        const bool aligned = (reinterpret_cast<uintptr_t>(f) & 15u) == 0;
+        const uint64_t NV = aligned ? N / VE : 0;
+        C mn = C(INFINITY), mx = C(-INFINITY);
+        double blk = 0.0;
+        int nb = 0;
+        for (uint64_t v = tid; v < NV; v += stride) {
+            C x[VE];
+            load_vec<T, VE>(f + v * VE, x);
+            if constexpr (WHAT == SP_MIN_U) {
+#pragma unroll
+                for (int j = 0; j < VE; ++j) mn = fmin(mn, x[j]);
+            } else if constexpr (WHAT == SP_MAX_U) {
+#pragma unroll
+                for (int j = 0; j < VE; ++j) mx = fmax(mx, x[j]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < VE; ++j) blk += point_value<WHAT>((double)x[j]);
+                if (++nb == kBlockVecs) {
+                    neu_add(s, c, blk);
+                    blk = 0.0;
+                    nb = 0;
+                }
             }
-            const double p2 = p * p;
-            neu_add(s, c, 0.5 * g2 - 0.5 * c1 * p2 + 0.25 * c2 * p2 * p2);
-        } else {
-            neu_add(s, c, p);
         }
+        for (uint64_t i = NV * VE + tid; i < N; i += stride) {
+            const C x = to_c(f[i]);
+            if constexpr (WHAT == SP_MIN_U) mn = fmin(mn, x);
+            else if constexpr (WHAT == SP_MAX_U) mx = fmax(mx, x);
+            else blk += point_value<WHAT>((double)x);
+        }
+        if constexpr (WHAT == SP_MIN_U) s = (double)mn;
+        else if constexpr (WHAT == SP_MAX_U) s = (double)mx;
+        else neu_add(s, c, blk);
     }
     block_combine<WHAT>(s, c);
     if (threadIdx.x == 0) {

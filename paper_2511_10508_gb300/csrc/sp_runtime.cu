@@ -279,6 +279,8 @@ static cudaError_t launch_one_step(sp_sim *s, cudaStream_t st) {
     a.ny = s->ny;
     a.nz = s->nz;
     a.k = s->k;
+    a.kf = {(float)s->k.c1, (float)s->k.c2, (float)s->k.sAC, (float)s->k.kq, (float)s->k.dq,
+            (float)s->k.duq, (float)s->k.dvq, (float)s->k.F, (float)s->k.Fk, (float)s->k.dt};
     switch (s->dtype) {
     case SP_F64: return launch_step_f64(s->model, s->stencil, a, st, s->n_sm);
     case SP_F32: return launch_step_f32(s->model, s->stencil, a, st, s->n_sm);

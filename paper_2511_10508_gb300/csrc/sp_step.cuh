@@ -3,150 +3,296 @@
 //
 // One pass per step (the paper, Sec. "Benchmarks", stores phi^3 in a temporary
 // field for conserved dynamics; here the chemical potential never leaves the
-// chip): each CTA owns a column strip of the grid and streams along the slowest
-// axis (rows in 2D, z-planes in 3D).  Input slices enter a shared-memory ring
-// with a periodic halo; Cahn-Hilliard computes mu for the slice plus an r-wide
-// halo into a second ring, then applies the outer Laplacian to mu.  The next
-// slice is fetched into registers while the current one is computed.  HBM
-// traffic per point and step: one read and one write of each field.
+// chip).  Every kernel streams along the slowest axis (rows in 2D, z-planes in
+// 3D) and keeps the slices it still needs on chip, so HBM traffic per point and
+// step is one read and one write of each field:
+//   step2d_batch_kernel  2D, FP64: shared-memory rings, batches of rows
+//   step2d_tile_kernel   2D, FP32/BF16: one CTA per tile, tile + halo fetched with cp.async
+//   step3d_kernel        3D, FP64: shared-memory plane rings
+//   step3d_vec_kernel    3D, FP32/BF16: plane rings of 16-byte chunks
 #pragma once
 
 #include "sp_common.cuh"
 
 namespace sp {
 
-// ===================================================================== 2D ==
+// ========================================================== 2D, batched ==
 //
-// CTA: NT threads, each owning V consecutive x points; tile width TW = NT*V.
-// Rows y0 .. y1-1 of strip [x0, x0+TW) are produced; rows are streamed from
-// y0-RIN to y1+RIN-1 (RIN = r, or 2r for Cahn-Hilliard).
-template <int MODEL, int ST, typename T, int NT, int V>
-__global__ void __launch_bounds__(NT) step2d_kernel(StepArgs a, int TH) {
+// Shared-memory ring kernel used for FP64 (bound by the FP64 pipe, so every
+// wasted FP64 lane counts).  CTA: NT threads; strip of TW = 2*NT columns,
+// thread t owns columns t and t+NT (consecutive threads, consecutive doubles:
+// no bank conflicts).  Rows are processed in batches of RB: a batch loads RB
+// new rows, computes RB new rows of mu (Cahn-Hilliard) as one flat work list
+// over all threads, then RB output rows.  Rows of mu and phi needed by the
+// next batch stay in the rings.  The grid is persistent: CTA c processes the
+// rows [c*R, (c+1)*R) of the flattened (strip, row) space, so every CTA has the
+// same work; a range that crosses a strip boundary is processed as two
+// segments.
+template <int MODEL, int ST, typename T, int NT, int RB>
+struct Step2dBatchShape {
     typedef typename Cmp<T>::type C;
-    constexpr int r = StencilInfo<ST>::r;
-    constexpr int RIN = (MODEL == CH) ? 2 * r : r;
-    constexpr int TW = NT * V;
-    constexpr int WIN = TW + 2 * RIN;
-    constexpr int DIN = 2 * r + 2;
-    constexpr int NF = (MODEL == GS) ? 2 : 1;
-    constexpr int WMU = (MODEL == CH) ? TW + 2 * r : 1;
-    constexpr int DMU = (MODEL == CH) ? 2 * r + 1 : 1;
-    __shared__ C s_in[NF][DIN][WIN];
-    __shared__ C s_mu[DMU][WMU];
+    static constexpr int r = StencilInfo<ST>::r;
+    static constexpr int RIN = (MODEL == CH) ? 2 * r : r;
+    static constexpr int TW = 2 * NT;
+    static constexpr int WIN = TW + 2 * RIN;
+    // phi ring: a batch uses RB + 2r rows (CH: rows [yb, yb+RB+2r); AC/GS:
+    // [yb-r, yb+RB+r)); the next batch's RB rows are committed while slow threads
+    // may still read this batch's rows, which stays collision-free when the ring
+    // has 2*RB + 2r slots (row differences lie in [1, 2RB+2r-1]).
+    static constexpr int DIN = 2 * RB + 2 * r;
+    static constexpr int NF = (MODEL == GS) ? 2 : 1;
+    // mu ring: a batch reads mu rows [yb-r, yb+RB+r); the next batch's rows are
+    // written only after a barrier that follows this batch's output.
+    static constexpr int WMU = (MODEL == CH) ? TW + 2 * r : 0;
+    static constexpr int DMU = (MODEL == CH) ? RB + 2 * r : 0;
+    static constexpr size_t smem_bytes = sizeof(C) * ((size_t)NF * DIN * WIN + (size_t)DMU * WMU);
+};
 
-    const ConstsC<C> k(a.k);
+template <int MODEL, int ST, typename T, int NT, int RB>
+__global__ void __launch_bounds__(NT) step2d_batch_kernel(StepArgs a, int strips, long long rows_per_cta) {
+    typedef Step2dBatchShape<MODEL, ST, T, NT, RB> Sh;
+    typedef typename Sh::C C;
+    constexpr int r = Sh::r, RIN = Sh::RIN, TW = Sh::TW, WIN = Sh::WIN, DIN = Sh::DIN, NF = Sh::NF;
+    constexpr int WMU = Sh::WMU, DMU = Sh::DMU;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C (*s_in)[DIN][WIN] = reinterpret_cast<C (*)[DIN][WIN]>(smem_raw);                  // [NF][DIN][WIN]
+    C (*s_mu)[WMU > 0 ? WMU : 1] =
+        reinterpret_cast<C (*)[WMU > 0 ? WMU : 1]>(smem_raw + sizeof(C) * (size_t)NF * DIN * WIN);  // [DMU][WMU]
+
+    const ConstsC<C> k(a.k, a.kf);
     const int nx = a.nx, ny = a.ny;
     const int t = threadIdx.x;
-    const int x0 = blockIdx.x * TW;
-    const int y0 = blockIdx.y * TH;
-    const int y1 = min(y0 + TH, ny);
-    if (y0 >= y1) return;  // uniform per CTA
-    const int nrows = (y1 - y0) + 2 * RIN;
-    const bool vec = (nx % V) == 0;
-    const int xg = x0 + t * V;
     const T *in[2] = {static_cast<const T *>(a.in0), static_cast<const T *>(a.in1)};
     T *out[2] = {static_cast<T *>(a.out0), static_cast<T *>(a.out1)};
 
-    // halo column handled by this thread (threads 0 .. 2*RIN-1)
-    const int hxi = (t < RIN) ? t : TW + t;  // smem column
-    const int hx = wrap_idx(x0 - RIN + hxi, nx);
+    long long g0 = (long long)blockIdx.x * rows_per_cta;
+    const long long gend = min(g0 + rows_per_cta, (long long)strips * ny);
+    while (g0 < gend) {
+        const int strip = (int)(g0 / ny);
+        const int y0 = (int)(g0 - (long long)strip * ny);
+        const int y1 = (int)min((long long)ny, (long long)y0 + (gend - g0));
+        g0 += y1 - y0;
+        const int x0 = strip * TW;
+        // columns of this thread (global, wrapped) and the halo column it loads
+        const int xa = wrap_idx(x0 + t, nx), xb = wrap_idx(x0 + t + NT, nx);
+        const bool has_halo = t < 2 * RIN;
+        const int hxi = (t < RIN) ? t : TW + t;
+        const int hx = wrap_idx(x0 - RIN + hxi, nx);
 
-    C pf[NF][V];
-    C ph[NF];
-    auto fetch = [&](int y) {
-        const size_t row = (size_t)wrap_idx(y, ny) * (size_t)nx;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            const T *src = in[f] + row;
-            if (vec && xg + V <= nx) {
-                load_vec<T, V>(src + xg, pf[f]);
-            } else {
-#pragma unroll
-                for (int v = 0; v < V; ++v) pf[f][v] = load_one(src + wrap_idx(xg + v, nx));
-            }
-            if (t < 2 * RIN) ph[f] = load_one(src + hx);
-        }
-    };
-    auto commit = [&](int slot) {
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-#pragma unroll
-            for (int v = 0; v < V; ++v) s_in[f][slot][RIN + t * V + v] = pf[f][v];
-            if (t < 2 * RIN) s_in[f][slot][hxi] = ph[f];
-        }
-    };
-    auto store = [&](int f, int y, const C (&vals)[V]) {
-        T *dst = out[f] + (size_t)y * (size_t)nx;
-        if (vec && xg + V <= nx) {
-            store_vec<T, V>(dst + xg, vals);
-        } else {
-#pragma unroll
-            for (int v = 0; v < V; ++v)
-                if (xg + v < nx) dst[xg + v] = from_c<T>(vals[v]);
-        }
-    };
+        // ring slot of global row y (rows relative to y0 - RIN, always >= 0)
+        auto slot_in = [&](int y) { return (y - y0 + RIN) % DIN; };
+        auto slot_mu = [&](int y) { return (y - y0 + r) % DMU; };
 
-    fetch(y0 - RIN);
-    for (int j = 0; j < nrows; ++j) {
-        commit(j % DIN);
-        if (j + 1 < nrows) fetch(y0 - RIN + j + 1);
-        __syncthreads();
-        if constexpr (MODEL == CH) {
-            if (j >= 2 * r) {
-                // mu of row y0 - r + (j - 2r) over columns x0-r .. x0+TW+r-1
-                const int jm = j - 2 * r;
-                auto mu_at = [&](int xm) {
-                    auto P = [&](int dx, int dy, int) -> C {
-                        return s_in[0][(j - r + dy) % DIN][xm + r + dx];
-                    };
-                    const C S = stencil_sum<ST, C>(P);
-                    const C p = s_in[0][(j - r) % DIN][xm + r];
-                    s_mu[jm % DMU][xm] = ch_mu<C>(p, S, k);
-                };
+        C pa[NF][RB], pb[NF][RB], ph[NF][RB];
+        // fetch `n` rows starting at global row y (wrapped) into registers
+        auto fetch = [&](int y, int n) {
 #pragma unroll
-                for (int v = 0; v < V; ++v) mu_at(t * V + v);
-                if (t < 2 * r) mu_at(TW + t);
-            }
-            __syncthreads();
-            if (j >= 4 * r) {
-                const int yo = y0 + j - 4 * r;
-                C o[V];
+            for (int i = 0; i < RB; ++i) {
+                if (i < n) {
+                    const size_t row = (size_t)wrap_idx(y + i, ny) * (size_t)nx;
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    const int xm = t * V + v + r;
-                    auto Pm = [&](int dx, int dy, int) -> C {
-                        return s_mu[(j - 3 * r + dy) % DMU][xm + dx];
-                    };
-                    const C Smu = stencil_sum<ST, C>(Pm);
-                    o[v] = ch_update<C>(s_in[0][(j - 2 * r) % DIN][RIN + t * V + v], Smu, k);
-                }
-                store(0, yo, o);
-            }
-        } else {
-            if (j >= 2 * r) {
-                const int yo = y0 + j - 2 * r;
-                C o0[V], o1[V];
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    const int xi = RIN + t * V + v;
-                    auto P0 = [&](int dx, int dy, int) -> C {
-                        return s_in[0][(j - r + dy) % DIN][xi + dx];
-                    };
-                    const C S0 = stencil_sum<ST, C>(P0);
-                    const C p0 = s_in[0][(j - r) % DIN][xi];
-                    if constexpr (MODEL == AC) {
-                        o0[v] = ac_update<C>(p0, S0, k);
-                    } else {
-                        auto P1 = [&](int dx, int dy, int) -> C {
-                            return s_in[NF - 1][(j - r + dy) % DIN][xi + dx];
-                        };
-                        const C S1 = stencil_sum<ST, C>(P1);
-                        const C p1 = s_in[NF - 1][(j - r) % DIN][xi];
-                        gs_update<C>(p0, p1, S0, S1, k, o0[v], o1[v]);
+                    for (int f = 0; f < NF; ++f) {
+                        pa[f][i] = load_one(in[f] + row + xa);
+                        pb[f][i] = load_one(in[f] + row + xb);
+                        if (has_halo) ph[f][i] = load_one(in[f] + row + hx);
                     }
                 }
-                store(0, yo, o0);
-                if constexpr (MODEL == GS) store(1, yo, o1);
+            }
+        };
+        auto commit = [&](int y, int n) {
+#pragma unroll
+            for (int i = 0; i < RB; ++i) {
+                if (i < n) {
+                    const int sl = slot_in(y + i);
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        s_in[f][sl][RIN + t] = pa[f][i];
+                        s_in[f][sl][RIN + t + NT] = pb[f][i];
+                        if (has_halo) s_in[f][sl][hxi] = ph[f][i];
+                    }
+                }
+            }
+        };
+        // mu rows [ya, ya + n) as one flat work list
+        auto compute_mu = [&](int ya, int n) {
+            if constexpr (MODEL == CH) {
+                const int items = n * WMU;
+                for (int q = t; q < items; q += NT) {
+                    const int i = q / WMU, c = q - i * WMU;
+                    const int y = ya + i;
+                    auto P = [&](int dx, int dy, int) -> C { return s_in[0][slot_in(y + dy)][c + r + dx]; };
+                    const C S = stencil_sum<ST, C>(P);
+                    s_mu[slot_mu(y)][c] = ch_mu<C>(s_in[0][slot_in(y)][c + r], S, k);
+                }
+            }
+        };
+        auto output = [&](int ya, int n) {
+#pragma unroll
+            for (int i = 0; i < RB; ++i) {
+                if (i < n) {
+                    const int y = ya + i;
+                    const size_t row = (size_t)y * (size_t)nx;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int c = t + h * NT;  // column within the strip
+                        const int x = x0 + c;
+                        C o0, o1 = C(0);
+                        if constexpr (MODEL == CH) {
+                            auto Pm = [&](int dx, int dy, int) -> C { return s_mu[slot_mu(y + dy)][c + r + dx]; };
+                            o0 = ch_update<C>(s_in[0][slot_in(y)][c + RIN], stencil_sum<ST, C>(Pm), k);
+                        } else {
+                            auto P0 = [&](int dx, int dy, int) -> C { return s_in[0][slot_in(y + dy)][c + RIN + dx]; };
+                            const C S0 = stencil_sum<ST, C>(P0);
+                            const C p0 = s_in[0][slot_in(y)][c + RIN];
+                            if constexpr (MODEL == AC) {
+                                o0 = ac_update<C>(p0, S0, k);
+                            } else {
+                                auto P1 = [&](int dx, int dy, int) -> C {
+                                    return s_in[NF - 1][slot_in(y + dy)][c + RIN + dx];
+                                };
+                                gs_update<C>(p0, s_in[NF - 1][slot_in(y)][c + RIN], S0, stencil_sum<ST, C>(P1), k,
+                                             o0, o1);
+                            }
+                        }
+                        if (x < nx) {
+                            out[0][row + x] = from_c<T>(o0);
+                            if constexpr (MODEL == GS) out[1][row + x] = from_c<T>(o1);
+                        }
+                    }
+                }
+            }
+        };
+
+        // prologue: rows [y0 - RIN, y0 + RIN - ...) that precede the first batch
+        constexpr int PRO = (MODEL == CH) ? 4 * r : 2 * r;  // phi rows before the first batch's new rows
+        {
+            int y = y0 - RIN;
+            for (int left = PRO; left > 0; left -= RB) {
+                const int n = left < RB ? left : RB;
+                fetch(y, n);
+                commit(y, n);
+                y += n;
+            }
+        }
+        __syncthreads();
+        if constexpr (MODEL == CH) {
+            compute_mu(y0 - r, 2 * r);  // mu rows carried into the first batch
+        }
+        // first batch's new rows
+        int ynew = y0 - RIN + PRO;   // = y0 + RIN (CH: y0 + 2r; AC/GS: y0 + r)
+        int nb = min(RB, y1 - y0);
+        fetch(ynew, nb);
+        for (int yb = y0; yb < y1; yb += RB) {
+            const int n = min(RB, y1 - yb);
+            commit(ynew, n);
+            ynew += n;
+            const int nn = min(RB, y1 - (yb + RB));
+            if (nn > 0) fetch(ynew, nn);
+            __syncthreads();
+            if constexpr (MODEL == CH) {
+                compute_mu(yb + r, n);
+                __syncthreads();
+            }
+            output(yb, n);
+        }
+        __syncthreads();  // the rings are reused by the next segment
+    }
+}
+
+// ============================================================= 2D, tiles ==
+//
+// Tile kernel for FP32 and BF16 storage (bound by HBM).  One CTA per BX x BY
+// output tile: the tile plus an R-wide halo (R = r, or 2r for Cahn-Hilliard)
+// is fetched in one shot as 16-byte chunks with cp.async (rows padded to whole
+// chunks: one chunk of halo on each side), Cahn-Hilliard computes mu on the
+// tile plus an r-wide ring, then every point of the tile is updated.  Many
+// small CTAs are resident per SM, so the loads of one CTA overlap the
+// arithmetic of the others; halo reads of neighbouring tiles hit L2.
+template <int MODEL, int ST, typename T, int BX, int BY>
+struct Step2dTileShape {
+    typedef typename Cmp<T>::type C;
+    static constexpr int r = StencilInfo<ST>::r;
+    static constexpr int R = (MODEL == CH) ? 2 * r : r;
+    static constexpr int CK = 16 / sizeof(T);          // elements per 16-byte chunk
+    static_assert(R <= CK, "halo wider than one chunk");
+    static constexpr int NCK = BX / CK + 2;            // chunks per row
+    static constexpr int SW = NCK * CK;                // row stride (elements of T)
+    static constexpr int HIN = BY + 2 * R;             // rows
+    static constexpr int NF = (MODEL == GS) ? 2 : 1;
+    static constexpr int WMU = (MODEL == CH) ? BX + 2 * r : 0, HMU = (MODEL == CH) ? BY + 2 * r : 0;
+    static constexpr size_t bytes_in = sizeof(T) * (size_t)NF * HIN * SW;
+    static constexpr size_t smem_bytes = bytes_in + sizeof(C) * (size_t)WMU * HMU;
+};
+
+template <int MODEL, int ST, typename T, int BX, int BY, int NT>
+__global__ void __launch_bounds__(NT) step2d_tile_kernel(StepArgs a) {
+    typedef Step2dTileShape<MODEL, ST, T, BX, BY> Sh;
+    typedef typename Sh::C C;
+    constexpr int r = Sh::r, R = Sh::R, CK = Sh::CK, NCK = Sh::NCK, SW = Sh::SW, HIN = Sh::HIN, NF = Sh::NF;
+    constexpr int WMU = Sh::WMU, HMU = Sh::HMU;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s_in = reinterpret_cast<T *>(smem_raw);                   // [NF][HIN][SW]
+    C *s_mu = reinterpret_cast<C *>(smem_raw + Sh::bytes_in);    // [HMU][WMU]
+
+    const ConstsC<C> k(a.k, a.kf);
+    const int nx = a.nx, ny = a.ny;
+    const int t = threadIdx.x;
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    const bool vec_ok = (nx % CK) == 0;
+    const T *in[2] = {static_cast<const T *>(a.in0), static_cast<const T *>(a.in1)};
+    T *out[2] = {static_cast<T *>(a.out0), static_cast<T *>(a.out1)};
+
+    // fetch: chunk c of row i covers columns x0 - CK + c*CK .. +CK-1
+    for (int q = t; q < HIN * NCK; q += NT) {
+        const int i = q / NCK, c = q - i * NCK;
+        const int y = wrap_idx(y0 - R + i, ny);
+        const int x = x0 - CK + c * CK;
+        const size_t row = (size_t)y * (size_t)nx;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            T *dst = s_in + ((size_t)f * HIN + i) * SW + c * CK;
+            if (vec_ok && x >= 0 && x + CK <= nx) {
+                cp_async16(dst, in[f] + row + x);
+            } else {
+#pragma unroll
+                for (int j = 0; j < CK; ++j) dst[j] = in[f][row + wrap_idx(x + j, nx)];
+            }
+        }
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+
+    auto phi = [&](int f, int i, int j) -> C { return to_c(s_in[((size_t)f * HIN + i) * SW + j]); };
+    if constexpr (MODEL == CH) {
+        // mu at (y0 - r + i, x0 - r + j), i < HMU, j < WMU
+        for (int q = t; q < HMU * WMU; q += NT) {
+            const int i = q / WMU, j = q - i * WMU;
+            const int ii = i + (R - r), jj = j + (CK - r);
+            auto P = [&](int dx, int dy, int) -> C { return phi(0, ii + dy, jj + dx); };
+            s_mu[q] = ch_mu<C>(phi(0, ii, jj), stencil_sum<ST, C>(P), k);
+        }
+        __syncthreads();
+    }
+    for (int q = t; q < BY * BX; q += NT) {
+        const int i = q / BX, j = q - i * BX;
+        const int y = y0 + i, x = x0 + j;
+        if (y >= ny || x >= nx) continue;
+        const size_t o = (size_t)y * (size_t)nx + x;
+        if constexpr (MODEL == CH) {
+            auto Pm = [&](int dx, int dy, int) -> C { return s_mu[(i + r + dy) * WMU + (j + r + dx)]; };
+            out[0][o] = from_c<T>(ch_update<C>(phi(0, i + R, j + CK), stencil_sum<ST, C>(Pm), k));
+        } else {
+            auto P0 = [&](int dx, int dy, int) -> C { return phi(0, i + R + dy, j + CK + dx); };
+            const C S0 = stencil_sum<ST, C>(P0);
+            if constexpr (MODEL == AC) {
+                out[0][o] = from_c<T>(ac_update<C>(phi(0, i + R, j + CK), S0, k));
+            } else {
+                auto P1 = [&](int dx, int dy, int) -> C { return phi(NF - 1, i + R + dy, j + CK + dx); };
+                C un, vn;
+                gs_update<C>(phi(0, i + R, j + CK), phi(NF - 1, i + R, j + CK), S0, stencil_sum<ST, C>(P1), k, un, vn);
+                out[0][o] = from_c<T>(un);
+                out[NF - 1][o] = from_c<T>(vn);
             }
         }
     }
@@ -172,7 +318,7 @@ struct Step3dShape {
 };
 
 template <int MODEL, int ST, typename T, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT) step3d_kernel(StepArgs a, int TZ) {
+__global__ void __launch_bounds__(NT) step3d_kernel(StepArgs a, int tiles_x, int tiles_y, long long planes_per_cta) {
     typedef Step3dShape<MODEL, ST, T, TX, TY, NT> Sh;
     typedef typename Sh::C C;
     constexpr int r = Sh::r, RIN = Sh::RIN, WIN = Sh::WIN, AIN = Sh::AIN, DIN = Sh::DIN, NF = Sh::NF;
@@ -181,17 +327,23 @@ __global__ void __launch_bounds__(NT) step3d_kernel(StepArgs a, int TZ) {
     C *s_in = reinterpret_cast<C *>(smem_raw);            // [NF][DIN][AIN]
     C *s_mu = s_in + (size_t)NF * DIN * AIN;               // [DMU][AMU]
 
-    const ConstsC<C> k(a.k);
+    const ConstsC<C> k(a.k, a.kf);
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int t = threadIdx.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * TZ;
-    const int z1 = min(z0 + TZ, nz);
-    if (z0 >= z1) return;
-    const int nplanes = (z1 - z0) + 2 * RIN;
     const size_t plane = (size_t)nx * (size_t)ny;
     const T *in[2] = {static_cast<const T *>(a.in0), static_cast<const T *>(a.in1)};
     T *out[2] = {static_cast<T *>(a.out0), static_cast<T *>(a.out1)};
+    // Persistent schedule: CTA c owns planes [c*P, (c+1)*P) of the flattened
+    // (tile, z) space, one segment per tile it touches.
+    long long g0 = (long long)blockIdx.x * planes_per_cta;
+    const long long gend = min(g0 + planes_per_cta, (long long)tiles_x * tiles_y * nz);
+    while (g0 < gend) {
+    const int tile = (int)(g0 / nz);
+    const int z0 = (int)(g0 - (long long)tile * nz);
+    const int z1 = (int)min((long long)nz, (long long)z0 + (gend - g0));
+    g0 += z1 - z0;
+    const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+    const int nplanes = (z1 - z0) + 2 * RIN;
 
     // per-thread load offsets within a plane (independent of z)
     int loff[EPT];
@@ -292,6 +444,245 @@ __global__ void __launch_bounds__(NT) step3d_kernel(StepArgs a, int TZ) {
             }
         }
     }
+    __syncthreads();  // the rings are reused by the next segment
+    }  // segments
+}
+
+// ======================================================== 3D, vectorised ==
+//
+// FP32 / BF16-storage 3D kernel.  A thread owns V = 4 consecutive x cells of
+// one row of a TX x TY tile (TX = 4*TXT, TY = TYT) and streams along z.  Plane
+// slices live in shared memory as rows of NCH = TX/4 + 2 chunks of 4 cells
+// (one halo chunk on each side, so any stencil radius up to 4 fits); all
+// shared-memory traffic is aligned 16-byte chunks.  Cahn-Hilliard computes mu
+// chunk-wise on the tile rows plus r halo rows and the two halo chunks; the
+// cells of a halo chunk beyond the needed r columns read neighbours outside
+// the row (kept inside the allocation by guard chunks) and are never used.
+template <int MODEL, int ST, typename T, int TXT, int TYT>
+struct Step3dVecShape {
+    typedef typename Cmp<T>::type C;
+    static constexpr int V = 4;
+    static constexpr int r = StencilInfo<ST>::r;
+    static constexpr int R = (MODEL == CH) ? 2 * r : r;
+    static_assert(R <= V, "halo wider than one chunk");
+    static constexpr int TX = TXT * V, TY = TYT, NT = TXT * TYT;
+    static constexpr int NCH = TXT + 2;          // chunks per row
+    static constexpr int SW = NCH * V;           // row stride (cells)
+    static constexpr int HIN = TY + 2 * R;       // rows of an input plane
+    static constexpr int PIN = HIN * SW;
+    static constexpr int HMU = TY + 2 * r;       // rows of a mu plane
+    static constexpr int PMU = HMU * SW;
+    static constexpr int DIN = 2 * r + 2;
+    static constexpr int DMU = (MODEL == CH) ? 2 * r + 1 : 0;
+    static constexpr int NF = (MODEL == GS) ? 2 : 1;
+    static constexpr int GUARD = 2 * V;          // cells before and after the planes
+    static constexpr int EPT = (HIN * NCH + NT - 1) / NT;  // input chunks per thread per field
+    static constexpr size_t smem_bytes = sizeof(C) * ((size_t)2 * GUARD + (size_t)NF * DIN * PIN + (size_t)DMU * PMU);
+};
+
+// Cells [-r, V+r) around the 4-cell chunk at p (16-byte aligned) into w.
+template <int r, int W>
+__device__ __forceinline__ void chunk_row(const float *p, float (&w)[W]) {
+    const float4 c = *reinterpret_cast<const float4 *>(p);
+    w[r + 0] = c.x; w[r + 1] = c.y; w[r + 2] = c.z; w[r + 3] = c.w;
+    if constexpr (r > 0) {
+        const float4 lq = *reinterpret_cast<const float4 *>(p - 4);
+        const float4 rq = *reinterpret_cast<const float4 *>(p + 4);
+        const float l[4] = {lq.x, lq.y, lq.z, lq.w}, rr[4] = {rq.x, rq.y, rq.z, rq.w};
+#pragma unroll
+        for (int d = 0; d < r; ++d) {
+            w[d] = l[4 - r + d];
+            w[r + 4 + d] = rr[d];
+        }
+    }
+}
+
+// Stencil sums S and centre values of the 4 cells of the chunk at row `row`,
+// chunk `ci` of the planes pl[0 .. 2r] (plane offsets -r .. r), row stride SW.
+template <int ST, int SW>
+__device__ __forceinline__ void chunk_sums(const float *const (&pl)[2 * StencilInfo<ST>::r + 1], int row, int ci,
+                                           float (&S)[4], float (&ctr)[4]) {
+    constexpr int r = StencilInfo<ST>::r;
+    constexpr int W = 4 + 2 * r;
+    float w[2 * r + 1][2 * r + 1][W];
+#pragma unroll
+    for (int dz = -r; dz <= r; ++dz)
+#pragma unroll
+        for (int dy = -r; dy <= r; ++dy)
+            if (ST == L27 || dz == 0 || dy == 0)  // cross stencils only read the axes
+                chunk_row<r, W>(pl[dz + r] + (row + dy) * SW + ci * 4, w[dz + r][dy + r]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        auto P = [&](int dx, int dy, int dz) -> float { return w[dz + r][dy + r][r + j + dx]; };
+        S[j] = stencil_sum<ST, float>(P);
+        ctr[j] = w[r][r][r + j];
+    }
+}
+
+template <int MODEL, int ST, typename T, int TXT, int TYT>
+__global__ void __launch_bounds__(TXT * TYT) step3d_vec_kernel(StepArgs a, int tiles_x, int tiles_y,
+                                                               long long planes_per_cta) {
+    typedef Step3dVecShape<MODEL, ST, T, TXT, TYT> Sh;
+    typedef typename Sh::C C;
+    constexpr int V = Sh::V, r = Sh::r, R = Sh::R, TX = Sh::TX, TY = Sh::TY, NT = Sh::NT;
+    constexpr int NCH = Sh::NCH, SW = Sh::SW, HIN = Sh::HIN, PIN = Sh::PIN, HMU = Sh::HMU, PMU = Sh::PMU;
+    constexpr int DIN = Sh::DIN, DMU = Sh::DMU, NF = Sh::NF, EPT = Sh::EPT;
+    typedef float4 Q;  // one chunk in shared memory (C is float here)
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *s_in = reinterpret_cast<C *>(smem_raw) + Sh::GUARD;   // [NF][DIN][PIN]
+    C *s_mu = s_in + (size_t)NF * DIN * PIN;                // [DMU][PMU]
+
+    const ConstsC<C> k(a.k, a.kf);
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int t = threadIdx.x;
+    const size_t plane = (size_t)nx * (size_t)ny;
+    const bool vec_ok = (nx % V) == 0;
+    const T *in[2] = {static_cast<const T *>(a.in0), static_cast<const T *>(a.in1)};
+    T *out[2] = {static_cast<T *>(a.out0), static_cast<T *>(a.out1)};
+    // Persistent schedule over the flattened (tile, z) space (see step3d_kernel).
+    long long g0 = (long long)blockIdx.x * planes_per_cta;
+    const long long gend = min(g0 + planes_per_cta, (long long)tiles_x * tiles_y * nz);
+    while (g0 < gend) {
+    const int tile = (int)(g0 / nz);
+    const int z0 = (int)(g0 - (long long)tile * nz);
+    const int z1 = (int)min((long long)nz, (long long)z0 + (gend - g0));
+    g0 += z1 - z0;
+    const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+    const int nplanes = (z1 - z0) + 2 * R;
+
+    // input chunks of this thread: plane-relative offset of the first cell, or -1
+    int goff[EPT];
+    bool gvec[EPT];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+        const int q = t + e * NT;
+        goff[e] = -1;
+        gvec[e] = false;
+        if (q < HIN * NCH) {
+            const int yi = q / NCH, ci = q - yi * NCH;
+            const int y = wrap_idx(y0 - R + yi, ny);
+            const int x = x0 - V + ci * V;
+            gvec[e] = vec_ok && x >= 0 && x + V <= nx;
+            goff[e] = y * nx + (gvec[e] ? x : 0);
+        }
+    }
+    C pf[NF][EPT][V];
+    auto fetch = [&](int z) {
+        const size_t zoff = (size_t)wrap_idx(z, nz) * plane;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            if (goff[e] < 0) continue;
+            const int q = t + e * NT;
+            const int ci = q % NCH;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                if (gvec[e]) {
+                    load_vec<T, V>(in[f] + zoff + goff[e], pf[f][e]);
+                } else {
+                    const int x = x0 - V + ci * V;
+#pragma unroll
+                    for (int j = 0; j < V; ++j) pf[f][e][j] = load_one(in[f] + zoff + goff[e] + wrap_idx(x + j, nx));
+                }
+            }
+        }
+    };
+    auto commit = [&](int slot) {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            if (goff[e] < 0) continue;
+            const int q = t + e * NT;
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+                *reinterpret_cast<Q *>(s_in + ((size_t)f * DIN + slot) * PIN + q * V) =
+                    make_float4(pf[f][e][0], pf[f][e][1], pf[f][e][2], pf[f][e][3]);
+        }
+    };
+    fetch(z0 - R);
+    for (int jz = 0; jz < nplanes; ++jz) {
+        commit(jz % DIN);
+        if (jz + 1 < nplanes) fetch(z0 - R + jz + 1);
+        __syncthreads();
+        if constexpr (MODEL == CH) {
+            if (jz >= 2 * r) {
+                C *mu = s_mu + (size_t)((jz - 2 * r) % DMU) * PMU;
+                const C *pl[2 * r + 1];
+#pragma unroll
+                for (int d = 0; d <= 2 * r; ++d) pl[d] = s_in + (size_t)((jz - 2 * r + d) % DIN) * PIN;
+                for (int q = t; q < HMU * NCH; q += NT) {
+                    const int ym = q / NCH, ci = q - ym * NCH;
+                    C S[V], p[V], m[V];
+                    chunk_sums<ST, SW>(pl, ym + r, ci, S, p);
+#pragma unroll
+                    for (int j = 0; j < V; ++j) m[j] = ch_mu<C>(p[j], S[j], k);
+                    *reinterpret_cast<Q *>(mu + ym * SW + ci * V) = make_float4(m[0], m[1], m[2], m[3]);
+                }
+            }
+            __syncthreads();
+            if (jz >= 4 * r) {
+                const int zo = z0 + jz - 4 * r;
+                const int tx = t % TXT, ty = t / TXT;
+                const int x = x0 + tx * V, y = y0 + ty;
+                if (y < ny && x < nx) {
+                    const C *plm[2 * r + 1];
+#pragma unroll
+                    for (int d = 0; d <= 2 * r; ++d) plm[d] = s_mu + (size_t)((jz - 4 * r + d) % DMU) * PMU;
+                    C S[V], dummy[V], o[V];
+                    chunk_sums<ST, SW>(plm, ty + r, tx + 1, S, dummy);
+                    const C *pc = s_in + (size_t)((jz - 2 * r) % DIN) * PIN + (ty + R) * SW + (tx + 1) * V;
+                    const Q c = *reinterpret_cast<const Q *>(pc);
+                    const C p[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+                    for (int j = 0; j < V; ++j) o[j] = ch_update<C>(p[j], S[j], k);
+                    T *dst = out[0] + (size_t)zo * plane + (size_t)y * nx;
+                    if (vec_ok && x + V <= nx) store_vec<T, V>(dst + x, o);
+                    else
+                        for (int j = 0; j < V; ++j)
+                            if (x + j < nx) dst[x + j] = from_c<T>(o[j]);
+                }
+            }
+        } else {
+            if (jz >= 2 * r) {
+                const int zo = z0 + jz - 2 * r;
+                const int tx = t % TXT, ty = t / TXT;
+                const int x = x0 + tx * V, y = y0 + ty;
+                if (y < ny && x < nx) {
+                    const C *pl0[2 * r + 1];
+#pragma unroll
+                    for (int d = 0; d <= 2 * r; ++d) pl0[d] = s_in + (size_t)((jz - 2 * r + d) % DIN) * PIN;
+                    C S0[V], p0[V], o0[V], o1[V];
+                    chunk_sums<ST, SW>(pl0, ty + r, tx + 1, S0, p0);
+                    if constexpr (MODEL == AC) {
+#pragma unroll
+                        for (int j = 0; j < V; ++j) o0[j] = ac_update<C>(p0[j], S0[j], k);
+                    } else {
+                        const C *pl1[2 * r + 1];
+#pragma unroll
+                        for (int d = 0; d <= 2 * r; ++d)
+                            pl1[d] = s_in + ((size_t)(NF - 1) * DIN + (jz - 2 * r + d) % DIN) * PIN;
+                        C S1[V], p1[V];
+                        chunk_sums<ST, SW>(pl1, ty + r, tx + 1, S1, p1);
+#pragma unroll
+                        for (int j = 0; j < V; ++j) gs_update<C>(p0[j], p1[j], S0[j], S1[j], k, o0[j], o1[j]);
+                    }
+                    const size_t o = (size_t)zo * plane + (size_t)y * nx;
+                    T *dst0 = out[0] + o;
+                    if (vec_ok && x + V <= nx) store_vec<T, V>(dst0 + x, o0);
+                    else
+                        for (int j = 0; j < V; ++j)
+                            if (x + j < nx) dst0[x + j] = from_c<T>(o0[j]);
+                    if constexpr (MODEL == GS) {
+                        T *dst1 = out[1] + o;
+                        if (vec_ok && x + V <= nx) store_vec<T, V>(dst1 + x, o1);
+                        else
+                            for (int j = 0; j < V; ++j)
+                                if (x + j < nx) dst1[x + j] = from_c<T>(o1[j]);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();  // the rings are reused by the next segment
+    }  // segments
 }
 
 }  // namespace sp

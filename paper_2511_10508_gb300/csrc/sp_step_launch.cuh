@@ -1,57 +1,93 @@
 // sp_step_launch.cuh -- host-side launch of the step kernels: tile choices per
 // storage type and stencil radius, and the grid size.
 //
-// Grid sizing: a CTA owns a column strip (2D: TW columns; 3D: a TX x TY tile)
-// and a run of rows/planes along the slowest axis.  The run length is chosen
-// so that the whole grid is one wave of resident CTAs (SMs x occupancy), but
-// never shorter than kMinRun slices, which bounds the redundant halo slices
-// (2*RIN per run) at a few percent.
+// Grid sizing: every kernel is persistent.  The work is the flattened space of
+// (column strip or xy tile, row or plane) pairs; the grid is one resident wave
+// and each CTA (2D FP32/BF16: each warp) takes an equal contiguous share, so no
+// SM waits for a tail of long-running CTAs.
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "sp_internal.h"
 #include "sp_step.cuh"
 
 namespace sp {
 
+// 3D tiles (x, y) per storage type and stencil radius.
 template <typename T> struct Tiles;
 template <> struct Tiles<double> {
-    static constexpr int NT2 = 128, V2 = 2;                  // 2D: 256 columns per strip
     template <int r> struct T3 { static constexpr int TX = (r == 1) ? 64 : 32, TY = 32, NT = 256; };
 };
 template <> struct Tiles<float> {
-    static constexpr int NT2 = 128, V2 = 4;                  // 2D: 512 columns per strip
     template <int r> struct T3 { static constexpr int TX = 64, TY = 16, NT = 256; };
 };
 template <> struct Tiles<bf16> {
-    static constexpr int NT2 = 128, V2 = 8;                  // 2D: 1024 columns per strip
     template <int r> struct T3 { static constexpr int TX = 64, TY = 16, NT = 256; };
 };
 
 constexpr int kMinRun = 32;
 
-inline int run_length(int n_slow, long long strips, int ctas_per_sm, int n_sm) {
+// Persistent grids: one resident wave of CTAs (SMs x occupancy), each owning an
+// equal share of the flattened (tile, slow-axis) work, but at least kMinRun
+// slices per CTA so that the halo slices of each segment stay a small fraction.
+inline long long persistent_ctas(long long total_slices, int ctas_per_sm, int n_sm) {
     const long long wave = (long long)n_sm * std::max(ctas_per_sm, 1);
-    long long chunks = (wave + strips - 1) / strips;
-    chunks = std::max<long long>(1, std::min<long long>(chunks, (n_slow + kMinRun - 1) / kMinRun));
-    return (int)((n_slow + chunks - 1) / chunks);
+    return std::max(1LL, std::min(wave, total_slices / kMinRun));
 }
+
+// Batched persistent 2D kernel (FP64): rows per batch and CTAs per SM.
+template <int MODEL> struct Batch2d { static constexpr int NT = 128, RB = (MODEL == CH) ? 8 : (MODEL == AC ? 4 : 2), CPS = 4; };
 
 template <int MODEL, int ST, typename T>
 cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm) {
-    if constexpr (StencilInfo<ST>::dims == 2) {
-        constexpr int NT = Tiles<T>::NT2, V = Tiles<T>::V2, TW = NT * V;
-        auto kern = step2d_kernel<MODEL, ST, T, NT, V>;
+    if constexpr (StencilInfo<ST>::dims == 2 && std::is_same<T, double>::value) {
+        typedef Batch2d<MODEL> B;
+        typedef Step2dBatchShape<MODEL, ST, T, B::NT, B::RB> Sh;
+        auto kern = step2d_batch_kernel<MODEL, ST, T, B::NT, B::RB>;
         static const int occ = [&] {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem_bytes);
             int o = 1;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, B::NT, Sh::smem_bytes);
             return o;
         }();
-        const int strips = (a.nx + TW - 1) / TW;
-        const int TH = run_length(a.ny, strips, occ, n_sm);
-        dim3 grid(strips, (a.ny + TH - 1) / TH);
-        kern<<<grid, NT, 0, s>>>(a, TH);
+        const int strips = (a.nx + Sh::TW - 1) / Sh::TW;
+        const long long total = (long long)strips * a.ny;
+        // equal rows per CTA; at least 4*RB rows each so that the ring warm-up stays small
+        long long ctas = (long long)n_sm * std::max(1, std::min(occ, B::CPS));
+        ctas = std::max(1LL, std::min(ctas, total / (4 * B::RB)));
+        const long long rows = (total + ctas - 1) / ctas;
+        ctas = (total + rows - 1) / rows;
+        kern<<<(unsigned)ctas, B::NT, Sh::smem_bytes, s>>>(a, strips, rows);
+    } else if constexpr (StencilInfo<ST>::dims == 2) {
+        // FP32 / BF16: one CTA per 128 x 32 tile
+        constexpr int BX = 128, BY = 32, NT = 256;
+        typedef Step2dTileShape<MODEL, ST, T, BX, BY> Sh;
+        auto kern = step2d_tile_kernel<MODEL, ST, T, BX, BY, NT>;
+        static const bool attr = [&] {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem_bytes);
+            return true;
+        }();
+        (void)attr;
+        dim3 grid((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY);
+        kern<<<grid, NT, Sh::smem_bytes, s>>>(a);
+    } else if constexpr (!std::is_same<T, double>::value) {
+        // FP32 / BF16 3D: vectorised plane kernel, 64 x 32 tiles
+        constexpr int TXT = 16, TYT = 32;
+        typedef Step3dVecShape<MODEL, ST, T, TXT, TYT> Sh;
+        auto kern = step3d_vec_kernel<MODEL, ST, T, TXT, TYT>;
+        static const int occ = [&] {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem_bytes);
+            int o = 1;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, Sh::NT, Sh::smem_bytes);
+            return o;
+        }();
+        const int tx = (a.nx + Sh::TX - 1) / Sh::TX, ty = (a.ny + Sh::TY - 1) / Sh::TY;
+        const long long ctas = persistent_ctas((long long)tx * ty * a.nz, occ, n_sm);
+        const long long planes = ((long long)tx * ty * a.nz + ctas - 1) / ctas;
+        kern<<<(unsigned)(((long long)tx * ty * a.nz + planes - 1) / planes), Sh::NT, Sh::smem_bytes, s>>>(
+            a, tx, ty, planes);
     } else {
         typedef typename Tiles<T>::template T3<StencilInfo<ST>::r> TT;
         typedef Step3dShape<MODEL, ST, T, TT::TX, TT::TY, TT::NT> Sh;
@@ -62,10 +98,11 @@ cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm) {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, TT::NT, Sh::smem_bytes);
             return o;
         }();
-        const long long strips = (long long)((a.nx + TT::TX - 1) / TT::TX) * ((a.ny + TT::TY - 1) / TT::TY);
-        const int TZ = run_length(a.nz, strips, occ, n_sm);
-        dim3 grid((a.nx + TT::TX - 1) / TT::TX, (a.ny + TT::TY - 1) / TT::TY, (a.nz + TZ - 1) / TZ);
-        kern<<<grid, TT::NT, Sh::smem_bytes, s>>>(a, TZ);
+        const int tx = (a.nx + TT::TX - 1) / TT::TX, ty = (a.ny + TT::TY - 1) / TT::TY;
+        const long long ctas = persistent_ctas((long long)tx * ty * a.nz, occ, n_sm);
+        const long long planes = ((long long)tx * ty * a.nz + ctas - 1) / ctas;
+        kern<<<(unsigned)(((long long)tx * ty * a.nz + planes - 1) / planes), TT::NT, Sh::smem_bytes, s>>>(
+            a, tx, ty, planes);
     }
     return cudaGetLastError();
 }

@@ -255,3 +255,26 @@ def test_mass_conservation_cahn_hilliard_gpu(sp):
         m1 = sim.reduce(sp.MASS)
         u = sim.read(0)
         assert abs(m1 - m0) <= 500 * 1e-15 * u.size * np.abs(u).max()
+
+
+def test_reduction_of_unaligned_field_pointer(sp):
+    """sp_reduce_field_noalloc takes any caller pointer: an element-aligned but not
+    16-byte-aligned base must take the scalar path and give the same sum."""
+    import ctypes
+    from paper_2511_10508_gb300 import _native as N
+
+    with sp.Simulation(sp.ALLEN_CAHN, (33, 65), dt=0.01, dtype=sp.F32, seed=3, ic_amp=0.4) as sim:
+        u = sim.read(0)
+        f = N.lib().sp_reduce_field_noalloc
+        f.restype = ctypes.c_int
+        f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                      ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                      ctypes.c_void_p]
+        out = ctypes.c_double(0)
+        # skip the first element: a 4-byte-aligned base; reduce the remaining 33*65-1 values as a 1-row grid
+        n = u.size - 1
+        rc = f(sp.SUM_U, sp.F32, sim.devptr(0) + 4, 2, (ctypes.c_int64 * 3)(n, 1, 1), 1.0, 1.0, 1.0,
+               ctypes.byref(out), None)
+        assert rc == N.SP_OK
+        ref = O.kahan_sum(u.ravel()[1:])
+        assert abs(out.value - ref) <= 1e-13 * np.abs(u).sum()
