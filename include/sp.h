@@ -197,6 +197,75 @@ int sp_steps_taken(const sp_sim *sim, int64_t *steps);
 /* Release all device memory of the simulation (synchronises its stream). */
 int sp_destroy(sp_sim *sim);
 
+/* --------------------------------------------------------------- serving -- */
+
+/*
+ * Continuous-batching server (the paper has no serving layer; it benchmarks
+ * one grid at a time, Sec. "Benchmarks").  Requests of any model, dimension,
+ * size and precision (FP64 or FP32 storage) arrive at any time; a scheduler
+ * thread admits them in arrival order whenever a slot and enough of the HBM
+ * budget are free (a request that does not fit yet lets smaller ones pass),
+ * keeps their fields resident, and advances all resident grids together in
+ * quanta of `quantum_steps` time steps: one batched launch per (dims, dtype)
+ * per step covers the tiles of every resident grid, and the quantum's launches
+ * are replayed from a CUDA graph while the resident set is unchanged.  A
+ * finished grid's FP64 mass (and optionally its fields, as FP64) are copied to
+ * host memory and its device memory is freed.  A grid's result does not depend
+ * on the other grids in the mix.
+ */
+typedef struct sp_server sp_server;
+
+typedef struct sp_request {
+    int model, dims;        /* as sp_create */
+    int64_t shape[3];       /* nx, ny, nz (nz = 1 in 2D) */
+    double h, dt;
+    sp_params params;       /* dtype must be SP_F64 or SP_F32 */
+    int64_t nsteps;         /* time steps to run (>= 1) */
+    int return_fields;      /* nonzero: keep an FP64 host copy of the final fields */
+    int fault;              /* fault injection for tests: 0 none, 1 the allocation fails */
+} sp_request;
+
+typedef struct sp_result {
+    int status;             /* SP_PENDING, SP_OK or the error of this request */
+    int64_t steps_done;
+    double t_submit, t_admit, t_finish;  /* seconds since server creation; -1 if not reached */
+    double mass;            /* h^d sum of field 0 at the end (FP64, compensated) */
+    const double *fields;   /* FP64 fields (field 0, then field 1), or NULL; owned by the
+                               server, valid until sp_release(ticket) */
+    size_t n_values;        /* number of doubles at `fields` */
+} sp_result;
+
+typedef struct sp_server_stats {
+    uint64_t submitted, admitted, finished, failed, quanta;
+    int64_t resident, pending;
+    size_t hbm_in_use;      /* bytes of field buffers of admitted requests */
+    double lups;            /* lattice-site updates done (points x steps) */
+    double busy_s;          /* seconds the scheduler spent running quanta */
+} sp_server_stats;
+
+/* Create a server on the current device with an HBM budget for field buffers,
+ * at most max_slots resident grids, and quanta of quantum_steps steps. */
+int sp_server_create(size_t hbm_budget_bytes, int max_slots, int quantum_steps, sp_server **out);
+
+/* Queue a request; *ticket identifies it.  SP_EBUDGET if it can never fit,
+ * SP_EUNSTABLE / SP_EINVAL as sp_create.  Never blocks on the device. */
+int sp_submit(sp_server *srv, const sp_request *req, uint64_t *ticket);
+
+/* Non-blocking status: SP_PENDING until the request is done, then its status;
+ * *out is filled in either case.  SP_ENOTFOUND for an unknown ticket. */
+int sp_poll(sp_server *srv, uint64_t ticket, sp_result *out);
+
+/* Block until the request is done or timeout_s seconds pass (SP_ETIMEOUT). */
+int sp_wait(sp_server *srv, uint64_t ticket, double timeout_s, sp_result *out);
+
+/* Free a finished request's host result (SP_EBUSY while it is pending). */
+int sp_release(sp_server *srv, uint64_t ticket);
+
+int sp_server_get_stats(sp_server *srv, sp_server_stats *out);
+
+/* Stop the scheduler, free every device and host buffer of the server. */
+int sp_server_destroy(sp_server *srv);
+
 /* Message of the calling thread's last failing call ("" if none). */
 const char *sp_last_error(void);
 

@@ -17,7 +17,7 @@ from ._native import (ALLEN_CAHN, BF16_F32, CAHN_HILLIARD, F32, F64, FREE_ENERGY
                       IC_NOISE, LAP_5, LAP_7, LAP_9BOX, LAP_9CROSS4, LAP_13CROSS4, LAP_27, LAP_DEFAULT, MASS,
                       MAX_U, MIN_U, SUM_U, SUM_V, SUMSQ_U, SpError)
 
-__all__ = ["Simulation", "params", "check_stability", "SpError", "ALLEN_CAHN", "CAHN_HILLIARD", "GRAY_SCOTT",
+__all__ = ["Simulation", "Server", "Result", "params", "check_stability", "SpError", "ALLEN_CAHN", "CAHN_HILLIARD", "GRAY_SCOTT",
            "LAP_5", "LAP_9BOX", "LAP_9CROSS4", "LAP_7", "LAP_27", "LAP_13CROSS4", "LAP_DEFAULT", "F64", "F32",
            "BF16_F32", "IC_NOISE", "IC_CONSTANT", "MASS", "FREE_ENERGY", "SUM_U", "SUM_V", "MIN_U", "MAX_U",
            "SUMSQ_U"]
@@ -149,3 +149,99 @@ class Simulation:
 
         t = torch.as_tensor(_CAI(), device="cuda")
         return t.view(tdt) if self.dtype == BF16_F32 else t
+
+
+class Result:
+    """Outcome of a served request (a copy; the server's buffers may be released)."""
+
+    def __init__(self, res: N.sp_result, shape, nfields: int):
+        self.status = res.status
+        self.steps_done = res.steps_done
+        self.t_submit, self.t_admit, self.t_finish = res.t_submit, res.t_admit, res.t_finish
+        self.mass = res.mass
+        self.fields = None
+        if res.fields and res.n_values:
+            flat = np.ctypeslib.as_array(res.fields, shape=(res.n_values,)).copy()
+            self.fields = flat.reshape((nfields,) + tuple(shape))
+
+    @property
+    def latency(self) -> float:
+        """Time to result: finish - submit (seconds)."""
+        return self.t_finish - self.t_submit
+
+
+class Server:
+    """Continuous-batching server (``sp_server_*``): submit grids at any time,
+    collect results by ticket."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 256, quantum_steps: int = 50):
+        h = ctypes.c_void_p()
+        N.check(N.lib().sp_server_create(int(hbm_budget_bytes), int(max_slots), int(quantum_steps),
+                                         ctypes.byref(h)), "sp_server_create")
+        self._h = h
+        self._meta = {}
+
+    def submit(self, model: int, shape, *, dt: float, nsteps: int, h: float = 1.0, prm: N.sp_params | None = None,
+               return_fields: bool = False, fault: int = 0, **kw) -> int:
+        shape = tuple(int(s) for s in shape)
+        dims = len(shape)
+        r = N.sp_request()
+        r.model, r.dims = model, dims
+        xyz = list(shape[::-1]) + [1] * (3 - dims)
+        for i in range(3):
+            r.shape[i] = xyz[i]
+        r.h, r.dt = h, dt
+        r.params = prm if prm is not None else params(model, dims, **kw)
+        r.nsteps = int(nsteps)
+        r.return_fields = int(bool(return_fields))
+        r.fault = int(fault)
+        t = ctypes.c_uint64(0)
+        N.check(N.lib().sp_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "sp_submit")
+        self._meta[t.value] = (shape, 2 if model == GRAY_SCOTT else 1)
+        return t.value
+
+    def poll(self, ticket: int):
+        """(status, Result or None): SP_PENDING (8) while running."""
+        res = N.sp_result()
+        rc = N.lib().sp_poll(self._h, ticket, ctypes.byref(res))
+        if rc == N.SP_PENDING:
+            return rc, None
+        shape, nf = self._meta[ticket]
+        return rc, Result(res, shape, nf)
+
+    def wait(self, ticket: int, timeout: float = 600.0) -> Result:
+        res = N.sp_result()
+        rc = N.lib().sp_wait(self._h, ticket, float(timeout), ctypes.byref(res))
+        if rc == N.SP_ETIMEOUT:
+            raise TimeoutError(f"ticket {ticket} not done after {timeout} s")
+        shape, nf = self._meta[ticket]
+        out = Result(res, shape, nf)
+        if rc != N.SP_OK:
+            raise SpError(rc, f"request {ticket}")
+        return out
+
+    def release(self, ticket: int) -> None:
+        N.check(N.lib().sp_release(self._h, ticket), "sp_release")
+        self._meta.pop(ticket, None)
+
+    def stats(self) -> dict:
+        st = N.sp_server_stats()
+        N.check(N.lib().sp_server_get_stats(self._h, ctypes.byref(st)), "sp_server_get_stats")
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            N.lib().sp_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -37,6 +37,25 @@ class sp_params(ctypes.Structure):
                 ("steps_per_launch", ctypes.c_int), ("flags", ctypes.c_int)]
 
 
+class sp_request(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("dims", ctypes.c_int), ("shape", ctypes.c_int64 * 3),
+                ("h", ctypes.c_double), ("dt", ctypes.c_double), ("params", sp_params),
+                ("nsteps", ctypes.c_int64), ("return_fields", ctypes.c_int), ("fault", ctypes.c_int)]
+
+
+class sp_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("steps_done", ctypes.c_int64), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_finish", ctypes.c_double), ("mass", ctypes.c_double),
+                ("fields", ctypes.POINTER(ctypes.c_double)), ("n_values", ctypes.c_size_t)]
+
+
+class sp_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("finished", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("quanta", ctypes.c_uint64), ("resident", ctypes.c_int64),
+                ("pending", ctypes.c_int64), ("hbm_in_use", ctypes.c_size_t), ("lups", ctypes.c_double),
+                ("busy_s", ctypes.c_double)]
+
+
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
 _P = ctypes.POINTER
@@ -54,6 +73,13 @@ _SIGS = {
     "sp_field_devptr": (ctypes.c_int, [_vp, ctypes.c_int, _P(_vp)]),
     "sp_steps_taken": (ctypes.c_int, [_vp, _P(_i64)]),
     "sp_destroy": (ctypes.c_int, [_vp]),
+    "sp_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, _P(_vp)]),
+    "sp_submit": (ctypes.c_int, [_vp, _P(sp_request), _P(ctypes.c_uint64)]),
+    "sp_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, _P(sp_result)]),
+    "sp_wait": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_double, _P(sp_result)]),
+    "sp_release": (ctypes.c_int, [_vp, ctypes.c_uint64]),
+    "sp_server_get_stats": (ctypes.c_int, [_vp, _P(sp_server_stats)]),
+    "sp_server_destroy": (ctypes.c_int, [_vp]),
     "sp_last_error": (ctypes.c_char_p, []),
     "sp_version": (ctypes.c_int, []),
 }

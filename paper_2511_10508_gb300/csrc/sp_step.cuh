@@ -201,22 +201,24 @@ __global__ void __launch_bounds__(NT) step2d_batch_kernel(StepArgs a, int strips
 
 // ============================================================= 2D, tiles ==
 //
-// Tile kernel for FP32 and BF16 storage (bound by HBM).  One CTA per BX x BY
-// output tile: the tile plus an R-wide halo (R = r, or 2r for Cahn-Hilliard)
-// is fetched in one shot as 16-byte chunks with cp.async (rows padded to whole
-// chunks: one chunk of halo on each side), Cahn-Hilliard computes mu on the
-// tile plus an r-wide ring, then every point of the tile is updated.  Many
-// small CTAs are resident per SM, so the loads of one CTA overlap the
-// arithmetic of the others; halo reads of neighbouring tiles hit L2.
+// Tile kernel for FP32 and BF16 storage (bound by HBM), also the 2D work unit
+// of the batched serving kernel.  One CTA per BX x BY output tile: the tile
+// plus an R-wide halo (R = r, or 2r for Cahn-Hilliard) is fetched in one shot
+// as 16-byte chunks with cp.async (rows padded to whole chunks: HC chunks of
+// halo on each side), Cahn-Hilliard computes mu on the tile plus an r-wide
+// ring, then every point of the tile is updated.  Many small CTAs are
+// resident per SM, so the loads of one CTA overlap the arithmetic of the
+// others; halo reads of neighbouring tiles hit L2.
 template <int MODEL, int ST, typename T, int BX, int BY>
 struct Step2dTileShape {
     typedef typename Cmp<T>::type C;
     static constexpr int r = StencilInfo<ST>::r;
     static constexpr int R = (MODEL == CH) ? 2 * r : r;
     static constexpr int CK = 16 / sizeof(T);          // elements per 16-byte chunk
-    static_assert(R <= CK, "halo wider than one chunk");
-    static constexpr int NCK = BX / CK + 2;            // chunks per row
+    static constexpr int HC = (R + CK - 1) / CK;       // halo chunks on each side
+    static constexpr int NCK = BX / CK + 2 * HC;       // chunks per row
     static constexpr int SW = NCK * CK;                // row stride (elements of T)
+    static constexpr int X0 = HC * CK;                 // smem column of the tile's first column
     static constexpr int HIN = BY + 2 * R;             // rows
     static constexpr int NF = (MODEL == GS) ? 2 : 1;
     static constexpr int WMU = (MODEL == CH) ? BX + 2 * r : 0, HMU = (MODEL == CH) ? BY + 2 * r : 0;
@@ -224,29 +226,27 @@ struct Step2dTileShape {
     static constexpr size_t smem_bytes = bytes_in + sizeof(C) * (size_t)WMU * HMU;
 };
 
+// One BX x BY tile with origin (x0, y0) of one grid; smem as in Step2dTileShape.
 template <int MODEL, int ST, typename T, int BX, int BY, int NT>
-__global__ void __launch_bounds__(NT) step2d_tile_kernel(StepArgs a) {
+__device__ __forceinline__ void tile2d(const T *in0, const T *in1, T *out0, T *out1, int nx, int ny,
+                                       const ConstsC<typename Cmp<T>::type> &k, int x0, int y0,
+                                       unsigned char *smem_raw) {
     typedef Step2dTileShape<MODEL, ST, T, BX, BY> Sh;
     typedef typename Sh::C C;
-    constexpr int r = Sh::r, R = Sh::R, CK = Sh::CK, NCK = Sh::NCK, SW = Sh::SW, HIN = Sh::HIN, NF = Sh::NF;
-    constexpr int WMU = Sh::WMU, HMU = Sh::HMU;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int r = Sh::r, R = Sh::R, CK = Sh::CK, NCK = Sh::NCK, SW = Sh::SW, X0 = Sh::X0, HIN = Sh::HIN;
+    constexpr int NF = Sh::NF, WMU = Sh::WMU, HMU = Sh::HMU;
     T *s_in = reinterpret_cast<T *>(smem_raw);                   // [NF][HIN][SW]
     C *s_mu = reinterpret_cast<C *>(smem_raw + Sh::bytes_in);    // [HMU][WMU]
-
-    const ConstsC<C> k(a.k, a.kf);
-    const int nx = a.nx, ny = a.ny;
     const int t = threadIdx.x;
-    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
     const bool vec_ok = (nx % CK) == 0;
-    const T *in[2] = {static_cast<const T *>(a.in0), static_cast<const T *>(a.in1)};
-    T *out[2] = {static_cast<T *>(a.out0), static_cast<T *>(a.out1)};
+    const T *in[2] = {in0, in1};
+    T *out[2] = {out0, out1};
 
-    // fetch: chunk c of row i covers columns x0 - CK + c*CK .. +CK-1
+    // fetch: chunk c of row i covers columns x0 - X0 + c*CK .. +CK-1
     for (int q = t; q < HIN * NCK; q += NT) {
         const int i = q / NCK, c = q - i * NCK;
         const int y = wrap_idx(y0 - R + i, ny);
-        const int x = x0 - CK + c * CK;
+        const int x = x0 - X0 + c * CK;
         const size_t row = (size_t)y * (size_t)nx;
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(NT) step2d_tile_kernel(StepArgs a) {
         // mu at (y0 - r + i, x0 - r + j), i < HMU, j < WMU
         for (int q = t; q < HMU * WMU; q += NT) {
             const int i = q / WMU, j = q - i * WMU;
-            const int ii = i + (R - r), jj = j + (CK - r);
+            const int ii = i + (R - r), jj = j + (X0 - r);
             auto P = [&](int dx, int dy, int) -> C { return phi(0, ii + dy, jj + dx); };
             s_mu[q] = ch_mu<C>(phi(0, ii, jj), stencil_sum<ST, C>(P), k);
         }
@@ -281,16 +281,130 @@ __global__ void __launch_bounds__(NT) step2d_tile_kernel(StepArgs a) {
         const size_t o = (size_t)y * (size_t)nx + x;
         if constexpr (MODEL == CH) {
             auto Pm = [&](int dx, int dy, int) -> C { return s_mu[(i + r + dy) * WMU + (j + r + dx)]; };
-            out[0][o] = from_c<T>(ch_update<C>(phi(0, i + R, j + CK), stencil_sum<ST, C>(Pm), k));
+            out[0][o] = from_c<T>(ch_update<C>(phi(0, i + R, j + X0), stencil_sum<ST, C>(Pm), k));
         } else {
-            auto P0 = [&](int dx, int dy, int) -> C { return phi(0, i + R + dy, j + CK + dx); };
+            auto P0 = [&](int dx, int dy, int) -> C { return phi(0, i + R + dy, j + X0 + dx); };
             const C S0 = stencil_sum<ST, C>(P0);
             if constexpr (MODEL == AC) {
-                out[0][o] = from_c<T>(ac_update<C>(phi(0, i + R, j + CK), S0, k));
+                out[0][o] = from_c<T>(ac_update<C>(phi(0, i + R, j + X0), S0, k));
             } else {
-                auto P1 = [&](int dx, int dy, int) -> C { return phi(NF - 1, i + R + dy, j + CK + dx); };
+                auto P1 = [&](int dx, int dy, int) -> C { return phi(NF - 1, i + R + dy, j + X0 + dx); };
                 C un, vn;
-                gs_update<C>(phi(0, i + R, j + CK), phi(NF - 1, i + R, j + CK), S0, stencil_sum<ST, C>(P1), k, un, vn);
+                gs_update<C>(phi(0, i + R, j + X0), phi(NF - 1, i + R, j + X0), S0, stencil_sum<ST, C>(P1), k,
+                             un, vn);
+                out[0][o] = from_c<T>(un);
+                out[NF - 1][o] = from_c<T>(vn);
+            }
+        }
+    }
+}
+
+template <int MODEL, int ST, typename T, int BX, int BY, int NT>
+__global__ void __launch_bounds__(NT) step2d_tile_kernel(StepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const ConstsC<typename Cmp<T>::type> k(a.k, a.kf);
+    tile2d<MODEL, ST, T, BX, BY, NT>(static_cast<const T *>(a.in0), static_cast<const T *>(a.in1),
+                                     static_cast<T *>(a.out0), static_cast<T *>(a.out1), a.nx, a.ny, k,
+                                     blockIdx.x * BX, blockIdx.y * BY, smem_raw);
+}
+
+// ============================================================== 3D, boxes ==
+//
+// 3D work unit of the batched serving kernel: one BX x BY x BZ box per CTA,
+// fetched with its R-wide halo in one shot (x padded to whole 16-byte chunks),
+// mu of Cahn-Hilliard on the box plus an r-wide shell, then the update.  Used
+// for the small 3D grids of the serving mix, where one box is a sizeable part
+// of a grid; large single grids use the plane-streaming kernels below.
+template <int MODEL, int ST, typename T, int BX, int BY, int BZ>
+struct Step3dBoxShape {
+    typedef typename Cmp<T>::type C;
+    static constexpr int r = StencilInfo<ST>::r;
+    static constexpr int R = (MODEL == CH) ? 2 * r : r;
+    static constexpr int CK = 16 / sizeof(T);
+    static constexpr int HC = (R + CK - 1) / CK;
+    static constexpr int NCK = BX / CK + 2 * HC;
+    static constexpr int SW = NCK * CK, X0 = HC * CK;
+    static constexpr int HIN = BY + 2 * R, DIN = BZ + 2 * R;
+    static constexpr int NF = (MODEL == GS) ? 2 : 1;
+    static constexpr int WMU = (MODEL == CH) ? BX + 2 * r : 0, HMU = (MODEL == CH) ? BY + 2 * r : 0,
+                         DMU = (MODEL == CH) ? BZ + 2 * r : 0;
+    static constexpr size_t bytes_in = sizeof(T) * (size_t)NF * DIN * HIN * SW;
+    static constexpr size_t smem_bytes = bytes_in + sizeof(C) * (size_t)WMU * HMU * DMU;
+};
+
+template <int MODEL, int ST, typename T, int BX, int BY, int BZ, int NT>
+__device__ __forceinline__ void box3d(const T *in0, const T *in1, T *out0, T *out1, int nx, int ny, int nz,
+                                      const ConstsC<typename Cmp<T>::type> &k, int x0, int y0, int z0,
+                                      unsigned char *smem_raw) {
+    typedef Step3dBoxShape<MODEL, ST, T, BX, BY, BZ> Sh;
+    typedef typename Sh::C C;
+    constexpr int r = Sh::r, R = Sh::R, CK = Sh::CK, NCK = Sh::NCK, SW = Sh::SW, X0 = Sh::X0;
+    constexpr int HIN = Sh::HIN, DIN = Sh::DIN, NF = Sh::NF, WMU = Sh::WMU, HMU = Sh::HMU, DMU = Sh::DMU;
+    T *s_in = reinterpret_cast<T *>(smem_raw);                   // [NF][DIN][HIN][SW]
+    C *s_mu = reinterpret_cast<C *>(smem_raw + Sh::bytes_in);    // [DMU][HMU][WMU]
+    const int t = threadIdx.x;
+    const bool vec_ok = (nx % CK) == 0;
+    const size_t plane = (size_t)nx * (size_t)ny;
+    const T *in[2] = {in0, in1};
+    T *out[2] = {out0, out1};
+
+    for (int q = t; q < DIN * HIN * NCK; q += NT) {
+        const int zi = q / (HIN * NCK), rem = q - zi * (HIN * NCK);
+        const int i = rem / NCK, c = rem - i * NCK;
+        const int z = wrap_idx(z0 - R + zi, nz), y = wrap_idx(y0 - R + i, ny);
+        const int x = x0 - X0 + c * CK;
+        const size_t row = (size_t)z * plane + (size_t)y * (size_t)nx;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            T *dst = s_in + (((size_t)f * DIN + zi) * HIN + i) * SW + c * CK;
+            if (vec_ok && x >= 0 && x + CK <= nx) {
+                cp_async16(dst, in[f] + row + x);
+            } else {
+#pragma unroll
+                for (int j = 0; j < CK; ++j) dst[j] = in[f][row + wrap_idx(x + j, nx)];
+            }
+        }
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+
+    auto phi = [&](int f, int zi, int i, int j) -> C {
+        return to_c(s_in[(((size_t)f * DIN + zi) * HIN + i) * SW + j]);
+    };
+    if constexpr (MODEL == CH) {
+        for (int q = t; q < DMU * HMU * WMU; q += NT) {
+            const int zm = q / (HMU * WMU), rem = q - zm * (HMU * WMU);
+            const int i = rem / WMU, j = rem - i * WMU;
+            const int zz = zm + (R - r), ii = i + (R - r), jj = j + (X0 - r);
+            auto P = [&](int dx, int dy, int dz) -> C { return phi(0, zz + dz, ii + dy, jj + dx); };
+            s_mu[q] = ch_mu<C>(phi(0, zz, ii, jj), stencil_sum<ST, C>(P), k);
+        }
+        __syncthreads();
+    }
+    for (int q = t; q < BZ * BY * BX; q += NT) {
+        const int zb = q / (BY * BX), rem = q - zb * (BY * BX);
+        const int i = rem / BX, j = rem - i * BX;
+        const int z = z0 + zb, y = y0 + i, x = x0 + j;
+        if (z >= nz || y >= ny || x >= nx) continue;
+        const size_t o = (size_t)z * plane + (size_t)y * (size_t)nx + x;
+        if constexpr (MODEL == CH) {
+            auto Pm = [&](int dx, int dy, int dz) -> C {
+                return s_mu[((zb + r + dz) * HMU + (i + r + dy)) * WMU + (j + r + dx)];
+            };
+            out[0][o] = from_c<T>(ch_update<C>(phi(0, zb + R, i + R, j + X0), stencil_sum<ST, C>(Pm), k));
+        } else {
+            auto P0 = [&](int dx, int dy, int dz) -> C { return phi(0, zb + R + dz, i + R + dy, j + X0 + dx); };
+            const C S0 = stencil_sum<ST, C>(P0);
+            if constexpr (MODEL == AC) {
+                out[0][o] = from_c<T>(ac_update<C>(phi(0, zb + R, i + R, j + X0), S0, k));
+            } else {
+                auto P1 = [&](int dx, int dy, int dz) -> C {
+                    return phi(NF - 1, zb + R + dz, i + R + dy, j + X0 + dx);
+                };
+                C un, vn;
+                gs_update<C>(phi(0, zb + R, i + R, j + X0), phi(NF - 1, zb + R, i + R, j + X0), S0,
+                             stencil_sum<ST, C>(P1), k, un, vn);
                 out[0][o] = from_c<T>(un);
                 out[NF - 1][o] = from_c<T>(vn);
             }

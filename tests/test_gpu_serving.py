@@ -1,0 +1,142 @@
+"""Continuous-batching server against single-grid runs and the FP64 oracle.
+
+A served grid runs the same tile arithmetic as a grid run alone, so its result
+must be identical bit for bit whatever else is resident; FP64 results also
+equal the oracle bit for bit.  Admission respects the HBM budget, a failed
+request does not disturb the others, and waits are bounded on the host.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sp():
+    import __graft_entry__
+
+    __graft_entry__._load_builder().build()
+    import paper_2511_10508_gb300 as sp
+
+    return sp
+
+
+def kw_for(model, seed):
+    if model == 2:
+        return dict(seed=seed, ic_amp=0.01, gs_patches=3, gs_patch=4)
+    return dict(seed=seed, ic_amp=0.3)
+
+
+# (model, shape, dtype, stencil, dt, nsteps)
+MIX = [
+    (1, (64, 64), 0, 0, 0.01, 37),
+    (0, (96, 130), 1, 0, 0.05, 55),
+    (2, (80, 72), 0, 0, 0.5, 23),
+    (1, (33, 45, 40), 1, 3, 0.002, 31),
+    (0, (20, 24, 36), 0, 4, 0.02, 64),
+    (2, (16, 18, 20), 1, 3, 0.25, 17),
+    (1, (130, 257), 1, 2, 0.002, 12),
+    (1, (24, 24, 24), 0, 5, 0.001, 9),
+    (0, (40, 520), 0, 1, 0.05, 80),
+]
+
+
+def alone(sp, model, shape, dtype, st, dt, n, seed):
+    with sp.Simulation(model, shape, dt=dt, stencil=st, dtype=dtype, **kw_for(model, seed)) as s:
+        s.step(n)
+        out = [s.read(f) for f in range(2 if model == 2 else 1)]
+        return np.stack(out), s.reduce(sp.MASS)
+
+
+def test_mix_equals_alone_and_oracle(sp):
+    with sp.Server(8 << 30, max_slots=16, quantum_steps=10) as srv:
+        tickets = []
+        for i, (m, shape, dt_, st, dt, n) in enumerate(MIX):
+            tickets.append(srv.submit(m, shape, dt=dt, nsteps=n, stencil=st, dtype=dt_, return_fields=True,
+                                      **kw_for(m, 100 + i)))
+        results = [srv.wait(t, timeout=300) for t in tickets]
+    for i, ((m, shape, dt_, st, dt, n), res) in enumerate(zip(MIX, results)):
+        assert res.status == 0 and res.steps_done == n
+        ref, mass = alone(sp, m, shape, dt_, st, dt, n, 100 + i)
+        assert np.array_equal(res.fields, ref), f"request {i} differs from its single-grid run"
+        assert abs(res.mass - mass) <= 1e-13 * (np.abs(ref[0]).sum() + 1)
+        if dt_ == 0:
+            k = kw_for(m, 100 + i)
+            if m == 2:
+                u, v = O.initial_condition(O.GS, shape, seed=k["seed"], amp=k["ic_amp"], patches=k["gs_patches"],
+                                           patch=k["gs_patch"])
+                ou, ov = O.step(O.GS, st, u, v, dt=dt, nsteps=n)
+                assert np.array_equal(res.fields[0], ou) and np.array_equal(res.fields[1], ov)
+            else:
+                u = O.initial_condition(m, shape, seed=k["seed"], amp=k["ic_amp"])
+                assert np.array_equal(res.fields[0], O.step(m, st, u, dt=dt, nsteps=n))
+
+
+def test_same_request_alone_and_in_mix(sp):
+    """One request served alone and the same request served among others."""
+    req = (1, (100, 140), 1, 0, 0.01, 45)
+    m, shape, dtype, st, dt, n = req
+    with sp.Server(4 << 30, quantum_steps=7) as srv:
+        t = srv.submit(m, shape, dt=dt, nsteps=n, stencil=st, dtype=dtype, return_fields=True, **kw_for(m, 5))
+        a = srv.wait(t)
+    with sp.Server(4 << 30, quantum_steps=7) as srv:
+        others = [srv.submit(mm, sh, dt=d, nsteps=nn, stencil=s2, dtype=dd, **kw_for(mm, 50 + j))
+                  for j, (mm, sh, dd, s2, d, nn) in enumerate(MIX[:5])]
+        t = srv.submit(m, shape, dt=dt, nsteps=n, stencil=st, dtype=dtype, return_fields=True, **kw_for(m, 5))
+        more = [srv.submit(mm, sh, dt=d, nsteps=nn, stencil=s2, dtype=dd, **kw_for(mm, 70 + j))
+                for j, (mm, sh, dd, s2, d, nn) in enumerate(MIX[5:])]
+        b = srv.wait(t)
+        for x in others + more:
+            srv.wait(x)
+    assert np.array_equal(a.fields, b.fields) and a.mass == b.mass
+
+
+def test_budget_admission_and_continuous_batching(sp):
+    """With room for two grids at a time, later requests are admitted only after
+    earlier ones finish and free their memory; all results stay correct."""
+    shape = (256, 256)
+    per = 2 * 256 * 256 * 8  # one FP64 Cahn-Hilliard grid: two levels
+    with sp.Server(2 * per, max_slots=8, quantum_steps=20) as srv:
+        with pytest.raises(sp.SpError):
+            srv.submit(1, (1024, 1024), dt=0.01, nsteps=10)  # larger than the whole budget
+        ts = [srv.submit(1, shape, dt=0.01, nsteps=40 + 20 * i, seed=i, ic_amp=0.2, return_fields=True)
+              for i in range(5)]
+        res = [srv.wait(t) for t in ts]
+        st = srv.stats()
+    assert st["finished"] == 5 and st["failed"] == 0 and st["hbm_in_use"] == 0
+    finishes = sorted(r.t_finish for r in res)
+    admits = sorted(r.t_admit for r in res)
+    # the third admission cannot precede the first completion (only two fit)
+    assert admits[2] >= finishes[0] - 1e-6
+    for i, r in enumerate(res):
+        u = O.initial_condition(O.CH, shape, seed=i, amp=0.2)
+        assert np.array_equal(r.fields[0], O.step(O.CH, O.S1, u, dt=0.01, nsteps=40 + 20 * i))
+
+
+def test_failed_request_does_not_disturb_others(sp):
+    with sp.Server(4 << 30, quantum_steps=10) as srv:
+        good = [srv.submit(0, (64, 96), dt=0.05, nsteps=30, seed=s, ic_amp=0.2, return_fields=True)
+                for s in range(3)]
+        bad = srv.submit(0, (64, 96), dt=0.05, nsteps=30, seed=9, fault=1)
+        with pytest.raises(sp.SpError) as e:
+            srv.wait(bad)
+        assert e.value.code == 3  # SP_ENOMEM, injected on the host
+        for s, t in enumerate(good):
+            r = srv.wait(t)
+            u = O.initial_condition(O.AC, (64, 96), seed=s, amp=0.2)
+            assert np.array_equal(r.fields[0], O.step(O.AC, O.S1, u, dt=0.05, nsteps=30))
+        assert srv.stats()["failed"] == 1
+
+
+def test_bounded_wait_and_poll(sp):
+    with sp.Server(4 << 30, quantum_steps=50) as srv:
+        t = srv.submit(1, (512, 512), dt=0.01, nsteps=3000)
+        status, res = srv.poll(t)
+        assert status == 8 and res is None  # SP_PENDING
+        with pytest.raises(TimeoutError):
+            srv.wait(t, timeout=0.0)
+        r = srv.wait(t, timeout=600)
+        assert r.steps_done == 3000 and r.t_admit >= r.t_submit and r.t_finish > r.t_admit
+        srv.release(t)
