@@ -155,7 +155,11 @@ struct sp_sim {
     size_t stage_elems;
     StepConsts k;
     int device, n_sm;
+    cudaGraphExec_t graph[2];  // kGraphSteps steps starting from level 0 / level 1
 };
+
+// Steps per captured graph; even, so a replay returns to the level it started from.
+constexpr int kGraphSteps = 32;
 
 static size_t dtype_size(int dt) { return dt == SP_F64 ? 8 : (dt == SP_F32 ? 4 : 2); }
 
@@ -183,6 +187,8 @@ static void release(sp_sim *s) {
             if (s->f[l][f]) cudaFree(s->f[l][f]);
     if (s->d_partials) cudaFree(s->d_partials);
     if (s->d_stage) cudaFree(s->d_stage);
+    for (int l = 0; l < 2; ++l)
+        if (s->graph[l]) cudaGraphExecDestroy(s->graph[l]);
     if (s->h_out) cudaFreeHost(s->h_out);
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
@@ -288,14 +294,44 @@ static cudaError_t launch_one_step(sp_sim *s, cudaStream_t st) {
     }
 }
 
+// Capture kGraphSteps steps starting from the current level into s->graph[s->cur].
+static cudaError_t capture_graph(sp_sim *s) {
+    const int start = s->cur;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i) {
+        e = launch_one_step(s, s->stream);
+        s->cur ^= 1;
+    }
+    s->cur = start;
+    const cudaError_t e2 = cudaStreamEndCapture(s->stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&s->graph[start], g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
+
+// Steps are issued as replays of a captured kGraphSteps-step graph (one per
+// starting level) plus eager launches for the remainder.  The first step of a
+// handle is always eager, so that the kernels' one-time set-up never runs
+// inside a capture.
 extern "C" int sp_step(sp_sim *s, int64_t nsteps, void *stream) {
     if (!s) return fail(SP_EINVAL, "sim is NULL");
     if (nsteps < 0) return fail(SP_EINVAL, "nsteps must be >= 0");
     const cudaStream_t st = pick(s, stream);
-    for (int64_t i = 0; i < nsteps; ++i) {
-        SP_CUDA(launch_one_step(s, st));
-        s->cur ^= 1;
-        s->steps += 1;
+    while (nsteps > 0) {
+        if (nsteps >= kGraphSteps && s->steps > 0) {
+            if (!s->graph[s->cur]) SP_CUDA(capture_graph(s));
+            SP_CUDA(cudaGraphLaunch(s->graph[s->cur], st));
+            s->steps += kGraphSteps;
+            nsteps -= kGraphSteps;
+        } else {
+            SP_CUDA(launch_one_step(s, st));
+            s->cur ^= 1;
+            s->steps += 1;
+            nsteps -= 1;
+        }
     }
     return SP_OK;
 }

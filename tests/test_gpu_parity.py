@@ -278,3 +278,19 @@ def test_reduction_of_unaligned_field_pointer(sp):
         assert rc == N.SP_OK
         ref = O.kahan_sum(u.ravel()[1:])
         assert abs(out.value - ref) <= 1e-13 * np.abs(u).sum()
+
+
+@pytest.mark.parametrize("model,shape,dtype", [(1, (70, 301), 0), (2, (40, 33, 65), 1), (0, (64, 64), 0)])
+def test_graph_replay_equals_eager(sp, model, shape, dtype):
+    """sp_step issues long runs as replays of a captured multi-step graph; the
+    result equals stepping one launch at a time, bit for bit."""
+    st = 0 if len(shape) == 2 else 3
+    a, dt = make(sp, model, shape, st, dtype=dtype)
+    b, _ = make(sp, model, shape, st, dtype=dtype)
+    with a, b:
+        a.step(133)
+        for _ in range(133):
+            b.step(1)
+        for f in range(2 if model == 2 else 1):
+            assert np.array_equal(a.read(f), b.read(f))
+        assert a.steps_taken == b.steps_taken == 133
