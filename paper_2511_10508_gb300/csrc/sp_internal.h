@@ -20,10 +20,26 @@ struct ReduceGeom {
 };
 
 // Step launchers, one per storage type (sp_step_f64.cu, sp_step_f32.cu,
-// sp_step_bf16.cu).  One forward-Euler step from a.in* to a.out*.
-cudaError_t launch_step_f64(int model, int stencil, const StepArgs &a, cudaStream_t s, int n_sm);
-cudaError_t launch_step_f32(int model, int stencil, const StepArgs &a, cudaStream_t s, int n_sm);
-cudaError_t launch_step_bf16(int model, int stencil, const StepArgs &a, cudaStream_t s, int n_sm);
+// sp_step_bf16.cu).  k forward-Euler steps from a.in* to a.out* in one launch;
+// k must be 1, or the value of steps_per_launch() for this model/stencil/dtype.
+cudaError_t launch_step_f64(int model, int stencil, const StepArgs &a, cudaStream_t s, int n_sm, int k);
+cudaError_t launch_step_f32(int model, int stencil, const StepArgs &a, cudaStream_t s, int n_sm, int k);
+cudaError_t launch_step_bf16(int model, int stencil, const StepArgs &a, cudaStream_t s, int n_sm, int k);
+
+// Steps fused per launch (temporal blocking) for a request of `requested`
+// (0 = the library's choice, 1 = none): 2D FP32 / BF16 grids support 2 and 4;
+// FP64 (bound by the FP64 pipe) and 3D run one step per launch.  The library's
+// choice follows measurement on GB300: blocking pays where the one-step tile
+// kernel is at the HBM bound (FP32 Gray-Scott 32768^2: 1 step 0.99 of the copy
+// bandwidth, 2 steps 1.31 effective, 4 steps 1.19); Cahn-Hilliard and BF16
+// storage are limited by on-chip work, so extra halo work only slows them.
+inline int steps_per_launch(int dims, int dtype, int model, int requested) {
+    if (dims != 2 || dtype == SP_F64) return 1;
+    if (requested == 0) return (dtype == SP_F32 && model != CH) ? 2 : 1;
+    if (requested >= 4) return 4;
+    if (requested >= 2) return 2;
+    return 1;
+}
 
 cudaError_t launch_ic(int dtype, void *u, void *v, int model, int dims, int nx, int ny, int nz,
                       uint64_t seed, int ic_kind, double mean, double amp, int patches, int patch,

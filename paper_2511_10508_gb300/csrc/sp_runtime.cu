@@ -156,9 +156,11 @@ struct sp_sim {
     StepConsts k;
     int device, n_sm;
     cudaGraphExec_t graph[2];  // kGraphSteps steps starting from level 0 / level 1
+    int spl;                   // steps fused per launch (temporal blocking)
 };
 
-// Steps per captured graph; even, so a replay returns to the level it started from.
+// Steps per captured graph.  A graph holds kGraphSteps / spl launches, an even
+// number for spl in {1, 2, 4}, so a replay returns to the level it started from.
 constexpr int kGraphSteps = 32;
 
 static size_t dtype_size(int dt) { return dt == SP_F64 ? 8 : (dt == SP_F32 ? 4 : 2); }
@@ -236,6 +238,7 @@ extern "C" int sp_create(int model, int dims, const int64_t shape[3], double h, 
     s->p.stencil = st;
     s->esize = dtype_size(prm.dtype);
     s->k = make_consts(*s);
+    s->spl = steps_per_launch(dims, prm.dtype, model, prm.steps_per_launch);
 
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, s->device);
@@ -275,7 +278,7 @@ extern "C" int sp_create(int model, int dims, const int64_t shape[3], double h, 
 
 static cudaStream_t pick(sp_sim *s, void *stream) { return stream ? (cudaStream_t)stream : s->stream; }
 
-static cudaError_t launch_one_step(sp_sim *s, cudaStream_t st) {
+static cudaError_t launch_one_step(sp_sim *s, cudaStream_t st, int k = 1) {
     StepArgs a;
     a.in0 = s->f[s->cur][0];
     a.in1 = s->nf > 1 ? s->f[s->cur][1] : s->f[s->cur][0];
@@ -288,9 +291,9 @@ static cudaError_t launch_one_step(sp_sim *s, cudaStream_t st) {
     a.kf = {(float)s->k.c1, (float)s->k.c2, (float)s->k.sAC, (float)s->k.kq, (float)s->k.dq,
             (float)s->k.duq, (float)s->k.dvq, (float)s->k.F, (float)s->k.Fk, (float)s->k.dt};
     switch (s->dtype) {
-    case SP_F64: return launch_step_f64(s->model, s->stencil, a, st, s->n_sm);
-    case SP_F32: return launch_step_f32(s->model, s->stencil, a, st, s->n_sm);
-    default: return launch_step_bf16(s->model, s->stencil, a, st, s->n_sm);
+    case SP_F64: return launch_step_f64(s->model, s->stencil, a, st, s->n_sm, k);
+    case SP_F32: return launch_step_f32(s->model, s->stencil, a, st, s->n_sm, k);
+    default: return launch_step_bf16(s->model, s->stencil, a, st, s->n_sm, k);
     }
 }
 
@@ -300,8 +303,9 @@ static cudaError_t capture_graph(sp_sim *s) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i) {
-        e = launch_one_step(s, s->stream);
+    // one launch (of spl steps) reads the current level and writes the other one
+    for (int i = 0; i < kGraphSteps && e == cudaSuccess; i += s->spl) {
+        e = launch_one_step(s, s->stream, s->spl);
         s->cur ^= 1;
     }
     s->cur = start;
@@ -321,11 +325,16 @@ extern "C" int sp_step(sp_sim *s, int64_t nsteps, void *stream) {
     if (nsteps < 0) return fail(SP_EINVAL, "nsteps must be >= 0");
     const cudaStream_t st = pick(s, stream);
     while (nsteps > 0) {
-        if (nsteps >= kGraphSteps && s->steps > 0) {
+        if (nsteps >= kGraphSteps && s->steps >= s->spl + 1) {
             if (!s->graph[s->cur]) SP_CUDA(capture_graph(s));
             SP_CUDA(cudaGraphLaunch(s->graph[s->cur], st));
             s->steps += kGraphSteps;
             nsteps -= kGraphSteps;
+        } else if (nsteps >= s->spl && s->spl > 1 && s->steps > 0) {
+            SP_CUDA(launch_one_step(s, st, s->spl));
+            s->cur ^= 1;  // one launch swaps the levels, however many steps it fuses
+            s->steps += s->spl;
+            nsteps -= s->spl;
         } else {
             SP_CUDA(launch_one_step(s, st));
             s->cur ^= 1;

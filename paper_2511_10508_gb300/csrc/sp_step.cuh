@@ -308,6 +308,128 @@ __global__ void __launch_bounds__(NT) step2d_tile_kernel(StepArgs a) {
                                      blockIdx.x * BX, blockIdx.y * BY, smem_raw);
 }
 
+// ================================================== 2D, temporal blocking ==
+//
+// K time steps per launch on one BX x BY tile (FP32 / BF16 storage): the tile
+// plus a K*R halo is fetched once (cp.async, rows padded to whole 16-byte
+// chunks), then step s = 0 .. K-1 updates the tile grown by the margin
+// m_s = R*(K-1-s) from one shared-memory buffer into the other; each step's
+// region is one halo width smaller than the region it reads, so every value it
+// uses was produced by the previous step (or loaded).  Intermediate values are
+// kept in the storage type, rounded exactly as a global store would round
+// them, so K blocked steps equal K single steps bit for bit.  Only the last
+// step writes to global memory: HBM traffic per point is one read and one
+// write per K steps.
+template <int MODEL, int ST, typename T, int BX, int BY, int K>
+struct Step2dTbShape {
+    typedef typename Cmp<T>::type C;
+    static constexpr int r = StencilInfo<ST>::r;
+    static constexpr int R = (MODEL == CH) ? 2 * r : r;
+    static constexpr int KR = K * R;                    // loaded halo
+    static constexpr int CK = 16 / sizeof(T);
+    static constexpr int HC = (KR + CK - 1) / CK;
+    static constexpr int NCK = BX / CK + 2 * HC;
+    static constexpr int SW = NCK * CK, X0 = HC * CK;
+    static constexpr int HIN = BY + 2 * KR;
+    static constexpr int NF = (MODEL == GS) ? 2 : 1;
+    static constexpr int MMU = R * (K - 1) + r;         // widest mu margin
+    static constexpr int WMU = (MODEL == CH) ? BX + 2 * MMU : 0, HMU = (MODEL == CH) ? BY + 2 * MMU : 0;
+    static constexpr size_t buf_elems = (size_t)HIN * SW;
+    static constexpr size_t bytes_in = sizeof(T) * (size_t)2 * NF * buf_elems;  // two levels per field
+    static constexpr size_t smem_bytes = bytes_in + sizeof(C) * (size_t)WMU * HMU;
+};
+
+template <int MODEL, int ST, typename T, int BX, int BY, int K, int NT>
+__global__ void __launch_bounds__(NT) step2d_tb_kernel(StepArgs a) {
+    typedef Step2dTbShape<MODEL, ST, T, BX, BY, K> Sh;
+    typedef typename Sh::C C;
+    constexpr int r = Sh::r, R = Sh::R, KR = Sh::KR, CK = Sh::CK, NCK = Sh::NCK, SW = Sh::SW, X0 = Sh::X0;
+    constexpr int HIN = Sh::HIN, NF = Sh::NF, WMU = Sh::WMU;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *buf = reinterpret_cast<T *>(smem_raw);                  // [2 levels][NF][HIN][SW]
+    C *s_mu = reinterpret_cast<C *>(smem_raw + Sh::bytes_in);  // [HMU][WMU]
+    const ConstsC<C> k(a.k, a.kf);
+    const int nx = a.nx, ny = a.ny;
+    const int t = threadIdx.x;
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    const bool vec_ok = (nx % CK) == 0;
+    const T *in[2] = {static_cast<const T *>(a.in0), static_cast<const T *>(a.in1)};
+    T *out[2] = {static_cast<T *>(a.out0), static_cast<T *>(a.out1)};
+    // element (i, j) of the tile frame (i in [-KR, BY+KR), j in [-X0, BX+X0)) of field f, level l
+    auto at = [&](int l, int f, int i, int j) -> T & {
+        return buf[((size_t)(l * NF + f) * HIN + (i + KR)) * SW + (j + X0)];
+    };
+
+    for (int q = t; q < HIN * NCK; q += NT) {
+        const int i = q / NCK, c = q - i * NCK;
+        const int y = wrap_idx(y0 - KR + i, ny);
+        const int x = x0 - X0 + c * CK;
+        const size_t row = (size_t)y * (size_t)nx;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            T *dst = buf + ((size_t)f * HIN + i) * SW + c * CK;
+            if (vec_ok && x >= 0 && x + CK <= nx) {
+                cp_async16(dst, in[f] + row + x);
+            } else {
+#pragma unroll
+                for (int j = 0; j < CK; ++j) dst[j] = in[f][row + wrap_idx(x + j, nx)];
+            }
+        }
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+        const int src = s & 1, dst = src ^ 1;
+        const int m = R * (K - 1 - s);  // margin of this step's output region
+        if constexpr (MODEL == CH) {
+            // mu on the region grown by m + r
+            const int mm = m + r, W = BX + 2 * mm, H = BY + 2 * mm;
+            for (int q = t; q < H * W; q += NT) {
+                const int i = q / W - mm, j = q % W - mm;
+                auto P = [&](int dx, int dy, int) -> C { return to_c(at(src, 0, i + dy, j + dx)); };
+                s_mu[(i + Sh::MMU) * WMU + (j + Sh::MMU)] = ch_mu<C>(to_c(at(src, 0, i, j)), stencil_sum<ST, C>(P), k);
+            }
+            __syncthreads();
+        }
+        const int W = BX + 2 * m, H = BY + 2 * m;
+        for (int q = t; q < H * W; q += NT) {
+            const int i = q / W - m, j = q % W - m;
+            C o0, o1 = C(0);
+            if constexpr (MODEL == CH) {
+                auto Pm = [&](int dx, int dy, int) -> C {
+                    return s_mu[(i + dy + Sh::MMU) * WMU + (j + dx + Sh::MMU)];
+                };
+                o0 = ch_update<C>(to_c(at(src, 0, i, j)), stencil_sum<ST, C>(Pm), k);
+            } else {
+                auto P0 = [&](int dx, int dy, int) -> C { return to_c(at(src, 0, i + dy, j + dx)); };
+                const C S0 = stencil_sum<ST, C>(P0);
+                if constexpr (MODEL == AC) {
+                    o0 = ac_update<C>(to_c(at(src, 0, i, j)), S0, k);
+                } else {
+                    auto P1 = [&](int dx, int dy, int) -> C { return to_c(at(src, NF - 1, i + dy, j + dx)); };
+                    gs_update<C>(to_c(at(src, 0, i, j)), to_c(at(src, NF - 1, i, j)), S0, stencil_sum<ST, C>(P1), k,
+                                 o0, o1);
+                }
+            }
+            if (s + 1 < K) {
+                at(dst, 0, i, j) = from_c<T>(o0);
+                if constexpr (MODEL == GS) at(dst, 1, i, j) = from_c<T>(o1);
+            } else {
+                const int y = y0 + i, x = x0 + j;
+                if (y < ny && x < nx) {
+                    const size_t o = (size_t)y * (size_t)nx + x;
+                    out[0][o] = from_c<T>(o0);
+                    if constexpr (MODEL == GS) out[1][o] = from_c<T>(o1);
+                }
+            }
+        }
+        if (s + 1 < K) __syncthreads();
+    }
+}
+
 // ============================================================== 3D, boxes ==
 //
 // 3D work unit of the batched serving kernel: one BX x BY x BZ box per CTA,

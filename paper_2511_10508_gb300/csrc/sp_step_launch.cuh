@@ -40,8 +40,28 @@ inline long long persistent_ctas(long long total_slices, int ctas_per_sm, int n_
 // Batched persistent 2D kernel (FP64): rows per batch and CTAs per SM.
 template <int MODEL> struct Batch2d { static constexpr int NT = 128, RB = (MODEL == CH) ? 8 : (MODEL == AC ? 4 : 2), CPS = 4; };
 
+// Temporally blocked 2D tile kernel (FP32 / BF16): K steps per launch.
+template <int MODEL, int ST, typename T, int K>
+cudaError_t launch_tb(const StepArgs &a, cudaStream_t s) {
+    constexpr int BX = 128, BY = 16, NT = 256;
+    typedef Step2dTbShape<MODEL, ST, T, BX, BY, K> Sh;
+    auto kern = step2d_tb_kernel<MODEL, ST, T, BX, BY, K, NT>;
+    static const bool attr = [&] {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem_bytes);
+        return true;
+    }();
+    (void)attr;
+    dim3 grid((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY);
+    kern<<<grid, NT, Sh::smem_bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int MODEL, int ST, typename T>
-cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm) {
+cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
+    if constexpr (StencilInfo<ST>::dims == 2 && !std::is_same<T, double>::value) {
+        if (k == 4) return launch_tb<MODEL, ST, T, 4>(a, s);
+        if (k == 2) return launch_tb<MODEL, ST, T, 2>(a, s);
+    }
     if constexpr (StencilInfo<ST>::dims == 2 && std::is_same<T, double>::value) {
         typedef Batch2d<MODEL> B;
         typedef Step2dBatchShape<MODEL, ST, T, B::NT, B::RB> Sh;
@@ -108,15 +128,15 @@ cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm) {
 }
 
 template <typename T>
-cudaError_t launch_step_dispatch(int model, int stencil, const StepArgs &a, cudaStream_t s, int n_sm) {
+cudaError_t launch_step_dispatch(int model, int stencil, const StepArgs &a, cudaStream_t s, int n_sm, int k) {
 #define SP_STENCILS(M)                                                   \
     switch (stencil) {                                                   \
-    case L5: return launch_step_t<M, L5, T>(a, s, n_sm);                 \
-    case L9BOX: return launch_step_t<M, L9BOX, T>(a, s, n_sm);           \
-    case L9X4: return launch_step_t<M, L9X4, T>(a, s, n_sm);             \
-    case L7: return launch_step_t<M, L7, T>(a, s, n_sm);                 \
-    case L27: return launch_step_t<M, L27, T>(a, s, n_sm);               \
-    case L13X4: return launch_step_t<M, L13X4, T>(a, s, n_sm);           \
+    case L5: return launch_step_t<M, L5, T>(a, s, n_sm, k);              \
+    case L9BOX: return launch_step_t<M, L9BOX, T>(a, s, n_sm, k);        \
+    case L9X4: return launch_step_t<M, L9X4, T>(a, s, n_sm, k);          \
+    case L7: return launch_step_t<M, L7, T>(a, s, n_sm, k);              \
+    case L27: return launch_step_t<M, L27, T>(a, s, n_sm, k);            \
+    case L13X4: return launch_step_t<M, L13X4, T>(a, s, n_sm, k);        \
     }                                                                    \
     break;
     switch (model) {

@@ -294,3 +294,21 @@ def test_graph_replay_equals_eager(sp, model, shape, dtype):
         for f in range(2 if model == 2 else 1):
             assert np.array_equal(a.read(f), b.read(f))
         assert a.steps_taken == b.steps_taken == 133
+
+
+@pytest.mark.parametrize("dtype", [1, 2])
+@pytest.mark.parametrize("model,st", [(m, s) for m in (0, 1, 2) for s in (0, 1, 2)])
+def test_temporal_blocking_equals_single_steps(sp, dtype, model, st):
+    """K steps fused in one launch (intermediate values rounded to the storage type
+    in shared memory) equal K single-step launches bit for bit."""
+    shape = (70, 301)
+    outs = []
+    for spl in (1, 2, 4):
+        sim, dt = make(sp, model, shape, st, dtype=dtype, steps_per_launch=spl)
+        with sim:
+            sim.step(1)       # first step of a handle is a single-step launch
+            sim.step(12)      # blocked launches (and single steps for the rest)
+            outs.append([sim.read(f, as_f64=False) for f in range(2 if model == 2 else 1)])
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(a, b)
