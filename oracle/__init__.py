@@ -66,6 +66,8 @@ def lib():
             L.or_u01.restype = dbl
             L.or_u01.argtypes = [u64, u64]
             L.or_initial_condition.argtypes = [c_int, c_int, i64, i64, i64, u64, dbl, dbl, i64, i64, ptr, ptr]
+            L.or_initial_condition_window.argtypes = [c_int, c_int, i64, i64, i64, u64, dbl, dbl, i64, i64,
+                                                      i64, i64, i64, i64, i64, i64, ptr, ptr]
             L.or_sum.restype = dbl
             L.or_sum.argtypes = [ptr, i64]
             L.or_mass.restype = dbl
@@ -169,6 +171,24 @@ def initial_condition(model: int, shape, *, seed: int, mean: float = 0.0, amp: f
                                     _p(u), None if v is None else _p(v))
     if rc:
         raise ValueError("or_initial_condition: bad arguments")
+    return u if model != GS else (u, v)
+
+
+def initial_condition_window(model: int, shape, origin, wshape, *, seed: int, mean: float = 0.0,
+                             amp: float = 0.01, patches: int = 0, patch: int = 0):
+    """Initial condition of the full grid ``shape`` evaluated on the periodic window
+    with lower corner ``origin`` and size ``wshape`` (all numpy order)."""
+    dims = len(shape)
+    full = list(shape[::-1]) + [1] * (3 - dims)
+    org = list(origin[::-1]) + [0] * (3 - dims)
+    win = list(wshape[::-1]) + [1] * (3 - dims)
+    u = np.empty(wshape, dtype=np.float64)
+    v = np.empty(wshape, dtype=np.float64) if model == GS else None
+    rc = lib().or_initial_condition_window(model, dims, full[0], full[1], full[2], seed, mean, amp, patches, patch,
+                                           org[0], org[1], org[2], win[0], win[1], win[2], _p(u),
+                                           None if v is None else _p(v))
+    if rc:
+        raise ValueError("or_initial_condition_window: bad arguments")
     return u if model != GS else (u, v)
 
 

@@ -368,6 +368,62 @@ int or_initial_condition(int model, int dims, int64_t nx, int64_t ny, int64_t nz
     return 0;
 }
 
+/*
+ * The same initial condition evaluated only on a window of the full grid:
+ * out[(k*wy + j)*wx + i] is the value at global point ((x0+i) mod nx,
+ * (y0+j) mod ny, (z0+k) mod nz) of or_initial_condition on the nx x ny x nz
+ * grid.  Lets tests check sampled windows of grids too large to generate whole.
+ */
+int or_initial_condition_window(int model, int dims, int64_t nx, int64_t ny, int64_t nz, uint64_t seed,
+                                double mean, double amp, int64_t patches, int64_t patch,
+                                int64_t x0, int64_t y0, int64_t z0, int64_t wx, int64_t wy, int64_t wz,
+                                double *u, double *v) {
+    if (nx < 1 || ny < 1 || nz < 1 || (dims == 2 && nz != 1) || (dims != 2 && dims != 3)) return -1;
+    if (wx < 1 || wy < 1 || wz < 1) return -1;
+    const int64_t N = nx * ny * nz;
+    int64_t *lo = NULL;
+    if (model == OR_GS) {
+        if (!v || patches < 0 || patch < 0 || patch > nx || patch > ny || (dims == 3 && patch > nz)) return -1;
+        lo = (int64_t *)malloc(sizeof(int64_t) * 3 * (size_t)(patches > 0 ? patches : 1));
+        if (!lo) return -1;
+        const int64_t nn[3] = {nx, ny, nz};
+        for (int64_t p = 0; p < patches; p++)
+            for (int a = 0; a < 3; a++) {
+                int64_t c = (int64_t)(or_splitmix64_nth(seed, (uint64_t)(2 * N + 3 * p + a)) % (uint64_t)nn[a]);
+                int64_t l = (c - patch / 2) % nn[a];
+                if (l < 0) l += nn[a];
+                lo[3 * p + a] = l;
+            }
+    } else if (model != OR_AC && model != OR_CH) {
+        return -1;
+    }
+    for (int64_t k = 0; k < wz; k++)
+        for (int64_t j = 0; j < wy; j++)
+            for (int64_t i = 0; i < wx; i++) {
+                int64_t x = (x0 + i) % nx; if (x < 0) x += nx;
+                int64_t y = (y0 + j) % ny; if (y < 0) y += ny;
+                int64_t z = (z0 + k) % nz; if (z < 0) z += nz;
+                const int64_t g = (z * ny + y) * nx + x;
+                const int64_t o = (k * wy + j) * wx + i;
+                if (model != OR_GS) {
+                    u[o] = mean + amp * (2.0 * or_u01(seed, (uint64_t)g) - 1.0);
+                    continue;
+                }
+                double bu = 1.0, bv = 0.0;
+                for (int64_t p = 0; p < patches; p++) {
+                    int64_t ox = (x - lo[3 * p + 0]) % nx; if (ox < 0) ox += nx;
+                    int64_t oy = (y - lo[3 * p + 1]) % ny; if (oy < 0) oy += ny;
+                    int64_t oz = 0;
+                    if (dims == 3) { oz = (z - lo[3 * p + 2]) % nz; if (oz < 0) oz += nz; }
+                    if (ox < patch && oy < patch && oz < (dims == 3 ? patch : 1)) { bu = 0.5; bv = 0.25; }
+                }
+                u[o] = bu + amp * (2.0 * or_u01(seed, (uint64_t)g) - 1.0);
+                v[o] = bv + amp * (2.0 * or_u01(seed, (uint64_t)(N + g)) - 1.0);
+            }
+    free(lo);
+    return 0;
+}
+
 /* -------------------------------------------------------- reductions ---- */
 
 /* Neumaier-compensated sum, sequential in index order. */

@@ -130,7 +130,11 @@ class Simulation:
         return s.value
 
     def field_tensor(self, field: int = 0):
-        """Zero-copy torch view of the current level (valid until the next step)."""
+        """Zero-copy torch view of the current level (valid until the next step).
+
+        The view is read on torch's stream; steps enqueued on another stream (the
+        simulation's own one when ``stream`` was None) must have completed first,
+        e.g. after ``torch.cuda.synchronize()``."""
         import torch
 
         tdt = {F64: torch.float64, F32: torch.float32, BF16_F32: torch.bfloat16}[self.dtype]

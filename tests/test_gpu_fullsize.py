@@ -1,0 +1,191 @@
+"""Parity at the benchmark configurations' full sizes, in the launch configuration
+that bench.py times (library defaults: persistent kernels, graph replay, FP32
+Gray-Scott with two steps per launch).
+
+Where the oracle finishes in seconds to about a minute the whole run is compared
+(256^2 Allen-Cahn x 1000 steps, 4096^2 Cahn-Hilliard x 10000 steps, 2048^2
+Gray-Scott x 5000 steps, 128^3 Cahn-Hilliard x 2000 steps).  On the largest grids
+(32768^2, 1024^3) sampled outputs are checked: after n steps a point depends only
+on the points within n*R (R = r, or 2r for Cahn-Hilliard), so the oracle runs the
+same n steps on a periodic window of half-width (n+1)*R around each sample, built
+from its own initial condition of the full grid, and the window centres must
+match.  FP64 is compared bit for bit; FP32 / BF16 storage against the FP64 oracle
+with the bounds stated per test.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sp():
+    import __graft_entry__
+
+    __graft_entry__._load_builder().build()
+    import paper_2511_10508_gb300 as sp
+
+    return sp
+
+
+def gpu_window(sim, field, origin, wshape):
+    """FP64 copy of a periodic window of the resident field (gathered on device)."""
+    import torch
+
+    torch.cuda.synchronize()  # the steps run on the library's stream, the view is read on torch's
+    t = sim.field_tensor(field)
+    idx = [torch.as_tensor((np.arange(w) + o) % n, device=t.device) for w, o, n in zip(wshape, origin, sim.shape)]
+    if len(idx) == 2:
+        sub = t[idx[0][:, None], idx[1][None, :]]
+    else:
+        sub = t[idx[0][:, None, None], idx[1][None, :, None], idx[2][None, None, :]]
+    return sub.to(torch.float64).cpu().numpy()
+
+
+def sample_points(shape, count, seed, extra=()):
+    rng = np.random.default_rng(seed)
+    pts = [tuple(int(rng.integers(0, n)) for n in shape) for _ in range(count)]
+    pts += [tuple(p) for p in extra]
+    # the corners of the grid exercise the periodic wrap
+    pts.append(tuple(0 for _ in shape))
+    pts.append(tuple(n - 1 for n in shape))
+    return pts
+
+
+def check_windows(sim, model, st, shape, dt, n, ic_kw, prm, points, exact, atol=0.0):
+    R = (2 if model == O.CH else 1) * O.STENCIL_RADIUS[st]
+    w = (n + 1) * R
+    wshape = (2 * w + 1,) * len(shape)
+    worst = 0.0
+    for pt in points:
+        origin = tuple(c - w for c in pt)
+        ic = O.initial_condition_window(model, shape, origin, wshape, **ic_kw)
+        ctr = (w,) * len(shape)
+        if model == O.GS:
+            ref = O.step(O.GS, st, ic[0], ic[1], dt=dt, prm=prm, nsteps=n)
+            got = [gpu_window(sim, f, pt, (1,) * len(shape)).ravel()[0] for f in (0, 1)]
+            want = [ref[0][ctr], ref[1][ctr]]
+        else:
+            ref = O.step(model, st, ic, dt=dt, prm=prm, nsteps=n)
+            got = [gpu_window(sim, 0, pt, (1,) * len(shape)).ravel()[0]]
+            want = [ref[ctr]]
+        for g, wv in zip(got, want):
+            if exact:
+                assert g == wv, (pt, g, wv)
+            worst = max(worst, abs(g - wv))
+    if not exact:
+        assert worst <= atol, worst
+    return worst
+
+
+# ---------------------------------------------------------------- 2D ----
+
+
+def test_allen_cahn_256_full_run(sp):
+    """256^2 Allen-Cahn, FP64, h = 1, dt = 0.05, 1000 steps, noise +-0.1: bitwise."""
+    shape, dt = (256, 256), 0.05
+    ic = O.initial_condition(O.AC, shape, seed=0, amp=0.1)
+    ref = O.step(O.AC, O.S1, ic, dt=dt, nsteps=1000)
+    with sp.Simulation(sp.ALLEN_CAHN, shape, dt=dt, seed=0, ic_amp=0.1) as s:
+        s.step(1000)
+        assert np.array_equal(s.read(0), ref)
+    with sp.Simulation(sp.ALLEN_CAHN, shape, dt=dt, seed=0, ic_amp=0.1, dtype=sp.F32) as s:
+        s.step(1000)
+        e = O.rel_l2(s.read(0), ref)
+    assert e < 1e-5, e  # FP32 storage: measured ~1e-7
+
+
+def test_cahn_hilliard_4096_lap5_full_run(sp):
+    """4096^2 Cahn-Hilliard, FP64, 5-point, dt = 0.01, 10000 steps from +-0.01 noise:
+    bitwise equal to the oracle (hence rel-L2 0 <= 1e-12); mass drift stated."""
+    shape, dt, n = (4096, 4096), 0.01, 10000
+    ic = O.initial_condition(O.CH, shape, seed=1, amp=0.01)
+    ref = O.step(O.CH, O.S1, ic, dt=dt, nsteps=n)
+    with sp.Simulation(sp.CAHN_HILLIARD, shape, dt=dt, seed=1, ic_amp=0.01) as s:
+        m0 = s.reduce(sp.MASS)
+        s.step(n)
+        got = s.read(0)
+        m1 = s.reduce(sp.MASS)
+    assert np.array_equal(got, ref)
+    drift = abs(m1 - m0) / (got.size * np.abs(got).max())
+    assert drift < 1e-13, drift
+
+
+def test_cahn_hilliard_4096_lap9x4_sampled(sp):
+    shape, dt, n = (4096, 4096), 0.01, 5
+    with sp.Simulation(sp.CAHN_HILLIARD, shape, dt=dt, seed=1, ic_amp=0.01, stencil=sp.LAP_9CROSS4) as s:
+        s.step(n)
+        check_windows(s, O.CH, O.S3, shape, dt, n, dict(seed=1, amp=0.01), O.params(),
+                      sample_points(shape, 24, 11), exact=True)
+
+
+GS_PRM = dict(Du=0.16, Dv=0.08, F=0.035, k=0.065)
+
+
+def gs_patch_centres(shape, seed, count):
+    N = int(np.prod(shape))
+    return [tuple(O.splitmix64_nth(seed, 2 * N + 3 * p + a) % shape[::-1][a] for a in range(2))[::-1]
+            for p in range(count)]
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_gray_scott_32768_sampled(sp, dtype):
+    """32768^2 Gray-Scott, dt = 1, 64 seeded 20x20 patches, 1% noise: sampled windows
+    (random points, patch centres, grid corners).  FP64 bitwise; FP32 storage (two
+    steps per launch) within 2e-6 of the FP64 oracle after 6 steps."""
+    shape, dt, n = (32768, 32768), 1.0, 6
+    kw = dict(seed=2, ic_amp=0.01, gs_patches=64, gs_patch=20, dtype=dtype)
+    pts = sample_points(shape, 16, 12, extra=gs_patch_centres(shape, 2, 8))
+    with sp.Simulation(sp.GRAY_SCOTT, shape, dt=dt, **kw) as s:
+        s.step(n)
+        check_windows(s, O.GS, O.S1, shape, dt, n, dict(seed=2, amp=0.01, patches=64, patch=20),
+                      O.params(**GS_PRM), pts, exact=(dtype == 0), atol=2e-6)
+
+
+def test_gray_scott_2048_full_run(sp):
+    """The same recipe on 2048^2 (16 patches, area-scaled) for all 5000 steps: bitwise."""
+    shape, dt, n = (2048, 2048), 1.0, 5000
+    u, v = O.initial_condition(O.GS, shape, seed=2, amp=0.01, patches=16, patch=20)
+    ru, rv = O.step(O.GS, O.S1, u, v, dt=dt, prm=O.params(**GS_PRM), nsteps=n)
+    with sp.Simulation(sp.GRAY_SCOTT, shape, dt=dt, seed=2, ic_amp=0.01, gs_patches=16, gs_patch=20) as s:
+        s.step(n)
+        assert np.array_equal(s.read(0), ru) and np.array_equal(s.read(1), rv)
+
+
+# ---------------------------------------------------------------- 3D ----
+
+
+@pytest.mark.parametrize("st", [O.S4, O.S5])
+def test_cahn_hilliard_128_cubed_full_run(sp, st):
+    """128^3 Cahn-Hilliard, dt = 0.005, 2000 steps from +-0.01 noise: FP64 bitwise.
+    FP32 storage within relative L2 1e-5 of the FP64 oracle.  BF16 storage: the
+    increments (~1e-6) are far below half an ulp of BF16 at |phi| ~ 0.01 (~2e-5),
+    so stored values barely move; its error is measured and bounded here only to
+    show it does not meet the FP32 bound (BF16 is not offered for this case)."""
+    shape, dt, n = (128, 128, 128), 0.005, 2000
+    ic = O.initial_condition(O.CH, shape, seed=3, amp=0.01)
+    ref = O.step(O.CH, st, ic, dt=dt, nsteps=n)
+    errs = {}
+    for dtype in (0, 1, 2):
+        with sp.Simulation(sp.CAHN_HILLIARD, shape, dt=dt, seed=3, ic_amp=0.01, stencil=st, dtype=dtype) as s:
+            s.step(n)
+            got = s.read(0)
+        if dtype == 0:
+            assert np.array_equal(got, ref)
+        errs[dtype] = O.rel_l2(got, ref)
+    assert errs[1] < 1e-5, errs
+    assert errs[2] > errs[1] and math.isfinite(errs[2]), errs
+    print(f"stencil {st}: rel-L2 vs FP64 oracle after {n} steps: FP32 {errs[1]:.3e}, BF16 {errs[2]:.3e}")
+
+
+@pytest.mark.parametrize("st,dtype", [(O.S4, 0), (O.S5, 0), (O.S4, 1), (O.S5, 1)])
+def test_cahn_hilliard_1024_cubed_sampled(sp, st, dtype):
+    shape, dt, n = (1024, 1024, 1024), 0.005, 2
+    with sp.Simulation(sp.CAHN_HILLIARD, shape, dt=dt, seed=3, ic_amp=0.01, stencil=st, dtype=dtype) as s:
+        s.step(n)
+        check_windows(s, O.CH, st, shape, dt, n, dict(seed=3, amp=0.01), O.params(), sample_points(shape, 12, 13),
+                      exact=(dtype == 0), atol=1e-8)

@@ -426,3 +426,23 @@ def test_gray_scott_patches(orc, dims):
     base_u = np.where(np.abs(u - 0.5) < 0.02, 0.5, 1.0)
     assert np.abs(u - base_u).max() <= 0.01
     assert np.abs(v - np.where(base_u == 0.5, 0.25, 0.0)).max() <= 0.01
+
+
+@pytest.mark.parametrize("model,shape", [(O.CH, (40, 48)), (O.GS, (40, 48)), (O.AC, (12, 14, 16)),
+                                         (O.GS, (12, 14, 16))])
+def test_initial_condition_window_matches_full_grid(orc, model, shape):
+    """A window of the initial condition, with periodic wrap, equals the same
+    slice of the full-grid initial condition (including Gray-Scott patches)."""
+    kw = dict(seed=7, amp=0.05)
+    if model == O.GS:
+        kw.update(patches=5, patch=6)
+    full = orc.initial_condition(model, shape, **kw)
+    dims = len(shape)
+    for origin in [(0,) * dims, (-3, 5, 11)[:dims], (35, 44, 13)[:dims]]:
+        wshape = (9, 7, 5)[:dims]
+        win = orc.initial_condition_window(model, shape, origin, wshape, **kw)
+        idx = np.ix_(*[(np.arange(w) + o) % n for w, o, n in zip(wshape, origin, shape)])
+        if model == O.GS:
+            assert np.array_equal(win[0], full[0][idx]) and np.array_equal(win[1], full[1][idx])
+        else:
+            assert np.array_equal(win, full[idx])
