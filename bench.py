@@ -270,6 +270,25 @@ def served_summary(sp, n_req=100, seed=4):
             "served_vs_fp64": burst_glups / fp64_glups}
 
 
+def reduce_max_over_ranks(values, device="cpu"):
+    """Element-wise maximum of `values` over all ranks (the job's time is the slowest
+    rank's); identity when torch.distributed is not initialised."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def replica_glups(lups_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job GLUPS of `world` independent replicas that each did `lups_per_rank`
+    updates, over the slowest rank's time (weak scaling: work per GPU is fixed)."""
+    return world * lups_per_rank / seconds / 1e9
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -336,6 +355,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch configuration")
     ap.add_argument("--served-requests", type=int, default=100)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -373,9 +393,13 @@ def main():
         sim.step(sub, stream=stream)
         sim.reduce(sp.MASS, stream=stream)
 
-    # warm-up
+    # warm-up (untimed); the library's autotuner picks the launch configuration
+    # here unless the workload fixes the steps per launch
+    if not spl_req and not args.no_autotune:
+        sim.autotune(stream=stream)
     for _ in range(args.warmup):
         bench_step()
+    spl, variant = sim.launch_config
     barrier()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 2)]
     with ClockSampler(local) as clocks:
@@ -390,12 +414,9 @@ def main():
         barrier()
     total_ms = ev[0].elapsed_time(ev[-1])
     step_ms = sum(ev[2 * i + 1].elapsed_time(ev[2 * i + 2]) for i in range(args.steps))
-    if world > 1:
-        t = torch.tensor([total_ms, step_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms, step_ms = float(t[0]), float(t[1])
+    total_ms, step_ms = reduce_max_over_ranks([total_ms, step_ms], device="cuda")
     lups = npts * sub * args.steps
-    value = world * lups / (total_ms * 1e-3) / 1e9
+    value = replica_glups(lups, world, total_ms * 1e-3)
     launch_ms = step_ms / (args.steps * sub)  # average duration of one step-kernel launch
 
     peaks = load_peaks()
@@ -410,7 +431,6 @@ def main():
         bpl = hbm_bytes_per_lup(model, dtype)
         achieved = bpl * npts / (launch_ms * 1e-3) / 1e9
         peak = float(peaks.get("hbm_gbs", 6800.0))
-        spl = 1 if dims == 3 else (spl_req if spl_req else (2 if (dtype == 1 and model != 1) else 1))
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None, "steps_per_launch": spl,
                 "note": f"{bpl} algorithmic bytes/LUP at one step per pass; peak = measured copy bandwidth"
@@ -440,13 +460,9 @@ def main():
             N.check(N.lib().sp_read(sim.handle, 0, host_out.ctypes.data, host_out.nbytes, 1,
                                     stream.cuda_stream), "sp_read")
         barrier()
-        el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            el = float(t[0])
+        el = reduce_max_over_ranks([time.perf_counter() - t0], device="cuda")[0]
         nf = 2 if model == 2 else 1
-        e2e = {"value": world * npts * sub * e2e_steps / el / 1e9, "unit": "GLUPS",
+        e2e = {"value": replica_glups(npts * sub * e2e_steps, world, el), "unit": "GLUPS",
                "h2d_bytes_per_step": npts * 8 * nf, "d2h_bytes_per_step": npts * 8 + 8, "steps": e2e_steps}
 
     cpu = None
@@ -457,7 +473,9 @@ def main():
     if rank == 0 and not args.no_served:
         served = served_summary(sp, n_req=args.served_requests)
 
-    launches_per_step = sub + 2
+    # step kernels (one per spl time steps, plus a single-step remainder) and the
+    # two reduction passes
+    launches_per_step = sub // spl + sub % spl + 2
     line = {"metric": "GLUPS", "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": {0: "f64", 1: "f32", 2: "bf16"}[dtype],
@@ -465,7 +483,9 @@ def main():
             "config": dict(workload_config(args.workload), parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks.summary(), "gpu_launches": launches_per_step * args.steps, "served": served,
-            "kernel_ms_per_time_step": launch_ms}
+            "kernel_ms_per_time_step": launch_ms,
+            "launch_config": {"steps_per_launch": spl, "kernel_family": variant,
+                              "autotuned": bool(not spl_req and not args.no_autotune)}}
     sim.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

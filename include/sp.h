@@ -107,8 +107,14 @@ typedef struct sp_params {
     int gs_patch;          /* Gray-Scott: patch side (points) */
     int steps_per_launch;  /* time steps fused per kernel launch (temporal blocking);
                               0 = the library's choice, 1 = none */
-    int flags;             /* reserved, must be 0 */
+    int flags;             /* SP_FLAG_* bits; other bits must be 0 */
 } sp_params;
+
+/* sp_params.flags: with steps_per_launch = 0, SP_FLAG_AUTOTUNE makes the first
+ * sp_step call that asks for at least 50 steps autotune as sp_autotune does
+ * (steps per launch for 2D FP32/BF16; strip or small-tile kernels for 2D FP64),
+ * counting the timed steps among the steps asked for. */
+#define SP_FLAG_AUTOTUNE 1
 
 /* Fill *p with the defaults: c1 = c2 = kappa = 1; Du = 0.16, Dv = 0.08, F = 0.035,
  * k = 0.065; default stencil of `dims`; FP64; seed 0; noise IC with mean 0 and
@@ -190,6 +196,20 @@ int sp_reduce_field_noalloc(int what, int dtype, const void *field, int dims, co
 /* Device pointer of field `field` at the current time level (storage type).
  * Valid until the next sp_step / sp_destroy. */
 int sp_field_devptr(sp_sim *sim, int field, void **dptr);
+
+/* Autotune now (no counterpart in the paper, whose kernels have fixed shapes):
+ * time each candidate launch configuration for this grid on `stream` (8 steps
+ * each, twice; all candidates give bit-identical results, so these are ordinary
+ * steps of the run) and keep the fastest.  A choice cached earlier in the
+ * process for the same (model, stencil, dtype, dims, grid size class) is taken
+ * without timing.  Blocks until the timing events complete.  *steps_taken
+ * receives the number of time steps advanced (0 to 49).  Captured graphs of
+ * another configuration are dropped. */
+int sp_autotune(sp_sim *sim, void *stream, int64_t *steps_taken);
+
+/* Launch configuration in use: steps fused per launch and kernel family
+ * (0 = the default for the grid, 1 = the alternative the autotuner may pick). */
+int sp_launch_config(const sp_sim *sim, int *steps_per_launch, int *variant);
 
 /* Number of time steps taken since creation. */
 int sp_steps_taken(const sp_sim *sim, int64_t *steps);

@@ -13,13 +13,13 @@ import ctypes
 import numpy as np
 
 from . import _native as N
-from ._native import (ALLEN_CAHN, BF16_F32, CAHN_HILLIARD, F32, F64, FREE_ENERGY, GRAY_SCOTT, IC_CONSTANT,
+from ._native import (ALLEN_CAHN, BF16_F32, CAHN_HILLIARD, F32, F64, FLAG_AUTOTUNE, FREE_ENERGY, GRAY_SCOTT, IC_CONSTANT,
                       IC_NOISE, LAP_5, LAP_7, LAP_9BOX, LAP_9CROSS4, LAP_13CROSS4, LAP_27, LAP_DEFAULT, MASS,
                       MAX_U, MIN_U, SUM_U, SUM_V, SUMSQ_U, SpError)
 
 __all__ = ["Simulation", "Server", "Result", "params", "check_stability", "SpError", "ALLEN_CAHN", "CAHN_HILLIARD", "GRAY_SCOTT",
            "LAP_5", "LAP_9BOX", "LAP_9CROSS4", "LAP_7", "LAP_27", "LAP_13CROSS4", "LAP_DEFAULT", "F64", "F32",
-           "BF16_F32", "IC_NOISE", "IC_CONSTANT", "MASS", "FREE_ENERGY", "SUM_U", "SUM_V", "MIN_U", "MAX_U",
+           "BF16_F32", "IC_NOISE", "IC_CONSTANT", "FLAG_AUTOTUNE", "MASS", "FREE_ENERGY", "SUM_U", "SUM_V", "MIN_U", "MAX_U",
            "SUMSQ_U"]
 
 _STORAGE = {F64: np.float64, F32: np.float32, BF16_F32: np.uint16}
@@ -122,6 +122,20 @@ class Simulation:
         p = ctypes.c_void_p()
         N.check(N.lib().sp_field_devptr(self._h, field, ctypes.byref(p)), "sp_field_devptr")
         return int(p.value)
+
+    def autotune(self, stream=None) -> int:
+        """Pick the fastest launch configuration for this grid by timing the
+        candidates; returns the time steps taken meanwhile (see sp_autotune)."""
+        n = ctypes.c_int64(0)
+        N.check(N.lib().sp_autotune(self._h, _stream_ptr(stream), ctypes.byref(n)), "sp_autotune")
+        return n.value
+
+    @property
+    def launch_config(self):
+        """(steps fused per launch, kernel family) currently used."""
+        a, b = ctypes.c_int(0), ctypes.c_int(0)
+        N.check(N.lib().sp_launch_config(self._h, ctypes.byref(a), ctypes.byref(b)), "sp_launch_config")
+        return a.value, b.value
 
     @property
     def steps_taken(self) -> int:

@@ -25,6 +25,7 @@ ALLEN_CAHN, CAHN_HILLIARD, GRAY_SCOTT = 0, 1, 2
 LAP_DEFAULT, LAP_5, LAP_9BOX, LAP_9CROSS4, LAP_7, LAP_27, LAP_13CROSS4 = -1, 0, 1, 2, 3, 4, 5
 F64, F32, BF16_F32 = 0, 1, 2
 IC_NOISE, IC_CONSTANT = 0, 1
+FLAG_AUTOTUNE = 1
 MASS, FREE_ENERGY, SUM_U, SUM_V, MIN_U, MAX_U, SUMSQ_U = range(7)
 
 
@@ -72,6 +73,8 @@ _SIGS = {
     "sp_reduce": (ctypes.c_int, [_vp, ctypes.c_int, _P(ctypes.c_double), _vp]),
     "sp_field_devptr": (ctypes.c_int, [_vp, ctypes.c_int, _P(_vp)]),
     "sp_steps_taken": (ctypes.c_int, [_vp, _P(_i64)]),
+    "sp_autotune": (ctypes.c_int, [_vp, _vp, _P(_i64)]),
+    "sp_launch_config": (ctypes.c_int, [_vp, _P(ctypes.c_int), _P(ctypes.c_int)]),
     "sp_destroy": (ctypes.c_int, [_vp]),
     "sp_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, _P(_vp)]),
     "sp_submit": (ctypes.c_int, [_vp, _P(sp_request), _P(ctypes.c_uint64)]),

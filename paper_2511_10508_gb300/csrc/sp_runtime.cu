@@ -6,12 +6,20 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
+#include <vector>
 
 #include "sp_internal.h"
 
 using namespace sp;
+
+namespace sp {
+thread_local int g_step_variant = 0;
+}
 
 // --------------------------------------------------------------- errors --
 
@@ -117,7 +125,7 @@ static int validate_params(int model, int dims, double h, double dt, const sp_pa
     for (double v : vals)
         if (!is_finite(v)) return fail(SP_EINVAL, "non-finite model coefficient");
     if (p.dtype < SP_F64 || p.dtype > SP_BF16_F32) return fail(SP_EINVAL, "unknown dtype %d", p.dtype);
-    if (p.flags != 0) return fail(SP_EINVAL, "flags must be 0");
+    if (p.flags & ~SP_FLAG_AUTOTUNE) return fail(SP_EINVAL, "unknown flags 0x%x", p.flags);
     if (p.steps_per_launch < 0) return fail(SP_EINVAL, "steps_per_launch must be >= 0");
     if (p.ic_kind != SP_IC_NOISE && p.ic_kind != SP_IC_CONSTANT) return fail(SP_EINVAL, "unknown ic_kind %d", p.ic_kind);
     if (!is_finite(p.ic_mean) || !is_finite(p.ic_amp)) return fail(SP_EINVAL, "non-finite ic_mean/ic_amp");
@@ -157,6 +165,8 @@ struct sp_sim {
     int device, n_sm;
     cudaGraphExec_t graph[2];  // kGraphSteps steps starting from level 0 / level 1
     int spl;                   // steps fused per launch (temporal blocking)
+    int variant;               // kernel family (see g_step_variant)
+    bool tune_pending;         // autotune on the next long sp_step
 };
 
 // Steps per captured graph.  A graph holds kGraphSteps / spl launches, an even
@@ -239,6 +249,8 @@ extern "C" int sp_create(int model, int dims, const int64_t shape[3], double h, 
     s->esize = dtype_size(prm.dtype);
     s->k = make_consts(*s);
     s->spl = steps_per_launch(dims, prm.dtype, model, prm.steps_per_launch);
+    s->variant = 0;
+    s->tune_pending = (prm.flags & SP_FLAG_AUTOTUNE) != 0 && prm.steps_per_launch == 0;
 
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, s->device);
@@ -278,7 +290,16 @@ extern "C" int sp_create(int model, int dims, const int64_t shape[3], double h, 
 
 static cudaStream_t pick(sp_sim *s, void *stream) { return stream ? (cudaStream_t)stream : s->stream; }
 
+static cudaError_t launch_one_step_impl(sp_sim *s, cudaStream_t st, int k);
+
 static cudaError_t launch_one_step(sp_sim *s, cudaStream_t st, int k = 1) {
+    g_step_variant = s->variant;
+    const cudaError_t e = launch_one_step_impl(s, st, k);
+    g_step_variant = 0;
+    return e;
+}
+
+static cudaError_t launch_one_step_impl(sp_sim *s, cudaStream_t st, int k) {
     StepArgs a;
     a.in0 = s->f[s->cur][0];
     a.in1 = s->nf > 1 ? s->f[s->cur][1] : s->f[s->cur][0];
@@ -295,6 +316,113 @@ static cudaError_t launch_one_step(sp_sim *s, cudaStream_t st, int k = 1) {
     case SP_F32: return launch_step_f32(s->model, s->stencil, a, st, s->n_sm, k);
     default: return launch_step_bf16(s->model, s->stencil, a, st, s->n_sm, k);
     }
+}
+
+// ---------------------------------------------------------------- autotune --
+//
+// Candidates: (steps per launch, kernel family).  Every candidate computes the
+// same values bit for bit, so the timed steps are ordinary steps of the run.
+// The winner is cached per (model, stencil, dtype, dims, log2 of the grid size).
+
+struct TuneKey {
+    int model, stencil, dtype, dims, size_log2;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(model, stencil, dtype, dims, size_log2) < std::tie(o.model, o.stencil, o.dtype, o.dims, o.size_log2);
+    }
+};
+struct TuneChoice {
+    int spl, variant;
+};
+constexpr int kTuneSteps = 8;  // divisible by every candidate's steps per launch
+constexpr int64_t kAutotuneMinSteps = 2 * 3 * kTuneSteps;
+static std::mutex g_tune_mu;
+static std::map<TuneKey, TuneChoice> g_tune_cache;
+
+// Graphs hold launches of one configuration: drop them when it changes.
+static void set_launch_config(sp_sim *s, TuneChoice c) {
+    if (c.spl == s->spl && c.variant == s->variant) return;
+    for (int l = 0; l < 2; ++l)
+        if (s->graph[l]) {
+            cudaGraphExecDestroy(s->graph[l]);
+            s->graph[l] = nullptr;
+        }
+    s->spl = c.spl;
+    s->variant = c.variant;
+}
+
+static TuneKey tune_key(const sp_sim *s) {
+    int lg = 0;
+    while (lg < 62 && (1ull << (lg + 1)) <= s->N) ++lg;
+    return {s->model, s->stencil, s->dtype, s->dims, lg};
+}
+
+static std::vector<TuneChoice> tune_candidates(const sp_sim *s) {
+    std::vector<TuneChoice> c;
+    if (s->dims == 2 && s->dtype != SP_F64) {
+        for (int spl : {1, 2, 4}) c.push_back({spl, 0});
+    } else if (s->dims == 2 || (s->dtype == SP_F64 && s->stencil == SP_LAP_27)) {
+        c.push_back({1, 0});
+        c.push_back({1, 1});
+    } else {
+        c.push_back({1, 0});
+    }
+    return c;
+}
+
+// Run the candidates on stream st (kTuneSteps steps each, timed with events);
+// returns the number of steps taken.
+static int64_t autotune(sp_sim *s, cudaStream_t st, int *rc) {
+    *rc = SP_OK;
+    const TuneKey key = tune_key(s);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            set_launch_config(s, it->second);
+            return 0;
+        }
+    }
+    const std::vector<TuneChoice> cand = tune_candidates(s);
+    if (cand.size() < 2) return 0;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        *rc = fail(SP_ECUDA, "autotune: cudaEventCreate failed");
+        return 0;
+    }
+    int64_t taken = 0;
+    float best = 1e30f;
+    TuneChoice win = {s->spl, s->variant};
+    for (int pass = 0; pass < 2; ++pass)  // pass 0 warms every candidate up, pass 1 is timed
+        for (const TuneChoice &c : cand) {
+            set_launch_config(s, c);
+            cudaEventRecord(e0, st);
+            for (int i = 0; i < kTuneSteps; i += c.spl) {
+                cudaError_t e = launch_one_step(s, st, c.spl);
+                if (e != cudaSuccess) {
+                    *rc = fail(SP_ECUDA, "autotune launch: %s", cudaGetErrorString(e));
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return taken;
+                }
+                s->cur ^= 1;
+                s->steps += c.spl;
+                taken += c.spl;
+            }
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (pass == 1 && ms < best) {
+                best = ms;
+                win = c;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    set_launch_config(s, win);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = win;
+    return taken;
 }
 
 // Capture kGraphSteps steps starting from the current level into s->graph[s->cur].
@@ -324,6 +452,18 @@ extern "C" int sp_step(sp_sim *s, int64_t nsteps, void *stream) {
     if (!s) return fail(SP_EINVAL, "sim is NULL");
     if (nsteps < 0) return fail(SP_EINVAL, "nsteps must be >= 0");
     const cudaStream_t st = pick(s, stream);
+    if (s->tune_pending && nsteps >= kAutotuneMinSteps + 1) {
+        s->tune_pending = false;
+        if (s->steps == 0) {  // the first step takes the eager path
+            SP_CUDA(launch_one_step(s, st));
+            s->cur ^= 1;
+            s->steps += 1;
+            nsteps -= 1;
+        }
+        int rc = SP_OK;
+        nsteps -= autotune(s, st, &rc);
+        if (rc != SP_OK) return rc;
+    }
     while (nsteps > 0) {
         if (nsteps >= kGraphSteps && s->steps >= s->spl + 1) {
             if (!s->graph[s->cur]) SP_CUDA(capture_graph(s));
@@ -436,6 +576,27 @@ extern "C" int sp_field_devptr(sp_sim *s, int field, void **dptr) {
     if (!s || !dptr) return fail(SP_EINVAL, "NULL argument");
     if (int rc = check_field(s, field)) return rc;
     *dptr = s->f[s->cur][field];
+    return SP_OK;
+}
+
+extern "C" int sp_autotune(sp_sim *s, void *stream, int64_t *steps_taken) {
+    if (!s || !steps_taken) return fail(SP_EINVAL, "NULL argument");
+    *steps_taken = 0;
+    const cudaStream_t st = pick(s, stream);
+    int rc = SP_OK;
+    s->tune_pending = false;
+    if (s->steps == 0) {  // the first step takes the eager path
+        if ((rc = sp_step(s, 1, stream)) != SP_OK) return rc;
+        *steps_taken = 1;
+    }
+    *steps_taken += autotune(s, st, &rc);
+    return rc;
+}
+
+extern "C" int sp_launch_config(const sp_sim *s, int *steps_per_launch, int *variant) {
+    if (!s || !steps_per_launch || !variant) return fail(SP_EINVAL, "NULL argument");
+    *steps_per_launch = s->spl;
+    *variant = s->variant;
     return SP_OK;
 }
 

@@ -9,6 +9,7 @@
 //   step2d_batch_kernel  2D, FP64: shared-memory rings, batches of rows
 //   step2d_tile_kernel   2D, FP32/BF16: one CTA per tile, tile + halo fetched with cp.async
 //   step3d_kernel        3D, FP64: shared-memory plane rings
+//   step3d_zreg_kernel   3D, FP64, 27-point: z-streaming with register queues
 //   step3d_vec_kernel    3D, FP32/BF16: plane rings of 16-byte chunks
 #pragma once
 
@@ -681,6 +682,211 @@ __global__ void __launch_bounds__(NT) step3d_kernel(StepArgs a, int tiles_x, int
         }
     }
     __syncthreads();  // the rings are reused by the next segment
+    }  // segments
+}
+
+// ================================================= 3D, 27-point, FP64 ==
+//
+// The 27-point stencil's fixed order (see sp_common.cuh) is built from per-plane
+// partial sums: the in-plane cross sum Cz and diagonal sum Dz of each of the
+// three planes.  Each thread owns fixed (x, y) points of a TX x TY tile and
+// streams along z, keeping the value, Cz and Dz of its points for the two
+// previous planes in registers; a plane's partial sums are then computed once
+// per point instead of once per use (14 instead of 26 FP64 operations per
+// stencil application, with the same operations in the same order, so results
+// are unchanged bit for bit).  Only the newest plane is read from shared
+// memory, so the input needs two plane buffers and mu (Cahn-Hilliard) one.
+//
+// Cahn-Hilliard per input plane j (z = z0 - 2 + j): mu of plane j-1 over the
+// tile plus one halo cell, then the output of plane j-2 from the mu partial
+// sums of planes j-3 .. j-1.  Allen-Cahn / Gray-Scott: output of plane j-1.
+// Barriers: after the commit of plane j, and (Cahn-Hilliard) after mu.
+template <int MODEL, int TX, int TY, int NT>
+struct Step3dZregShape {
+    static constexpr int r = 1;
+    static constexpr int RIN = (MODEL == CH) ? 2 : 1;
+    static constexpr int WIN = TX + 2 * RIN, HIN = TY + 2 * RIN, AIN = WIN * HIN;
+    static constexpr int NF = (MODEL == GS) ? 2 : 1;
+    static constexpr int WMU = TX + 2, HMU = TY + 2, AMU = (MODEL == CH) ? WMU * HMU : 0;
+    static constexpr int EPT = (AIN + NT - 1) / NT;       // loaded cells per thread per field
+    static constexpr int EMU = (AMU + NT - 1) / NT;       // mu points per thread
+    static constexpr int EOUT = TX * TY / NT;             // output points per thread
+    static_assert(TX * TY % NT == 0 && NT % TX == 0, "tile rows must map to whole threads");
+    static constexpr size_t smem_bytes = sizeof(double) * ((size_t)2 * NF * AIN + (size_t)AMU);
+};
+
+// in-plane cross and diagonal sums of the 27-point stencil at p (row pitch W)
+__device__ __forceinline__ void plane_sums27(const double *p, int W, double &Cz, double &Dz) {
+    Cz = (p[-1] + p[1]) + (p[-W] + p[W]);
+    Dz = (p[-W - 1] + p[-W + 1]) + (p[W - 1] + p[W + 1]);
+}
+
+// stencil sum from the centre value, its z neighbours and the three planes'
+// partial sums (m = z-1, 0 = z, p = z+1)
+__device__ __forceinline__ double combine27(double fm, double f0, double fp, double Cm, double C0, double Cp,
+                                            double Dm, double D0, double Dp) {
+    const double F = C0 + (fm + fp);
+    const double E = D0 + (Cm + Cp);
+    const double K = Dm + Dp;
+    return FMA(-128.0, f0, FMA(14.0, F, FMA(3.0, E, K)));
+}
+
+template <int MODEL, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT) step3d_zreg_kernel(StepArgs a, int tiles_x, int tiles_y,
+                                                         long long planes_per_cta) {
+    typedef Step3dZregShape<MODEL, TX, TY, NT> Sh;
+    typedef double C;
+    constexpr int RIN = Sh::RIN, WIN = Sh::WIN, AIN = Sh::AIN, NF = Sh::NF;
+    constexpr int WMU = Sh::WMU, AMU = Sh::AMU, EPT = Sh::EPT, EMU = Sh::EMU, EOUT = Sh::EOUT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *s_in = reinterpret_cast<C *>(smem_raw);  // [2][NF][AIN]
+    C *s_mu = s_in + (size_t)2 * NF * AIN;      // [AMU]
+
+    const ConstsC<C> k(a.k, a.kf);
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int t = threadIdx.x;
+    const size_t plane = (size_t)nx * (size_t)ny;
+    const double *in[2] = {static_cast<const double *>(a.in0), static_cast<const double *>(a.in1)};
+    double *out[2] = {static_cast<double *>(a.out0), static_cast<double *>(a.out1)};
+    // output points of this thread: rows oy + e * (NT / TX), column ox
+    const int ox = t % TX, oy = t / TX;
+    constexpr int OSTEP = NT / TX;
+
+    long long g0 = (long long)blockIdx.x * planes_per_cta;
+    const long long gend = min(g0 + planes_per_cta, (long long)tiles_x * tiles_y * nz);
+    while (g0 < gend) {
+        const int tile = (int)(g0 / nz);
+        const int z0 = (int)(g0 - (long long)tile * nz);
+        const int z1 = (int)min((long long)nz, (long long)z0 + (gend - g0));
+        g0 += z1 - z0;
+        const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+        const int nplanes = (z1 - z0) + 2 * RIN;
+
+        int loff[EPT];
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            const int c = t + e * NT;
+            if (c < AIN) {
+                const int yi = c / WIN, xi = c - yi * WIN;
+                loff[e] = wrap_idx(y0 - RIN + yi, ny) * nx + wrap_idx(x0 - RIN + xi, nx);
+            } else {
+                loff[e] = -1;
+            }
+        }
+        C pf[NF][EPT];
+        auto fetch = [&](int z) {
+            const size_t zoff = (size_t)wrap_idx(z, nz) * plane;
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+#pragma unroll
+                for (int e = 0; e < EPT; ++e)
+                    if (loff[e] >= 0) pf[f][e] = load_one(in[f] + zoff + loff[e]);
+        };
+
+        // register queues: index 0 = plane j-2, 1 = plane j-1 (of the streamed quantity)
+        C qf[NF][EOUT][2], qC[NF][EOUT][2], qD[NF][EOUT][2];
+        constexpr int EM = EMU > 0 ? EMU : 1;
+        C mf[EM][2], mC[EM][2], mD[EM][2];  // Cahn-Hilliard: phi partials at mu points
+        C pq[EOUT][2];                          // Cahn-Hilliard: phi at output points
+        (void)mf; (void)mC; (void)mD; (void)pq;
+
+        fetch(z0 - RIN);
+        for (int j = 0; j < nplanes; ++j) {
+            C *buf = s_in + (size_t)(j & 1) * NF * AIN;
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+#pragma unroll
+                for (int e = 0; e < EPT; ++e)
+                    if (loff[e] >= 0) buf[(size_t)f * AIN + t + e * NT] = pf[f][e];
+            if (j + 1 < nplanes) fetch(z0 - RIN + j + 1);
+            __syncthreads();
+            if constexpr (MODEL == CH) {
+                // mu of plane j-1 at the tile points plus one halo cell
+#pragma unroll
+                for (int e = 0; e < EMU; ++e) {
+                    const int c = t + e * NT;
+                    if (c < AMU) {
+                        const int ym = c / WMU, xm = c - ym * WMU;
+                        const C *p = buf + (ym + 1) * WIN + (xm + 1);
+                        C Cz, Dz;
+                        plane_sums27(p, WIN, Cz, Dz);
+                        const C f0 = p[0];
+                        if (j >= 2) {
+                            const C S = combine27(mf[e][0], mf[e][1], f0, mC[e][0], mC[e][1], Cz, mD[e][0], mD[e][1], Dz);
+                            s_mu[c] = ch_mu<C>(mf[e][1], S, k);
+                        }
+                        mf[e][0] = mf[e][1], mf[e][1] = f0;
+                        mC[e][0] = mC[e][1], mC[e][1] = Cz;
+                        mD[e][0] = mD[e][1], mD[e][1] = Dz;
+                    }
+                }
+                C pnow[EOUT];
+#pragma unroll
+                for (int e = 0; e < EOUT; ++e) pnow[e] = buf[(oy + e * OSTEP + RIN) * WIN + ox + RIN];
+                __syncthreads();
+                if (j >= 2) {
+                    // mu partial sums of plane j-1; output of plane j-2
+                    const int zo = z0 - 4 + j;
+#pragma unroll
+                    for (int e = 0; e < EOUT; ++e) {
+                        const int yy = oy + e * OSTEP;
+                        const C *m = s_mu + (yy + 1) * WMU + (ox + 1);
+                        C Cz, Dz;
+                        plane_sums27(m, WMU, Cz, Dz);
+                        const C m0 = m[0];
+                        if (j >= 4) {
+                            const C S = combine27(qf[0][e][0], qf[0][e][1], m0, qC[0][e][0], qC[0][e][1], Cz,
+                                                  qD[0][e][0], qD[0][e][1], Dz);
+                            const int x = x0 + ox, y = y0 + yy;
+                            if (x < nx && y < ny)
+                                out[0][(size_t)zo * plane + (size_t)y * nx + x] = ch_update<C>(pq[e][0], S, k);
+                        }
+                        qf[0][e][0] = qf[0][e][1], qf[0][e][1] = m0;
+                        qC[0][e][0] = qC[0][e][1], qC[0][e][1] = Cz;
+                        qD[0][e][0] = qD[0][e][1], qD[0][e][1] = Dz;
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < EOUT; ++e) pq[e][0] = pq[e][1], pq[e][1] = pnow[e];
+            } else {
+                // output of plane j-1
+                const int zo = z0 - 2 + j;
+#pragma unroll
+                for (int e = 0; e < EOUT; ++e) {
+                    const int yy = oy + e * OSTEP;
+                    C f0[NF], S[NF];
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        const C *p = buf + (size_t)f * AIN + (yy + 1) * WIN + (ox + 1);
+                        C Cz, Dz;
+                        plane_sums27(p, WIN, Cz, Dz);
+                        f0[f] = p[0];
+                        if (j >= 2)
+                            S[f] = combine27(qf[f][e][0], qf[f][e][1], f0[f], qC[f][e][0], qC[f][e][1], Cz,
+                                             qD[f][e][0], qD[f][e][1], Dz);
+                        qC[f][e][0] = qC[f][e][1], qC[f][e][1] = Cz;
+                        qD[f][e][0] = qD[f][e][1], qD[f][e][1] = Dz;
+                    }
+                    if (j >= 2) {
+                        const int x = x0 + ox, y = y0 + yy;
+                        if (x < nx && y < ny) {
+                            const size_t o = (size_t)zo * plane + (size_t)y * nx + x;
+                            if constexpr (MODEL == AC) {
+                                out[0][o] = ac_update<C>(qf[0][e][1], S[0], k);
+                            } else {
+                                C un, vn;
+                                gs_update<C>(qf[0][e][1], qf[NF - 1][e][1], S[0], S[NF - 1], k, un, vn);
+                                out[0][o] = un;
+                                out[NF - 1][o] = vn;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) qf[f][e][0] = qf[f][e][1], qf[f][e][1] = f0[f];
+                }
+            }
+        }
+        __syncthreads();  // the buffers are reused by the next segment
     }  // segments
 }
 

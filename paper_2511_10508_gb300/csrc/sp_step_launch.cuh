@@ -28,6 +28,7 @@ template <> struct Tiles<bf16> {
 };
 
 constexpr int kMinRun = 32;
+constexpr long long kSmallGrid2d = 1LL << 20;  // FP64 2D grids up to 1024^2 use small tiles
 
 // Persistent grids: one resident wave of CTAs (SMs x occupancy), each owning an
 // equal share of the flattened (tile, slow-axis) work, but at least kMinRun
@@ -63,6 +64,20 @@ cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
         if (k == 2) return launch_tb<MODEL, ST, T, 2>(a, s);
     }
     if constexpr (StencilInfo<ST>::dims == 2 && std::is_same<T, double>::value) {
+        const bool small = (long long)a.nx * a.ny <= kSmallGrid2d;
+        if (small != (g_step_variant == 1)) {
+            // small grids are latency bound: many small tiles instead of a few long strips
+            constexpr int BX = 32, BY = 16, NT = 128;
+            typedef Step2dTileShape<MODEL, ST, T, BX, BY> Sh;
+            auto kern = step2d_tile_kernel<MODEL, ST, T, BX, BY, NT>;
+            static const bool attr = [&] {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem_bytes);
+                return true;
+            }();
+            (void)attr;
+            kern<<<dim3((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY), NT, Sh::smem_bytes, s>>>(a);
+            return cudaGetLastError();
+        }
         typedef Batch2d<MODEL> B;
         typedef Step2dBatchShape<MODEL, ST, T, B::NT, B::RB> Sh;
         auto kern = step2d_batch_kernel<MODEL, ST, T, B::NT, B::RB>;
@@ -107,6 +122,22 @@ cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
         const long long ctas = persistent_ctas((long long)tx * ty * a.nz, occ, n_sm);
         const long long planes = ((long long)tx * ty * a.nz + ctas - 1) / ctas;
         kern<<<(unsigned)(((long long)tx * ty * a.nz + planes - 1) / planes), Sh::NT, Sh::smem_bytes, s>>>(
+            a, tx, ty, planes);
+    } else if (ST == L27 && g_step_variant == 0) {
+        // FP64 27-point: z-streaming kernel with per-plane partial sums in registers
+        constexpr int TX = 32, TY = 32, NT = 256;
+        typedef Step3dZregShape<MODEL, TX, TY, NT> Sh;
+        auto kern = step3d_zreg_kernel<MODEL, TX, TY, NT>;
+        static const int occ = [&] {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem_bytes);
+            int o = 1;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT, Sh::smem_bytes);
+            return o;
+        }();
+        const int tx = (a.nx + TX - 1) / TX, ty = (a.ny + TY - 1) / TY;
+        const long long ctas = persistent_ctas((long long)tx * ty * a.nz, occ, n_sm);
+        const long long planes = ((long long)tx * ty * a.nz + ctas - 1) / ctas;
+        kern<<<(unsigned)(((long long)tx * ty * a.nz + planes - 1) / planes), NT, Sh::smem_bytes, s>>>(
             a, tx, ty, planes);
     } else {
         typedef typename Tiles<T>::template T3<StencilInfo<ST>::r> TT;

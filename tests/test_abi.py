@@ -57,7 +57,7 @@ def test_params_default(sp):
 
 @pytest.mark.parametrize("bad", [
     dict(model=7), dict(dims=4), dict(stencil=9),
-    dict(h=0.0), dict(dt=-1.0), dict(h=float("nan")), dict(dtype=5), dict(flags=1),
+    dict(h=0.0), dict(dt=-1.0), dict(h=float("nan")), dict(dtype=5), dict(flags=2),
     dict(stencil=3),  # 3D stencil on a 2D grid
 ])
 def test_invalid_arguments_rejected_before_device(sp, bad):

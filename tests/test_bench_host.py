@@ -1,0 +1,85 @@
+"""Host-side logic of bench.py (no GPU): the multi-rank timing aggregation with
+two gloo ranks on the CPU, the reference arm's non-zero ranks, and the served
+request stream (every request inside the forward-Euler bound, the configured mix)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+PORT = _free_port()
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # rank r took (r+1) ms in total and 10*(world-r) ms in its kernels
+        got = bench.reduce_max_over_ranks([rank + 1.0, 10.0 * (world - rank)])
+        out.put((rank, got, bench.replica_glups(1e9, world, got[0] * 1e-3)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_with_gloo():
+    import torch.multiprocessing as mp
+
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, PORT, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, got, glups in res:
+        assert got == [2.0, 20.0]                      # both ranks see the slowest rank's times
+        assert glups == pytest.approx(2 * 1e9 / 2e-3 / 1e9)  # all ranks' work over the slowest time
+
+
+
+def test_replica_glups_is_whole_job():
+    assert bench.replica_glups(4e9, 4, 2.0) == pytest.approx(8.0)
+
+
+def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+
+    class A:
+        workload, steps, warmup = bench.DEFAULT, 3, 3
+
+    assert bench.run_reference(A()) == 0
+
+
+def test_served_request_stream():
+    import paper_2511_10508_gb300 as sp
+
+    reqs = bench.served_requests(400, 4)
+    assert len(reqs) == 400
+    models = [m for m, *_ in reqs]
+    dims = [len(sh) for _, sh, *_ in reqs]
+    assert set(models) == {0, 1, 2} and set(dims) == {2, 3}
+    for m, sh, dt, n, kw in reqs:
+        lo, hi = (64, 2048) if len(sh) == 2 else (32, 256)
+        assert lo <= sh[0] <= hi and 100 <= n <= 5000 and kw["dtype"] in (0, 1)
+        p = sp.params(m, len(sh), **{k: v for k, v in kw.items()})
+        ok, f = sp.check_stability(m, len(sh), 1.0, dt, p)
+        assert ok, (m, sh, dt, kw, f)
+    # log-uniform sides: the median 2D side is near sqrt(64*2048) = 362
+    s2 = np.array([sh[0] for _, sh, *_ in reqs if len(sh) == 2])
+    assert 250 < np.median(s2) < 520
+    assert bench.served_requests(400, 4) == reqs  # seeded
