@@ -45,6 +45,7 @@ WORKLOADS = {
     "ch2d-16384-bf16-lap5-k4": (1, 2, (16384, 16384), 0.01, 0, 2, 20, 4),
     "ch2d-8192-f32-lap5": (1, 2, (8192, 8192), 0.01, 0, 1, 10),
     "ch3d-384-f32-lap7": (1, 3, (384, 384, 384), 0.005, 3, 1, 10),
+    "ch3d-384-f64-lap27": (1, 3, (384, 384, 384), 0.005, 4, 0, 4),
     "ac2d-256-f64-lap5": (0, 2, (256, 256), 0.05, 0, 0, 1000),
     "gs2d-32768-f32-lap5": (2, 2, (32768, 32768), 1.0, 0, 1, 10),
     "gs2d-32768-f64-lap5": (2, 2, (32768, 32768), 1.0, 0, 0, 2),
@@ -357,6 +358,7 @@ def main():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch configuration")
     ap.add_argument("--served-requests", type=int, default=100)
+    ap.add_argument("--launch-config", default="", help="pin 'steps_per_launch,family' instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -395,7 +397,9 @@ def main():
 
     # warm-up (untimed); the library's autotuner picks the launch configuration
     # here unless the workload fixes the steps per launch
-    if not spl_req and not args.no_autotune:
+    if args.launch_config:
+        sim.launch_config = tuple(int(x) for x in args.launch_config.split(","))
+    elif not spl_req and not args.no_autotune:
         sim.autotune(stream=stream)
     for _ in range(args.warmup):
         bench_step()
@@ -485,7 +489,7 @@ def main():
             "clocks": clocks.summary(), "gpu_launches": launches_per_step * args.steps, "served": served,
             "kernel_ms_per_time_step": launch_ms,
             "launch_config": {"steps_per_launch": spl, "kernel_family": variant,
-                              "autotuned": bool(not spl_req and not args.no_autotune)}}
+                              "autotuned": bool(not spl_req and not args.no_autotune and not args.launch_config)}}
     sim.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -111,8 +111,9 @@ typedef struct sp_params {
 } sp_params;
 
 /* sp_params.flags: with steps_per_launch = 0, SP_FLAG_AUTOTUNE makes the first
- * sp_step call that asks for at least 50 steps autotune as sp_autotune does
- * (steps per launch for 2D FP32/BF16; strip or small-tile kernels for 2D FP64),
+ * sp_step call that asks for at least 66 steps autotune as sp_autotune does
+ * (steps per launch and kernel family for 2D FP32/BF16; strip or small-tile
+ * kernels for 2D FP64; two kernel families for the 3D FP64 27-point stencil),
  * counting the timed steps among the steps asked for. */
 #define SP_FLAG_AUTOTUNE 1
 
@@ -203,9 +204,16 @@ int sp_field_devptr(sp_sim *sim, int field, void **dptr);
  * steps of the run) and keep the fastest.  A choice cached earlier in the
  * process for the same (model, stencil, dtype, dims, grid size class) is taken
  * without timing.  Blocks until the timing events complete.  *steps_taken
- * receives the number of time steps advanced (0 to 49).  Captured graphs of
+ * receives the number of time steps advanced (0 to 65).  Captured graphs of
  * another configuration are dropped. */
 int sp_autotune(sp_sim *sim, void *stream, int64_t *steps_taken);
+
+/* Pin a launch configuration (for instance one that sp_autotune chose in an
+ * earlier run): steps fused per launch (1, or 2 / 4 for 2D FP32/BF16) and kernel
+ * family (0, or 1 where sp_launch_config documents an alternative).  Every
+ * available configuration gives bit-identical results.  SP_EINVAL if the pair is
+ * not available for this grid; cancels a pending SP_FLAG_AUTOTUNE. */
+int sp_set_launch_config(sp_sim *sim, int steps_per_launch, int variant);
 
 /* Launch configuration in use: steps fused per launch and kernel family
  * (0 = the default for the grid, 1 = the alternative the autotuner may pick). */

@@ -137,6 +137,11 @@ class Simulation:
         N.check(N.lib().sp_launch_config(self._h, ctypes.byref(a), ctypes.byref(b)), "sp_launch_config")
         return a.value, b.value
 
+    @launch_config.setter
+    def launch_config(self, cfg) -> None:
+        spl, variant = cfg
+        N.check(N.lib().sp_set_launch_config(self._h, int(spl), int(variant)), "sp_set_launch_config")
+
     @property
     def steps_taken(self) -> int:
         s = ctypes.c_int64(0)

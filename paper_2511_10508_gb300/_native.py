@@ -74,6 +74,7 @@ _SIGS = {
     "sp_field_devptr": (ctypes.c_int, [_vp, ctypes.c_int, _P(_vp)]),
     "sp_steps_taken": (ctypes.c_int, [_vp, _P(_i64)]),
     "sp_autotune": (ctypes.c_int, [_vp, _vp, _P(_i64)]),
+    "sp_set_launch_config": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "sp_launch_config": (ctypes.c_int, [_vp, _P(ctypes.c_int), _P(ctypes.c_int)]),
     "sp_destroy": (ctypes.c_int, [_vp]),
     "sp_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, _P(_vp)]),

@@ -334,7 +334,7 @@ struct TuneChoice {
     int spl, variant;
 };
 constexpr int kTuneSteps = 8;  // divisible by every candidate's steps per launch
-constexpr int64_t kAutotuneMinSteps = 2 * 3 * kTuneSteps;
+constexpr int64_t kAutotuneMinSteps = 2 * 4 * kTuneSteps;
 static std::mutex g_tune_mu;
 static std::map<TuneKey, TuneChoice> g_tune_cache;
 
@@ -359,6 +359,7 @@ static TuneKey tune_key(const sp_sim *s) {
 static std::vector<TuneChoice> tune_candidates(const sp_sim *s) {
     std::vector<TuneChoice> c;
     if (s->dims == 2 && s->dtype != SP_F64) {
+        c.push_back({1, 1});
         for (int spl : {1, 2, 4}) c.push_back({spl, 0});
     } else if (s->dims == 2 || (s->dtype == SP_F64 && s->stencil == SP_LAP_27)) {
         c.push_back({1, 0});
@@ -591,6 +592,23 @@ extern "C" int sp_autotune(sp_sim *s, void *stream, int64_t *steps_taken) {
     }
     *steps_taken += autotune(s, st, &rc);
     return rc;
+}
+
+extern "C" int sp_set_launch_config(sp_sim *s, int steps_per_launch, int variant) {
+    if (!s) return fail(SP_EINVAL, "sim is NULL");
+    for (const TuneChoice &c : tune_candidates(s))
+        if (c.spl == steps_per_launch && c.variant == variant) {
+            s->tune_pending = false;
+            set_launch_config(s, c);
+            return SP_OK;
+        }
+    if (steps_per_launch == 1 && variant == 0) {  // the default is always available
+        s->tune_pending = false;
+        set_launch_config(s, {1, 0});
+        return SP_OK;
+    }
+    return fail(SP_EINVAL, "launch configuration (%d steps per launch, family %d) is not available for this grid",
+                steps_per_launch, variant);
 }
 
 extern "C" int sp_launch_config(const sp_sim *s, int *steps_per_launch, int *variant) {

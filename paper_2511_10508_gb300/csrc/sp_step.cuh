@@ -8,6 +8,7 @@
 // step is one read and one write of each field:
 //   step2d_batch_kernel  2D, FP64: shared-memory rings, batches of rows
 //   step2d_tile_kernel   2D, FP32/BF16: one CTA per tile, tile + halo fetched with cp.async
+//   step2d_warp_kernel   2D, FP32/BF16: one warp per column strip, rows in registers
 //   step3d_kernel        3D, FP64: shared-memory plane rings
 //   step3d_zreg_kernel   3D, FP64, 27-point: z-streaming with register queues
 //   step3d_vec_kernel    3D, FP32/BF16: plane rings of 16-byte chunks
@@ -532,6 +533,167 @@ __device__ __forceinline__ void box3d(const T *in0, const T *in1, T *out0, T *ou
                 out[NF - 1][o] = from_c<T>(vn);
             }
         }
+    }
+}
+
+// ===================================================== 2D, warp rows ==
+//
+// FP32 / BF16-storage 2D kernel without shared memory or barriers.  A warp
+// owns a strip of 32 x V columns (V = one 16-byte vector per lane) and streams
+// down the rows of a segment.  Lanes 0 and 31 only supply halo columns; lanes
+// 1..30 produce the 30 x V output columns of the strip.  The x neighbours of a
+// lane's vector come from the adjacent lanes by warp shuffles, the y
+// neighbours from a register window of the last 2r+1 rows (phi, and mu for
+// Cahn-Hilliard).  The row loop is unrolled by the window length so that the
+// window rotates by renaming registers.  Rows arrive through a per-warp ring of
+// D rows in shared memory filled by cp.async (each lane copies and later reads
+// only its own 16 bytes, so no barrier is needed), keeping D-1 rows of loads in
+// flight per warp.  Same expressions in the same order as the other FP32
+// kernels, so results are identical to them bit for bit.
+//
+// Requirements (checked by the launcher): nx a multiple of V and 16-byte
+// aligned field pointers, so that every vector, wrapped or not, is aligned.
+template <int MODEL, int ST, typename T>
+struct Step2dWarpShape {
+    typedef typename Cmp<T>::type C;
+    static constexpr int r = StencilInfo<ST>::r;
+    static constexpr int V = 16 / (int)sizeof(T);
+    static constexpr int RIN = (MODEL == CH) ? 2 * r : r;
+    static constexpr int NF = (MODEL == GS) ? 2 : 1;
+    static constexpr int U = 2 * r + 1;        // window rows = unroll = prefetch depth
+    static constexpr int XW = V + 2 * r;       // a row of the window: own vector plus r halo each side
+    static constexpr int OUT_COLS = 30 * V;    // output columns per strip
+    static constexpr int D = 8;                // rows in the per-warp load ring
+    static constexpr size_t warp_smem = (size_t)D * NF * 32 * 16;
+    static_assert(V >= 2 * r, "the halo lanes must cover the mu halo");
+};
+
+template <int MODEL, int ST, typename T, int NT>
+__global__ void __launch_bounds__(NT) step2d_warp_kernel(StepArgs a, int strips, long long rows_per_warp) {
+    typedef Step2dWarpShape<MODEL, ST, T> Sh;
+    typedef typename Sh::C C;
+    typedef uint4 W;
+    constexpr int r = Sh::r, V = Sh::V, RIN = Sh::RIN, NF = Sh::NF, U = Sh::U, XW = Sh::XW, D = Sh::D;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    W *ring = reinterpret_cast<W *>(smem_raw) + (size_t)(threadIdx.x >> 5) * D * NF * 32;  // [D][NF][32]
+
+    const ConstsC<C> k(a.k, a.kf);
+    const int nx = a.nx, ny = a.ny;
+    const int lane = threadIdx.x & 31;
+    const long long wid = (long long)blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
+    const T *in[2] = {static_cast<const T *>(a.in0), static_cast<const T *>(a.in1)};
+    T *out[2] = {static_cast<T *>(a.out0), static_cast<T *>(a.out1)};
+
+    long long g0 = wid * rows_per_warp;
+    const long long gend = min(g0 + rows_per_warp, (long long)strips * ny);
+    while (g0 < gend) {
+        const int strip = (int)(g0 / ny);
+        const int y0 = (int)(g0 - (long long)strip * ny);
+        const int y1 = (int)min((long long)ny, (long long)y0 + (gend - g0));
+        g0 += y1 - y0;
+        const int col = strip * Sh::OUT_COLS + (lane - 1) * V;  // first column of this lane
+        const int colw = wrap_idx(col, nx);
+        const bool store = lane >= 1 && lane <= 30 && col < nx;
+        const int jbeg = y0 - RIN;
+        const int n = (y1 - y0) + 2 * RIN;
+
+        // row i of the segment goes to ring slot i % D; one cp.async group per row
+        auto issue = [&](int i) {
+            if (i < n) {
+                const size_t off = (size_t)wrap_idx(jbeg + i, ny) * nx + colw;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) cp_async16(&ring[((i % D) * NF + f) * 32 + lane], in[f] + off);
+            }
+            cp_async_commit();  // empty groups keep the count uniform
+        };
+#pragma unroll
+        for (int s = 0; s < D - 1; ++s) issue(s);
+
+        C ph[NF][U][XW];
+        C mu[MODEL == CH ? U : 1][XW];
+        (void)mu;
+        for (int i0 = 0; i0 < n; i0 += U) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + u;
+                if (i < n) {
+                    const int j = jbeg + i;
+                    // the slot read in the previous iteration is refilled; row i has landed
+                    issue(i + D - 1);
+                    cp_async_wait<D - 1>();
+                    // unpack row j and extend it with the neighbouring lanes' edge values
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        union { W w; T t[V]; } raw;
+                        raw.w = ring[((i % D) * NF + f) * 32 + lane];
+                        C *row = ph[f][u];
+#pragma unroll
+                        for (int c = 0; c < V; ++c) row[r + c] = to_c(raw.t[c]);
+#pragma unroll
+                        for (int h = 0; h < r; ++h) {
+                            row[h] = __shfl_up_sync(FULL, row[V + h], 1);
+                            row[r + V + h] = __shfl_down_sync(FULL, row[r + h], 1);
+                        }
+                    }
+                    // window slot of the row `m` iterations back
+#define SLOT(m) ((u - (m) + 4 * U) % U)
+                    if constexpr (MODEL == CH) {
+                        if (i >= 2 * r) {
+                            // mu of row j - r
+                            C *m = mu[u];
+#pragma unroll
+                            for (int c = 0; c < V; ++c) {
+                                auto P = [&](int dx, int dy, int) -> C { return ph[0][SLOT(r - dy)][r + c + dx]; };
+                                m[r + c] = ch_mu<C>(ph[0][SLOT(r)][r + c], stencil_sum<ST, C>(P), k);
+                            }
+#pragma unroll
+                            for (int h = 0; h < r; ++h) {
+                                m[h] = __shfl_up_sync(FULL, m[V + h], 1);
+                                m[r + V + h] = __shfl_down_sync(FULL, m[r + h], 1);
+                            }
+                            if (i >= 4 * r) {
+                                // output row j - 2r from mu rows j - 3r .. j - r
+                                C o[V];
+#pragma unroll
+                                for (int c = 0; c < V; ++c) {
+                                    auto Pm = [&](int dx, int dy, int) -> C { return mu[SLOT(r - dy)][r + c + dx]; };
+                                    o[c] = ch_update<C>(ph[0][SLOT(2 * r)][r + c], stencil_sum<ST, C>(Pm), k);
+                                }
+                                if (store) store_vec<T, V>(out[0] + (size_t)(j - 2 * r) * nx + col, o);
+                            }
+                        }
+                    } else {
+                        if (i >= 2 * r) {
+                            // output row j - r
+                            C o0[V], o1[V];
+#pragma unroll
+                            for (int c = 0; c < V; ++c) {
+                                auto P0 = [&](int dx, int dy, int) -> C { return ph[0][SLOT(r - dy)][r + c + dx]; };
+                                const C S0 = stencil_sum<ST, C>(P0);
+                                const C p0 = ph[0][SLOT(r)][r + c];
+                                if constexpr (MODEL == AC) {
+                                    o0[c] = ac_update<C>(p0, S0, k);
+                                } else {
+                                    auto P1 = [&](int dx, int dy, int) -> C {
+                                        return ph[NF - 1][SLOT(r - dy)][r + c + dx];
+                                    };
+                                    gs_update<C>(p0, ph[NF - 1][SLOT(r)][r + c], S0, stencil_sum<ST, C>(P1), k, o0[c],
+                                                 o1[c]);
+                                }
+                            }
+                            if (store) {
+                                const size_t o = (size_t)(j - r) * nx + col;
+                                store_vec<T, V>(out[0] + o, o0);
+                                if constexpr (MODEL == GS) store_vec<T, V>(out[NF - 1] + o, o1);
+                            }
+                        }
+                    }
+#undef SLOT
+                }
+            }
+        }
+        cp_async_wait<0>();  // the ring is reused by the next segment
     }
 }
 

@@ -96,6 +96,28 @@ cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
         ctas = (total + rows - 1) / rows;
         kern<<<(unsigned)ctas, B::NT, Sh::smem_bytes, s>>>(a, strips, rows);
     } else if constexpr (StencilInfo<ST>::dims == 2) {
+        typedef Step2dWarpShape<MODEL, ST, T> WS;
+        const bool aligned = ((uintptr_t)a.in0 | (uintptr_t)a.in1 | (uintptr_t)a.out0 | (uintptr_t)a.out1) % 16 == 0;
+        if (g_step_variant == 0 && a.nx % WS::V == 0 && aligned) {
+            // FP32 / BF16: one warp per column strip, persistent equal shares of rows
+            constexpr int NT = 256;
+            auto kern = step2d_warp_kernel<MODEL, ST, T, NT>;
+            constexpr size_t smem = WS::warp_smem * (NT / 32);
+            static const int occ = [&] {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                int o = 1;
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT, smem);
+                return o;
+            }();
+            const int strips = (a.nx + WS::OUT_COLS - 1) / WS::OUT_COLS;
+            const long long total = (long long)strips * a.ny;
+            long long warps = (long long)n_sm * std::max(occ, 1) * (NT / 32);
+            warps = std::max(1LL, std::min(warps, total / kMinRun));
+            const long long rows = (total + warps - 1) / warps;
+            warps = (total + rows - 1) / rows;
+            kern<<<(unsigned)((warps + NT / 32 - 1) / (NT / 32)), NT, smem, s>>>(a, strips, rows);
+            return cudaGetLastError();
+        }
         // FP32 / BF16: one CTA per 128 x 32 tile
         constexpr int BX = 128, BY = 32, NT = 256;
         typedef Step2dTileShape<MODEL, ST, T, BX, BY> Sh;

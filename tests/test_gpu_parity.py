@@ -352,3 +352,46 @@ def test_autotune_keeps_results(sp, model, shape, dtype, st):
             assert np.array_equal(ra, rv)
         else:
             assert np.array_equal(ra, O.step(model, st, ic, dt=dt, prm=oparams(prm), nsteps=n))
+
+
+@pytest.mark.parametrize("shape", [(70, 296), (45, 64), (9, 8), (130, 488)])
+@pytest.mark.parametrize("model,st", CASES_2D)
+@pytest.mark.parametrize("dtype", [1, 2])
+def test_2d_kernel_families_agree(sp, dtype, model, st, shape):
+    """2D FP32 / BF16 single steps: the warp-strip kernel (family 0; needs nx a
+    multiple of the 16-byte vector) and the shared-memory tile kernel (family 1)
+    evaluate the same expressions, so they agree bit for bit.  Shapes: two strips
+    plus a ragged one, a grid narrower than one strip, nx equal to one vector,
+    and several strips with rows split across warps."""
+    outs = []
+    for variant in (0, 1):
+        sim, dt = make(sp, model, shape, st, dtype=dtype)
+        with sim:
+            sim.launch_config = (1, variant)
+            assert sim.launch_config == (1, variant)
+            sim.step(13)
+            outs.append([sim.read(f, as_f64=False) for f in range(2 if model == 2 else 1)])
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+    if dtype == 1:
+        ic = oracle_ic(model, shape, sim.prm)
+        if model == 2:
+            ref = O.step(O.GS, st, ic[0], ic[1], dt=dt, prm=oparams(sim.prm), nsteps=13)[0]
+        else:
+            ref = O.step(model, st, ic, dt=dt, prm=oparams(sim.prm), nsteps=13)
+        assert O.rel_l2(outs[0][0].astype(np.float64), ref) < TOL[1]
+
+
+def test_set_launch_config_rejects_unavailable(sp):
+    sim, _ = make(sp, 1, (64, 64), 0, dtype=0)
+    with sim:
+        with pytest.raises(sp.SpError):
+            sim.launch_config = (2, 0)  # FP64 has no temporal blocking
+        with pytest.raises(sp.SpError):
+            sim.launch_config = (1, 7)
+        sim.launch_config = (1, 1)
+        assert sim.launch_config == (1, 1)
+    sim, _ = make(sp, 1, (20, 24, 28), 3, dtype=1)
+    with sim:
+        with pytest.raises(sp.SpError):
+            sim.launch_config = (1, 1)  # 3D FP32 has one family
