@@ -569,7 +569,7 @@ struct Step2dWarpShape {
 };
 
 template <int MODEL, int ST, typename T, int NT>
-__global__ void __launch_bounds__(NT) step2d_warp_kernel(StepArgs a, int strips, long long rows_per_warp) {
+__global__ void __launch_bounds__(NT) step2d_warp_kernel(StepArgs a, int strips, int groups, long long rows_per_cta) {
     typedef Step2dWarpShape<MODEL, ST, T> Sh;
     typedef typename Sh::C C;
     typedef uint4 W;
@@ -581,17 +581,23 @@ __global__ void __launch_bounds__(NT) step2d_warp_kernel(StepArgs a, int strips,
     const ConstsC<C> k(a.k, a.kf);
     const int nx = a.nx, ny = a.ny;
     const int lane = threadIdx.x & 31;
-    const long long wid = (long long)blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
+    // The warps of a CTA take adjacent strips (a group) over the same rows, so a
+    // CTA reads contiguous spans of each row and the strips' overlapping halo
+    // columns are shared through the caches.  CTAs own equal shares of the
+    // flattened (group, row) space.
+    const int wpc = blockDim.x >> 5, warp = threadIdx.x >> 5;
     const T *in[2] = {static_cast<const T *>(a.in0), static_cast<const T *>(a.in1)};
     T *out[2] = {static_cast<T *>(a.out0), static_cast<T *>(a.out1)};
 
-    long long g0 = wid * rows_per_warp;
-    const long long gend = min(g0 + rows_per_warp, (long long)strips * ny);
+    long long g0 = (long long)blockIdx.x * rows_per_cta;
+    const long long gend = min(g0 + rows_per_cta, (long long)groups * ny);
     while (g0 < gend) {
-        const int strip = (int)(g0 / ny);
-        const int y0 = (int)(g0 - (long long)strip * ny);
+        const int group = (int)(g0 / ny);
+        const int y0 = (int)(g0 - (long long)group * ny);
         const int y1 = (int)min((long long)ny, (long long)y0 + (gend - g0));
         g0 += y1 - y0;
+        const int strip = group * wpc + warp;
+        if (strip >= strips) continue;
         const int col = strip * Sh::OUT_COLS + (lane - 1) * V;  // first column of this lane
         const int colw = wrap_idx(col, nx);
         const bool store = lane >= 1 && lane <= 30 && col < nx;

@@ -99,23 +99,28 @@ cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
         typedef Step2dWarpShape<MODEL, ST, T> WS;
         const bool aligned = ((uintptr_t)a.in0 | (uintptr_t)a.in1 | (uintptr_t)a.out0 | (uintptr_t)a.out1) % 16 == 0;
         if (g_step_variant == 0 && a.nx % WS::V == 0 && aligned) {
-            // FP32 / BF16: one warp per column strip, persistent equal shares of rows
+            // FP32 / BF16: one warp per column strip, up to 8 adjacent strips per
+            // CTA, persistent equal shares of (strip group, row)
             constexpr int NT = 256;
             auto kern = step2d_warp_kernel<MODEL, ST, T, NT>;
-            constexpr size_t smem = WS::warp_smem * (NT / 32);
-            static const int occ = [&] {
-                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                int o = 1;
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT, smem);
-                return o;
+            static const bool attr = [&] {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(WS::warp_smem * (NT / 32)));
+                return true;
             }();
+            (void)attr;
             const int strips = (a.nx + WS::OUT_COLS - 1) / WS::OUT_COLS;
-            const long long total = (long long)strips * a.ny;
-            long long warps = (long long)n_sm * std::max(occ, 1) * (NT / 32);
-            warps = std::max(1LL, std::min(warps, total / kMinRun));
-            const long long rows = (total + warps - 1) / warps;
-            warps = (total + rows - 1) / rows;
-            kern<<<(unsigned)((warps + NT / 32 - 1) / (NT / 32)), NT, smem, s>>>(a, strips, rows);
+            const int wpc = std::min(NT / 32, strips);
+            const size_t smem = WS::warp_smem * wpc;
+            int occ = 1;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * wpc, smem);
+            const int groups = (strips + wpc - 1) / wpc;
+            const long long total = (long long)groups * a.ny;
+            long long ctas = (long long)n_sm * std::max(occ, 1);
+            ctas = std::max(1LL, std::min(ctas, total / kMinRun));
+            const long long rows = (total + ctas - 1) / ctas;
+            ctas = (total + rows - 1) / rows;
+            kern<<<(unsigned)ctas, 32 * wpc, smem, s>>>(a, strips, groups, rows);
             return cudaGetLastError();
         }
         // FP32 / BF16: one CTA per 128 x 32 tile
