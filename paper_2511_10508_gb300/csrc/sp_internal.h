@@ -36,7 +36,8 @@ cudaError_t launch_step_bf16(int model, int stencil, const StepArgs &a, cudaStre
 // Kernel variant chosen per launch: 0 = the default for the grid, 1 = the
 // alternative family (2D FP64: small tiles instead of strips, or strips instead
 // of small tiles for grids up to 1024^2; 2D FP32/BF16 single steps: shared-
-// memory tiles instead of warp strips; 3D FP64 27-point: shared-memory plane
+// memory tiles instead of warp strips; 3D FP32/BF16: register-staged plane
+// rings instead of the cp.async ring; 3D FP64 27-point: shared-memory plane
 // rings instead of z-streaming).  Set around each launch by the runtime.
 extern thread_local int g_step_variant;
 

@@ -11,7 +11,8 @@
 //   step2d_warp_kernel   2D, FP32/BF16: one warp per column strip, rows in registers
 //   step3d_kernel        3D, FP64: shared-memory plane rings
 //   step3d_zreg_kernel   3D, FP64, 27-point: z-streaming with register queues
-//   step3d_vec_kernel    3D, FP32/BF16: plane rings of 16-byte chunks
+//   step3d_async_kernel  3D, FP32/BF16: cp.async plane ring, planes in flight
+//   step3d_vec_kernel    3D, FP32/BF16: plane rings of 16-byte chunks (any nx)
 #pragma once
 
 #include "sp_common.cuh"
@@ -563,7 +564,7 @@ struct Step2dWarpShape {
     static constexpr int U = 2 * r + 1;        // window rows = unroll = prefetch depth
     static constexpr int XW = V + 2 * r;       // a row of the window: own vector plus r halo each side
     static constexpr int OUT_COLS = 30 * V;    // output columns per strip
-    static constexpr int D = 8;                // rows in the per-warp load ring
+    static constexpr int D = (NF == 1 && sizeof(T) == 2) ? 12 : 8;  // rows in the per-warp load ring
     static constexpr size_t warp_smem = (size_t)D * NF * 32 * 16;
     static_assert(V >= 2 * r, "the halo lanes must cover the mu halo");
 };
@@ -1055,6 +1056,230 @@ __global__ void __launch_bounds__(NT) step3d_zreg_kernel(StepArgs a, int tiles_x
             }
         }
         __syncthreads();  // the buffers are reused by the next segment
+    }  // segments
+}
+
+// ================================================== 3D, asynchronous ring ==
+//
+// FP32 / BF16-storage 3D kernel.  A thread owns one 16-byte chunk of V cells
+// (V = 4 for FP32, 8 for BF16) of a TX x TY tile and the CTA streams along z.
+// Input planes (tile plus halo: HIN rows of NCH = TX/V + 2 chunks, kept in the
+// storage type) arrive through a ring of D planes in shared memory filled by
+// cp.async, P planes ahead of the one being computed; each thread copies its
+// own chunks and a barrier per plane publishes them.  Cahn-Hilliard computes mu
+// chunk-wise over the tile rows plus r halo rows and the two halo chunks (FP32,
+// a ring of 2r+1 planes) behind a second barrier.  Stencil rows are read only
+// where the stencil has taps (x halos only on the centre row of the cross
+// stencils).  The same expressions in the same order as the other FP32
+// kernels, so results are identical to them bit for bit.
+//
+// Requirements (checked by the launcher): nx a multiple of V and 16-byte
+// aligned field pointers, so that every chunk, wrapped or not, is one aligned
+// 16-byte copy.
+template <int MODEL, int ST, typename T, int TXT, int TY>
+struct Step3dAsyncShape {
+    typedef typename Cmp<T>::type C;
+    static constexpr int V = 16 / (int)sizeof(T);
+    static constexpr int r = StencilInfo<ST>::r;
+    static constexpr int R = (MODEL == CH) ? 2 * r : r;
+    static_assert(R <= V, "halo wider than one chunk");
+    static_assert(MODEL != CH || V >= 2 * r, "halo chunk must cover the mu halo");
+    static constexpr int TX = TXT * V, NT = TXT * TY;
+    static constexpr int NCH = TXT + 2;              // chunks per row (one halo chunk each side)
+    static constexpr int SW = NCH * V;               // row stride (cells)
+    static constexpr int HIN = TY + 2 * R, PIN = HIN * SW;
+    static constexpr int P = 3;                      // planes in flight
+    static constexpr int D = P + 2 * r + 1;          // input ring slots
+    static constexpr int HMU = TY + 2 * r, PMU = HMU * SW;
+    static constexpr int DMU = (MODEL == CH) ? 2 * r + 1 : 0;
+    static constexpr int NF = (MODEL == GS) ? 2 : 1;
+    static constexpr int EPT = (HIN * NCH + NT - 1) / NT;  // chunk copies per thread per field
+    static constexpr int GUARD = 16;                 // bytes before and after each region
+    static constexpr size_t in_bytes = sizeof(T) * (size_t)NF * D * PIN;
+    static constexpr size_t mu_off = GUARD + in_bytes + GUARD;
+    static constexpr size_t smem_bytes = mu_off + sizeof(C) * (size_t)DMU * PMU + GUARD;
+};
+
+// The V cells at p (16-byte aligned, a multiple of 16 bytes), widened to float.
+template <typename T, int V>
+__device__ __forceinline__ void lds_chunk(const T *p, float *w) {
+    constexpr int NQ = V * (int)sizeof(T) / 16;
+    static_assert(NQ * 16 == V * (int)sizeof(T), "whole 16-byte pieces");
+    union { uint4 q[NQ]; T t[V]; } u;
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) u.q[i] = reinterpret_cast<const uint4 *>(p)[i];
+#pragma unroll
+    for (int i = 0; i < V; ++i) w[i] = to_c(u.t[i]);
+}
+
+// Stencil sums and centre values of the V cells of chunk ci on row `row` of the
+// planes pl[0 .. 2r] (z offsets -r .. r), row stride SW cells.
+template <int ST, typename T, int V, int SW>
+__device__ __forceinline__ void async_chunk_sums(const T *const (&pl)[2 * StencilInfo<ST>::r + 1], int row, int ci,
+                                                 float (&S)[V], float (&ctr)[V]) {
+    constexpr int r = StencilInfo<ST>::r;
+    constexpr int W = V + 2 * r;
+    float w[2 * r + 1][2 * r + 1][W];
+#pragma unroll
+    for (int dz = -r; dz <= r; ++dz)
+#pragma unroll
+        for (int dy = -r; dy <= r; ++dy) {
+            const bool full = (ST == L27) || (dz == 0 && dy == 0);  // x taps on this row
+            if (ST == L27 || dz == 0 || dy == 0) {
+                const T *p = pl[dz + r] + (row + dy) * SW + ci * V;
+                float *wr = w[dz + r][dy + r];
+                lds_chunk<T, V>(p, wr + r);
+                if (full && r > 0) {
+                    float lq[V], rq[V];
+                    lds_chunk<T, V>(p - V, lq);
+                    lds_chunk<T, V>(p + V, rq);
+#pragma unroll
+                    for (int d = 0; d < r; ++d) {
+                        wr[d] = lq[V - r + d];
+                        wr[r + V + d] = rq[d];
+                    }
+                }
+            }
+        }
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        auto Pf = [&](int dx, int dy, int dz) -> float { return w[dz + r][dy + r][r + j + dx]; };
+        S[j] = stencil_sum<ST, float>(Pf);
+        ctr[j] = w[r][r][r + j];
+    }
+}
+
+template <int MODEL, int ST, typename T, int TXT, int TY>
+__global__ void __launch_bounds__(TXT * TY) step3d_async_kernel(StepArgs a, int tiles_x, int tiles_y,
+                                                                 long long planes_per_cta) {
+    typedef Step3dAsyncShape<MODEL, ST, T, TXT, TY> Sh;
+    typedef typename Sh::C C;
+    constexpr int V = Sh::V, r = Sh::r, R = Sh::R, TX = Sh::TX, NT = Sh::NT, NCH = Sh::NCH, SW = Sh::SW;
+    constexpr int HIN = Sh::HIN, PIN = Sh::PIN, P = Sh::P, D = Sh::D, HMU = Sh::HMU, PMU = Sh::PMU;
+    constexpr int DMU = Sh::DMU, NF = Sh::NF, EPT = Sh::EPT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s_in = reinterpret_cast<T *>(smem_raw + Sh::GUARD);      // [NF][D][PIN]
+    C *s_mu = reinterpret_cast<C *>(smem_raw + Sh::mu_off);     // [DMU][PMU]
+
+    const ConstsC<C> k(a.k, a.kf);
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int t = threadIdx.x;
+    const size_t plane = (size_t)nx * (size_t)ny;
+    const T *in[2] = {static_cast<const T *>(a.in0), static_cast<const T *>(a.in1)};
+    T *out[2] = {static_cast<T *>(a.out0), static_cast<T *>(a.out1)};
+    const int tc = t % TXT, ty = t / TXT;  // output chunk of this thread
+
+    long long g0 = (long long)blockIdx.x * planes_per_cta;
+    const long long gend = min(g0 + planes_per_cta, (long long)tiles_x * tiles_y * nz);
+    while (g0 < gend) {
+        const int tile = (int)(g0 / nz);
+        const int z0 = (int)(g0 - (long long)tile * nz);
+        const int z1 = (int)min((long long)nz, (long long)z0 + (gend - g0));
+        g0 += z1 - z0;
+        const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+        const int nplanes = (z1 - z0) + 2 * R;
+
+        // global (plane-relative) offsets of this thread's chunk copies, or -1
+        int goff[EPT];
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            const int q = t + e * NT;
+            goff[e] = -1;
+            if (q < HIN * NCH) {
+                const int yi = q / NCH, ci = q - yi * NCH;
+                goff[e] = wrap_idx(y0 - R + yi, ny) * nx + wrap_idx(x0 - V + ci * V, nx);
+            }
+        }
+        auto issue = [&](int j) {
+            if (j < nplanes) {
+                const size_t zoff = (size_t)wrap_idx(z0 - R + j, nz) * plane;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    T *slot = s_in + ((size_t)f * D + j % D) * PIN;
+#pragma unroll
+                    for (int e = 0; e < EPT; ++e)
+                        if (goff[e] >= 0) cp_async16(slot + (t + e * NT) * V, in[f] + zoff + goff[e]);
+                }
+            }
+            cp_async_commit();  // empty groups keep the count uniform
+        };
+        auto in_plane = [&](int f, int j) -> const T * { return s_in + ((size_t)f * D + j % D) * PIN; };
+
+#pragma unroll
+        for (int j = 0; j < P; ++j) issue(j);
+        for (int j = 0; j < nplanes; ++j) {
+            cp_async_wait<P - 1>();
+            __syncthreads();  // plane j complete for every thread; planes <= j-1 no longer read
+            issue(j + P);
+            if constexpr (MODEL == CH) {
+                if (j >= 2 * r) {
+                    // mu of plane j - r over the tile rows plus r halo rows and the halo chunks
+                    C *mu = s_mu + (size_t)((j - r) % DMU) * PMU;
+                    const T *pl[2 * r + 1];
+#pragma unroll
+                    for (int d = 0; d <= 2 * r; ++d) pl[d] = in_plane(0, j - 2 * r + d);
+                    for (int q = t; q < HMU * NCH; q += NT) {
+                        const int ym = q / NCH, ci = q - ym * NCH;
+                        float S[V], p[V];
+                        async_chunk_sums<ST, T, V, SW>(pl, ym + r, ci, S, p);
+                        float m[V];
+#pragma unroll
+                        for (int i = 0; i < V; ++i) m[i] = ch_mu<C>(p[i], S[i], k);
+#pragma unroll
+                        for (int i = 0; i < V; i += 4)
+                            *reinterpret_cast<float4 *>(mu + ym * SW + ci * V + i) =
+                                make_float4(m[i], m[i + 1], m[i + 2], m[i + 3]);
+                    }
+                }
+                __syncthreads();
+                if (j >= 4 * r) {
+                    // output plane j - 2r from mu planes j - 3r .. j - r
+                    const int zo = z0 - 4 * r + j;
+                    const int x = x0 + tc * V, y = y0 + ty;
+                    if (x < nx && y < ny) {
+                        const C *plm[2 * r + 1];
+#pragma unroll
+                        for (int d = 0; d <= 2 * r; ++d) plm[d] = s_mu + (size_t)((j - 3 * r + d) % DMU) * PMU;
+                        float S[V], dummy[V], p[V], o[V];
+                        async_chunk_sums<ST, C, V, SW>(plm, ty + r, tc + 1, S, dummy);
+                        lds_chunk<T, V>(in_plane(0, j - 2 * r) + (ty + R) * SW + (tc + 1) * V, p);
+#pragma unroll
+                        for (int i = 0; i < V; ++i) o[i] = ch_update<C>(p[i], S[i], k);
+                        store_vec<T, V>(out[0] + (size_t)zo * plane + (size_t)y * nx + x, o);
+                    }
+                }
+            } else {
+                if (j >= 2 * r) {
+                    // output plane j - r
+                    const int zo = z0 - 2 * r + j;
+                    const int x = x0 + tc * V, y = y0 + ty;
+                    if (x < nx && y < ny) {
+                        const T *pl0[2 * r + 1];
+#pragma unroll
+                        for (int d = 0; d <= 2 * r; ++d) pl0[d] = in_plane(0, j - 2 * r + d);
+                        float S0[V], p0[V], o0[V], o1[V];
+                        async_chunk_sums<ST, T, V, SW>(pl0, ty + r, tc + 1, S0, p0);
+                        if constexpr (MODEL == AC) {
+#pragma unroll
+                            for (int i = 0; i < V; ++i) o0[i] = ac_update<C>(p0[i], S0[i], k);
+                        } else {
+                            const T *pl1[2 * r + 1];
+#pragma unroll
+                            for (int d = 0; d <= 2 * r; ++d) pl1[d] = in_plane(NF - 1, j - 2 * r + d);
+                            float S1[V], p1[V];
+                            async_chunk_sums<ST, T, V, SW>(pl1, ty + r, tc + 1, S1, p1);
+#pragma unroll
+                            for (int i = 0; i < V; ++i) gs_update<C>(p0[i], p1[i], S0[i], S1[i], k, o0[i], o1[i]);
+                        }
+                        const size_t o = (size_t)zo * plane + (size_t)y * nx + x;
+                        store_vec<T, V>(out[0] + o, o0);
+                        if constexpr (MODEL == GS) store_vec<T, V>(out[NF - 1] + o, o1);
+                    }
+                }
+            }
+        }
+        cp_async_wait<0>();
+        __syncthreads();  // the rings are reused by the next segment
     }  // segments
 }
 

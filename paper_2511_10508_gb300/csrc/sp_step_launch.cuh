@@ -135,7 +135,26 @@ cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
         dim3 grid((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY);
         kern<<<grid, NT, Sh::smem_bytes, s>>>(a);
     } else if constexpr (!std::is_same<T, double>::value) {
-        // FP32 / BF16 3D: vectorised plane kernel, 64 x 32 tiles
+        constexpr int ATX = 16, ATY = 16;
+        typedef Step3dAsyncShape<MODEL, ST, T, ATX, ATY> AS;
+        const bool aligned = ((uintptr_t)a.in0 | (uintptr_t)a.in1 | (uintptr_t)a.out0 | (uintptr_t)a.out1) % 16 == 0;
+        if (g_step_variant == 0 && a.nx % AS::V == 0 && aligned) {
+            // FP32 / BF16 3D: cp.async plane ring with planes in flight
+            auto kern = step3d_async_kernel<MODEL, ST, T, ATX, ATY>;
+            static const int occ = [&] {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AS::smem_bytes);
+                int o = 1;
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, AS::NT, AS::smem_bytes);
+                return o;
+            }();
+            const int tx = (a.nx + AS::TX - 1) / AS::TX, ty = (a.ny + ATY - 1) / ATY;
+            const long long ctas = persistent_ctas((long long)tx * ty * a.nz, occ, n_sm);
+            const long long planes = ((long long)tx * ty * a.nz + ctas - 1) / ctas;
+            kern<<<(unsigned)(((long long)tx * ty * a.nz + planes - 1) / planes), AS::NT, AS::smem_bytes, s>>>(
+                a, tx, ty, planes);
+            return cudaGetLastError();
+        }
+        // FP32 / BF16 3D, any nx: vectorised plane kernel, 64 x 32 tiles
         constexpr int TXT = 16, TYT = 32;
         typedef Step3dVecShape<MODEL, ST, T, TXT, TYT> Sh;
         auto kern = step3d_vec_kernel<MODEL, ST, T, TXT, TYT>;
