@@ -33,12 +33,13 @@ cudaError_t launch_step_bf16(int model, int stencil, const StepArgs &a, cudaStre
 // kernel is at the HBM bound (FP32 Gray-Scott 32768^2: 1 step 0.99 of the copy
 // bandwidth, 2 steps 1.31 effective, 4 steps 1.19); Cahn-Hilliard and BF16
 // storage are limited by on-chip work, so extra halo work only slows them.
-// Kernel variant chosen per launch: 0 = the default for the grid, 1 = the
-// alternative family (2D FP64: small tiles instead of strips, or strips instead
+// Kernel variant chosen per launch: 0 = the default for the grid, 1 (and 2) =
+// alternative families (2D FP64: small tiles instead of strips, or strips instead
 // of small tiles for grids up to 1024^2; 2D FP32/BF16 single steps: shared-
-// memory tiles instead of warp strips; 3D FP32/BF16: register-staged plane
-// rings instead of the cp.async ring; 3D FP64 27-point: shared-memory plane
-// rings instead of z-streaming).  Set around each launch by the runtime.
+// memory tiles instead of warp strips; 3D FP32/BF16: 1 = cp.async plane ring,
+// 2 = register-staged plane rings, instead of warp rows; 3D FP64 27-point:
+// shared-memory plane rings instead of z-streaming).  Set around each launch by
+// the runtime.
 extern thread_local int g_step_variant;
 
 inline int steps_per_launch(int dims, int dtype, int model, int requested) {

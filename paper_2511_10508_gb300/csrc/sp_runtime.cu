@@ -361,9 +361,10 @@ static std::vector<TuneChoice> tune_candidates(const sp_sim *s) {
     if (s->dims == 2 && s->dtype != SP_F64) {
         c.push_back({1, 1});
         for (int spl : {1, 2, 4}) c.push_back({spl, 0});
-    } else if (s->dims == 2 || s->dtype != SP_F64 || s->stencil == SP_LAP_27) {
+    } else if (s->dims == 2 || s->stencil == SP_LAP_27 || s->dtype != SP_F64) {
         c.push_back({1, 0});
         c.push_back({1, 1});
+        if (s->dims == 3 && s->dtype != SP_F64) c.push_back({1, 2});
     } else {
         c.push_back({1, 0});
     }

@@ -11,6 +11,7 @@
 //   step2d_warp_kernel   2D, FP32/BF16: one warp per column strip, rows in registers
 //   step3d_kernel        3D, FP64: shared-memory plane rings
 //   step3d_zreg_kernel   3D, FP64, 27-point: z-streaming with register queues
+//   step3d_wr_kernel     3D, FP32/BF16: warp per tile row, z in register queues
 //   step3d_async_kernel  3D, FP32/BF16: cp.async plane ring, planes in flight
 //   step3d_vec_kernel    3D, FP32/BF16: plane rings of 16-byte chunks (any nx)
 #pragma once
@@ -1059,6 +1060,283 @@ __global__ void __launch_bounds__(NT) step3d_zreg_kernel(StepArgs a, int tiles_x
     }  // segments
 }
 
+// ===================================================== 3D, warp rows ==
+//
+// FP32 / BF16-storage 3D kernel built like the 2D warp-strip kernel.  Warp w
+// of a CTA owns input row w of a tile (TY output rows plus R halo rows on each
+// side) and lane l the chunk l of 4 cells of that row (16 bytes FP32, 8 bytes
+// BF16): lanes 1..30 are the tile's 30 chunks, lanes 0 and 31 halo chunks.  Planes stream along z through a ring
+// of P+1 planes in shared memory filled by cp.async (each thread copies its own
+// chunk).  Neighbours: x from the adjacent lanes (warp shuffles), y from the
+// rows above and below in shared memory, z from per-thread register queues of
+// the previous planes' values and in-plane partial sums (the stencil's fixed
+// order is a sum over planes of in-plane partial sums, see sp_common.cuh).  A
+// Cahn-Hilliard thread keeps the mu of its own chunk in registers and shares
+// it through one mu plane in shared memory.  Same expressions in the same
+// order as the other FP32 kernels: identical results bit for bit.
+//
+// Requirements (checked by the launcher): nx a multiple of 4 and 16-byte
+// aligned field pointers.
+
+// Number of in-plane partial sums per plane.
+template <int ST> struct Planar { static constexpr int NP = (ST == L7) ? 1 : 2; };
+
+// In-plane partial sums of plane z for the V cells of a chunk.  row(dy) points
+// at a row extended by r cells on each side (index r + c is cell c).
+template <int ST, int V, int XW, typename RowFn>
+__device__ __forceinline__ void planar_sums(const RowFn &row, float (&ps)[Planar<ST>::NP][V]) {
+    const float *w0 = row(0);
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
+        const int x = StencilInfo<ST>::r + c;
+        if constexpr (ST == L7) {
+            ps[0][c] = (w0[x - 1] + w0[x + 1]) + (row(-1)[x] + row(1)[x]);
+        } else if constexpr (ST == L27) {
+            const float *wm = row(-1), *wp = row(1);
+            ps[0][c] = (w0[x - 1] + w0[x + 1]) + (wm[x] + wp[x]);
+            ps[1][c] = (wm[x - 1] + wm[x + 1]) + (wp[x - 1] + wp[x + 1]);
+        } else {  // L13X4
+            ps[0][c] = (w0[x - 1] + w0[x + 1]) + (row(-1)[x] + row(1)[x]);
+            ps[1][c] = (w0[x - 2] + w0[x + 2]) + (row(-2)[x] + row(2)[x]);
+        }
+    }
+}
+
+// Stencil sum at the centre plane from the values f[k] and partial sums p[k]
+// of planes k = 0 .. 2r (z offsets -r .. r), cell c.
+template <int ST, typename FA, typename PA>
+__device__ __forceinline__ float planar_combine(const FA &f, const PA &p, int c) {
+    if constexpr (ST == L7) {
+        return FMA(-6.f, f(1)[c], p(1)[0][c] + (f(0)[c] + f(2)[c]));
+    } else if constexpr (ST == L27) {
+        const float F = p(1)[0][c] + (f(0)[c] + f(2)[c]);
+        const float E = p(1)[1][c] + (p(0)[0][c] + p(2)[0][c]);
+        const float K = p(0)[1][c] + p(2)[1][c];
+        return FMA(-128.f, f(1)[c], FMA(14.f, F, FMA(3.f, E, K)));
+    } else {  // L13X4
+        const float F1 = p(2)[0][c] + (f(1)[c] + f(3)[c]);
+        const float F2 = p(2)[1][c] + (f(0)[c] + f(4)[c]);
+        return FMA(-90.f, f(2)[c], FMA(16.f, F1, -F2));
+    }
+}
+
+template <int MODEL, int ST, typename T, int TY>
+struct Step3dWrShape {
+    typedef typename Cmp<T>::type C;
+    static constexpr int V = 4;                       // cells per lane (16 bytes FP32, 8 bytes BF16)
+    static constexpr int CB = V * (int)sizeof(T);     // chunk bytes
+    static constexpr int r = StencilInfo<ST>::r;
+    static constexpr int R = (MODEL == CH) ? 2 * r : r;
+    static_assert(V >= 2 * r, "a lane's chunk must cover the halo");
+    static constexpr int TXC = 30;                    // output chunks per tile row
+    static constexpr int TX = TXC * V;
+    static constexpr int HIN = TY + 2 * R;            // warps = input rows
+    static constexpr int NT = 32 * HIN;
+    static constexpr int XW = V + 2 * r;
+    static constexpr int NP = Planar<ST>::NP;
+    static constexpr int Q = 2 * r + 1;               // planes in a queue (incl. the newest)
+    static constexpr int P = 3;                       // planes in flight
+    static constexpr int NF = (MODEL == GS) ? 2 : 1;
+    static constexpr size_t plane_bytes = (size_t)HIN * 32 * CB;
+    static constexpr size_t in_bytes = (size_t)(P + 1) * NF * plane_bytes;
+    static constexpr size_t mu_bytes = (MODEL == CH) ? (size_t)HIN * 32 * V * sizeof(float) : 0;
+    static constexpr size_t smem_bytes = in_bytes + mu_bytes;
+};
+
+template <int MODEL, int ST, typename T, int TY>
+__global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT)
+    step3d_wr_kernel(StepArgs a, int tiles_x, int tiles_y, int segs) {
+    typedef Step3dWrShape<MODEL, ST, T, TY> Sh;
+    typedef float C;
+    constexpr int V = Sh::V, r = Sh::r, R = Sh::R, HIN = Sh::HIN, XW = Sh::XW, NP = Sh::NP, Q = Sh::Q;
+    constexpr int P = Sh::P, NF = Sh::NF, CB = Sh::CB;
+    constexpr unsigned FULL = 0xffffffffu;
+    typedef typename VecT<CB>::type W;                                      // one chunk
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    W *s_in = reinterpret_cast<W *>(smem_raw);                              // [P+1][NF][HIN][32]
+    float *s_mu = reinterpret_cast<float *>(smem_raw + Sh::in_bytes);      // [HIN][32][V]
+
+    const ConstsC<C> k(a.k, a.kf);
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const size_t plane = (size_t)nx * (size_t)ny;
+    const T *in[2] = {static_cast<const T *>(a.in0), static_cast<const T *>(a.in1)};
+    T *out[2] = {static_cast<T *>(a.out0), static_cast<T *>(a.out1)};
+    const bool mu_row = (MODEL == CH) && w >= r && w < HIN - r;
+    const bool out_row = w >= R && w < HIN - R;
+
+    // chunk of row `row` (this lane's column) in the input ring slot, widened
+    auto ring_chunk = [&](int slot, int f, int row, float *dst) {
+        union { W q; T t[V]; } u;
+        u.q = s_in[((size_t)(slot * NF + f) * HIN + row) * 32 + lane];
+#pragma unroll
+        for (int i = 0; i < V; ++i) dst[i] = to_c(u.t[i]);
+    };
+    // extend a row chunk held in ext[r .. r+V) with r cells from each neighbouring lane
+    auto extend = [&](float *ext) {
+#pragma unroll
+        for (int h = 0; h < r; ++h) {
+            ext[h] = __shfl_up_sync(FULL, ext[V + h], 1);
+            ext[r + V + h] = __shfl_down_sync(FULL, ext[r + h], 1);
+        }
+    };
+
+    const int tiles = tiles_x * tiles_y;
+    for (long long it = blockIdx.x; it < (long long)tiles * segs; it += gridDim.x) {
+        const int seg = (int)(it / tiles), tile = (int)(it - (long long)seg * tiles);
+        const int z0 = (int)((long long)seg * nz / segs), z1 = (int)((long long)(seg + 1) * nz / segs);
+        const int x0 = (tile % tiles_x) * Sh::TX, y0 = (tile / tiles_x) * TY;
+        const int n = (z1 - z0) + 2 * R;
+        const int col = x0 + (lane - 1) * V;                       // first cell of this lane's chunk
+        const size_t goff = (size_t)wrap_idx(y0 - R + w, ny) * nx + wrap_idx(col, nx);
+        const int yo = y0 - R + w;                                 // output row (if out_row)
+        const bool store = out_row && lane >= 1 && lane <= 30 && col < nx && yo < ny;
+
+        auto issue = [&](int j) {
+            if (j < n) {
+                const size_t zoff = (size_t)wrap_idx(z0 - R + j, nz) * plane;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    W *dst = &s_in[((size_t)((j % (P + 1)) * NF + f) * HIN + w) * 32 + lane];
+                    if constexpr (CB == 16) cp_async16(dst, in[f] + zoff + goff);
+                    else cp_async8(dst, in[f] + zoff + goff);
+                }
+            }
+            cp_async_commit();
+        };
+#pragma unroll
+        for (int j = 0; j < P; ++j) issue(j);
+
+        // shift-register queues: index k holds plane j - (Q-1) + k after plane j arrives
+        float qf[NF][Q][V], qp[NF][Q][NP][V];
+        float qm[MODEL == CH ? Q : 1][V], qmp[MODEL == CH ? Q : 1][NP][V];
+        (void)qm; (void)qmp;
+        auto f0q = [&](int kk) -> const float * { return qf[0][kk]; };
+        auto p0q = [&](int kk) -> const float(*)[V] { return qp[0][kk]; };
+        auto f1q = [&](int kk) -> const float * { return qf[NF - 1][kk]; };
+        auto p1q = [&](int kk) -> const float(*)[V] { return qp[NF - 1][kk]; };
+        auto mfq = [&](int kk) -> const float * { return qm[kk]; };
+        auto mpq = [&](int kk) -> const float(*)[V] { return qmp[kk]; };
+        (void)f1q; (void)p1q; (void)mfq; (void)mpq;
+
+        for (int j = 0; j < n; ++j) {
+            cp_async_wait<P - 1>();
+            __syncthreads();  // plane j published; plane j-1's slot and the mu plane are free
+            issue(j + P);
+            const int slot = j % (P + 1);
+            if ((MODEL == CH && mu_row) || (MODEL != CH && out_row)) {
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+#pragma unroll
+                    for (int kk = 0; kk < Q - 1; ++kk) {  // age the queues by one plane
+#pragma unroll
+                        for (int c = 0; c < V; ++c) {
+                            qf[f][kk][c] = qf[f][kk + 1][c];
+#pragma unroll
+                            for (int np = 0; np < NP; ++np) qp[f][kk][np][c] = qp[f][kk + 1][np][c];
+                        }
+                    }
+                    float ext[2 * r + 1][XW];
+                    ring_chunk(slot, f, w, ext[r] + r);
+                    extend(ext[r]);
+#pragma unroll
+                    for (int dy = 1; dy <= r; ++dy) {
+                        ring_chunk(slot, f, w - dy, ext[r - dy] + r);
+                        ring_chunk(slot, f, w + dy, ext[r + dy] + r);
+                        if constexpr (ST == L27) {
+                            extend(ext[r - dy]);
+                            extend(ext[r + dy]);
+                        }
+                    }
+                    auto row = [&](int dy) -> const float * { return ext[r + dy]; };
+                    planar_sums<ST, V, XW>(row, qp[f][Q - 1]);
+#pragma unroll
+                    for (int c = 0; c < V; ++c) qf[f][Q - 1][c] = ext[r][r + c];
+                }
+            }
+            // stencils of plane j - r from the queues (planes j - 2r .. j)
+            if constexpr (MODEL == CH) {
+                float mu[V];
+                if (mu_row && j >= 2 * r) {
+#pragma unroll
+                    for (int c = 0; c < V; ++c) mu[c] = ch_mu<C>(qf[0][r][c], planar_combine<ST>(f0q, p0q, c), k);
+#pragma unroll
+                    for (int i = 0; i < V; i += 4)
+                        *reinterpret_cast<float4 *>(&s_mu[((size_t)w * 32 + lane) * V + i]) =
+                            make_float4(mu[i], mu[i + 1], mu[i + 2], mu[i + 3]);
+                }
+                __syncthreads();  // mu plane j - r published
+                if (out_row && j >= 2 * r) {
+                    // phi of plane j - 2r (output centre) before the mu queue ages
+                    float pc[V];
+#pragma unroll
+                    for (int c = 0; c < V; ++c) pc[c] = qf[0][0][c];
+#pragma unroll
+                    for (int kk = 0; kk < Q - 1; ++kk) {
+#pragma unroll
+                        for (int c = 0; c < V; ++c) {
+                            qm[kk][c] = qm[kk + 1][c];
+#pragma unroll
+                            for (int np = 0; np < NP; ++np) qmp[kk][np][c] = qmp[kk + 1][np][c];
+                        }
+                    }
+                    float ext[2 * r + 1][XW];
+#pragma unroll
+                    for (int c = 0; c < V; ++c) ext[r][r + c] = mu[c];
+                    extend(ext[r]);
+#pragma unroll
+                    for (int dy = -r; dy <= r; ++dy) {
+                        if (dy == 0) continue;
+                        const float *src = &s_mu[((size_t)(w + dy) * 32 + lane) * V];
+#pragma unroll
+                        for (int i = 0; i < V; i += 4) {
+                            const float4 v4 = *reinterpret_cast<const float4 *>(src + i);
+                            ext[r + dy][r + i] = v4.x;
+                            ext[r + dy][r + i + 1] = v4.y;
+                            ext[r + dy][r + i + 2] = v4.z;
+                            ext[r + dy][r + i + 3] = v4.w;
+                        }
+                        if constexpr (ST == L27) extend(ext[r + dy]);
+                    }
+                    auto row = [&](int dy) -> const float * { return ext[r + dy]; };
+                    planar_sums<ST, V, XW>(row, qmp[Q - 1]);
+#pragma unroll
+                    for (int c = 0; c < V; ++c) qm[Q - 1][c] = mu[c];
+                    if (j >= 4 * r) {
+                        // output plane j - 2r from mu planes j - 3r .. j - r
+                        float o[V];
+#pragma unroll
+                        for (int c = 0; c < V; ++c) o[c] = ch_update<C>(pc[c], planar_combine<ST>(mfq, mpq, c), k);
+                        if (store)
+                            store_vec<T, V>(out[0] + (size_t)(z0 - 4 * r + j) * plane + (size_t)yo * nx + col, o);
+                    }
+                }
+            } else {
+                if (out_row && j >= 2 * r) {
+                    float o0[V], o1[V];
+#pragma unroll
+                    for (int c = 0; c < V; ++c) {
+                        const float S0 = planar_combine<ST>(f0q, p0q, c);
+                        const float p0 = qf[0][r][c];
+                        if constexpr (MODEL == AC) {
+                            o0[c] = ac_update<C>(p0, S0, k);
+                        } else {
+                            gs_update<C>(p0, qf[NF - 1][r][c], S0, planar_combine<ST>(f1q, p1q, c), k, o0[c], o1[c]);
+                        }
+                    }
+                    if (store) {
+                        const size_t o = (size_t)(z0 - 2 * r + j) * plane + (size_t)yo * nx + col;
+                        store_vec<T, V>(out[0] + o, o0);
+                        if constexpr (MODEL == GS) store_vec<T, V>(out[NF - 1] + o, o1);
+                    }
+                }
+            }
+        }
+        cp_async_wait<0>();
+        __syncthreads();  // the ring is reused by the next item
+    }
+}
+
 // ================================================== 3D, asynchronous ring ==
 //
 // FP32 / BF16-storage 3D kernel.  A thread owns one 16-byte chunk of V cells
@@ -1150,8 +1428,7 @@ __device__ __forceinline__ void async_chunk_sums(const T *const (&pl)[2 * Stenci
 }
 
 template <int MODEL, int ST, typename T, int TXT, int TY>
-__global__ void __launch_bounds__(TXT * TY) step3d_async_kernel(StepArgs a, int tiles_x, int tiles_y,
-                                                                 long long planes_per_cta) {
+__global__ void __launch_bounds__(TXT * TY) step3d_async_kernel(StepArgs a, int tiles_x, int tiles_y, int segs) {
     typedef Step3dAsyncShape<MODEL, ST, T, TXT, TY> Sh;
     typedef typename Sh::C C;
     constexpr int V = Sh::V, r = Sh::r, R = Sh::R, TX = Sh::TX, NT = Sh::NT, NCH = Sh::NCH, SW = Sh::SW;
@@ -1169,13 +1446,13 @@ __global__ void __launch_bounds__(TXT * TY) step3d_async_kernel(StepArgs a, int 
     T *out[2] = {static_cast<T *>(a.out0), static_cast<T *>(a.out1)};
     const int tc = t % TXT, ty = t / TXT;  // output chunk of this thread
 
-    long long g0 = (long long)blockIdx.x * planes_per_cta;
-    const long long gend = min(g0 + planes_per_cta, (long long)tiles_x * tiles_y * nz);
-    while (g0 < gend) {
-        const int tile = (int)(g0 / nz);
-        const int z0 = (int)(g0 - (long long)tile * nz);
-        const int z1 = (int)min((long long)nz, (long long)z0 + (gend - g0));
-        g0 += z1 - z0;
+    // Work items (z segment, tile), segment-major, handed out round by round:
+    // all CTAs stream the same z range at the same time, so the halo rows that
+    // neighbouring tiles share are still in L2 when the second tile reads them.
+    const int tiles = tiles_x * tiles_y;
+    for (long long it = blockIdx.x; it < (long long)tiles * segs; it += gridDim.x) {
+        const int seg = (int)(it / tiles), tile = (int)(it - (long long)seg * tiles);
+        const int z0 = (int)((long long)seg * nz / segs), z1 = (int)((long long)(seg + 1) * nz / segs);
         const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
         const int nplanes = (z1 - z0) + 2 * R;
 

@@ -38,6 +38,23 @@ inline long long persistent_ctas(long long total_slices, int ctas_per_sm, int n_
     return std::max(1LL, std::min(wave, total_slices / kMinRun));
 }
 
+// Number of equal z segments for a lockstep schedule of `tiles` x segments work
+// items over `wave` resident CTAs: minimises rounds x (planes per segment +
+// halo planes), the time of the slowest CTA.
+inline int lockstep_segments(long long tiles, int nz, int halo, long long wave) {
+    int best = 1;
+    double best_cost = 0;
+    for (int sgs = 1; sgs <= std::min(nz, 64); ++sgs) {
+        const long long rounds = (tiles * sgs + wave - 1) / wave;
+        const double cost = (double)rounds * ((double)nz / sgs + halo);
+        if (sgs == 1 || cost < best_cost * 0.999) {
+            best = sgs;
+            best_cost = cost;
+        }
+    }
+    return best;
+}
+
 // Batched persistent 2D kernel (FP64): rows per batch and CTAs per SM.
 template <int MODEL> struct Batch2d { static constexpr int NT = 128, RB = (MODEL == CH) ? 8 : (MODEL == AC ? 4 : 2), CPS = 4; };
 
@@ -138,7 +155,32 @@ cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
         constexpr int ATX = 16, ATY = 16;
         typedef Step3dAsyncShape<MODEL, ST, T, ATX, ATY> AS;
         const bool aligned = ((uintptr_t)a.in0 | (uintptr_t)a.in1 | (uintptr_t)a.out0 | (uintptr_t)a.out1) % 16 == 0;
-        if (g_step_variant == 0 && a.nx % AS::V == 0 && aligned) {
+        constexpr int WTY = 8;
+        typedef Step3dWrShape<MODEL, ST, T, WTY> WS;
+        auto wkern = step3d_wr_kernel<MODEL, ST, T, WTY>;
+        // the warp-row kernel is the default unless its register queues spill
+        static const bool wr_spills = [&] {
+            cudaFuncAttributes fa{};
+            return cudaFuncGetAttributes(&fa, wkern) != cudaSuccess || fa.localSizeBytes > 0;
+        }();
+        const int fam = (g_step_variant == 0 && wr_spills) ? 1 : g_step_variant;
+        if (fam == 0 && a.nx % WS::V == 0 && aligned) {
+            // FP32 / BF16 3D: warp per tile row, z neighbours in registers
+            auto kern = wkern;
+            static const int occ = [&] {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WS::smem_bytes);
+                int o = 1;
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, WS::NT, WS::smem_bytes);
+                return o;
+            }();
+            const int tx = (a.nx + WS::TX - 1) / WS::TX, ty = (a.ny + WTY - 1) / WTY;
+            const long long wave = (long long)n_sm * std::max(occ, 1);
+            const int segs = lockstep_segments((long long)tx * ty, a.nz, 2 * WS::R, wave);
+            const long long items = (long long)tx * ty * segs;
+            kern<<<(unsigned)std::min(items, wave), WS::NT, WS::smem_bytes, s>>>(a, tx, ty, segs);
+            return cudaGetLastError();
+        }
+        if (fam != 2 && a.nx % AS::V == 0 && aligned) {
             // FP32 / BF16 3D: cp.async plane ring with planes in flight
             auto kern = step3d_async_kernel<MODEL, ST, T, ATX, ATY>;
             static const int occ = [&] {
@@ -148,10 +190,10 @@ cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
                 return o;
             }();
             const int tx = (a.nx + AS::TX - 1) / AS::TX, ty = (a.ny + ATY - 1) / ATY;
-            const long long ctas = persistent_ctas((long long)tx * ty * a.nz, occ, n_sm);
-            const long long planes = ((long long)tx * ty * a.nz + ctas - 1) / ctas;
-            kern<<<(unsigned)(((long long)tx * ty * a.nz + planes - 1) / planes), AS::NT, AS::smem_bytes, s>>>(
-                a, tx, ty, planes);
+            const long long wave = (long long)n_sm * std::max(occ, 1);
+            const int segs = lockstep_segments((long long)tx * ty, a.nz, 2 * AS::R, wave);
+            const long long items = (long long)tx * ty * segs;
+            kern<<<(unsigned)std::min(items, wave), AS::NT, AS::smem_bytes, s>>>(a, tx, ty, segs);
             return cudaGetLastError();
         }
         // FP32 / BF16 3D, any nx: vectorised plane kernel, 64 x 32 tiles

@@ -337,7 +337,7 @@ def test_autotune_keeps_results(sp, model, shape, dtype, st):
         spl, var = c.launch_config
         assert b.launch_config == c.launch_config  # the second tuning came from the cache
         if len(shape) == 3:
-            assert spl == 1 and var in ((0, 1) if (dtype != 0 or st == 4) else (0,))
+            assert spl == 1 and var in ((0, 1, 2) if dtype != 0 else (0, 1) if st == 4 else (0,))
         elif dtype == 0:
             assert spl == 1 and var in (0, 1)
         else:
@@ -401,20 +401,21 @@ def test_set_launch_config_rejects_unavailable(sp):
 @pytest.mark.parametrize("model,st", CASES_3D)
 @pytest.mark.parametrize("dtype", [1, 2])
 def test_3d_kernel_families_agree(sp, dtype, model, st, shape):
-    """3D FP32 / BF16: the cp.async plane-ring kernel (family 0; needs nx a
-    multiple of the 16-byte chunk) and the register-staged ring kernel (family 1)
-    agree bit for bit.  Shapes: ragged tiles in y and z, several x tiles with a
-    ragged one, a grid smaller than one tile in every axis (neighbours wrap),
-    and a long z axis split across CTAs."""
+    """3D FP32 / BF16: the warp-row kernel (family 0), the cp.async plane-ring
+    kernel (family 1; both need nx a multiple of the chunk) and the
+    register-staged ring kernel (family 2) agree bit for bit.  Shapes: ragged
+    tiles in y and z, several x tiles with a ragged one, a grid smaller than one
+    tile in every axis (neighbours wrap), and a long z axis split across CTAs."""
     outs = []
-    for variant in (0, 1):
+    for variant in (0, 1, 2):
         sim, dt = make(sp, model, shape, st, dtype=dtype)
         with sim:
             sim.launch_config = (1, variant)
             sim.step(7)
             outs.append([sim.read(f, as_f64=False) for f in range(2 if model == 2 else 1)])
-    for a, b in zip(*outs):
-        assert np.array_equal(a, b)
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            assert np.array_equal(a, b)
     if dtype == 1:
         ic = oracle_ic(model, shape, sim.prm)
         if model == 2:
