@@ -70,6 +70,14 @@ ESIZE = {0: 8, 1: 4, 2: 2}
 STENCIL_OPS = {0: 4, 1: 6, 2: 8, 3: 6, 4: 12, 5: 12}
 
 
+# DRAM bytes (read + write) per step launch of the dominant kernel, from an ncu
+# capture of the same kernel and workload (summaries in profiles/); workloads
+# without a capture of the current kernel report null.
+NCU_TRAFFIC = {
+    "ch2d-4096-f64-lap5": (242.47e6, "profiles/step2d_batch_ch_f64_lap5_4096.txt"),
+}
+
+
 def fp64_ops_per_lup(model: int, st: int) -> int:
     s = STENCIL_OPS[st]
     return {0: s + 5, 1: 2 * s + 5, 2: 2 * s + 9}[model]
@@ -424,11 +432,12 @@ def main():
     launch_ms = step_ms / (args.steps * sub)  # average duration of one step-kernel launch
 
     peaks = load_peaks()
+    traffic = NCU_TRAFFIC[args.workload][0] if (args.workload in NCU_TRAFFIC and spl == 1 and variant == 0) else None
     if dtype == 0:
         ops = fp64_ops_per_lup(model, st)
         achieved = ops * npts / (launch_ms * 1e-3) / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "FP64 Gop/s",
-                "frac": achieved / FP64_PEAK_GOPS, "traffic": None,
+                "frac": achieved / FP64_PEAK_GOPS, "traffic": traffic,
                 "note": f"{ops} FP64 ops/LUP (fixed evaluation order); peak = 152 SMs x 2 FP64 ops/clk x 2.07 GHz; "
                         f"HBM side {hbm_bytes_per_lup(model, dtype) * npts / (launch_ms * 1e-3) / 1e9:.0f} GB/s"}
     else:
@@ -436,7 +445,7 @@ def main():
         achieved = bpl * npts / (launch_ms * 1e-3) / 1e9
         peak = float(peaks.get("hbm_gbs", 6800.0))
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "steps_per_launch": spl,
+                "traffic": traffic, "steps_per_launch": spl,
                 "note": f"{bpl} algorithmic bytes/LUP at one step per pass; peak = measured copy bandwidth"
                         + ("" if "hbm_gbs" in peaks else " (fallback)")
                         + (f"; {spl} steps per HBM pass, so this is an effective rate" if spl > 1 else "")}

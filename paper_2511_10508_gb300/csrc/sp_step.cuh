@@ -1072,8 +1072,9 @@ __global__ void __launch_bounds__(NT) step3d_zreg_kernel(StepArgs a, int tiles_x
 // the previous planes' values and in-plane partial sums (the stencil's fixed
 // order is a sum over planes of in-plane partial sums, see sp_common.cuh).  A
 // Cahn-Hilliard thread keeps the mu of its own chunk in registers and shares
-// it through one mu plane in shared memory.  Same expressions in the same
-// order as the other FP32 kernels: identical results bit for bit.
+// it through one mu plane in shared memory.  The plane loop is unrolled by the
+// queue length so that queues rotate by renaming registers.  Same expressions
+// in the same order as the other FP32 kernels: identical results bit for bit.
 //
 // Requirements (checked by the launcher): nx a multiple of 4 and 16-byte
 // aligned field pointers.
@@ -1207,128 +1208,118 @@ __global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT)
 #pragma unroll
         for (int j = 0; j < P; ++j) issue(j);
 
-        // shift-register queues: index k holds plane j - (Q-1) + k after plane j arrives
+        // queues, slot (j % Q) holds plane j: values and partial sums
         float qf[NF][Q][V], qp[NF][Q][NP][V];
         float qm[MODEL == CH ? Q : 1][V], qmp[MODEL == CH ? Q : 1][NP][V];
         (void)qm; (void)qmp;
-        auto f0q = [&](int kk) -> const float * { return qf[0][kk]; };
-        auto p0q = [&](int kk) -> const float(*)[V] { return qp[0][kk]; };
-        auto f1q = [&](int kk) -> const float * { return qf[NF - 1][kk]; };
-        auto p1q = [&](int kk) -> const float(*)[V] { return qp[NF - 1][kk]; };
-        auto mfq = [&](int kk) -> const float * { return qm[kk]; };
-        auto mpq = [&](int kk) -> const float(*)[V] { return qmp[kk]; };
-        (void)f1q; (void)p1q; (void)mfq; (void)mpq;
 
-        for (int j = 0; j < n; ++j) {
-            cp_async_wait<P - 1>();
-            __syncthreads();  // plane j published; plane j-1's slot and the mu plane are free
-            issue(j + P);
-            const int slot = j % (P + 1);
-            if ((MODEL == CH && mu_row) || (MODEL != CH && out_row)) {
+        for (int j0 = 0; j0 < n; j0 += Q) {
 #pragma unroll
-                for (int f = 0; f < NF; ++f) {
+            for (int u = 0; u < Q; ++u) {
+                const int j = j0 + u;
+                if (j < n) {
+                    cp_async_wait<P - 1>();
+                    __syncthreads();  // plane j published; plane j-1's slot and the mu plane are free
+                    issue(j + P);
+                    const int slot = j % (P + 1);
+#define QS(m) ((u - (m) + 4 * Q) % Q)   /* queue slot of plane j - m */
+                    if ((MODEL == CH && mu_row) || (MODEL != CH && out_row)) {
 #pragma unroll
-                    for (int kk = 0; kk < Q - 1; ++kk) {  // age the queues by one plane
+                        for (int f = 0; f < NF; ++f) {
+                            float ext[2 * r + 1][XW];
+                            ring_chunk(slot, f, w, ext[r] + r);
+                            extend(ext[r]);
 #pragma unroll
-                        for (int c = 0; c < V; ++c) {
-                            qf[f][kk][c] = qf[f][kk + 1][c];
+                            for (int dy = 1; dy <= r; ++dy) {
+                                ring_chunk(slot, f, w - dy, ext[r - dy] + r);
+                                ring_chunk(slot, f, w + dy, ext[r + dy] + r);
+                                if constexpr (ST == L27) {
+                                    extend(ext[r - dy]);
+                                    extend(ext[r + dy]);
+                                }
+                            }
+                            auto row = [&](int dy) -> const float * { return ext[r + dy]; };
+                            planar_sums<ST, V, XW>(row, qp[f][QS(0)]);
 #pragma unroll
-                            for (int np = 0; np < NP; ++np) qp[f][kk][np][c] = qp[f][kk + 1][np][c];
+                            for (int c = 0; c < V; ++c) qf[f][QS(0)][c] = ext[r][r + c];
                         }
                     }
-                    float ext[2 * r + 1][XW];
-                    ring_chunk(slot, f, w, ext[r] + r);
-                    extend(ext[r]);
+                    // stencil of plane j - r from the queues (planes j - 2r .. j)
+                    auto f0q = [&](int kk) -> const float * { return qf[0][QS(2 * r - kk)]; };
+                    auto p0q = [&](int kk) -> const float(*)[V] { return qp[0][QS(2 * r - kk)]; };
+                    auto f1q = [&](int kk) -> const float * { return qf[NF - 1][QS(2 * r - kk)]; };
+                    auto p1q = [&](int kk) -> const float(*)[V] { return qp[NF - 1][QS(2 * r - kk)]; };
+                    (void)f1q; (void)p1q;
+                    if constexpr (MODEL == CH) {
+                        float mu[V];
+                        if (mu_row && j >= 2 * r) {
 #pragma unroll
-                    for (int dy = 1; dy <= r; ++dy) {
-                        ring_chunk(slot, f, w - dy, ext[r - dy] + r);
-                        ring_chunk(slot, f, w + dy, ext[r + dy] + r);
-                        if constexpr (ST == L27) {
-                            extend(ext[r - dy]);
-                            extend(ext[r + dy]);
+                            for (int c = 0; c < V; ++c)
+                                mu[c] = ch_mu<C>(qf[0][QS(r)][c], planar_combine<ST>(f0q, p0q, c), k);
+#pragma unroll
+                            for (int i = 0; i < V; i += 4)
+                                *reinterpret_cast<float4 *>(&s_mu[((size_t)w * 32 + lane) * V + i]) =
+                                    make_float4(mu[i], mu[i + 1], mu[i + 2], mu[i + 3]);
+                        }
+                        __syncthreads();  // mu plane j - r published
+                        if (out_row && j >= 2 * r) {
+                            float ext[2 * r + 1][XW];
+#pragma unroll
+                            for (int c = 0; c < V; ++c) ext[r][r + c] = mu[c];
+                            extend(ext[r]);
+#pragma unroll
+                            for (int dy = -r; dy <= r; ++dy) {
+                                if (dy == 0) continue;
+                                const float *src = &s_mu[((size_t)(w + dy) * 32 + lane) * V];
+#pragma unroll
+                                for (int i = 0; i < V; i += 4) {
+                                    const float4 v4 = *reinterpret_cast<const float4 *>(src + i);
+                                    ext[r + dy][r + i] = v4.x;
+                                    ext[r + dy][r + i + 1] = v4.y;
+                                    ext[r + dy][r + i + 2] = v4.z;
+                                    ext[r + dy][r + i + 3] = v4.w;
+                                }
+                                if constexpr (ST == L27) extend(ext[r + dy]);
+                            }
+                            auto row = [&](int dy) -> const float * { return ext[r + dy]; };
+                            planar_sums<ST, V, XW>(row, qmp[QS(0)]);
+#pragma unroll
+                            for (int c = 0; c < V; ++c) qm[QS(0)][c] = mu[c];
+                            if (j >= 4 * r) {
+                                // output plane j - 2r: mu planes j - 3r .. j - r sit in mu queue
+                                // slots of iterations j - 2r .. j; phi of plane j - 2r in qf
+                                auto mf = [&](int kk) -> const float * { return qm[QS(2 * r - kk)]; };
+                                auto mp = [&](int kk) -> const float(*)[V] { return qmp[QS(2 * r - kk)]; };
+                                float o[V];
+#pragma unroll
+                                for (int c = 0; c < V; ++c)
+                                    o[c] = ch_update<C>(qf[0][QS(2 * r)][c], planar_combine<ST>(mf, mp, c), k);
+                                if (store)
+                                    store_vec<T, V>(out[0] + (size_t)(z0 - 4 * r + j) * plane + (size_t)yo * nx + col, o);
+                            }
+                        }
+                    } else {
+                        if (out_row && j >= 2 * r) {
+                            float o0[V], o1[V];
+#pragma unroll
+                            for (int c = 0; c < V; ++c) {
+                                const float S0 = planar_combine<ST>(f0q, p0q, c);
+                                const float p0 = qf[0][QS(r)][c];
+                                if constexpr (MODEL == AC) {
+                                    o0[c] = ac_update<C>(p0, S0, k);
+                                } else {
+                                    gs_update<C>(p0, qf[NF - 1][QS(r)][c], S0, planar_combine<ST>(f1q, p1q, c),
+                                                 k, o0[c], o1[c]);
+                                }
+                            }
+                            if (store) {
+                                const size_t o = (size_t)(z0 - 2 * r + j) * plane + (size_t)yo * nx + col;
+                                store_vec<T, V>(out[0] + o, o0);
+                                if constexpr (MODEL == GS) store_vec<T, V>(out[NF - 1] + o, o1);
+                            }
                         }
                     }
-                    auto row = [&](int dy) -> const float * { return ext[r + dy]; };
-                    planar_sums<ST, V, XW>(row, qp[f][Q - 1]);
-#pragma unroll
-                    for (int c = 0; c < V; ++c) qf[f][Q - 1][c] = ext[r][r + c];
-                }
-            }
-            // stencils of plane j - r from the queues (planes j - 2r .. j)
-            if constexpr (MODEL == CH) {
-                float mu[V];
-                if (mu_row && j >= 2 * r) {
-#pragma unroll
-                    for (int c = 0; c < V; ++c) mu[c] = ch_mu<C>(qf[0][r][c], planar_combine<ST>(f0q, p0q, c), k);
-#pragma unroll
-                    for (int i = 0; i < V; i += 4)
-                        *reinterpret_cast<float4 *>(&s_mu[((size_t)w * 32 + lane) * V + i]) =
-                            make_float4(mu[i], mu[i + 1], mu[i + 2], mu[i + 3]);
-                }
-                __syncthreads();  // mu plane j - r published
-                if (out_row && j >= 2 * r) {
-                    // phi of plane j - 2r (output centre) before the mu queue ages
-                    float pc[V];
-#pragma unroll
-                    for (int c = 0; c < V; ++c) pc[c] = qf[0][0][c];
-#pragma unroll
-                    for (int kk = 0; kk < Q - 1; ++kk) {
-#pragma unroll
-                        for (int c = 0; c < V; ++c) {
-                            qm[kk][c] = qm[kk + 1][c];
-#pragma unroll
-                            for (int np = 0; np < NP; ++np) qmp[kk][np][c] = qmp[kk + 1][np][c];
-                        }
-                    }
-                    float ext[2 * r + 1][XW];
-#pragma unroll
-                    for (int c = 0; c < V; ++c) ext[r][r + c] = mu[c];
-                    extend(ext[r]);
-#pragma unroll
-                    for (int dy = -r; dy <= r; ++dy) {
-                        if (dy == 0) continue;
-                        const float *src = &s_mu[((size_t)(w + dy) * 32 + lane) * V];
-#pragma unroll
-                        for (int i = 0; i < V; i += 4) {
-                            const float4 v4 = *reinterpret_cast<const float4 *>(src + i);
-                            ext[r + dy][r + i] = v4.x;
-                            ext[r + dy][r + i + 1] = v4.y;
-                            ext[r + dy][r + i + 2] = v4.z;
-                            ext[r + dy][r + i + 3] = v4.w;
-                        }
-                        if constexpr (ST == L27) extend(ext[r + dy]);
-                    }
-                    auto row = [&](int dy) -> const float * { return ext[r + dy]; };
-                    planar_sums<ST, V, XW>(row, qmp[Q - 1]);
-#pragma unroll
-                    for (int c = 0; c < V; ++c) qm[Q - 1][c] = mu[c];
-                    if (j >= 4 * r) {
-                        // output plane j - 2r from mu planes j - 3r .. j - r
-                        float o[V];
-#pragma unroll
-                        for (int c = 0; c < V; ++c) o[c] = ch_update<C>(pc[c], planar_combine<ST>(mfq, mpq, c), k);
-                        if (store)
-                            store_vec<T, V>(out[0] + (size_t)(z0 - 4 * r + j) * plane + (size_t)yo * nx + col, o);
-                    }
-                }
-            } else {
-                if (out_row && j >= 2 * r) {
-                    float o0[V], o1[V];
-#pragma unroll
-                    for (int c = 0; c < V; ++c) {
-                        const float S0 = planar_combine<ST>(f0q, p0q, c);
-                        const float p0 = qf[0][r][c];
-                        if constexpr (MODEL == AC) {
-                            o0[c] = ac_update<C>(p0, S0, k);
-                        } else {
-                            gs_update<C>(p0, qf[NF - 1][r][c], S0, planar_combine<ST>(f1q, p1q, c), k, o0[c], o1[c]);
-                        }
-                    }
-                    if (store) {
-                        const size_t o = (size_t)(z0 - 2 * r + j) * plane + (size_t)yo * nx + col;
-                        store_vec<T, V>(out[0] + o, o0);
-                        if constexpr (MODEL == GS) store_vec<T, V>(out[NF - 1] + o, o1);
-                    }
+#undef QS
                 }
             }
         }
