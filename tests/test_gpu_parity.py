@@ -423,3 +423,36 @@ def test_3d_kernel_families_agree(sp, dtype, model, st, shape):
         else:
             ref = O.step(model, st, ic, dt=dt, prm=oparams(sim.prm), nsteps=7)
         assert O.rel_l2(outs[0][0].astype(np.float64), ref) < TOL[1]
+
+
+def test_two_host_threads_step_independent_grids(sp):
+    """Two simulations stepped (and autotuned) concurrently from two host threads
+    give the same fields as when run one after the other: the launch
+    configuration is per simulation and the autotune cache is shared safely."""
+    import threading
+
+    cases = [(1, (300, 296), 1, 0), (2, (40, 33, 64), 1, 3)]
+
+    def run(model, shape, dtype, st, out, idx, tune):
+        sim, _ = make(sp, model, shape, st, dtype=dtype)
+        with sim:
+            if tune:
+                sim.autotune()
+                sim.step(120 - sim.steps_taken)
+            else:
+                sim.step(120)
+            out[idx] = [sim.read(f, as_f64=False) for f in range(2 if model == 2 else 1)]
+
+    seq = [None, None]
+    for i, c in enumerate(cases):
+        run(*c, seq, i, False)
+    par = [None, None]
+    ts = [threading.Thread(target=run, args=(*c, par, i, True)) for i, c in enumerate(cases)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join(timeout=300)
+    for a, b in zip(seq, par):
+        assert b is not None
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
