@@ -210,9 +210,13 @@ int sp_autotune(sp_sim *sim, void *stream, int64_t *steps_taken);
 
 /* Pin a launch configuration (for instance one that sp_autotune chose in an
  * earlier run): steps fused per launch (1, or 2 / 4 for 2D FP32/BF16) and kernel
- * family (0, or 1 where sp_launch_config documents an alternative).  Every
- * available configuration gives bit-identical results.  SP_EINVAL if the pair is
- * not available for this grid; cancels a pending SP_FLAG_AUTOTUNE. */
+ * family (0, or 1 / 2 where sp_launch_config documents an alternative).  Family 3
+ * (Cahn-Hilliard only, one step per launch) is an ablation with no use in
+ * production: the unfused two-pass step of the paper's solver, which writes mu to
+ * a temporary field in device memory (allocated here, N values of the compute
+ * precision; SP_ENOMEM if that fails) and reads it back for the outer Laplacian.
+ * Every available configuration gives bit-identical results.  SP_EINVAL if the
+ * pair is not available for this grid; cancels a pending SP_FLAG_AUTOTUNE. */
 int sp_set_launch_config(sp_sim *sim, int steps_per_launch, int variant);
 
 /* Launch configuration in use: steps fused per launch and kernel family

@@ -50,6 +50,11 @@ inline int steps_per_launch(int dims, int dtype, int model, int requested) {
     return 1;
 }
 
+// Unfused Cahn-Hilliard step (ablation only, kernel family kUnfusedFamily): mu
+// into the caller's temporary of N compute-precision values, then the update.
+constexpr int kUnfusedFamily = 3;
+cudaError_t launch_unfused_ch(int dtype, int stencil, const StepArgs &a, void *mu, cudaStream_t s, int n_sm);
+
 cudaError_t launch_ic(int dtype, void *u, void *v, int model, int dims, int nx, int ny, int nz,
                       uint64_t seed, int ic_kind, double mean, double amp, int patches, int patch,
                       cudaStream_t s, int n_sm);

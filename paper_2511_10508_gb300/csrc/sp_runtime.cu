@@ -166,6 +166,7 @@ struct sp_sim {
     cudaGraphExec_t graph[2];  // kGraphSteps steps starting from level 0 / level 1
     int spl;                   // steps fused per launch (temporal blocking)
     int variant;               // kernel family (see g_step_variant)
+    void *mu_tmp;              // unfused ablation: mu temporary (allocated on first use)
     bool tune_pending;         // autotune on the next long sp_step
 };
 
@@ -199,6 +200,7 @@ static void release(sp_sim *s) {
             if (s->f[l][f]) cudaFree(s->f[l][f]);
     if (s->d_partials) cudaFree(s->d_partials);
     if (s->d_stage) cudaFree(s->d_stage);
+    if (s->mu_tmp) cudaFree(s->mu_tmp);
     for (int l = 0; l < 2; ++l)
         if (s->graph[l]) cudaGraphExecDestroy(s->graph[l]);
     if (s->h_out) cudaFreeHost(s->h_out);
@@ -311,6 +313,7 @@ static cudaError_t launch_one_step_impl(sp_sim *s, cudaStream_t st, int k) {
     a.k = s->k;
     a.kf = {(float)s->k.c1, (float)s->k.c2, (float)s->k.sAC, (float)s->k.kq, (float)s->k.dq,
             (float)s->k.duq, (float)s->k.dvq, (float)s->k.F, (float)s->k.Fk, (float)s->k.dt};
+    if (s->variant == kUnfusedFamily) return launch_unfused_ch(s->dtype, s->stencil, a, s->mu_tmp, st, s->n_sm);
     switch (s->dtype) {
     case SP_F64: return launch_step_f64(s->model, s->stencil, a, st, s->n_sm, k);
     case SP_F32: return launch_step_f32(s->model, s->stencil, a, st, s->n_sm, k);
@@ -606,6 +609,20 @@ extern "C" int sp_set_launch_config(sp_sim *s, int steps_per_launch, int variant
     if (steps_per_launch == 1 && variant == 0) {  // the default is always available
         s->tune_pending = false;
         set_launch_config(s, {1, 0});
+        return SP_OK;
+    }
+    if (steps_per_launch == 1 && variant == kUnfusedFamily && s->model == SP_CAHN_HILLIARD) {
+        if (!s->mu_tmp) {
+            const size_t bytes = s->N * (s->dtype == SP_F64 ? sizeof(double) : sizeof(float));
+            const cudaError_t e = cudaMalloc(&s->mu_tmp, bytes);
+            if (e != cudaSuccess) {
+                s->mu_tmp = nullptr;
+                return fail(SP_ENOMEM, "unfused ablation: cudaMalloc of %zu bytes failed: %s", bytes,
+                            cudaGetErrorString(e));
+            }
+        }
+        s->tune_pending = false;
+        set_launch_config(s, {1, kUnfusedFamily});
         return SP_OK;
     }
     return fail(SP_EINVAL, "launch configuration (%d steps per launch, family %d) is not available for this grid",

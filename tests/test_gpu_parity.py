@@ -456,3 +456,34 @@ def test_two_host_threads_step_independent_grids(sp):
         assert b is not None
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("st,shape", [(0, (70, 301)), (1, (45, 64)), (2, (40, 33)), (3, (20, 18, 36)),
+                                      (4, (17, 24, 33)), (5, (20, 18, 36))])
+@pytest.mark.parametrize("dtype", [0, 1, 2])
+def test_unfused_ablation_equals_fused(sp, dtype, st, shape):
+    """Kernel family 3 (Cahn-Hilliard only) is the unfused two-pass ablation: mu
+    through a device-memory temporary, then the outer Laplacian.  Same expressions
+    in the same order, so it equals the fused kernels bit for bit (40 steps, so
+    graph replay is included)."""
+    outs = []
+    for fam in (None, 3):
+        sim, dt = make(sp, 1, shape, st, dtype=dtype)
+        with sim:
+            if fam is not None:
+                sim.launch_config = (1, fam)
+                assert sim.launch_config == (1, 3)
+            sim.step(40)
+            outs.append(sim.read(0, as_f64=False))
+    assert np.array_equal(outs[0], outs[1])
+    if dtype == 0:
+        ic = oracle_ic(1, shape, sim.prm)
+        assert np.array_equal(outs[1], O.step(1, st, ic, dt=dt, prm=oparams(sim.prm), nsteps=40))
+
+
+def test_unfused_ablation_only_for_cahn_hilliard(sp):
+    for model in (0, 2):
+        sim, _ = make(sp, model, (32, 32), 0)
+        with sim:
+            with pytest.raises(sp.SpError):
+                sim.launch_config = (1, 3)
