@@ -23,7 +23,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sp_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-AC, CH, GS = 0, 1, 2
+AC, CH, GS, MC = 0, 1, 2, 3
+TWO_FIELD = (GS, MC)
 S1, S2, S3, S4, S5, S6 = range(6)
 STENCIL_DIMS = {S1: 2, S2: 2, S3: 2, S4: 3, S5: 3, S6: 3}
 STENCIL_RADIUS = {S1: 1, S2: 1, S3: 2, S4: 1, S5: 1, S6: 2}
@@ -74,6 +75,8 @@ def lib():
             L.or_mass.argtypes = [c_int, i64, i64, i64, dbl, ptr]
             L.or_free_energy.restype = dbl
             L.or_free_energy.argtypes = [c_int, i64, i64, i64, dbl, dbl, dbl, ptr]
+            L.or_free_energy_c.restype = dbl
+            L.or_free_energy_c.argtypes = [c_int, i64, i64, i64, dbl, dbl, dbl, dbl, ptr, ptr]
             L.or_rel_l2.restype = dbl
             L.or_rel_l2.argtypes = [ptr, ptr, i64]
             _lib = L
@@ -98,9 +101,9 @@ def _shape3(a: np.ndarray, dims: int):
     return nx, ny, nz
 
 
-def params(c1=1.0, c2=1.0, kappa=1.0, Du=0.16, Dv=0.08, F=0.035, k=0.065) -> np.ndarray:
-    """Parameter vector in the oracle's order: c1, c2, kappa, Du, Dv, F, k."""
-    return np.array([c1, c2, kappa, Du, Dv, F, k], dtype=np.float64)
+def params(c1=1.0, c2=1.0, kappa=1.0, Du=0.16, Dv=0.08, F=0.035, k=0.065, c3=0.5) -> np.ndarray:
+    """Parameter vector in the oracle's order: c1, c2, kappa, Du, Dv, F, k, c3."""
+    return np.array([c1, c2, kappa, Du, Dv, F, k, c3], dtype=np.float64)
 
 
 def num_threads() -> int:
@@ -149,7 +152,7 @@ def step(model: int, st: int, u, v=None, *, h: float = 1.0, dt: float, prm=None,
                        None if vv is None else _p(vv), int(nsteps))
     if rc:
         raise ValueError("or_step: bad arguments or out of memory")
-    return u if model != GS else (u, vv)
+    return u if model not in TWO_FIELD else (u, vv)
 
 
 def splitmix64_nth(seed: int, n: int) -> int:
@@ -165,13 +168,13 @@ def initial_condition(model: int, shape, *, seed: int, mean: float = 0.0, amp: f
     """Seeded initial fields; ``shape`` is (ny, nx) or (nz, ny, nx)."""
     dims = len(shape)
     u = np.empty(shape, dtype=np.float64)
-    v = np.empty(shape, dtype=np.float64) if model == GS else None
+    v = np.empty(shape, dtype=np.float64) if model in TWO_FIELD else None
     nx, ny, nz = _shape3(u, dims)
     rc = lib().or_initial_condition(model, dims, nx, ny, nz, seed, mean, amp, patches, patch,
                                     _p(u), None if v is None else _p(v))
     if rc:
         raise ValueError("or_initial_condition: bad arguments")
-    return u if model != GS else (u, v)
+    return u if model not in TWO_FIELD else (u, v)
 
 
 def initial_condition_window(model: int, shape, origin, wshape, *, seed: int, mean: float = 0.0,
@@ -183,13 +186,13 @@ def initial_condition_window(model: int, shape, origin, wshape, *, seed: int, me
     org = list(origin[::-1]) + [0] * (3 - dims)
     win = list(wshape[::-1]) + [1] * (3 - dims)
     u = np.empty(wshape, dtype=np.float64)
-    v = np.empty(wshape, dtype=np.float64) if model == GS else None
+    v = np.empty(wshape, dtype=np.float64) if model in TWO_FIELD else None
     rc = lib().or_initial_condition_window(model, dims, full[0], full[1], full[2], seed, mean, amp, patches, patch,
                                            org[0], org[1], org[2], win[0], win[1], win[2], _p(u),
                                            None if v is None else _p(v))
     if rc:
         raise ValueError("or_initial_condition_window: bad arguments")
-    return u if model != GS else (u, v)
+    return u if model not in TWO_FIELD else (u, v)
 
 
 def kahan_sum(f) -> float:
@@ -209,6 +212,14 @@ def free_energy(f, h: float = 1.0, c1: float = 1.0, c2: float = 1.0) -> float:
     dims = f.ndim
     nx, ny, nz = _shape3(f, dims)
     return lib().or_free_energy(dims, nx, ny, nz, h, c1, c2, _p(f))
+
+
+def free_energy_c(phi, rho, h: float = 1.0, c1: float = 1.0, c2: float = 1.0, c3: float = 0.5) -> float:
+    """Discrete Model C free energy of (phi, rho) (see or_free_energy_c)."""
+    phi, rho = _f64(phi), _f64(rho)
+    dims = phi.ndim
+    nx, ny, nz = _shape3(phi, dims)
+    return lib().or_free_energy_c(dims, nx, ny, nz, h, c1, c2, c3, _p(phi), _p(rho))
 
 
 def rel_l2(a, b) -> float:

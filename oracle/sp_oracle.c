@@ -39,7 +39,14 @@
  *    same stencil, composed (L_h applied to mu), not a direct biharmonic;
  *  - Gray-Scott, both fields read from the old time level:
  *      du/dt = Du lap u - u v^2 + F (1 - u)
- *      dv/dt = Dv lap v + u v^2 - (F + k) v.
+ *      dv/dt = Dv lap v + u v^2 - (F + k) v;
+ *  - Model C (Sec. "Model C"), a non-conserved phi (u) coupled to a conserved
+ *    density rho (v).  The printed equation and the paper's free-energy listing
+ *    F = int [ LANDAU(phi) + rho^2/2 - c3 phi^2 rho ] disagree in two signs;
+ *    this oracle follows the listing (phi relaxes by -dF/dphi, rho is conserved
+ *    with chemical potential dF/drho):
+ *      dphi/dt = lap phi + c1 phi - c2 phi^3 + 2 c3 phi rho
+ *      drho/dt = lap (rho - c3 phi^2).
  *
  * Fixed evaluation order (the FP64 parity contract), per point:
  *   class sums of neighbours as written in stencil_sum(), then
@@ -52,6 +59,10 @@
  *                  ru  = fma(F, 1-u, fma(Du/q_h2, S(u), -uvv))
  *                  rv  = fma(-(F+k), v, fma(Dv/q_h2, S(v), uvv))
  *                  u'  = fma(dt, ru, u);  v' = fma(dt, rv, v)
+ *   Model C:       m   = fma(-c3, u*u, v)                 (every point first)
+ *                  gr  = fma(-c2, u*u, fma(2*c3, v, c1))
+ *                  u'  = fma(dt, fma(u, gr, (1/q_h2)*S(u)), u)
+ *                  v'  = fma(dt/q_h2, S(m), v)
  * Compile with -ffp-contract=off so that no other multiply-add is fused.
  */
 #include <math.h>
@@ -63,9 +74,9 @@
 #endif
 
 enum { OR_S1 = 0, OR_S2 = 1, OR_S3 = 2, OR_S4 = 3, OR_S5 = 4, OR_S6 = 5 };
-enum { OR_AC = 0, OR_CH = 1, OR_GS = 2 };
+enum { OR_AC = 0, OR_CH = 1, OR_GS = 2, OR_MC = 3 };
 /* parameter vector: c1, c2, kappa, Du, Dv, F, k */
-enum { P_C1 = 0, P_C2, P_KAPPA, P_DU, P_DV, P_F, P_K, P_COUNT };
+enum { P_C1 = 0, P_C2, P_KAPPA, P_DU, P_DV, P_F, P_K, P_C3, P_COUNT };
 
 #define OR_MAXR 2
 
@@ -225,22 +236,24 @@ int or_chemical_potential(int st, int64_t nx, int64_t ny, int64_t nz, double h, 
 
 /*
  * Advance nsteps forward-Euler steps in place.  u is the only field of
- * Allen-Cahn / Cahn-Hilliard; Gray-Scott has u and v.  prm = {c1, c2, kappa,
- * Du, Dv, F, k}.  Returns 0, or -1 on bad arguments / allocation failure.
+ * Allen-Cahn / Cahn-Hilliard; Gray-Scott has u and v, Model C phi = u and
+ * rho = v.  prm = {c1, c2, kappa, Du, Dv, F, k, c3}.  Returns 0, or -1 on bad
+ * arguments / allocation failure.
  */
 int or_step(int model, int st, int64_t nx, int64_t ny, int64_t nz, double h, double dt,
             const double *prm, double *u, double *v, int64_t nsteps) {
     grid_t g;
-    if (check_grid(st, nx, ny, nz) || model < OR_AC || model > OR_GS || nsteps < 0) return -1;
-    if (model == OR_GS && !v) return -1;
+    if (check_grid(st, nx, ny, nz) || model < OR_AC || model > OR_MC || nsteps < 0) return -1;
+    const int two = (model == OR_GS || model == OR_MC);
+    if (two && !v) return -1;
     if (grid_init(&g, nx, ny, nz)) return -1;
     const int64_t n = nx * ny * nz;
     const double q_h2 = ((double)or_stencil_q(st) * h) * h;
     const double c1 = prm[P_C1], c2 = prm[P_C2];
     double *un = (double *)malloc(sizeof(double) * (size_t)n);
-    double *vn = (model == OR_GS) ? (double *)malloc(sizeof(double) * (size_t)n) : NULL;
-    double *mu = (model == OR_CH) ? (double *)malloc(sizeof(double) * (size_t)n) : NULL;
-    if (!un || (model == OR_GS && !vn) || (model == OR_CH && !mu)) {
+    double *vn = two ? (double *)malloc(sizeof(double) * (size_t)n) : NULL;
+    double *mu = (model == OR_CH || model == OR_MC) ? (double *)malloc(sizeof(double) * (size_t)n) : NULL;
+    if (!un || (two && !vn) || ((model == OR_CH || model == OR_MC) && !mu)) {
         free(un); free(vn); free(mu); grid_free(&g);
         return -1;
     }
@@ -268,6 +281,22 @@ int or_step(int model, int st, int64_t nx, int64_t ny, int64_t nz, double h, dou
                         const int64_t i = (z * ny + y) * nx + x;
                         un[i] = fma(dq, stencil_sum(st, mu, &g, x, y, z), uc[i]);
                     }
+        } else if (model == OR_MC) {
+            /* chemical potential of the conserved density at every point first */
+            const double c3 = prm[P_C3], c3x2 = 2.0 * prm[P_C3];
+#pragma omp parallel for schedule(static)
+            for (int64_t i = 0; i < n; i++) mu[i] = fma(-c3, uc[i] * uc[i], vc[i]);
+            const double sAC = 1.0 / q_h2, dq = dt / q_h2;
+#pragma omp parallel for collapse(2) schedule(static)
+            for (int64_t z = 0; z < nz; z++)
+                for (int64_t y = 0; y < ny; y++)
+                    for (int64_t x = 0; x < nx; x++) {
+                        const int64_t i = (z * ny + y) * nx + x;
+                        const double p = uc[i], r = vc[i];
+                        const double gr = fma(-c2, p * p, fma(c3x2, r, c1));
+                        un[i] = fma(dt, fma(p, gr, sAC * stencil_sum(st, uc, &g, x, y, z)), p);
+                        vn[i] = fma(dq, stencil_sum(st, mu, &g, x, y, z), r);
+                    }
         } else {
             const double duq = prm[P_DU] / q_h2, dvq = prm[P_DV] / q_h2;
             const double F = prm[P_F], Fk = prm[P_F] + prm[P_K];
@@ -286,10 +315,10 @@ int or_step(int model, int st, int64_t nx, int64_t ny, int64_t nz, double h, dou
         }
         /* ping-pong: the new level becomes current */
         double *t = uc; uc = un; un = t;
-        if (model == OR_GS) { t = vc; vc = vn; vn = t; }
+        if (two) { t = vc; vc = vn; vn = t; }
     }
     if (uc != u) { memcpy(u, uc, sizeof(double) * (size_t)n); un = uc; }
-    if (model == OR_GS && vc != v) { memcpy(v, vc, sizeof(double) * (size_t)n); vn = vc; }
+    if (two && vc != v) { memcpy(v, vc, sizeof(double) * (size_t)n); vn = vc; }
     free(un); free(vn); free(mu);
     grid_free(&g);
     return 0;
@@ -333,6 +362,15 @@ int or_initial_condition(int model, int dims, int64_t nx, int64_t ny, int64_t nz
     if (model == OR_AC || model == OR_CH) {
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < N; i++) u[i] = mean + amp * (2.0 * or_u01(seed, (uint64_t)i) - 1.0);
+        return 0;
+    }
+    if (model == OR_MC) {
+        if (!v) return -1;
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < N; i++) {
+            u[i] = mean + amp * (2.0 * or_u01(seed, (uint64_t)i) - 1.0);
+            v[i] = mean + amp * (2.0 * or_u01(seed, (uint64_t)(N + i)) - 1.0);
+        }
         return 0;
     }
     if (model != OR_GS || !v || patches < 0 || patch < 0) return -1;
@@ -394,6 +432,8 @@ int or_initial_condition_window(int model, int dims, int64_t nx, int64_t ny, int
                 if (l < 0) l += nn[a];
                 lo[3 * p + a] = l;
             }
+    } else if (model == OR_MC) {
+        if (!v) return -1;
     } else if (model != OR_AC && model != OR_CH) {
         return -1;
     }
@@ -407,6 +447,7 @@ int or_initial_condition_window(int model, int dims, int64_t nx, int64_t ny, int
                 const int64_t o = (k * wy + j) * wx + i;
                 if (model != OR_GS) {
                     u[o] = mean + amp * (2.0 * or_u01(seed, (uint64_t)g) - 1.0);
+                    if (model == OR_MC) v[o] = mean + amp * (2.0 * or_u01(seed, (uint64_t)(N + g)) - 1.0);
                     continue;
                 }
                 double bu = 1.0, bv = 0.0;
@@ -476,6 +517,37 @@ double or_free_energy(int dims, int64_t nx, int64_t ny, int64_t nz, double h, do
     const double r = cell_volume(dims, h) * or_sum(e, n);
     free(e);
     return r;
+}
+
+/*
+ * Discrete Model C free energy (the paper's listing for Model C): the Landau
+ * terms of phi as in or_free_energy plus the density terms rho^2/2 - c3 phi^2 rho:
+ *   F_h = h^d sum_i [ 1/2 |D+ phi|^2 - c1/2 phi^2 + c2/4 phi^4 + 1/2 rho^2 - c3 phi^2 rho ].
+ */
+double or_free_energy_c(int dims, int64_t nx, int64_t ny, int64_t nz, double h, double c1, double c2, double c3,
+                        const double *f, const double *rho) {
+    const int64_t n = nx * ny * nz;
+    double *e = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!e) return NAN;
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int64_t z = 0; z < nz; z++)
+        for (int64_t y = 0; y < ny; y++)
+            for (int64_t x = 0; x < nx; x++) {
+                const int64_t i = (z * ny + y) * nx + x;
+                const double p = f[i], r = rho[i];
+                const double gx = (f[(z * ny + y) * nx + (x + 1) % nx] - p) / h;
+                const double gy = (f[(z * ny + (y + 1) % ny) * nx + x] - p) / h;
+                double g2 = gx * gx + gy * gy;
+                if (dims == 3) {
+                    const double gz = (f[(((z + 1) % nz) * ny + y) * nx + x] - p) / h;
+                    g2 += gz * gz;
+                }
+                const double p2 = p * p;
+                e[i] = 0.5 * g2 - 0.5 * c1 * p2 + 0.25 * c2 * p2 * p2 + 0.5 * r * r - c3 * p2 * r;
+            }
+    const double res = cell_volume(dims, h) * or_sum(e, n);
+    free(e);
+    return res;
 }
 
 /* Relative L2 distance ||a - b|| / ||b|| (plain, with compensated sums). */

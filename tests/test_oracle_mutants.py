@@ -41,6 +41,15 @@ MUTANTS = {
                         "u[i] = mean + amp * or_u01(seed, (uint64_t)i);"),
     "splitmix increment": ("(n + 1u) * UINT64_C(0x9E3779B97F4A7C15)", "n * UINT64_C(0x9E3779B97F4A7C15)"),
     "patch corner": ("int64_t l = (c - patch / 2) % nn[a];", "int64_t l = (c - patch) % nn[a];"),
+    "Model C printed coupling sign in phi": ("fma(c3x2, r, c1)", "fma(-c3x2, r, c1)"),
+    "Model C coupling without factor 2": ("c3x2 = 2.0 * prm[P_C3]", "c3x2 = prm[P_C3]"),
+    "Model C printed sign in rho": ("mu[i] = fma(-c3, uc[i] * uc[i], vc[i]);",
+                                    "mu[i] = fma(c3, uc[i] * uc[i], vc[i]);"),
+    "Model C density Laplacian of rho only": ("vn[i] = fma(dq, stencil_sum(st, mu, &g, x, y, z), r);",
+                                              "vn[i] = fma(dq, stencil_sum(st, vc, &g, x, y, z), r);"),
+    "Model C free-energy coupling sign": ("+ 0.5 * r * r - c3 * p2 * r", "+ 0.5 * r * r + c3 * p2 * r"),
+    "Model C density noise stream": ("            v[i] = mean + amp * (2.0 * or_u01(seed, (uint64_t)(N + i)) - 1.0);",
+                                     "            v[i] = mean + amp * (2.0 * or_u01(seed, (uint64_t)i) - 1.0);"),
 }
 
 

@@ -12,7 +12,11 @@ Each test states what it checks and which mistake in the oracle it would catch:
   * Gray-Scott uniform steady states (u v = F + k, F (1 - u) = (F + k) v);
   * fixed points, mass conservation, shift equivariance;
   * the free energy against a closed form and a summation-by-parts identity;
-  * the SplitMix64 generator against published outputs; the noise statistics.
+  * the SplitMix64 generator against published outputs; the noise statistics;
+  * Model C (Sec. "Model C", signs from the paper's free-energy listing): exact
+    reduction to Allen-Cahn and diffusion when uncoupled, the uniform-state
+    update, linear response of both fields to single Fourier modes, density
+    conservation, free-energy decrease and its closed form.
 """
 import math
 import os
@@ -309,7 +313,7 @@ def test_cahn_hilliard_mass_conservation(orc, st):
     assert drift < 200 * 1e-15
 
 
-@pytest.mark.parametrize("model,st", [(m, s) for m in (O.AC, O.CH, O.GS) for s in ALL])
+@pytest.mark.parametrize("model,st", [(m, s) for m in (O.AC, O.CH, O.GS, O.MC) for s in ALL])
 def test_periodic_shift_equivariance(orc, model, st):
     """Stepping a rolled field equals rolling the stepped field, bit for bit
     (periodic wrap and translation invariance of every term)."""
@@ -317,11 +321,12 @@ def test_periodic_shift_equivariance(orc, model, st):
     shape = SHAPES[dims]
     shift = (3, -5, 2)[:dims]
     axes = tuple(range(dims))
-    dt = {O.AC: 0.05, O.CH: 0.002, O.GS: 0.5}[model]
-    if model == O.GS:
-        u, v = orc.initial_condition(O.GS, shape, seed=5, amp=0.1, patches=2, patch=3)
-        a = orc.step(O.GS, st, u, v, dt=dt, nsteps=3)
-        b = orc.step(O.GS, st, np.roll(u, shift, axes), np.roll(v, shift, axes), dt=dt, nsteps=3)
+    dt = {O.AC: 0.05, O.CH: 0.002, O.GS: 0.5, O.MC: 0.02}[model]
+    if model in (O.GS, O.MC):
+        kw = dict(patches=2, patch=3) if model == O.GS else {}
+        u, v = orc.initial_condition(model, shape, seed=5, amp=0.1, **kw)
+        a = orc.step(model, st, u, v, dt=dt, nsteps=3)
+        b = orc.step(model, st, np.roll(u, shift, axes), np.roll(v, shift, axes), dt=dt, nsteps=3)
         assert np.array_equal(np.roll(a[0], shift, axes), b[0])
         assert np.array_equal(np.roll(a[1], shift, axes), b[1])
     else:
@@ -429,7 +434,7 @@ def test_gray_scott_patches(orc, dims):
 
 
 @pytest.mark.parametrize("model,shape", [(O.CH, (40, 48)), (O.GS, (40, 48)), (O.AC, (12, 14, 16)),
-                                         (O.GS, (12, 14, 16))])
+                                         (O.GS, (12, 14, 16)), (O.MC, (40, 48)), (O.MC, (12, 14, 16))])
 def test_initial_condition_window_matches_full_grid(orc, model, shape):
     """A window of the initial condition, with periodic wrap, equals the same
     slice of the full-grid initial condition (including Gray-Scott patches)."""
@@ -442,7 +447,122 @@ def test_initial_condition_window_matches_full_grid(orc, model, shape):
         wshape = (9, 7, 5)[:dims]
         win = orc.initial_condition_window(model, shape, origin, wshape, **kw)
         idx = np.ix_(*[(np.arange(w) + o) % n for w, o, n in zip(wshape, origin, shape)])
-        if model == O.GS:
+        if model in (O.GS, O.MC):
             assert np.array_equal(win[0], full[0][idx]) and np.array_equal(win[1], full[1][idx])
         else:
             assert np.array_equal(win, full[idx])
+
+
+# ------------------------------------------------------------ Model C
+#
+# F = sum h^d [ 1/2 |D+ phi|^2 - c1/2 phi^2 + c2/4 phi^4 + 1/2 rho^2 - c3 phi^2 rho ]
+# dphi/dt = -dF/dphi = lap phi + c1 phi - c2 phi^3 + 2 c3 phi rho
+# drho/dt = lap dF/drho = lap (rho - c3 phi^2)
+
+MC_DT = 0.02
+
+
+@pytest.mark.parametrize("st", ALL)
+def test_model_c_uncoupled_reduces_to_allen_cahn_and_diffusion(orc, st):
+    """With c3 = 0 the two fields decouple: phi follows Allen-Cahn bit for bit, and a
+    Fourier mode of rho decays exactly as (1 - dt lambda / h^2)^n."""
+    dims = O.STENCIL_DIMS[st]
+    shape = SHAPES[dims]
+    h, n = 1.0, 25
+    phi = orc.initial_condition(O.AC, shape, seed=13, amp=0.6)
+    rho, th = mode_field(shape, (1, 3, 2)[:dims], amp=0.4)
+    prm = O.params(c1=0.8, c2=1.2, c3=0.0)
+    a, b = orc.step(O.MC, st, phi, rho, h=h, dt=MC_DT, prm=prm, nsteps=n)
+    assert np.array_equal(a, orc.step(O.AC, st, phi, h=h, dt=MC_DT, prm=prm, nsteps=n))
+    lam = symbol(st, th)
+    np.testing.assert_allclose(b, (1 - MC_DT * lam / h ** 2) ** n * rho, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("c3", [0.5, 0.3])
+def test_model_c_uniform_state_update(orc, c3):
+    """Uniform (phi0, rho0): the Laplacians vanish, rho stays exactly, and phi moves by
+    dt phi0 (c1 - c2 phi0^2 + 2 c3 rho0) (the coupling's sign and factor 2)."""
+    c1, c2, phi0, rho0 = 0.8, 1.1, 0.6, -0.7
+    u = np.full(SHAPES[2], phi0)
+    v = np.full(SHAPES[2], rho0)
+    a, b = orc.step(O.MC, O.S1, u, v, dt=MC_DT, prm=O.params(c1=c1, c2=c2, c3=c3), nsteps=1)
+    assert np.all(b == rho0)
+    expect = phi0 + MC_DT * phi0 * (c1 - c2 * phi0 ** 2 + 2 * c3 * rho0)
+    np.testing.assert_allclose(a, expect, rtol=4e-16, atol=0)
+
+
+@pytest.mark.parametrize("st", ALL)
+def test_model_c_linear_response_of_both_fields(orc, st):
+    """About a uniform state (phi0, rho0), a small Fourier mode in phi or in rho
+    evolves for one step by the linearised update
+        dphi' = dphi + dt [ (-lam + c1 - 3 c2 phi0^2 + 2 c3 rho0) dphi + 2 c3 phi0 drho ]
+        drho' = drho + dt [ -lam (drho - 2 c3 phi0 dphi) ]
+    (lam = lambda/h^2 of the stencil): fixes the sign and size of every term of both
+    equations, including the two couplings."""
+    dims = O.STENCIL_DIMS[st]
+    shape = SHAPES[dims]
+    h, eps = 1.1, 1e-6
+    c1, c2, c3, phi0, rho0 = 0.9, 1.3, 0.5, 0.35, 0.25
+    prm = O.params(c1=c1, c2=c2, c3=c3)
+    mode, th = mode_field(shape, (2, 1, 3)[:dims])
+    lam = symbol(st, th) / h ** 2
+    base = [np.full(shape, phi0), np.full(shape, rho0)]
+    b0 = orc.step(O.MC, st, *base, h=h, dt=MC_DT, prm=prm, nsteps=1)
+    a_phi = c1 - 3 * c2 * phi0 ** 2 + 2 * c3 * rho0
+    for which in (0, 1):
+        pert = [base[0] + (eps * mode if which == 0 else 0), base[1] + (eps * mode if which == 1 else 0)]
+        out = orc.step(O.MC, st, *pert, h=h, dt=MC_DT, prm=prm, nsteps=1)
+        dphi, drho = (eps, 0.0) if which == 0 else (0.0, eps)
+        pred_phi = dphi + MC_DT * ((-lam + a_phi) * dphi + 2 * c3 * phi0 * drho)
+        pred_rho = drho + MC_DT * (-lam * (drho - 2 * c3 * phi0 * dphi))
+        np.testing.assert_allclose(out[0] - b0[0], pred_phi * mode, rtol=0, atol=1e-3 * eps)
+        np.testing.assert_allclose(out[1] - b0[1], pred_rho * mode, rtol=0, atol=1e-3 * eps)
+
+
+@pytest.mark.parametrize("st", [O.S1, O.S3, O.S4, O.S5])
+def test_model_c_conserves_density(orc, st):
+    """drho/dt is a Laplacian: the sum of rho is conserved to rounding, the sum of phi
+    is not."""
+    dims = O.STENCIL_DIMS[st]
+    shape = SHAPES[dims]
+    u, v = orc.initial_condition(O.MC, shape, seed=17, mean=0.1, amp=0.5)
+    a, b = orc.step(O.MC, st, u, v, dt=MC_DT, nsteps=200)
+    assert abs(b.sum() - v.sum()) / (v.size * np.abs(v).max()) < 200 * 1e-15
+    assert abs(a.sum() - u.sum()) > 1e-3
+
+
+@pytest.mark.parametrize("st", [O.S1, O.S4])
+def test_model_c_free_energy_decreases(orc, st):
+    """The dynamics are the gradient flow of the listing's free energy, so for a small
+    time step F decreases at every step (the printed equation's signs would not be a
+    gradient flow of this F)."""
+    dims = O.STENCIL_DIMS[st]
+    shape = SHAPES[dims]
+    u, v = orc.initial_condition(O.MC, shape, seed=19, mean=0.2, amp=0.8)
+    prm = O.params(c1=1.0, c2=1.0, c3=0.5)
+    F = [O.free_energy_c(u, v, c1=1.0, c2=1.0, c3=0.5)]
+    for _ in range(60):
+        u, v = orc.step(O.MC, st, u, v, dt=0.005, prm=prm, nsteps=1)
+        F.append(O.free_energy_c(u, v, c1=1.0, c2=1.0, c3=0.5))
+    assert all(b < a for a, b in zip(F, F[1:])), F
+
+
+def test_model_c_free_energy_closed_form(orc):
+    """Uniform fields: F = V (-c1/2 phi0^2 + c2/4 phi0^4 + rho0^2/2 - c3 phi0^2 rho0)."""
+    shape, h = (6, 8, 10), 0.5
+    c1, c2, c3, phi0, rho0 = 0.7, 1.4, 0.45, 0.6, -0.3
+    F = O.free_energy_c(np.full(shape, phi0), np.full(shape, rho0), h=h, c1=c1, c2=c2, c3=c3)
+    V = np.prod(shape) * h ** 3
+    expect = V * (-c1 / 2 * phi0 ** 2 + c2 / 4 * phi0 ** 4 + rho0 ** 2 / 2 - c3 * phi0 ** 2 * rho0)
+    assert math.isclose(F, expect, rel_tol=1e-13)
+
+
+def test_model_c_initial_condition_streams(orc):
+    """Model C's two fields are uniform noise from generator streams i (phi) and N + i
+    (rho), independent of each other."""
+    shape = (9, 11)
+    u, v = orc.initial_condition(O.MC, shape, seed=21, mean=0.1, amp=0.4)
+    N = u.size
+    for i in (0, 5, N - 1):
+        assert u.ravel()[i] == 0.1 + 0.4 * (2 * O.u01(21, i) - 1)
+        assert v.ravel()[i] == 0.1 + 0.4 * (2 * O.u01(21, N + i) - 1)
