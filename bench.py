@@ -57,13 +57,18 @@ WORKLOADS = {
     "ch3d-1024-f32-lap13x4": (1, 3, (1024, 1024, 1024), 0.005, 5, 1, 5),
     "gs3d-512-f32-lap7": (2, 3, (512, 512, 512), 0.5, 3, 1, 10),
     "ac3d-1024-f32-lap27": (0, 3, (1024, 1024, 1024), 0.05, 4, 1, 5),
+    # Model C (phi coupled to a conserved rho), c3 = 0.5
+    "mc2d-4096-f64-lap5": (3, 2, (4096, 4096), 0.02, 0, 0, 100),
+    "mc2d-16384-f32-lap5": (3, 2, (16384, 16384), 0.02, 0, 1, 20),
+    "mc3d-512-f64-lap7": (3, 3, (512, 512, 512), 0.02, 3, 0, 4),
+    "mc3d-512-f32-lap7": (3, 3, (512, 512, 512), 0.02, 3, 1, 10),
     # ablation: the unfused Cahn-Hilliard step (mu through a device-memory temporary)
     "ch2d-4096-f64-lap5-unfused": (1, 2, (4096, 4096), 0.01, 0, 0, 100, 1, 3),
     "ch2d-16384-f32-lap5-unfused": (1, 2, (16384, 16384), 0.01, 0, 1, 20, 1, 3),
     "ch3d-1024-f32-lap7-unfused": (1, 3, (1024, 1024, 1024), 0.005, 3, 1, 5, 1, 3),
 }
 DEFAULT = "ch2d-4096-f64-lap5"
-MODEL_NAME = {0: "Allen-Cahn", 1: "Cahn-Hilliard", 2: "Gray-Scott"}
+MODEL_NAME = {0: "Allen-Cahn", 1: "Cahn-Hilliard", 2: "Gray-Scott", 3: "Model C"}
 STENCIL_NAME = {0: "5-point", 1: "9-point box", 2: "4th-order 9-point cross", 3: "7-point", 4: "27-point",
                 5: "4th-order 13-point cross"}
 DTYPE_NAME = {0: "f64", 1: "f32", 2: "bf16-storage/f32"}
@@ -86,11 +91,12 @@ NCU_TRAFFIC = {
 
 def fp64_ops_per_lup(model: int, st: int) -> int:
     s = STENCIL_OPS[st]
-    return {0: s + 5, 1: 2 * s + 5, 2: 2 * s + 9}[model]
+    # Model C: mu of the density once per point (2), two stencils, the update (7)
+    return {0: s + 5, 1: 2 * s + 5, 2: 2 * s + 9, 3: 2 * s + 9}[model]
 
 
 def hbm_bytes_per_lup(model: int, dtype: int) -> int:
-    nf = 2 if model == 2 else 1
+    nf = 2 if model in (2, 3) else 1
     return 2 * nf * ESIZE[dtype]
 
 
@@ -174,11 +180,13 @@ def oracle_rate(model, dims, shape, dt, st, budget_s=15.0, max_steps=2000):
     npts = int(np.prod(shape))
     if model == 2:
         u, v = O.initial_condition(O.GS, shape, seed=2, amp=0.01, patches=64, patch=20)
+    elif model == 3:
+        u, v = O.initial_condition(O.MC, shape, seed=1, amp=0.01)
     else:
         u = O.initial_condition(model, shape, seed=1, amp=0.01)
         v = None
     def run(n):
-        if model == 2:
+        if v is not None:
             O.step(model, st, u, v, dt=dt, prm=prm, nsteps=n)
         else:
             O.step(model, st, u, dt=dt, prm=prm, nsteps=n)
@@ -334,19 +342,21 @@ def run_reference(args):
     prm = O.params()
     if model == 2:
         u, v = O.initial_condition(O.GS, shape, seed=2, amp=0.01, patches=64, patch=20)
+    elif model == 3:
+        u, v = O.initial_condition(O.MC, shape, seed=1, amp=0.01)
     else:
         u, v = O.initial_condition(model, shape, seed=1, amp=0.01), None
     # one reference step = a bounded sample: `per` oracle time steps of the full grid
     t0 = time.perf_counter()
-    O.step(model, st, u, v, dt=dt, prm=prm, nsteps=1) if model == 2 else O.step(model, st, u, dt=dt, prm=prm, nsteps=1)
+    O.step(model, st, u, v, dt=dt, prm=prm, nsteps=1) if v is not None else O.step(model, st, u, dt=dt, prm=prm, nsteps=1)
     t1 = time.perf_counter() - t0
     total_budget = 120.0
     per = int(max(1, min(sub, total_budget / max(t1, 1e-6) / max(1, args.steps + args.warmup))))
     for _ in range(args.warmup):
-        O.step(model, st, u, v, dt=dt, prm=prm, nsteps=per) if model == 2 else O.step(model, st, u, dt=dt, prm=prm, nsteps=per)
+        O.step(model, st, u, v, dt=dt, prm=prm, nsteps=per) if v is not None else O.step(model, st, u, dt=dt, prm=prm, nsteps=per)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        O.step(model, st, u, v, dt=dt, prm=prm, nsteps=per) if model == 2 else O.step(model, st, u, dt=dt, prm=prm, nsteps=per)
+        O.step(model, st, u, v, dt=dt, prm=prm, nsteps=per) if v is not None else O.step(model, st, u, dt=dt, prm=prm, nsteps=per)
     el = time.perf_counter() - t0
     val = npts * per * args.steps / el / 1e9
     line = {"impl": "reference", "metric": "GLUPS", "value": val, "unit": "GLUPS", "n_gpus": world,
@@ -478,7 +488,7 @@ def main():
         host_out = torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
         host_in[...] = sim.read(0, stream=stream)
         host_v = None
-        if model == 2:
+        if model in (2, 3):
             host_v = torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
             host_v[...] = sim.read(1, stream=stream)
         e2e_steps = max(1, min(args.steps, 5))
@@ -486,7 +496,7 @@ def main():
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             sim.write(0, host_in, stream=stream)
-            if model == 2:
+            if host_v is not None:
                 sim.write(1, host_v, stream=stream)
             sim.step(sub, stream=stream)
             sim.reduce(sp.MASS, stream=stream)
@@ -496,7 +506,7 @@ def main():
                                     stream.cuda_stream), "sp_read")
         barrier()
         el = reduce_max_over_ranks([time.perf_counter() - t0], device="cuda")[0]
-        nf = 2 if model == 2 else 1
+        nf = 2 if model in (2, 3) else 1
         e2e = {"value": replica_glups(npts * sub * e2e_steps, world, el), "unit": "GLUPS",
                "h2d_bytes_per_step": npts * 8 * nf, "d2h_bytes_per_step": npts * 8 + 8, "steps": e2e_steps}
 

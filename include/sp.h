@@ -57,7 +57,12 @@ typedef enum sp_status {
 typedef enum sp_model {
     SP_ALLEN_CAHN = 0,     /* Model A, Eq. (model-a): dphi/dt = lap phi + c1 phi - c2 phi^3 */
     SP_CAHN_HILLIARD = 1,  /* Model B, Eq. (model-b): dphi/dt = lap(c2 phi^3 - c1 phi - kappa lap phi) */
-    SP_GRAY_SCOTT = 2      /* du/dt = Du lap u - u v^2 + F(1-u); dv/dt = Dv lap v + u v^2 - (F+k) v */
+    SP_GRAY_SCOTT = 2,     /* du/dt = Du lap u - u v^2 + F(1-u); dv/dt = Dv lap v + u v^2 - (F+k) v */
+    SP_MODEL_C = 3         /* Model C (Sec. "Model C"), phi = field 0 (non-conserved), rho = field 1
+                              (conserved), signs from the paper's free-energy listing
+                              F = Landau(phi) + rho^2/2 - c3 phi^2 rho:
+                              dphi/dt = lap phi + c1 phi - c2 phi^3 + 2 c3 phi rho;
+                              drho/dt = lap(rho - c3 phi^2) */
 } sp_model;
 
 /* Laplacian stencils (integer weights over a denominator q; L f = sum w f / (q h^2)). */
@@ -84,10 +89,12 @@ typedef enum sp_ic_kind {
 } sp_ic_kind;
 
 typedef enum sp_reduce_what {
-    SP_MASS = 0,           /* h^d * sum phi (field 0), compensated FP64 */
-    SP_FREE_ENERGY = 1,    /* h^d sum [1/2 |grad+ phi|^2 - c1/2 phi^2 + c2/4 phi^4] (field 0) */
+    SP_MASS = 0,           /* h^d * sum of the conserved field (field 1, rho, for Model C;
+                              field 0 otherwise), compensated FP64 */
+    SP_FREE_ENERGY = 1,    /* h^d sum [1/2 |grad+ phi|^2 - c1/2 phi^2 + c2/4 phi^4] (field 0);
+                              Model C adds + rho^2/2 - c3 phi^2 rho */
     SP_SUM_U = 2,          /* sum of field 0 (no h^d) */
-    SP_SUM_V = 3,          /* sum of field 1 (Gray-Scott) */
+    SP_SUM_V = 3,          /* sum of field 1 (Gray-Scott, Model C) */
     SP_MIN_U = 4,          /* minimum of field 0 */
     SP_MAX_U = 5,          /* maximum of field 0 */
     SP_SUMSQ_U = 6         /* sum of squares of field 0 */
@@ -98,6 +105,7 @@ typedef enum sp_reduce_what {
 typedef struct sp_params {
     double c1, c2, kappa;  /* Allen-Cahn / Cahn-Hilliard coefficients (defaults 1) */
     double Du, Dv, F, k;   /* Gray-Scott coefficients */
+    double c3;             /* Model C coupling (default 0.5, the paper's value) */
     int stencil;           /* sp_stencil */
     int dtype;             /* sp_dtype */
     uint64_t seed;         /* initial-condition seed */
@@ -261,7 +269,7 @@ typedef struct sp_result {
     int status;             /* SP_PENDING, SP_OK or the error of this request */
     int64_t steps_done;
     double t_submit, t_admit, t_finish;  /* seconds since server creation; -1 if not reached */
-    double mass;            /* h^d sum of field 0 at the end (FP64, compensated) */
+    double mass;            /* SP_MASS of the grid at the end (FP64, compensated) */
     const double *fields;   /* FP64 fields (field 0, then field 1), or NULL; owned by the
                                server, valid until sp_release(ticket) */
     size_t n_values;        /* number of doubles at `fields` */

@@ -21,7 +21,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 # enums (mirrors sp.h)
 SP_OK, SP_EINVAL, SP_EUNSTABLE, SP_ENOMEM, SP_EBUDGET, SP_ECUDA, SP_ETIMEOUT, SP_EBUSY, SP_PENDING, SP_ENOTFOUND = range(10)
-ALLEN_CAHN, CAHN_HILLIARD, GRAY_SCOTT = 0, 1, 2
+ALLEN_CAHN, CAHN_HILLIARD, GRAY_SCOTT, MODEL_C = 0, 1, 2, 3
 LAP_DEFAULT, LAP_5, LAP_9BOX, LAP_9CROSS4, LAP_7, LAP_27, LAP_13CROSS4 = -1, 0, 1, 2, 3, 4, 5
 F64, F32, BF16_F32 = 0, 1, 2
 IC_NOISE, IC_CONSTANT = 0, 1
@@ -32,7 +32,7 @@ MASS, FREE_ENERGY, SUM_U, SUM_V, MIN_U, MAX_U, SUMSQ_U = range(7)
 class sp_params(ctypes.Structure):
     _fields_ = [("c1", ctypes.c_double), ("c2", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("Du", ctypes.c_double), ("Dv", ctypes.c_double), ("F", ctypes.c_double), ("k", ctypes.c_double),
-                ("stencil", ctypes.c_int), ("dtype", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("c3", ctypes.c_double), ("stencil", ctypes.c_int), ("dtype", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("ic_kind", ctypes.c_int), ("ic_mean", ctypes.c_double), ("ic_amp", ctypes.c_double),
                 ("gs_patches", ctypes.c_int), ("gs_patch", ctypes.c_int),
                 ("steps_per_launch", ctypes.c_int), ("flags", ctypes.c_int)]

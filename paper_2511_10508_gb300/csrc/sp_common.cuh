@@ -26,6 +26,8 @@
 //     Gray-Scott:    uvv = (u*v)*v
 //                    u' = fma(dt, fma(F, 1-u, fma(Du/q_h2, S(u), -uvv)), u)
 //                    v' = fma(dt, fma(-(F+k), v, fma(Dv/q_h2, S(v), uvv)), v)
+//     Model C:       m = fma(-c3, u*u, v) at every tap; g = fma(-c2, u*u, fma(2 c3, v, c1))
+//                    u' = fma(dt, fma(u, g, (1/q_h2)*S(u)), u);  v' = fma(dt/q_h2, S(m), v)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -34,7 +36,7 @@
 
 namespace sp {
 
-enum Model : int { AC = 0, CH = 1, GS = 2 };
+enum Model : int { AC = 0, CH = 1, GS = 2, MC = 3 };
 enum Stencil : int { L5 = 0, L9BOX = 1, L9X4 = 2, L7 = 3, L27 = 4, L13X4 = 5 };
 
 template <int ST> struct StencilInfo;
@@ -170,25 +172,34 @@ struct StepConsts {
     double duq, dvq; // Du / q_h2, Dv / q_h2    (Gray-Scott)
     double F, Fk;    // F, F + k
     double dt;
+    double c3, c3x2; // Model C coupling c3 and 2 c3
 };
 
 // The same coefficients rounded once to FP32 on the host, so that FP32/BF16
 // kernels contain no FP64 instruction (a double->float conversion runs on the
 // FP64 pipe, which the compiler may re-run inside loops).
 struct StepConstsF {
-    float c1, c2, sAC, kq, dq, duq, dvq, F, Fk, dt;
+    float c1, c2, sAC, kq, dq, duq, dvq, F, Fk, dt, c3, c3x2;
 };
+
+// FP32 copies, each rounded once from the FP64 value.
+inline StepConstsF to_float(const StepConsts &k) {
+    return {(float)k.c1, (float)k.c2, (float)k.sAC, (float)k.kq, (float)k.dq, (float)k.duq,
+            (float)k.dvq, (float)k.F,  (float)k.Fk, (float)k.dt, (float)k.c3, (float)k.c3x2};
+}
 
 template <typename C> struct ConstsC;
 template <> struct ConstsC<double> {
-    double c1, c2, sAC, kq, dq, duq, dvq, F, Fk, dt;
+    double c1, c2, sAC, kq, dq, duq, dvq, F, Fk, dt, c3, c3x2;
     __device__ __forceinline__ ConstsC(const StepConsts &k, const StepConstsF &)
-        : c1(k.c1), c2(k.c2), sAC(k.sAC), kq(k.kq), dq(k.dq), duq(k.duq), dvq(k.dvq), F(k.F), Fk(k.Fk), dt(k.dt) {}
+        : c1(k.c1), c2(k.c2), sAC(k.sAC), kq(k.kq), dq(k.dq), duq(k.duq), dvq(k.dvq), F(k.F), Fk(k.Fk), dt(k.dt),
+          c3(k.c3), c3x2(k.c3x2) {}
 };
 template <> struct ConstsC<float> {
-    float c1, c2, sAC, kq, dq, duq, dvq, F, Fk, dt;
+    float c1, c2, sAC, kq, dq, duq, dvq, F, Fk, dt, c3, c3x2;
     __device__ __forceinline__ ConstsC(const StepConsts &, const StepConstsF &k)
-        : c1(k.c1), c2(k.c2), sAC(k.sAC), kq(k.kq), dq(k.dq), duq(k.duq), dvq(k.dvq), F(k.F), Fk(k.Fk), dt(k.dt) {}
+        : c1(k.c1), c2(k.c2), sAC(k.sAC), kq(k.kq), dq(k.dq), duq(k.duq), dvq(k.dvq), F(k.F), Fk(k.Fk), dt(k.dt),
+          c3(k.c3), c3x2(k.c3x2) {}
 };
 
 // Allen-Cahn update of one point from its value and stencil sum.
@@ -218,6 +229,45 @@ __device__ __forceinline__ void gs_update(C u, C v, C Su, C Sv, const ConstsC<C>
     const C rv = FMA(-k.Fk, v, FMA(k.dvq, Sv, uvv));
     un = FMA(k.dt, ru, u);
     vn = FMA(k.dt, rv, v);
+}
+
+// Model C: chemical potential of the conserved density at one point, from its
+// phi and rho (evaluated at every stencil tap, so it never needs a buffer).
+template <typename C>
+__device__ __forceinline__ C mc_mu(C p, C r, const ConstsC<C> &k) {
+    return FMA(-k.c3, p * p, r);
+}
+
+// Model C update of (phi, rho) from the values, the stencil sum of phi and the
+// stencil sum of the density's chemical potential.
+template <typename C>
+__device__ __forceinline__ void mc_update(C p, C r, C Sp, C Sm, const ConstsC<C> &k, C &pn, C &rn) {
+    const C g = FMA(-k.c2, p * p, FMA(k.c3x2, r, k.c1));
+    pn = FMA(k.dt, FMA(p, g, k.sAC * Sp), p);
+    rn = FMA(k.dq, Sm, r);
+}
+
+// Fields per model (Gray-Scott u, v; Model C phi, rho).
+template <int MODEL> __host__ __device__ constexpr int num_fields() { return (MODEL == GS || MODEL == MC) ? 2 : 1; }
+
+// Second stencil sum of a two-field model from the accessors of field 0 and
+// field 1 at the taps: of field 1 itself (Gray-Scott), or of Model C's density
+// chemical potential mc_mu evaluated at every tap.
+template <int MODEL, int ST, typename C, typename A0, typename A1>
+__device__ __forceinline__ C second_sum(const A0 &P0, const A1 &P1, const ConstsC<C> &k) {
+    if constexpr (MODEL == MC) {
+        auto Pm = [&](int dx, int dy, int dz) -> C { return mc_mu<C>(P0(dx, dy, dz), P1(dx, dy, dz), k); };
+        return stencil_sum<ST, C>(Pm);
+    } else {
+        return stencil_sum<ST, C>(P1);
+    }
+}
+
+// Update of a two-field model from centre values and the two stencil sums.
+template <int MODEL, typename C>
+__device__ __forceinline__ void two_field_update(C p0, C p1, C S0, C S1, const ConstsC<C> &k, C &o0, C &o1) {
+    if constexpr (MODEL == MC) mc_update<C>(p0, p1, S0, S1, k, o0, o1);
+    else gs_update<C>(p0, p1, S0, S1, k, o0, o1);
 }
 
 // ------------------------------------------------------- launch records --

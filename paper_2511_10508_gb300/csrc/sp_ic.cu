@@ -51,6 +51,8 @@ __global__ void ic_kernel(T *u, T *v, int model, int dims, int nx, int ny, int n
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
         if (!gs) {
             u[i] = round_store<T>(ic_kind == SP_IC_NOISE ? noise(seed, i, mean, amp) : mean);
+            // Model C: rho from the second stream
+            if (model == MC) v[i] = round_store<T>(ic_kind == SP_IC_NOISE ? noise(seed, N + i, mean, amp) : mean);
             continue;
         }
         if (ic_kind != SP_IC_NOISE) {

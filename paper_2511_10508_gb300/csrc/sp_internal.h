@@ -17,6 +17,8 @@ constexpr int kReduceBlocksPerSM = 2;
 struct ReduceGeom {
     int nx, ny, nz, dims;
     double h, cell_volume, c1, c2;
+    double c3 = 0.0;            // Model C free energy: coupling
+    const void *rho = nullptr;  // Model C free energy: the density field (else null)
 };
 
 // Step launchers, one per storage type (sp_step_f64.cu, sp_step_f32.cu,

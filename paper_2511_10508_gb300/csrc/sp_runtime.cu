@@ -72,6 +72,7 @@ extern "C" void sp_params_default(int model, int dims, sp_params *p) {
     p->Dv = 0.08;
     p->F = 0.035;
     p->k = 0.065;
+    p->c3 = 0.5;
     p->stencil = dims == 3 ? SP_LAP_7 : SP_LAP_5;
     p->dtype = SP_F64;
     p->seed = 0;
@@ -107,14 +108,19 @@ static double max_growth(int model, int st, double h, const sp_params &p) {
                 if (ls > 0 && ls < lam) m = std::fmax(m, std::fabs(ls * (p.kappa * ls + a)));
             }
         }
-    } else {
+    } else if (model == SP_GRAY_SCOTT) {
         m = std::fmax(std::fabs(p.Du * lam + p.F), std::fabs(p.Dv * lam + p.F + p.k));
+    } else {
+        // Model C: phi as Allen-Cahn about rho = 0, rho diffuses with unit mobility
+        const double as[2] = {p.c1 - 3.0 * p.c2, p.c1};
+        for (double a : as) m = std::fmax(m, std::fmax(std::fabs(a), std::fabs(-lam + a)));
+        m = std::fmax(m, lam);
     }
     return m;
 }
 
 static int validate_params(int model, int dims, double h, double dt, const sp_params &p, int *st_out) {
-    if (model < SP_ALLEN_CAHN || model > SP_GRAY_SCOTT) return fail(SP_EINVAL, "unknown model %d", model);
+    if (model < SP_ALLEN_CAHN || model > SP_MODEL_C) return fail(SP_EINVAL, "unknown model %d", model);
     if (dims != 2 && dims != 3) return fail(SP_EINVAL, "dims must be 2 or 3 (got %d)", dims);
     const int st = resolve_stencil(p.stencil, dims);
     if (st < SP_LAP_5 || st > SP_LAP_13CROSS4) return fail(SP_EINVAL, "unknown stencil %d", p.stencil);
@@ -189,6 +195,8 @@ static StepConsts make_consts(const sp_sim &s) {
     k.F = s.p.F;
     k.Fk = s.p.F + s.p.k;
     k.dt = s.dt;
+    k.c3 = s.p.c3;
+    k.c3x2 = 2.0 * s.p.c3;
     return k;
 }
 
@@ -239,7 +247,7 @@ extern "C" int sp_create(int model, int dims, const int64_t shape[3], double h, 
     s->dims = dims;
     s->stencil = st;
     s->dtype = prm.dtype;
-    s->nf = model == SP_GRAY_SCOTT ? 2 : 1;
+    s->nf = (model == SP_GRAY_SCOTT || model == SP_MODEL_C) ? 2 : 1;
     s->nx = (int)nx;
     s->ny = (int)ny;
     s->nz = (int)nz;
@@ -311,8 +319,7 @@ static cudaError_t launch_one_step_impl(sp_sim *s, cudaStream_t st, int k) {
     a.ny = s->ny;
     a.nz = s->nz;
     a.k = s->k;
-    a.kf = {(float)s->k.c1, (float)s->k.c2, (float)s->k.sAC, (float)s->k.kq, (float)s->k.dq,
-            (float)s->k.duq, (float)s->k.dvq, (float)s->k.F, (float)s->k.Fk, (float)s->k.dt};
+    a.kf = to_float(s->k);
     if (s->variant == kUnfusedFamily) return launch_unfused_ch(s->dtype, s->stencil, a, s->mu_tmp, st, s->n_sm);
     switch (s->dtype) {
     case SP_F64: return launch_step_f64(s->model, s->stencil, a, st, s->n_sm, k);
@@ -557,8 +564,9 @@ extern "C" int sp_write(sp_sim *s, int field, const void *host_src, size_t bytes
 extern "C" int sp_reduce(sp_sim *s, int what, double *out, void *stream) {
     if (!s || !out) return fail(SP_EINVAL, "NULL argument");
     if (what < SP_MASS || what > SP_SUMSQ_U) return fail(SP_EINVAL, "unknown reduction %d", what);
-    if (what == SP_SUM_V && s->nf < 2) return fail(SP_EINVAL, "SP_SUM_V needs the Gray-Scott model");
-    const int field = what == SP_SUM_V ? 1 : 0;
+    if (what == SP_SUM_V && s->nf < 2) return fail(SP_EINVAL, "SP_SUM_V needs a two-field model");
+    // Model C: the conserved field is rho (field 1)
+    const int field = (what == SP_SUM_V || (what == SP_MASS && s->model == SP_MODEL_C)) ? 1 : 0;
     ReduceGeom g;
     g.nx = s->nx;
     g.ny = s->ny;
@@ -568,6 +576,9 @@ extern "C" int sp_reduce(sp_sim *s, int what, double *out, void *stream) {
     g.cell_volume = s->dims == 3 ? (s->h * s->h) * s->h : s->h * s->h;
     g.c1 = s->p.c1;
     g.c2 = s->p.c2;
+    g.c3 = s->p.c3;
+    // Model C free energy adds rho^2/2 - c3 phi^2 rho
+    g.rho = (what == SP_FREE_ENERGY && s->model == SP_MODEL_C) ? s->f[s->cur][1] : nullptr;
     const cudaStream_t st = pick(s, stream);
     double *d_out = s->d_partials + 2 * (size_t)s->nred;
     SP_CUDA(launch_reduce(s->dtype, what, s->f[s->cur][field], g, s->d_partials, s->nred, d_out, st));

@@ -53,7 +53,7 @@ template <typename T> constexpr size_t batch2d_smem() {
     size_t m = 0;
 #define SP_M(MO, ST) m = std::max(m, Step2dTileShape<MO, ST, T, kB2X, kB2Y>::smem_bytes);
     SP_M(AC, L5) SP_M(AC, L9BOX) SP_M(AC, L9X4) SP_M(CH, L5) SP_M(CH, L9BOX) SP_M(CH, L9X4)
-    SP_M(GS, L5) SP_M(GS, L9BOX) SP_M(GS, L9X4)
+    SP_M(GS, L5) SP_M(GS, L9BOX) SP_M(GS, L9X4) SP_M(MC, L5) SP_M(MC, L9BOX) SP_M(MC, L9X4)
 #undef SP_M
     return m;
 }
@@ -61,7 +61,7 @@ template <typename T> constexpr size_t batch3d_smem() {
     size_t m = 0;
 #define SP_M(MO, ST) m = std::max(m, Step3dBoxShape<MO, ST, T, kB3X, kB3Y, kB3Z>::smem_bytes);
     SP_M(AC, L7) SP_M(AC, L27) SP_M(AC, L13X4) SP_M(CH, L7) SP_M(CH, L27) SP_M(CH, L13X4)
-    SP_M(GS, L7) SP_M(GS, L27) SP_M(GS, L13X4)
+    SP_M(GS, L7) SP_M(GS, L27) SP_M(GS, L13X4) SP_M(MC, L7) SP_M(MC, L27) SP_M(MC, L13X4)
 #undef SP_M
     return m;
 }
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kBatchNT) batch2d_kernel(const GridDesc *__res
         break;
     switch (g.model * 8 + g.stencil) {
         SP_C(AC, L5) SP_C(AC, L9BOX) SP_C(AC, L9X4) SP_C(CH, L5) SP_C(CH, L9BOX) SP_C(CH, L9X4)
-        SP_C(GS, L5) SP_C(GS, L9BOX) SP_C(GS, L9X4)
+        SP_C(GS, L5) SP_C(GS, L9BOX) SP_C(GS, L9X4) SP_C(MC, L5) SP_C(MC, L9BOX) SP_C(MC, L9X4)
     }
 #undef SP_C
 }
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kBatchNT) batch3d_kernel(const GridDesc *__res
         break;
     switch (g.model * 8 + g.stencil) {
         SP_C(AC, L7) SP_C(AC, L27) SP_C(AC, L13X4) SP_C(CH, L7) SP_C(CH, L27) SP_C(CH, L13X4)
-        SP_C(GS, L7) SP_C(GS, L27) SP_C(GS, L13X4)
+        SP_C(GS, L7) SP_C(GS, L27) SP_C(GS, L13X4) SP_C(MC, L7) SP_C(MC, L27) SP_C(MC, L13X4)
     }
 #undef SP_C
 }
@@ -219,6 +219,8 @@ static StepConsts consts_of(const sp_request &r, int stencil) {
     k.F = r.params.F;
     k.Fk = r.params.F + r.params.k;
     k.dt = r.dt;
+    k.c3 = r.params.c3;
+    k.c3x2 = 2.0 * r.params.c3;
     return k;
 }
 
@@ -284,8 +286,7 @@ static cudaError_t upload_descriptors(sp_server *S, int Q) {
         d.parity = q->parity;
         d.steps = (int)std::min<int64_t>(Q, q->steps_left);
         d.k = q->k;
-        d.kf = {(float)q->k.c1, (float)q->k.c2, (float)q->k.sAC, (float)q->k.kq, (float)q->k.dq,
-                (float)q->k.duq, (float)q->k.dvq, (float)q->k.F, (float)q->k.Fk, (float)q->k.dt};
+        d.kf = to_float(q->k);
     }
     if (S->resident.empty()) return cudaSuccess;
     return cudaMemcpyAsync(S->d_grids, S->h_grids, sizeof(GridDesc) * S->resident.size(), cudaMemcpyHostToDevice,
@@ -347,7 +348,9 @@ static int retire(sp_server *S, Req *q) {
     g.c2 = q->r.params.c2;
     const int nb = reduce_blocks(q->N, S->n_sm);
     double *d_out = S->d_partials + 2 * (size_t)S->nred;
-    cudaError_t e = launch_reduce(q->r.params.dtype, SP_MASS, q->buf[cur][0], g, S->d_partials, nb, d_out, S->stream);
+    // the mass of the conserved field (Model C: rho)
+    const int mf = q->r.model == SP_MODEL_C ? 1 : 0;
+    cudaError_t e = launch_reduce(q->r.params.dtype, SP_MASS, q->buf[cur][mf], g, S->d_partials, nb, d_out, S->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(S->h_scalar, d_out, sizeof(double), cudaMemcpyDeviceToHost, S->stream);
     if (e == cudaSuccess && q->r.return_fields) {
         q->host.resize((size_t)q->N * q->nf);
@@ -521,7 +524,7 @@ extern "C" int sp_submit(sp_server *S, const sp_request *r, uint64_t *ticket) {
     q->r = *r;
     q->r.params = p;
     q->stencil = st;
-    q->nf = r->model == SP_GRAY_SCOTT ? 2 : 1;
+    q->nf = (r->model == SP_GRAY_SCOTT || r->model == SP_MODEL_C) ? 2 : 1;
     q->nx = (int)nx;
     q->ny = (int)ny;
     q->nz = (int)nz;

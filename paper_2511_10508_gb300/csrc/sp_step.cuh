@@ -14,6 +14,7 @@
 //   step3d_wr_kernel     3D, FP32/BF16: warp per tile row, z in register queues
 //   step3d_async_kernel  3D, FP32/BF16: cp.async plane ring, planes in flight
 //   step3d_vec_kernel    3D, FP32/BF16: plane rings of 16-byte chunks (any nx)
+//   step3d_box_kernel    3D, FP32/BF16 Model C: one CTA per box
 #pragma once
 
 #include "sp_common.cuh"
@@ -44,7 +45,7 @@ struct Step2dBatchShape {
     // may still read this batch's rows, which stays collision-free when the ring
     // has 2*RB + 2r slots (row differences lie in [1, 2RB+2r-1]).
     static constexpr int DIN = 2 * RB + 2 * r;
-    static constexpr int NF = (MODEL == GS) ? 2 : 1;
+    static constexpr int NF = num_fields<MODEL>();
     // mu ring: a batch reads mu rows [yb-r, yb+RB+r); the next batch's rows are
     // written only after a barrier that follows this batch's output.
     static constexpr int WMU = (MODEL == CH) ? TW + 2 * r : 0;
@@ -154,13 +155,13 @@ __global__ void __launch_bounds__(NT) step2d_batch_kernel(StepArgs a, int strips
                                 auto P1 = [&](int dx, int dy, int) -> C {
                                     return s_in[NF - 1][slot_in(y + dy)][c + RIN + dx];
                                 };
-                                gs_update<C>(p0, s_in[NF - 1][slot_in(y)][c + RIN], S0, stencil_sum<ST, C>(P1), k,
-                                             o0, o1);
+                                two_field_update<MODEL, C>(p0, s_in[NF - 1][slot_in(y)][c + RIN], S0,
+                                                           second_sum<MODEL, ST, C>(P0, P1, k), k, o0, o1);
                             }
                         }
                         if (x < nx) {
                             out[0][row + x] = from_c<T>(o0);
-                            if constexpr (MODEL == GS) out[1][row + x] = from_c<T>(o1);
+                            if constexpr (num_fields<MODEL>() == 2) out[1][row + x] = from_c<T>(o1);
                         }
                     }
                 }
@@ -224,7 +225,7 @@ struct Step2dTileShape {
     static constexpr int SW = NCK * CK;                // row stride (elements of T)
     static constexpr int X0 = HC * CK;                 // smem column of the tile's first column
     static constexpr int HIN = BY + 2 * R;             // rows
-    static constexpr int NF = (MODEL == GS) ? 2 : 1;
+    static constexpr int NF = num_fields<MODEL>();
     static constexpr int WMU = (MODEL == CH) ? BX + 2 * r : 0, HMU = (MODEL == CH) ? BY + 2 * r : 0;
     static constexpr size_t bytes_in = sizeof(T) * (size_t)NF * HIN * SW;
     static constexpr size_t smem_bytes = bytes_in + sizeof(C) * (size_t)WMU * HMU;
@@ -294,8 +295,8 @@ __device__ __forceinline__ void tile2d(const T *in0, const T *in1, T *out0, T *o
             } else {
                 auto P1 = [&](int dx, int dy, int) -> C { return phi(NF - 1, i + R + dy, j + X0 + dx); };
                 C un, vn;
-                gs_update<C>(phi(0, i + R, j + X0), phi(NF - 1, i + R, j + X0), S0, stencil_sum<ST, C>(P1), k,
-                             un, vn);
+                two_field_update<MODEL, C>(phi(0, i + R, j + X0), phi(NF - 1, i + R, j + X0), S0,
+                                           second_sum<MODEL, ST, C>(P0, P1, k), k, un, vn);
                 out[0][o] = from_c<T>(un);
                 out[NF - 1][o] = from_c<T>(vn);
             }
@@ -335,7 +336,7 @@ struct Step2dTbShape {
     static constexpr int NCK = BX / CK + 2 * HC;
     static constexpr int SW = NCK * CK, X0 = HC * CK;
     static constexpr int HIN = BY + 2 * KR;
-    static constexpr int NF = (MODEL == GS) ? 2 : 1;
+    static constexpr int NF = num_fields<MODEL>();
     static constexpr int MMU = R * (K - 1) + r;         // widest mu margin
     static constexpr int WMU = (MODEL == CH) ? BX + 2 * MMU : 0, HMU = (MODEL == CH) ? BY + 2 * MMU : 0;
     static constexpr size_t buf_elems = (size_t)HIN * SW;
@@ -414,19 +415,19 @@ __global__ void __launch_bounds__(NT) step2d_tb_kernel(StepArgs a) {
                     o0 = ac_update<C>(to_c(at(src, 0, i, j)), S0, k);
                 } else {
                     auto P1 = [&](int dx, int dy, int) -> C { return to_c(at(src, NF - 1, i + dy, j + dx)); };
-                    gs_update<C>(to_c(at(src, 0, i, j)), to_c(at(src, NF - 1, i, j)), S0, stencil_sum<ST, C>(P1), k,
-                                 o0, o1);
+                    two_field_update<MODEL, C>(to_c(at(src, 0, i, j)), to_c(at(src, NF - 1, i, j)), S0,
+                                               second_sum<MODEL, ST, C>(P0, P1, k), k, o0, o1);
                 }
             }
             if (s + 1 < K) {
                 at(dst, 0, i, j) = from_c<T>(o0);
-                if constexpr (MODEL == GS) at(dst, 1, i, j) = from_c<T>(o1);
+                if constexpr (num_fields<MODEL>() == 2) at(dst, 1, i, j) = from_c<T>(o1);
             } else {
                 const int y = y0 + i, x = x0 + j;
                 if (y < ny && x < nx) {
                     const size_t o = (size_t)y * (size_t)nx + x;
                     out[0][o] = from_c<T>(o0);
-                    if constexpr (MODEL == GS) out[1][o] = from_c<T>(o1);
+                    if constexpr (num_fields<MODEL>() == 2) out[1][o] = from_c<T>(o1);
                 }
             }
         }
@@ -451,7 +452,7 @@ struct Step3dBoxShape {
     static constexpr int NCK = BX / CK + 2 * HC;
     static constexpr int SW = NCK * CK, X0 = HC * CK;
     static constexpr int HIN = BY + 2 * R, DIN = BZ + 2 * R;
-    static constexpr int NF = (MODEL == GS) ? 2 : 1;
+    static constexpr int NF = num_fields<MODEL>();
     static constexpr int WMU = (MODEL == CH) ? BX + 2 * r : 0, HMU = (MODEL == CH) ? BY + 2 * r : 0,
                          DMU = (MODEL == CH) ? BZ + 2 * r : 0;
     static constexpr size_t bytes_in = sizeof(T) * (size_t)NF * DIN * HIN * SW;
@@ -529,13 +530,23 @@ __device__ __forceinline__ void box3d(const T *in0, const T *in1, T *out0, T *ou
                     return phi(NF - 1, zb + R + dz, i + R + dy, j + X0 + dx);
                 };
                 C un, vn;
-                gs_update<C>(phi(0, zb + R, i + R, j + X0), phi(NF - 1, zb + R, i + R, j + X0), S0,
-                             stencil_sum<ST, C>(P1), k, un, vn);
+                two_field_update<MODEL, C>(phi(0, zb + R, i + R, j + X0), phi(NF - 1, zb + R, i + R, j + X0), S0,
+                                           second_sum<MODEL, ST, C>(P0, P1, k), k, un, vn);
                 out[0][o] = from_c<T>(un);
                 out[NF - 1][o] = from_c<T>(vn);
             }
         }
     }
+}
+
+// One CTA per BX x BY x BZ box of a single grid (Model C, FP32 / BF16 3D).
+template <int MODEL, int ST, typename T, int BX, int BY, int BZ, int NT>
+__global__ void __launch_bounds__(NT) step3d_box_kernel(StepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const ConstsC<typename Cmp<T>::type> k(a.k, a.kf);
+    box3d<MODEL, ST, T, BX, BY, BZ, NT>(static_cast<const T *>(a.in0), static_cast<const T *>(a.in1),
+                                        static_cast<T *>(a.out0), static_cast<T *>(a.out1), a.nx, a.ny, a.nz, k,
+                                        blockIdx.x * BX, blockIdx.y * BY, blockIdx.z * BZ, smem_raw);
 }
 
 // ===================================================== 2D, warp rows ==
@@ -561,7 +572,7 @@ struct Step2dWarpShape {
     static constexpr int r = StencilInfo<ST>::r;
     static constexpr int V = 16 / (int)sizeof(T);
     static constexpr int RIN = (MODEL == CH) ? 2 * r : r;
-    static constexpr int NF = (MODEL == GS) ? 2 : 1;
+    static constexpr int NF = num_fields<MODEL>();
     static constexpr int U = 2 * r + 1;        // window rows = unroll = prefetch depth
     static constexpr int XW = V + 2 * r;       // a row of the window: own vector plus r halo each side
     static constexpr int OUT_COLS = 30 * V;    // output columns per strip
@@ -686,14 +697,14 @@ __global__ void __launch_bounds__(NT) step2d_warp_kernel(StepArgs a, int strips,
                                     auto P1 = [&](int dx, int dy, int) -> C {
                                         return ph[NF - 1][SLOT(r - dy)][r + c + dx];
                                     };
-                                    gs_update<C>(p0, ph[NF - 1][SLOT(r)][r + c], S0, stencil_sum<ST, C>(P1), k, o0[c],
-                                                 o1[c]);
+                                    two_field_update<MODEL, C>(p0, ph[NF - 1][SLOT(r)][r + c], S0,
+                                                               second_sum<MODEL, ST, C>(P0, P1, k), k, o0[c], o1[c]);
                                 }
                             }
                             if (store) {
                                 const size_t o = (size_t)(j - r) * nx + col;
                                 store_vec<T, V>(out[0] + o, o0);
-                                if constexpr (MODEL == GS) store_vec<T, V>(out[NF - 1] + o, o1);
+                                if constexpr (num_fields<MODEL>() == 2) store_vec<T, V>(out[NF - 1] + o, o1);
                             }
                         }
                     }
@@ -717,7 +728,7 @@ struct Step3dShape {
     static constexpr int RIN = (MODEL == CH) ? 2 * r : r;
     static constexpr int WIN = TX + 2 * RIN, HIN = TY + 2 * RIN, AIN = WIN * HIN;
     static constexpr int DIN = 2 * r + 2;
-    static constexpr int NF = (MODEL == GS) ? 2 : 1;
+    static constexpr int NF = num_fields<MODEL>();
     static constexpr int WMU = TX + 2 * r, HMU = TY + 2 * r, AMU = WMU * HMU;
     static constexpr int DMU = (MODEL == CH) ? 2 * r + 1 : 0;
     static constexpr int EPT = (AIN + NT - 1) / NT;  // loaded cells per thread per field
@@ -840,10 +851,10 @@ __global__ void __launch_bounds__(NT) step3d_kernel(StepArgs a, int tiles_x, int
                         auto P1 = [&](int dx, int dy, int dz) -> C {
                             return S_in(NF - 1, (j - r + dz) % DIN)[b + dy * WIN + dx];
                         };
-                        const C S1 = stencil_sum<ST, C>(P1);
+                        const C S1 = second_sum<MODEL, ST, C>(P0, P1, k);
                         const C p1 = S_in(NF - 1, (j - r) % DIN)[b];
                         C un, vn;
-                        gs_update<C>(p0, p1, S0, S1, k, un, vn);
+                        two_field_update<MODEL, C>(p0, p1, S0, S1, k, un, vn);
                         out[0][o] = from_c<T>(un);
                         out[NF - 1][o] = from_c<T>(vn);
                     }
@@ -876,7 +887,7 @@ struct Step3dZregShape {
     static constexpr int r = 1;
     static constexpr int RIN = (MODEL == CH) ? 2 : 1;
     static constexpr int WIN = TX + 2 * RIN, HIN = TY + 2 * RIN, AIN = WIN * HIN;
-    static constexpr int NF = (MODEL == GS) ? 2 : 1;
+    static constexpr int NF = num_fields<MODEL>();
     static constexpr int WMU = TX + 2, HMU = TY + 2, AMU = (MODEL == CH) ? WMU * HMU : 0;
     static constexpr int EPT = (AIN + NT - 1) / NT;       // loaded cells per thread per field
     static constexpr int EMU = (AMU + NT - 1) / NT;       // mu points per thread
@@ -904,6 +915,7 @@ __device__ __forceinline__ double combine27(double fm, double f0, double fp, dou
 template <int MODEL, int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT) step3d_zreg_kernel(StepArgs a, int tiles_x, int tiles_y,
                                                          long long planes_per_cta) {
+    static_assert(MODEL != MC, "Model C runs on the accessor-based kernels");
     typedef Step3dZregShape<MODEL, TX, TY, NT> Sh;
     typedef double C;
     constexpr int RIN = Sh::RIN, WIN = Sh::WIN, AIN = Sh::AIN, NF = Sh::NF;
@@ -1137,7 +1149,7 @@ struct Step3dWrShape {
     static constexpr int NP = Planar<ST>::NP;
     static constexpr int Q = 2 * r + 1;               // planes in a queue (incl. the newest)
     static constexpr int P = 3;                       // planes in flight
-    static constexpr int NF = (MODEL == GS) ? 2 : 1;
+    static constexpr int NF = num_fields<MODEL>();
     static constexpr size_t plane_bytes = (size_t)HIN * 32 * CB;
     static constexpr size_t in_bytes = (size_t)(P + 1) * NF * plane_bytes;
     static constexpr size_t mu_bytes = (MODEL == CH) ? (size_t)HIN * 32 * V * sizeof(float) : 0;
@@ -1147,6 +1159,7 @@ struct Step3dWrShape {
 template <int MODEL, int ST, typename T, int TY>
 __global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT)
     step3d_wr_kernel(StepArgs a, int tiles_x, int tiles_y, int segs) {
+    static_assert(MODEL != MC, "Model C runs on the accessor-based kernels");
     typedef Step3dWrShape<MODEL, ST, T, TY> Sh;
     typedef float C;
     constexpr int V = Sh::V, r = Sh::r, R = Sh::R, HIN = Sh::HIN, XW = Sh::XW, NP = Sh::NP, Q = Sh::Q;
@@ -1315,7 +1328,7 @@ __global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT)
                             if (store) {
                                 const size_t o = (size_t)(z0 - 2 * r + j) * plane + (size_t)yo * nx + col;
                                 store_vec<T, V>(out[0] + o, o0);
-                                if constexpr (MODEL == GS) store_vec<T, V>(out[NF - 1] + o, o1);
+                                if constexpr (num_fields<MODEL>() == 2) store_vec<T, V>(out[NF - 1] + o, o1);
                             }
                         }
                     }
@@ -1361,7 +1374,7 @@ struct Step3dAsyncShape {
     static constexpr int D = P + 2 * r + 1;          // input ring slots
     static constexpr int HMU = TY + 2 * r, PMU = HMU * SW;
     static constexpr int DMU = (MODEL == CH) ? 2 * r + 1 : 0;
-    static constexpr int NF = (MODEL == GS) ? 2 : 1;
+    static constexpr int NF = num_fields<MODEL>();
     static constexpr int EPT = (HIN * NCH + NT - 1) / NT;  // chunk copies per thread per field
     static constexpr int GUARD = 16;                 // bytes before and after each region
     static constexpr size_t in_bytes = sizeof(T) * (size_t)NF * D * PIN;
@@ -1420,6 +1433,7 @@ __device__ __forceinline__ void async_chunk_sums(const T *const (&pl)[2 * Stenci
 
 template <int MODEL, int ST, typename T, int TXT, int TY>
 __global__ void __launch_bounds__(TXT * TY) step3d_async_kernel(StepArgs a, int tiles_x, int tiles_y, int segs) {
+    static_assert(MODEL != MC, "Model C runs on the accessor-based kernels");
     typedef Step3dAsyncShape<MODEL, ST, T, TXT, TY> Sh;
     typedef typename Sh::C C;
     constexpr int V = Sh::V, r = Sh::r, R = Sh::R, TX = Sh::TX, NT = Sh::NT, NCH = Sh::NCH, SW = Sh::SW;
@@ -1541,7 +1555,7 @@ __global__ void __launch_bounds__(TXT * TY) step3d_async_kernel(StepArgs a, int 
                         }
                         const size_t o = (size_t)zo * plane + (size_t)y * nx + x;
                         store_vec<T, V>(out[0] + o, o0);
-                        if constexpr (MODEL == GS) store_vec<T, V>(out[NF - 1] + o, o1);
+                        if constexpr (num_fields<MODEL>() == 2) store_vec<T, V>(out[NF - 1] + o, o1);
                     }
                 }
             }
@@ -1577,7 +1591,7 @@ struct Step3dVecShape {
     static constexpr int PMU = HMU * SW;
     static constexpr int DIN = 2 * r + 2;
     static constexpr int DMU = (MODEL == CH) ? 2 * r + 1 : 0;
-    static constexpr int NF = (MODEL == GS) ? 2 : 1;
+    static constexpr int NF = num_fields<MODEL>();
     static constexpr int GUARD = 2 * V;          // cells before and after the planes
     static constexpr int EPT = (HIN * NCH + NT - 1) / NT;  // input chunks per thread per field
     static constexpr size_t smem_bytes = sizeof(C) * ((size_t)2 * GUARD + (size_t)NF * DIN * PIN + (size_t)DMU * PMU);
@@ -1625,6 +1639,7 @@ __device__ __forceinline__ void chunk_sums(const float *const (&pl)[2 * StencilI
 template <int MODEL, int ST, typename T, int TXT, int TYT>
 __global__ void __launch_bounds__(TXT * TYT) step3d_vec_kernel(StepArgs a, int tiles_x, int tiles_y,
                                                                long long planes_per_cta) {
+    static_assert(MODEL != MC, "Model C runs on the accessor-based kernels");
     typedef Step3dVecShape<MODEL, ST, T, TXT, TYT> Sh;
     typedef typename Sh::C C;
     constexpr int V = Sh::V, r = Sh::r, R = Sh::R, TX = Sh::TX, TY = Sh::TY, NT = Sh::NT;
@@ -1773,7 +1788,7 @@ __global__ void __launch_bounds__(TXT * TYT) step3d_vec_kernel(StepArgs a, int t
                     else
                         for (int j = 0; j < V; ++j)
                             if (x + j < nx) dst0[x + j] = from_c<T>(o0[j]);
-                    if constexpr (MODEL == GS) {
+                    if constexpr (num_fields<MODEL>() == 2) {
                         T *dst1 = out[1] + o;
                         if (vec_ok && x + V <= nx) store_vec<T, V>(dst1 + x, o1);
                         else

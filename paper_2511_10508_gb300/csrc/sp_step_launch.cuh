@@ -74,6 +74,25 @@ cudaError_t launch_tb(const StepArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// FP64 27-point: z-streaming kernel with per-plane partial sums in registers.
+template <int MODEL, typename T>
+cudaError_t launch_zreg(const StepArgs &a, cudaStream_t s, int n_sm) {
+    constexpr int TX = 32, TY = 32, NT = 256;
+    typedef Step3dZregShape<MODEL, TX, TY, NT> Sh;
+    auto kern = step3d_zreg_kernel<MODEL, TX, TY, NT>;
+    static const int occ = [&] {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem_bytes);
+        int o = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT, Sh::smem_bytes);
+        return o;
+    }();
+    const int tx = (a.nx + TX - 1) / TX, ty = (a.ny + TY - 1) / TY;
+    const long long ctas = persistent_ctas((long long)tx * ty * a.nz, occ, n_sm);
+    const long long planes = ((long long)tx * ty * a.nz + ctas - 1) / ctas;
+    kern<<<(unsigned)(((long long)tx * ty * a.nz + planes - 1) / planes), NT, Sh::smem_bytes, s>>>(a, tx, ty, planes);
+    return cudaGetLastError();
+}
+
 template <int MODEL, int ST, typename T>
 cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
     if constexpr (StencilInfo<ST>::dims == 2 && !std::is_same<T, double>::value) {
@@ -151,6 +170,18 @@ cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
         (void)attr;
         dim3 grid((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY);
         kern<<<grid, NT, Sh::smem_bytes, s>>>(a);
+    } else if constexpr (!std::is_same<T, double>::value && MODEL == MC) {
+        // Model C, FP32 / BF16 3D: one CTA per box (the accessor-based box code)
+        constexpr int BX = 32, BY = 8, BZ = 8, NT = 256;
+        typedef Step3dBoxShape<MODEL, ST, T, BX, BY, BZ> Sh;
+        auto kern = step3d_box_kernel<MODEL, ST, T, BX, BY, BZ, NT>;
+        static const bool attr = [&] {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem_bytes);
+            return true;
+        }();
+        (void)attr;
+        const int bx = (a.nx + BX - 1) / BX, by = (a.ny + BY - 1) / BY, bz = (a.nz + BZ - 1) / BZ;
+        kern<<<dim3((unsigned)bx, (unsigned)by, (unsigned)bz), NT, Sh::smem_bytes, s>>>(a);
     } else if constexpr (!std::is_same<T, double>::value) {
         constexpr int ATX = 16, ATY = 16;
         typedef Step3dAsyncShape<MODEL, ST, T, ATX, ATY> AS;
@@ -211,23 +242,10 @@ cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
         const long long planes = ((long long)tx * ty * a.nz + ctas - 1) / ctas;
         kern<<<(unsigned)(((long long)tx * ty * a.nz + planes - 1) / planes), Sh::NT, Sh::smem_bytes, s>>>(
             a, tx, ty, planes);
-    } else if (ST == L27 && g_step_variant == 0) {
-        // FP64 27-point: z-streaming kernel with per-plane partial sums in registers
-        constexpr int TX = 32, TY = 32, NT = 256;
-        typedef Step3dZregShape<MODEL, TX, TY, NT> Sh;
-        auto kern = step3d_zreg_kernel<MODEL, TX, TY, NT>;
-        static const int occ = [&] {
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem_bytes);
-            int o = 1;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT, Sh::smem_bytes);
-            return o;
-        }();
-        const int tx = (a.nx + TX - 1) / TX, ty = (a.ny + TY - 1) / TY;
-        const long long ctas = persistent_ctas((long long)tx * ty * a.nz, occ, n_sm);
-        const long long planes = ((long long)tx * ty * a.nz + ctas - 1) / ctas;
-        kern<<<(unsigned)(((long long)tx * ty * a.nz + planes - 1) / planes), NT, Sh::smem_bytes, s>>>(
-            a, tx, ty, planes);
     } else {
+        if constexpr (MODEL != MC) {
+            if (ST == L27 && g_step_variant == 0) return launch_zreg<MODEL, T>(a, s, n_sm);
+        }
         typedef typename Tiles<T>::template T3<StencilInfo<ST>::r> TT;
         typedef Step3dShape<MODEL, ST, T, TT::TX, TT::TY, TT::NT> Sh;
         auto kern = step3d_kernel<MODEL, ST, T, TT::TX, TT::TY, TT::NT>;
@@ -262,6 +280,7 @@ cudaError_t launch_step_dispatch(int model, int stencil, const StepArgs &a, cuda
     case AC: SP_STENCILS(AC)
     case CH: SP_STENCILS(CH)
     case GS: SP_STENCILS(GS)
+    case MC: SP_STENCILS(MC)
     }
 #undef SP_STENCILS
     return cudaErrorInvalidValue;

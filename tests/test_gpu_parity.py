@@ -15,8 +15,9 @@ import oracle as O
 pytestmark = pytest.mark.gpu
 
 MODELS = {0: "AC", 1: "CH", 2: "GS"}
-DT = {0: 0.05, 1: 0.005, 2: 0.5}
-DT3 = {0: 0.05, 1: 0.002, 2: 0.25}
+DT = {0: 0.05, 1: 0.005, 2: 0.5, 3: 0.02}
+DT3 = {0: 0.05, 1: 0.002, 2: 0.25, 3: 0.02}
+TWO = (2, 3)  # two-field models: Gray-Scott, Model C
 
 
 @pytest.fixture(scope="module")
@@ -49,11 +50,11 @@ def oracle_ic(model, shape, prm):
 
 
 def oparams(prm):
-    return O.params(c1=prm.c1, c2=prm.c2, kappa=prm.kappa, Du=prm.Du, Dv=prm.Dv, F=prm.F, k=prm.k)
+    return O.params(c1=prm.c1, c2=prm.c2, kappa=prm.kappa, Du=prm.Du, Dv=prm.Dv, F=prm.F, k=prm.k, c3=prm.c3)
 
 
-CASES_2D = [(m, s) for m in (0, 1, 2) for s in (0, 1, 2)]
-CASES_3D = [(m, s) for m in (0, 1, 2) for s in (3, 4, 5)]
+CASES_2D = [(m, s) for m in (0, 1, 2, 3) for s in (0, 1, 2)]
+CASES_3D = [(m, s) for m in (0, 1, 2, 3) for s in (3, 4, 5)]
 
 
 @pytest.mark.parametrize("model,st", CASES_2D + CASES_3D)
@@ -64,15 +65,15 @@ def test_fp64_bitwise(sp, model, st):
     with sim:
         ic = oracle_ic(model, shape, sim.prm)
         u0 = sim.read(0)
-        if model == 2:
+        if model in TWO:
             assert np.array_equal(u0, ic[0]) and np.array_equal(sim.read(1), ic[1])
         else:
             assert np.array_equal(u0, ic)
         n = 9
         sim.step(n)
         assert sim.steps_taken == n
-        if model == 2:
-            ru, rv = O.step(O.GS, st, ic[0], ic[1], dt=dt, prm=oparams(sim.prm), nsteps=n)
+        if model in TWO:
+            ru, rv = O.step(model, st, ic[0], ic[1], dt=dt, prm=oparams(sim.prm), nsteps=n)
             gu, gv = sim.read(0), sim.read(1)
             assert np.array_equal(gu, ru), np.abs(gu - ru).max()
             assert np.array_equal(gv, rv), np.abs(gv - rv).max()
@@ -84,7 +85,7 @@ def test_fp64_bitwise(sp, model, st):
 
 @pytest.mark.parametrize("shape", [(1, 1), (3, 5), (2, 7), (5, 1), (33, 257), (1, 1, 1), (2, 3, 5), (3, 1, 4),
                                    (40, 33, 65)])
-@pytest.mark.parametrize("model", [0, 1, 2])
+@pytest.mark.parametrize("model", [0, 1, 2, 3])
 def test_fp64_bitwise_small_and_degenerate(sp, shape, model):
     """Sides smaller than the stencil radius (neighbours wrap several times), a
     single point, and sides one past a tile boundary."""
@@ -95,8 +96,8 @@ def test_fp64_bitwise_small_and_degenerate(sp, shape, model):
         with sim:
             ic = oracle_ic(model, shape, sim.prm)
             sim.step(5)
-            if model == 2:
-                ru, rv = O.step(O.GS, st, ic[0], ic[1], dt=dt, prm=oparams(sim.prm), nsteps=5)
+            if model in TWO:
+                ru, rv = O.step(model, st, ic[0], ic[1], dt=dt, prm=oparams(sim.prm), nsteps=5)
                 assert np.array_equal(sim.read(0), ru) and np.array_equal(sim.read(1), rv)
             else:
                 ref = O.step(model, st, ic, dt=dt, prm=oparams(sim.prm), nsteps=5)
@@ -106,13 +107,14 @@ def test_fp64_bitwise_small_and_degenerate(sp, shape, model):
 def test_fp64_long_slab_streaming(sp):
     """A tall grid is split into several slabs along the streamed axis; the slab
     seams must be invisible (bitwise) over many steps."""
-    for model, st, shape in [(1, 0, (1500, 300)), (1, 2, (900, 257)), (1, 3, (200, 40, 70)), (2, 4, (150, 33, 66))]:
+    for model, st, shape in [(1, 0, (1500, 300)), (1, 2, (900, 257)), (1, 3, (200, 40, 70)), (2, 4, (150, 33, 66)),
+                             (3, 0, (1200, 300)), (3, 4, (150, 33, 66))]:
         sim, dt = make(sp, model, shape, st)
         with sim:
             ic = oracle_ic(model, shape, sim.prm)
             sim.step(12)
-            if model == 2:
-                ru, rv = O.step(O.GS, st, ic[0], ic[1], dt=dt, prm=oparams(sim.prm), nsteps=12)
+            if model in TWO:
+                ru, rv = O.step(model, st, ic[0], ic[1], dt=dt, prm=oparams(sim.prm), nsteps=12)
                 assert np.array_equal(sim.read(0), ru) and np.array_equal(sim.read(1), rv)
             else:
                 ref = O.step(model, st, ic, dt=dt, prm=oparams(sim.prm), nsteps=12)
@@ -127,7 +129,8 @@ TOL = {1: 1e-5, 2: 1e-2}
 
 
 @pytest.mark.parametrize("dtype", [1, 2])
-@pytest.mark.parametrize("model,st", [(0, 0), (1, 0), (1, 2), (2, 0), (0, 3), (1, 3), (1, 4), (2, 3), (1, 5)])
+@pytest.mark.parametrize("model,st", [(0, 0), (1, 0), (1, 2), (2, 0), (0, 3), (1, 3), (1, 4), (2, 3), (1, 5),
+                                      (3, 0), (3, 2), (3, 3), (3, 4)])
 def test_reduced_precision_against_fp64_oracle(sp, dtype, model, st):
     dims = O.STENCIL_DIMS[st]
     shape = (60, 1100) if dims == 2 else (36, 40, 72)
@@ -135,14 +138,14 @@ def test_reduced_precision_against_fp64_oracle(sp, dtype, model, st):
     with sim:
         u0 = sim.read(0)  # the rounded initial field, widened exactly
         ic = oracle_ic(model, shape, sim.prm)
-        first = ic[0] if model == 2 else ic
+        first = ic[0] if model in TWO else ic
         # initial condition: the FP64 value rounded once to the storage type
         ulp = 2.0 ** -24 if dtype == 1 else 2.0 ** -8
         assert np.all(np.abs(u0 - first) <= ulp * np.abs(first) + 1e-300)
         n = 10
-        if model == 2:
+        if model in TWO:
             v0 = sim.read(1)
-            ru, rv = O.step(O.GS, st, u0, v0, dt=dt, prm=oparams(sim.prm), nsteps=n)
+            ru, rv = O.step(model, st, u0, v0, dt=dt, prm=oparams(sim.prm), nsteps=n)
             sim.step(n)
             eu, ev = O.rel_l2(sim.read(0), ru), O.rel_l2(sim.read(1), rv)
             assert eu < TOL[dtype] and ev < TOL[dtype], (eu, ev)
@@ -291,13 +294,13 @@ def test_graph_replay_equals_eager(sp, model, shape, dtype):
         a.step(133)
         for _ in range(133):
             b.step(1)
-        for f in range(2 if model == 2 else 1):
+        for f in range(2 if model in TWO else 1):
             assert np.array_equal(a.read(f), b.read(f))
         assert a.steps_taken == b.steps_taken == 133
 
 
 @pytest.mark.parametrize("dtype", [1, 2])
-@pytest.mark.parametrize("model,st", [(m, s) for m in (0, 1, 2) for s in (0, 1, 2)])
+@pytest.mark.parametrize("model,st", [(m, s) for m in (0, 1, 2, 3) for s in (0, 1, 2)])
 def test_temporal_blocking_equals_single_steps(sp, dtype, model, st):
     """K steps fused in one launch (intermediate values rounded to the storage type
     in shared memory) equal K single-step launches bit for bit."""
@@ -308,7 +311,7 @@ def test_temporal_blocking_equals_single_steps(sp, dtype, model, st):
         with sim:
             sim.step(1)       # first step of a handle is a single-step launch
             sim.step(12)      # blocked launches (and single steps for the rest)
-            outs.append([sim.read(f, as_f64=False) for f in range(2 if model == 2 else 1)])
+            outs.append([sim.read(f, as_f64=False) for f in range(2 if model in TWO else 1)])
     for o in outs[1:]:
         for a, b in zip(outs[0], o):
             assert np.array_equal(a, b)
@@ -342,13 +345,13 @@ def test_autotune_keeps_results(sp, model, shape, dtype, st):
             assert spl == 1 and var in (0, 1)
         else:
             assert spl in (1, 2, 4) and var == 0
-        for f in range(2 if model == 2 else 1):
+        for f in range(2 if model in TWO else 1):
             ra = a.read(f, as_f64=False)
             assert np.array_equal(ra, b.read(f, as_f64=False)) and np.array_equal(ra, c.read(f, as_f64=False))
     if dtype == 0:
         ic = oracle_ic(model, shape, prm)
-        if model == 2:
-            ru, rv = O.step(O.GS, st, ic[0], ic[1], dt=dt, prm=oparams(prm), nsteps=n)
+        if model in TWO:
+            ru, rv = O.step(model, st, ic[0], ic[1], dt=dt, prm=oparams(prm), nsteps=n)
             assert np.array_equal(ra, rv)
         else:
             assert np.array_equal(ra, O.step(model, st, ic, dt=dt, prm=oparams(prm), nsteps=n))
@@ -370,13 +373,13 @@ def test_2d_kernel_families_agree(sp, dtype, model, st, shape):
             sim.launch_config = (1, variant)
             assert sim.launch_config == (1, variant)
             sim.step(13)
-            outs.append([sim.read(f, as_f64=False) for f in range(2 if model == 2 else 1)])
+            outs.append([sim.read(f, as_f64=False) for f in range(2 if model in TWO else 1)])
     for a, b in zip(*outs):
         assert np.array_equal(a, b)
     if dtype == 1:
         ic = oracle_ic(model, shape, sim.prm)
-        if model == 2:
-            ref = O.step(O.GS, st, ic[0], ic[1], dt=dt, prm=oparams(sim.prm), nsteps=13)[0]
+        if model in TWO:
+            ref = O.step(model, st, ic[0], ic[1], dt=dt, prm=oparams(sim.prm), nsteps=13)[0]
         else:
             ref = O.step(model, st, ic, dt=dt, prm=oparams(sim.prm), nsteps=13)
         assert O.rel_l2(outs[0][0].astype(np.float64), ref) < TOL[1]
@@ -412,14 +415,14 @@ def test_3d_kernel_families_agree(sp, dtype, model, st, shape):
         with sim:
             sim.launch_config = (1, variant)
             sim.step(7)
-            outs.append([sim.read(f, as_f64=False) for f in range(2 if model == 2 else 1)])
+            outs.append([sim.read(f, as_f64=False) for f in range(2 if model in TWO else 1)])
     for other in outs[1:]:
         for a, b in zip(outs[0], other):
             assert np.array_equal(a, b)
     if dtype == 1:
         ic = oracle_ic(model, shape, sim.prm)
-        if model == 2:
-            ref = O.step(O.GS, st, ic[0], ic[1], dt=dt, prm=oparams(sim.prm), nsteps=7)[0]
+        if model in TWO:
+            ref = O.step(model, st, ic[0], ic[1], dt=dt, prm=oparams(sim.prm), nsteps=7)[0]
         else:
             ref = O.step(model, st, ic, dt=dt, prm=oparams(sim.prm), nsteps=7)
         assert O.rel_l2(outs[0][0].astype(np.float64), ref) < TOL[1]
@@ -441,7 +444,7 @@ def test_two_host_threads_step_independent_grids(sp):
                 sim.step(120 - sim.steps_taken)
             else:
                 sim.step(120)
-            out[idx] = [sim.read(f, as_f64=False) for f in range(2 if model == 2 else 1)]
+            out[idx] = [sim.read(f, as_f64=False) for f in range(2 if model in TWO else 1)]
 
     seq = [None, None]
     for i, c in enumerate(cases):
@@ -487,3 +490,33 @@ def test_unfused_ablation_only_for_cahn_hilliard(sp):
         with sim:
             with pytest.raises(sp.SpError):
                 sim.launch_config = (1, 3)
+
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("shape,st", [((64, 96), 0), ((20, 24, 28), 3), ((17, 20, 23), 4)])
+def test_model_c_reductions(sp, dtype, shape, st):
+    """Model C: SP_MASS is the conserved density's (field 1), conserved over the
+    run; SP_FREE_ENERGY adds rho^2/2 - c3 phi^2 rho and matches the oracle's."""
+    sim, dt = make(sp, 3, shape, st, dtype=dtype)
+    with sim:
+        m0 = sim.reduce(sp.MASS)
+        sim.step(40)
+        u, v = sim.read(0), sim.read(1)
+        scale = np.abs(v).sum() + 1.0
+        assert abs(sim.reduce(sp.MASS) - O.mass(v)) <= 1e-13 * scale
+        assert abs(sim.reduce(sp.MASS) - m0) <= (1e-12 if dtype == 0 else 1e-4) * scale
+        assert abs(sim.reduce(sp.SUM_V) - O.kahan_sum(v)) <= 1e-13 * scale
+        fe = O.free_energy_c(u, v, c1=sim.prm.c1, c2=sim.prm.c2, c3=sim.prm.c3)
+        assert abs(sim.reduce(sp.FREE_ENERGY) - fe) <= 1e-12 * (abs(fe) + np.abs(u).sum() + scale)
+
+
+def test_model_c_free_energy_decreases_on_gpu(sp):
+    """The GPU path of Model C is a gradient flow of the listing's free energy too."""
+    sim, _ = make(sp, 3, (96, 128), 0, dt=0.005, ic_amp=0.8, ic_mean=0.2)
+    with sim:
+        F = [sim.reduce(sp.FREE_ENERGY)]
+        for _ in range(30):
+            sim.step(2)
+            F.append(sim.reduce(sp.FREE_ENERGY))
+    assert all(b < a for a, b in zip(F, F[1:])), F

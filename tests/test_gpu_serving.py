@@ -29,6 +29,9 @@ def kw_for(model, seed):
     return dict(seed=seed, ic_amp=0.3)
 
 
+TWO = (2, 3)  # two-field models: Gray-Scott, Model C
+
+
 # (model, shape, dtype, stencil, dt, nsteps)
 MIX = [
     (1, (64, 64), 0, 0, 0.01, 37),
@@ -40,13 +43,15 @@ MIX = [
     (1, (130, 257), 1, 2, 0.002, 12),
     (1, (24, 24, 24), 0, 5, 0.001, 9),
     (0, (40, 520), 0, 1, 0.05, 80),
+    (3, (72, 90), 0, 0, 0.02, 33),
+    (3, (18, 20, 22), 1, 4, 0.02, 21),
 ]
 
 
 def alone(sp, model, shape, dtype, st, dt, n, seed):
     with sp.Simulation(model, shape, dt=dt, stencil=st, dtype=dtype, **kw_for(model, seed)) as s:
         s.step(n)
-        out = [s.read(f) for f in range(2 if model == 2 else 1)]
+        out = [s.read(f) for f in range(2 if model in TWO else 1)]
         return np.stack(out), s.reduce(sp.MASS)
 
 
@@ -61,13 +66,16 @@ def test_mix_equals_alone_and_oracle(sp):
         assert res.status == 0 and res.steps_done == n
         ref, mass = alone(sp, m, shape, dt_, st, dt, n, 100 + i)
         assert np.array_equal(res.fields, ref), f"request {i} differs from its single-grid run"
-        assert abs(res.mass - mass) <= 1e-13 * (np.abs(ref[0]).sum() + 1)
+        assert abs(res.mass - mass) <= 1e-13 * (np.abs(ref).sum() + 1)
         if dt_ == 0:
             k = kw_for(m, 100 + i)
-            if m == 2:
-                u, v = O.initial_condition(O.GS, shape, seed=k["seed"], amp=k["ic_amp"], patches=k["gs_patches"],
-                                           patch=k["gs_patch"])
-                ou, ov = O.step(O.GS, st, u, v, dt=dt, nsteps=n)
+            if m in TWO:
+                if m == 2:
+                    u, v = O.initial_condition(O.GS, shape, seed=k["seed"], amp=k["ic_amp"], patches=k["gs_patches"],
+                                               patch=k["gs_patch"])
+                else:
+                    u, v = O.initial_condition(O.MC, shape, seed=k["seed"], amp=k["ic_amp"])
+                ou, ov = O.step(m, st, u, v, dt=dt, nsteps=n)
                 assert np.array_equal(res.fields[0], ou) and np.array_equal(res.fields[1], ov)
             else:
                 u = O.initial_condition(m, shape, seed=k["seed"], amp=k["ic_amp"])
