@@ -62,6 +62,11 @@ WORKLOADS = {
     "mc2d-16384-f32-lap5": (3, 2, (16384, 16384), 0.02, 0, 1, 20),
     "mc3d-512-f64-lap7": (3, 3, (512, 512, 512), 0.02, 3, 0, 4),
     "mc3d-512-f32-lap7": (3, 3, (512, 512, 512), 0.02, 3, 1, 10),
+    # semi-implicit Fourier spectral scheme (cuFFT transforms), the stencil entry unused
+    "ch2d-4096-f64-spectral": (1, 2, (4096, 4096), 0.5, 0, 0, 20),
+    "ac2d-4096-f64-spectral": (0, 2, (4096, 4096), 0.5, 0, 0, 20),
+    "ch2d-8192-f32-spectral": (1, 2, (8192, 8192), 0.5, 0, 1, 20),
+    "ch3d-256-f64-spectral": (1, 3, (256, 256, 256), 0.5, 3, 0, 10),
     # ablation: the unfused Cahn-Hilliard step (mu through a device-memory temporary)
     "ch2d-4096-f64-lap5-unfused": (1, 2, (4096, 4096), 0.01, 0, 0, 100, 1, 3),
     "ch2d-16384-f32-lap5-unfused": (1, 2, (16384, 16384), 0.01, 0, 1, 20, 1, 3),
@@ -87,6 +92,21 @@ STENCIL_OPS = {0: 4, 1: 6, 2: 8, 3: 6, 4: 12, 5: 12}
 NCU_TRAFFIC = {
     "ch2d-4096-f64-lap5": (242.47e6, "profiles/step2d_batch_ch_f64_lap5_4096.txt"),
 }
+
+
+def spectral_ops_per_lup(npts: int) -> float:
+    """FP64 operations per update of the spectral step: two real transforms at the
+    radix-2 count of 2.5 log2(N) each, the cube (3) and the Fourier update (about
+    6.5 per real point)."""
+    import math
+
+    return 5.0 * math.log2(npts) + 9.5
+
+
+# bytes per update of the spectral step at one pass per stage: cube 2P, forward
+# transform 2P, update 4P (resident spectrum and the transform's output in, both
+# copies out, each half-spectrum ~ P per point), inverse transform 2P
+SPECTRAL_BYTES_PER_LUP_IN_P = 10
 
 
 def fp64_ops_per_lup(model: int, st: int) -> int:
@@ -170,7 +190,7 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_rate(model, dims, shape, dt, st, budget_s=15.0, max_steps=2000):
+def oracle_rate(model, dims, shape, dt, st, budget_s=15.0, max_steps=2000, spectral=False):
     """FP64 oracle GLUPS on the host cores over a bounded sample of the workload."""
     import numpy as np
 
@@ -178,6 +198,20 @@ def oracle_rate(model, dims, shape, dt, st, budget_s=15.0, max_steps=2000):
 
     prm = O.params()
     npts = int(np.prod(shape))
+    if spectral:
+        from oracle import spectral as SO
+
+        u = O.initial_condition(model, shape, seed=1, amp=0.01)
+        t0 = time.perf_counter()
+        SO.step(model, u, dt=dt, nsteps=1)
+        t1 = time.perf_counter() - t0
+        n = int(max(1, min(max_steps, budget_s / max(t1, 1e-6))))
+        t0 = time.perf_counter()
+        SO.step(model, u, dt=dt, nsteps=n)
+        el = time.perf_counter() - t0
+        return {"value": npts * n / el / 1e9, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+                "sample": f"{n} FP64 spectral oracle steps (numpy FFT) of the full {'x'.join(map(str, shape[::-1]))} "
+                          f"grid ({el:.1f} s)"}
     if model == 2:
         u, v = O.initial_condition(O.GS, shape, seed=2, amp=0.01, patches=64, patch=20)
     elif model == 3:
@@ -372,9 +406,11 @@ def run_reference(args):
 
 def workload_config(name):
     model, dims, shape, dt, st, dtype, sub = WORKLOADS[name][:7]
+    lap = ("semi-implicit Fourier spectral scheme (continuous Laplacian)" if name.endswith("-spectral")
+           else f"{STENCIL_NAME[st]} Laplacian, forward Euler")
     return {"workload": f"{MODEL_NAME[model]} {dims}D {'x'.join(map(str, shape[::-1]))} {DTYPE_NAME[dtype]}, "
-                        f"{STENCIL_NAME[st]} Laplacian, dt={dt}, h=1, periodic",
-            "model": MODEL_NAME[model], "grid": list(shape[::-1]), "stencil": STENCIL_NAME[st],
+                        f"{lap}, dt={dt}, h=1, periodic",
+            "model": MODEL_NAME[model], "grid": list(shape[::-1]), "stencil": lap,
             "storage": DTYPE_NAME[dtype], "time_steps_per_bench_step": sub,
             "l2": "inputs larger than L2 (ping-pong field buffers exceed the 126 MB L2)"
             if int(__import__("numpy").prod(shape)) * ESIZE[dtype] * 2 > 126e6 else "L2-resident (small grid)"}
@@ -413,7 +449,9 @@ def main():
     model, dims, shape, dt, st, dtype, sub = WORKLOADS[args.workload][:7]
     spl_req = WORKLOADS[args.workload][7] if len(WORKLOADS[args.workload]) > 7 else 0
     npts = int(np.prod(shape))
-    kw = dict(stencil=st, dtype=dtype, seed=1 + rank, ic_amp=0.01, steps_per_launch=spl_req)
+    spectral = args.workload.endswith("-spectral")
+    kw = dict(stencil=st, dtype=dtype, seed=1 + rank, ic_amp=0.01, steps_per_launch=spl_req,
+              scheme=sp.SCHEME_SPECTRAL if spectral else sp.SCHEME_FD)
     if model == 2:
         kw.update(seed=2 + rank, gs_patches=64, gs_patch=20)
     sim = sp.Simulation(model, shape, dt=dt, **kw)
@@ -464,7 +502,22 @@ def main():
 
     peaks = load_peaks()
     traffic = NCU_TRAFFIC[args.workload][0] if (args.workload in NCU_TRAFFIC and spl == 1 and variant == 0) else None
-    if dtype == 0:
+    if spectral and dtype == 0:
+        ops = spectral_ops_per_lup(npts)
+        achieved = ops * npts / (launch_ms * 1e-3) / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "FP64 Gop/s",
+                "frac": achieved / FP64_PEAK_GOPS, "traffic": None,
+                "note": f"semi-implicit spectral step, {ops:.1f} FP64 ops/LUP by the model 5 log2 N + 9.5 "
+                        "(two real cuFFT transforms at 2.5 log2 N each, cube, Fourier update)"}
+    elif spectral:
+        bpl = SPECTRAL_BYTES_PER_LUP_IN_P * ESIZE[dtype]
+        achieved = bpl * npts / (launch_ms * 1e-3) / 1e9
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "traffic": None,
+                "note": f"semi-implicit spectral step, {bpl} bytes/LUP at one pass per stage (cube, forward "
+                        "transform, Fourier update, inverse transform)"}
+    elif dtype == 0:
         ops = fp64_ops_per_lup(model, st)
         achieved = ops * npts / (launch_ms * 1e-3) / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "FP64 Gop/s",
@@ -512,7 +565,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_rate(model, dims, shape, dt, st)
+        cpu = oracle_rate(model, dims, shape, dt, st, spectral=spectral)
 
     served = None
     if rank == 0 and not args.no_served:

@@ -102,6 +102,23 @@ typedef enum sp_reduce_what {
 
 /* ----------------------------------------------------------- parameters -- */
 
+/* Time integration.  SP_SCHEME_FD: forward Euler with the finite-difference
+ * stencil (every model).  SP_SCHEME_SPECTRAL: the paper's semi-implicit Fourier
+ * spectral scheme (Sec. "Construction of Semi-Implicit Fourier Spectral Scheme"),
+ * Allen-Cahn and Cahn-Hilliard, FP64 or FP32: linear terms implicit in Fourier
+ * space with the continuous symbol -|k|^2 (k = 2 pi m / (n h) per axis), the
+ * cubic term explicit; phi^' = (phi^ + dt N^) / (1 - dt L(k)) with
+ *   Allen-Cahn     L = c1 - |k|^2,              N = -c2 phi^3
+ *   Cahn-Hilliard  L = |k|^2 (c1 - kappa |k|^2), N^ = -|k|^2 (c2 phi^3)^.
+ * The stencil is ignored; the step needs 1 - dt L(k) > 0 for all k (dt c1 < 1,
+ * resp. kappa > 0 and dt c1^2 / (4 kappa) < 1; SP_EUNSTABLE otherwise).  That
+ * keeps the step defined; with the cubic term explicit it is not unconditionally
+ * stable (Cahn-Hilliard from +-0.5 noise, h = 1: bounded at dt = 0.5, four times
+ * the forward-Euler limit of the 5-point stencil, divergent at dt = 1).  The
+ * spectrum stays resident on the device: sp_write refreshes it, a write through
+ * sp_field_devptr does not. */
+typedef enum sp_scheme { SP_SCHEME_FD = 0, SP_SCHEME_SPECTRAL = 1 } sp_scheme;
+
 typedef struct sp_params {
     double c1, c2, kappa;  /* Allen-Cahn / Cahn-Hilliard coefficients (defaults 1) */
     double Du, Dv, F, k;   /* Gray-Scott coefficients */
@@ -115,6 +132,7 @@ typedef struct sp_params {
     int gs_patch;          /* Gray-Scott: patch side (points) */
     int steps_per_launch;  /* time steps fused per kernel launch (temporal blocking);
                               0 = the library's choice, 1 = none */
+    int scheme;            /* sp_scheme (default SP_SCHEME_FD) */
     int flags;             /* SP_FLAG_* bits; other bits must be 0 */
 } sp_params;
 
@@ -288,7 +306,9 @@ typedef struct sp_server_stats {
 int sp_server_create(size_t hbm_budget_bytes, int max_slots, int quantum_steps, sp_server **out);
 
 /* Queue a request; *ticket identifies it.  SP_EBUDGET if it can never fit,
- * SP_EUNSTABLE / SP_EINVAL as sp_create.  Never blocks on the device. */
+ * SP_EUNSTABLE / SP_EINVAL as sp_create; served requests use FP64 or FP32 storage
+ * and the finite-difference scheme (SP_EINVAL otherwise).  Never blocks on the
+ * device. */
 int sp_submit(sp_server *srv, const sp_request *req, uint64_t *ticket);
 
 /* Non-blocking status: SP_PENDING until the request is done, then its status;

@@ -26,6 +26,7 @@ LAP_DEFAULT, LAP_5, LAP_9BOX, LAP_9CROSS4, LAP_7, LAP_27, LAP_13CROSS4 = -1, 0, 
 F64, F32, BF16_F32 = 0, 1, 2
 IC_NOISE, IC_CONSTANT = 0, 1
 FLAG_AUTOTUNE = 1
+SCHEME_FD, SCHEME_SPECTRAL = 0, 1
 MASS, FREE_ENERGY, SUM_U, SUM_V, MIN_U, MAX_U, SUMSQ_U = range(7)
 
 
@@ -35,7 +36,7 @@ class sp_params(ctypes.Structure):
                 ("c3", ctypes.c_double), ("stencil", ctypes.c_int), ("dtype", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("ic_kind", ctypes.c_int), ("ic_mean", ctypes.c_double), ("ic_amp", ctypes.c_double),
                 ("gs_patches", ctypes.c_int), ("gs_patch", ctypes.c_int),
-                ("steps_per_launch", ctypes.c_int), ("flags", ctypes.c_int)]
+                ("steps_per_launch", ctypes.c_int), ("scheme", ctypes.c_int), ("flags", ctypes.c_int)]
 
 
 class sp_request(ctypes.Structure):

@@ -57,6 +57,17 @@ inline int steps_per_launch(int dims, int dtype, int model, int requested) {
 constexpr int kUnfusedFamily = 3;
 cudaError_t launch_unfused_ch(int dtype, int stencil, const StepArgs &a, void *mu, cudaStream_t s, int n_sm);
 
+// Semi-implicit Fourier spectral scheme (sp_spectral.cu): a plan holds the cuFFT
+// plans and the resident spectrum.  Functions return SP_* status codes.
+struct SpectralPlan;
+int spectral_create(int dtype, int dims, int nx, int ny, int nz, SpectralPlan **out);
+void spectral_destroy(SpectralPlan *P);
+size_t spectral_bytes(const SpectralPlan *P);
+int spectral_load(SpectralPlan *P, const void *phi, cudaStream_t s);
+int spectral_step(SpectralPlan *P, int model, void *phi, void *nbuf, double h, double dt, double c1, double c2,
+                  double kappa, cudaStream_t s, int n_sm);
+const char *spectral_last_error();
+
 cudaError_t launch_ic(int dtype, void *u, void *v, int model, int dims, int nx, int ny, int nz,
                       uint64_t seed, int ic_kind, double mean, double amp, int patches, int patch,
                       cudaStream_t s, int n_sm);

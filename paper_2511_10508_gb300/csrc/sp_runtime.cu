@@ -127,13 +127,20 @@ static int validate_params(int model, int dims, double h, double dt, const sp_pa
     if (stencil_dims(st) != dims) return fail(SP_EINVAL, "stencil %d is %dD but the grid is %dD", st, stencil_dims(st), dims);
     if (!(is_finite(h) && h > 0)) return fail(SP_EINVAL, "h must be finite and > 0");
     if (!(is_finite(dt) && dt > 0)) return fail(SP_EINVAL, "dt must be finite and > 0");
-    const double vals[7] = {p.c1, p.c2, p.kappa, p.Du, p.Dv, p.F, p.k};
+    const double vals[8] = {p.c1, p.c2, p.kappa, p.Du, p.Dv, p.F, p.k, p.c3};
     for (double v : vals)
         if (!is_finite(v)) return fail(SP_EINVAL, "non-finite model coefficient");
     if (p.dtype < SP_F64 || p.dtype > SP_BF16_F32) return fail(SP_EINVAL, "unknown dtype %d", p.dtype);
     if (p.flags & ~SP_FLAG_AUTOTUNE) return fail(SP_EINVAL, "unknown flags 0x%x", p.flags);
     if (p.steps_per_launch < 0) return fail(SP_EINVAL, "steps_per_launch must be >= 0");
     if (p.ic_kind != SP_IC_NOISE && p.ic_kind != SP_IC_CONSTANT) return fail(SP_EINVAL, "unknown ic_kind %d", p.ic_kind);
+    if (p.scheme != SP_SCHEME_FD && p.scheme != SP_SCHEME_SPECTRAL) return fail(SP_EINVAL, "unknown scheme %d", p.scheme);
+    if (p.scheme == SP_SCHEME_SPECTRAL) {
+        if (model != SP_ALLEN_CAHN && model != SP_CAHN_HILLIARD)
+            return fail(SP_EINVAL, "the spectral scheme covers Allen-Cahn and Cahn-Hilliard");
+        if (p.dtype != SP_F64 && p.dtype != SP_F32) return fail(SP_EINVAL, "the spectral scheme runs in FP64 or FP32");
+        if (p.steps_per_launch > 1) return fail(SP_EINVAL, "the spectral scheme runs one step per launch");
+    }
     if (!is_finite(p.ic_mean) || !is_finite(p.ic_amp)) return fail(SP_EINVAL, "non-finite ic_mean/ic_amp");
     *st_out = st;
     return SP_OK;
@@ -143,6 +150,17 @@ extern "C" int sp_check_stability(int model, int dims, double h, double dt, cons
     if (!p) return fail(SP_EINVAL, "params is NULL");
     int st;
     if (int rc = validate_params(model, dims, h, dt, *p, &st)) return rc;
+    if (p->scheme == SP_SCHEME_SPECTRAL) {
+        // the implicit linear part needs 1 - dt L(k) > 0 for every k
+        double f = dt * p->c1;
+        if (model == SP_CAHN_HILLIARD) {
+            if (!(p->kappa > 0)) return fail(SP_EUNSTABLE, "spectral Cahn-Hilliard needs kappa > 0");
+            f = dt * p->c1 * p->c1 / (4.0 * p->kappa);
+        }
+        if (factor) *factor = f;
+        if (!(f < 1.0)) return fail(SP_EUNSTABLE, "dt max L(k) = %.6g >= 1: the semi-implicit step is undefined", f);
+        return SP_OK;
+    }
     const double f = dt * max_growth(model, st, h, *p);
     if (factor) *factor = f;
     if (!(f <= 2.0)) return fail(SP_EUNSTABLE, "dt*max|sigma| = %.6g > 2: forward Euler is unstable", f);
@@ -174,6 +192,8 @@ struct sp_sim {
     int variant;               // kernel family (see g_step_variant)
     void *mu_tmp;              // unfused ablation: mu temporary (allocated on first use)
     bool tune_pending;         // autotune on the next long sp_step
+    SpectralPlan *spec;        // semi-implicit spectral scheme (else null)
+    bool spec_dirty;           // the resident spectrum must be recomputed from phi
 };
 
 // Steps per captured graph.  A graph holds kGraphSteps / spl launches, an even
@@ -209,6 +229,7 @@ static void release(sp_sim *s) {
     if (s->d_partials) cudaFree(s->d_partials);
     if (s->d_stage) cudaFree(s->d_stage);
     if (s->mu_tmp) cudaFree(s->mu_tmp);
+    spectral_destroy(s->spec);
     for (int l = 0; l < 2; ++l)
         if (s->graph[l]) cudaGraphExecDestroy(s->graph[l]);
     if (s->h_out) cudaFreeHost(s->h_out);
@@ -294,6 +315,15 @@ extern "C" int sp_create(int model, int dims, const int64_t shape[3], double h, 
         release(s);
         return fail(SP_ECUDA, "initial condition: %s", cudaGetErrorString(e));
     }
+    if (prm.scheme == SP_SCHEME_SPECTRAL) {
+        int rc = spectral_create(s->dtype, dims, s->nx, s->ny, s->nz, &s->spec);
+        if (rc == SP_OK) rc = spectral_load(s->spec, s->f[0][0], s->stream);
+        if (rc == SP_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = SP_ECUDA;
+        if (rc != SP_OK) {
+            release(s);
+            return fail(rc, "spectral set-up: %s", spectral_last_error());
+        }
+    }
     *out = s;
     return SP_OK;
 }
@@ -368,6 +398,7 @@ static TuneKey tune_key(const sp_sim *s) {
 
 static std::vector<TuneChoice> tune_candidates(const sp_sim *s) {
     std::vector<TuneChoice> c;
+    if (s->spec) return {{1, 0}};
     if (s->dims == 2 && s->dtype != SP_F64) {
         c.push_back({1, 1});
         for (int spl : {1, 2, 4}) c.push_back({spl, 0});
@@ -464,6 +495,20 @@ extern "C" int sp_step(sp_sim *s, int64_t nsteps, void *stream) {
     if (!s) return fail(SP_EINVAL, "sim is NULL");
     if (nsteps < 0) return fail(SP_EINVAL, "nsteps must be >= 0");
     const cudaStream_t st = pick(s, stream);
+    if (s->spec) {
+        // semi-implicit spectral scheme: phi stays in level 0, the spectrum on the device
+        for (int64_t i = 0; i < nsteps; ++i) {
+            if (s->spec_dirty) {
+                if (int rc = spectral_load(s->spec, s->f[0][0], st)) return fail(rc, "%s", spectral_last_error());
+                s->spec_dirty = false;
+            }
+            if (int rc = spectral_step(s->spec, s->model, s->f[0][0], s->f[1][0], s->h, s->dt, s->p.c1, s->p.c2,
+                                       s->p.kappa, st, s->n_sm))
+                return fail(rc, "spectral step: %s", spectral_last_error());
+            s->steps += 1;
+        }
+        return SP_OK;
+    }
     if (s->tune_pending && nsteps >= kAutotuneMinSteps + 1) {
         s->tune_pending = false;
         if (s->steps == 0) {  // the first step takes the eager path
@@ -558,6 +603,7 @@ extern "C" int sp_write(sp_sim *s, int field, const void *host_src, size_t bytes
         }
     }
     SP_CUDA(cudaStreamSynchronize(st));
+    if (s->spec) s->spec_dirty = true;  // the resident spectrum no longer matches phi
     return SP_OK;
 }
 
@@ -622,7 +668,7 @@ extern "C" int sp_set_launch_config(sp_sim *s, int steps_per_launch, int variant
         set_launch_config(s, {1, 0});
         return SP_OK;
     }
-    if (steps_per_launch == 1 && variant == kUnfusedFamily && s->model == SP_CAHN_HILLIARD) {
+    if (steps_per_launch == 1 && variant == kUnfusedFamily && s->model == SP_CAHN_HILLIARD && !s->spec) {
         if (!s->mu_tmp) {
             const size_t bytes = s->N * (s->dtype == SP_F64 ? sizeof(double) : sizeof(float));
             const cudaError_t e = cudaMalloc(&s->mu_tmp, bytes);

@@ -57,7 +57,8 @@ def test_params_default(sp):
 
 @pytest.mark.parametrize("bad", [
     dict(model=7), dict(dims=4), dict(stencil=9),
-    dict(h=0.0), dict(dt=-1.0), dict(h=float("nan")), dict(dtype=5), dict(flags=2),
+    dict(h=0.0), dict(dt=-1.0), dict(h=float("nan")), dict(dtype=5), dict(flags=2), dict(scheme=2),
+    dict(scheme=1, model=2), dict(scheme=1, model=3), dict(scheme=1, dtype=2),
     dict(stencil=3),  # 3D stencil on a 2D grid
 ])
 def test_invalid_arguments_rejected_before_device(sp, bad):
@@ -67,7 +68,7 @@ def test_invalid_arguments_rejected_before_device(sp, bad):
     dims = bad.get("dims", 2)
     p = N.sp_params()
     N.lib().sp_params_default(0, 2, ctypes.byref(p))
-    for k in ("stencil", "dtype", "flags"):
+    for k in ("stencil", "dtype", "flags", "scheme"):
         if k in bad:
             setattr(p, k, bad[k])
     shape = (ctypes.c_int64 * 3)(16, 16, 1)
@@ -145,3 +146,19 @@ def test_stability_of_the_benchmark_configurations(sp):
         assert ok and f == pytest.approx(want, rel=1e-12), (model, dims, kw, f, want)
     ok, f = sp.check_stability(sp.CAHN_HILLIARD, 2, 1.0, 0.03, sp.params(sp.CAHN_HILLIARD, 2))
     assert not ok and f == pytest.approx(2.4)
+
+
+def test_spectral_scheme_stability_bound(sp):
+    """Semi-implicit spectral scheme: the step needs 1 - dt L(k) > 0 for all k, i.e.
+    dt c1 < 1 (Allen-Cahn) and dt c1^2 / (4 kappa) < 1 (Cahn-Hilliard); the stencil
+    bound of forward Euler does not apply (dt = 5 is fine for Cahn-Hilliard)."""
+    ok, f = sp.check_stability(sp.ALLEN_CAHN, 2, 1.0, 0.99, sp.params(sp.ALLEN_CAHN, 2, scheme=sp.SCHEME_SPECTRAL))
+    assert ok and abs(f - 0.99) < 1e-15
+    ok, _ = sp.check_stability(sp.ALLEN_CAHN, 2, 1.0, 1.0, sp.params(sp.ALLEN_CAHN, 2, scheme=sp.SCHEME_SPECTRAL))
+    assert not ok
+    ok, f = sp.check_stability(sp.CAHN_HILLIARD, 3, 1.0, 3.9, sp.params(sp.CAHN_HILLIARD, 3, scheme=sp.SCHEME_SPECTRAL))
+    assert ok and abs(f - 3.9 / 4) < 1e-15
+    ok, _ = sp.check_stability(sp.CAHN_HILLIARD, 3, 1.0, 4.0, sp.params(sp.CAHN_HILLIARD, 3, scheme=sp.SCHEME_SPECTRAL))
+    assert not ok
+    ok, _ = sp.check_stability(sp.CAHN_HILLIARD, 2, 1.0, 0.5, sp.params(sp.CAHN_HILLIARD, 2))
+    assert not ok  # forward Euler with the 5-point stencil is unstable at this dt
