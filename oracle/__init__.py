@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sp_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-AC, CH, GS, MC = 0, 1, 2, 3
+AC, CH, GS, MC, MH = 0, 1, 2, 3, 4
 TWO_FIELD = (GS, MC)
 S1, S2, S3, S4, S5, S6 = range(6)
 STENCIL_DIMS = {S1: 2, S2: 2, S3: 2, S4: 3, S5: 3, S6: 3}
@@ -75,6 +75,12 @@ def lib():
             L.or_mass.argtypes = [c_int, i64, i64, i64, dbl, ptr]
             L.or_free_energy.restype = dbl
             L.or_free_energy.argtypes = [c_int, i64, i64, i64, dbl, dbl, dbl, ptr]
+            L.or_step_h.restype = c_int
+            L.or_step_h.argtypes = [c_int, i64, i64, i64, dbl, dbl, ptr, ptr, ptr, ptr, ptr, i64]
+            L.or_initial_condition_h.restype = c_int
+            L.or_initial_condition_h.argtypes = [c_int, i64, i64, i64, ctypes.c_uint64, dbl, dbl, ptr, ptr, ptr, ptr]
+            L.or_free_energy_h.restype = dbl
+            L.or_free_energy_h.argtypes = [c_int, i64, i64, i64, dbl, dbl, dbl, ptr, ptr, ptr, ptr]
             L.or_free_energy_c.restype = dbl
             L.or_free_energy_c.argtypes = [c_int, i64, i64, i64, dbl, dbl, dbl, dbl, ptr, ptr]
             L.or_rel_l2.restype = dbl
@@ -227,3 +233,41 @@ def rel_l2(a, b) -> float:
     b = _f64(b).ravel()
     assert a.size == b.size
     return lib().or_rel_l2(_p(a), _p(b), a.size)
+
+
+def step_h(st: int, m, j, *, h: float = 1.0, dt: float, prm=None, nsteps: int = 1):
+    """Model H: return (m, [j_x, j_y(, j_z)]) after ``nsteps`` steps (copies)."""
+    m = np.array(m, dtype=np.float64, copy=True, order="C")
+    js = [np.array(c, dtype=np.float64, copy=True, order="C") for c in j]
+    prm = params() if prm is None else _f64(prm)
+    dims = STENCIL_DIMS[st]
+    if len(js) != dims or any(c.shape != m.shape for c in js):
+        raise ValueError("step_h: j needs one array per axis, shaped like m")
+    nx, ny, nz = _shape3(m, dims)
+    rc = lib().or_step_h(st, nx, ny, nz, h, dt, _p(prm), _p(m), _p(js[0]), _p(js[1]),
+                         _p(js[2]) if dims == 3 else None, int(nsteps))
+    if rc:
+        raise ValueError("or_step_h: bad arguments or out of memory")
+    return m, js
+
+
+def initial_condition_h(shape, *, seed: int, mean: float = 0.0, amp: float = 0.01):
+    """Model H initial fields (m, [j_x, j_y(, j_z)])."""
+    dims = len(shape)
+    m = np.empty(shape, dtype=np.float64)
+    js = [np.empty(shape, dtype=np.float64) for _ in range(dims)]
+    nx, ny, nz = _shape3(m, dims)
+    rc = lib().or_initial_condition_h(dims, nx, ny, nz, seed, mean, amp, _p(m), _p(js[0]), _p(js[1]),
+                                      _p(js[2]) if dims == 3 else None)
+    if rc:
+        raise ValueError("or_initial_condition_h: bad arguments")
+    return m, js
+
+
+def free_energy_h(m, j, h: float = 1.0, c1: float = 1.0, c2: float = 1.0) -> float:
+    m = _f64(m)
+    js = [_f64(c) for c in j]
+    dims = m.ndim
+    nx, ny, nz = _shape3(m, dims)
+    return lib().or_free_energy_h(dims, nx, ny, nz, h, c1, c2, _p(m), _p(js[0]), _p(js[1]),
+                                  _p(js[2]) if dims == 3 else None)

@@ -46,7 +46,18 @@
  *    this oracle follows the listing (phi relaxes by -dF/dphi, rho is conserved
  *    with chemical potential dF/drho):
  *      dphi/dt = lap phi + c1 phi - c2 phi^3 + 2 c3 phi rho
- *      drho/dt = lap (rho - c3 phi^2).
+ *      drho/dt = lap (rho - c3 phi^2);
+ *  - Model H (Sec. "Model H", transverse projector set to unity as the paper
+ *    does), a conserved scalar m and a d-vector j.  The printed j equation and
+ *    the paper's EQUATION_OF listing differ in the sign of the coupling; this
+ *    oracle follows the listing, with which the two couplings cancel in
+ *    dF/dt for F = int [ LANDAU(m) + |j|^2/2 ]:
+ *      mu     = -lap m - c1 m + c2 m^3          (kappa = 1 by default)
+ *      dm/dt  = lap mu - c3 div(m j)
+ *      dj/dt  = lap j  - c3 m grad mu
+ *    grad and div by central differences of the Laplacian stencil's order:
+ *    D f = f(+1) - f(-1) over 2h (radius-1 stencils), fma(8, f(+1) - f(-1),
+ *    -(f(+2) - f(-2))) over 12h (radius 2).
  *
  * Fixed evaluation order (the FP64 parity contract), per point:
  *   class sums of neighbours as written in stencil_sum(), then
@@ -59,6 +70,10 @@
  *                  ru  = fma(F, 1-u, fma(Du/q_h2, S(u), -uvv))
  *                  rv  = fma(-(F+k), v, fma(Dv/q_h2, S(v), uvv))
  *                  u'  = fma(dt, ru, u);  v' = fma(dt, rv, v)
+ *   Model H:       mu  = fma(m, fma(c2, m*m, -c1), -((kappa/q_h2)*S(m)))   (every point first)
+ *                  div = (D_x(m j_x) + D_y(m j_y)) [+ D_z(m j_z)],  c3g = c3 * g (g = 1/(2h) or 1/(12h))
+ *                  m'  = fma(dt, fma(1/q_h2, S(mu), -(c3g * div)), m)
+ *                  j_a' = fma(dt, fma(1/q_h2, S(j_a), -(c3g * (m * D_a mu))), j_a)
  *   Model C:       m   = fma(-c3, u*u, v)                 (every point first)
  *                  gr  = fma(-c2, u*u, fma(2*c3, v, c1))
  *                  u'  = fma(dt, fma(u, gr, (1/q_h2)*S(u)), u)
@@ -74,7 +89,7 @@
 #endif
 
 enum { OR_S1 = 0, OR_S2 = 1, OR_S3 = 2, OR_S4 = 3, OR_S5 = 4, OR_S6 = 5 };
-enum { OR_AC = 0, OR_CH = 1, OR_GS = 2, OR_MC = 3 };
+enum { OR_AC = 0, OR_CH = 1, OR_GS = 2, OR_MC = 3, OR_MH = 4 };
 /* parameter vector: c1, c2, kappa, Du, Dv, F, k */
 enum { P_C1 = 0, P_C2, P_KAPPA, P_DU, P_DV, P_F, P_K, P_C3, P_COUNT };
 
@@ -324,6 +339,84 @@ int or_step(int model, int st, int64_t nx, int64_t ny, int64_t nz, double h, dou
     return 0;
 }
 
+/* Central difference along axis a (0 = x) of f at (x, y, z), unscaled: radius 1
+ * f(+1) - f(-1); radius 2 fma(8, f(+1) - f(-1), -(f(+2) - f(-2))). */
+static double central_diff(int radius, int a, const double *f, const grid_t *g, int64_t x, int64_t y, int64_t z) {
+    const int ex = (a == 0), ey = (a == 1), ez = (a == 2);
+    const double d1 = at(f, g, x, y, z, ex, ey, ez) - at(f, g, x, y, z, -ex, -ey, -ez);
+    if (radius == 1) return d1;
+    const double d2 = at(f, g, x, y, z, 2 * ex, 2 * ey, 2 * ez) - at(f, g, x, y, z, -2 * ex, -2 * ey, -2 * ez);
+    return fma(8.0, d1, -d2);
+}
+
+/*
+ * Model H: advance m and j (dims components: j[0] = x, j[1] = y, j[2] = z) by
+ * nsteps forward-Euler steps in place.  prm = {c1, c2, kappa, Du, Dv, F, k, c3}
+ * (only c1, c2, kappa, c3 enter).  Returns 0, or -1 on bad arguments / memory.
+ */
+int or_step_h(int st, int64_t nx, int64_t ny, int64_t nz, double h, double dt, const double *prm, double *m,
+              double *j0, double *j1, double *j2, int64_t nsteps) {
+    grid_t g;
+    const int dims = or_stencil_dims(st);
+    if (check_grid(st, nx, ny, nz) || nsteps < 0 || !m || !j0 || !j1 || (dims == 3 && !j2)) return -1;
+    if (grid_init(&g, nx, ny, nz)) return -1;
+    const int64_t n = nx * ny * nz;
+    const int radius = or_stencil_radius(st);
+    const double q_h2 = ((double)or_stencil_q(st) * h) * h;
+    const double sL = 1.0 / q_h2, kq = prm[P_KAPPA] / q_h2;
+    const double c3g = prm[P_C3] * (radius == 1 ? 1.0 / (2.0 * h) : 1.0 / (12.0 * h));
+    double *jc[3] = {j0, j1, j2};
+    double *mn = (double *)malloc(sizeof(double) * (size_t)n);
+    double *mu = (double *)malloc(sizeof(double) * (size_t)n);
+    double *mj = (double *)malloc(sizeof(double) * (size_t)n * (size_t)dims);
+    double *jn[3] = {NULL, NULL, NULL};
+    int bad = !mn || !mu || !mj;
+    for (int a = 0; a < dims; a++) {
+        jn[a] = (double *)malloc(sizeof(double) * (size_t)n);
+        bad |= !jn[a];
+    }
+    if (bad) {
+        free(mn); free(mu); free(mj);
+        for (int a = 0; a < 3; a++) free(jn[a]);
+        grid_free(&g);
+        return -1;
+    }
+    double *mc = m;
+    double *jcur[3] = {jc[0], jc[1], dims == 3 ? jc[2] : NULL};
+    for (int64_t s = 0; s < nsteps; s++) {
+        ch_mu(st, &g, mc, mu, kq, prm[P_C1], prm[P_C2]);
+        /* the fluxes m j_a at every point */
+        for (int a = 0; a < dims; a++) {
+#pragma omp parallel for schedule(static)
+            for (int64_t i = 0; i < n; i++) mj[(size_t)a * n + i] = mc[i] * jcur[a][i];
+        }
+#pragma omp parallel for collapse(2) schedule(static)
+        for (int64_t z = 0; z < nz; z++)
+            for (int64_t y = 0; y < ny; y++)
+                for (int64_t x = 0; x < nx; x++) {
+                    const int64_t i = (z * ny + y) * nx + x;
+                    double div = central_diff(radius, 0, mj, &g, x, y, z) +
+                                 central_diff(radius, 1, mj + (size_t)n, &g, x, y, z);
+                    if (dims == 3) div = div + central_diff(radius, 2, mj + 2 * (size_t)n, &g, x, y, z);
+                    mn[i] = fma(dt, fma(sL, stencil_sum(st, mu, &g, x, y, z), -(c3g * div)), mc[i]);
+                    for (int a = 0; a < dims; a++) {
+                        const double gm = central_diff(radius, a, mu, &g, x, y, z);
+                        jn[a][i] = fma(dt, fma(sL, stencil_sum(st, jcur[a], &g, x, y, z), -(c3g * (mc[i] * gm))),
+                                       jcur[a][i]);
+                    }
+                }
+        double *t = mc; mc = mn; mn = t;
+        for (int a = 0; a < dims; a++) { t = jcur[a]; jcur[a] = jn[a]; jn[a] = t; }
+    }
+    if (mc != m) { memcpy(m, mc, sizeof(double) * (size_t)n); mn = mc; }
+    for (int a = 0; a < dims; a++)
+        if (jcur[a] != jc[a]) { memcpy(jc[a], jcur[a], sizeof(double) * (size_t)n); jn[a] = jcur[a]; }
+    free(mn); free(mu); free(mj);
+    for (int a = 0; a < dims; a++) free(jn[a]);
+    grid_free(&g);
+    return 0;
+}
+
 /* ---------------------------------------------------------------- IC ---- */
 
 /*
@@ -559,4 +652,41 @@ double or_rel_l2(const double *a, const double *b, int64_t n) {
     const double num = or_sum(d, n), den = or_sum(r, n);
     free(d); free(r);
     return den > 0 ? sqrt(num / den) : sqrt(num);
+}
+
+/*
+ * Model H initial condition: m_i = mean + amp (2U(i) - 1), j_a,i = amp (2U((a+1)N + i) - 1).
+ */
+int or_initial_condition_h(int dims, int64_t nx, int64_t ny, int64_t nz, uint64_t seed, double mean, double amp,
+                           double *m, double *j0, double *j1, double *j2) {
+    if (nx < 1 || ny < 1 || nz < 1 || (dims == 2 && nz != 1) || (dims != 2 && dims != 3)) return -1;
+    if (!m || !j0 || !j1 || (dims == 3 && !j2)) return -1;
+    const int64_t N = nx * ny * nz;
+    double *jc[3] = {j0, j1, j2};
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; i++) {
+        m[i] = mean + amp * (2.0 * or_u01(seed, (uint64_t)i) - 1.0);
+        for (int a = 0; a < dims; a++) jc[a][i] = amp * (2.0 * or_u01(seed, (uint64_t)((a + 1) * N + i)) - 1.0);
+    }
+    return 0;
+}
+
+/* Model H free energy: the Landau terms of m (as or_free_energy) plus h^d sum |j|^2 / 2. */
+double or_free_energy_h(int dims, int64_t nx, int64_t ny, int64_t nz, double h, double c1, double c2,
+                        const double *m, const double *j0, const double *j1, const double *j2) {
+    const int64_t n = nx * ny * nz;
+    const double land = or_free_energy(dims, nx, ny, nz, h, c1, c2, m);
+    double *e = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!e) return NAN;
+    const double *jc[3] = {j0, j1, j2};
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        double q = j0[i] * j0[i] + j1[i] * j1[i];
+        if (dims == 3) q = q + j2[i] * j2[i];
+        e[i] = 0.5 * q;
+    }
+    (void)jc;
+    const double r = land + cell_volume(dims, h) * or_sum(e, n);
+    free(e);
+    return r;
 }

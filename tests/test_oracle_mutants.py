@@ -48,6 +48,15 @@ MUTANTS = {
     "Model C density Laplacian of rho only": ("vn[i] = fma(dq, stencil_sum(st, mu, &g, x, y, z), r);",
                                               "vn[i] = fma(dq, stencil_sum(st, vc, &g, x, y, z), r);"),
     "Model C free-energy coupling sign": ("+ 0.5 * r * r - c3 * p2 * r", "+ 0.5 * r * r + c3 * p2 * r"),
+    "Model H printed coupling sign in j": ("-(c3g * (mc[i] * gm)))", "(c3g * (mc[i] * gm)))"),
+    "Model H divergence sign": ("fma(sL, stencil_sum(st, mu, &g, x, y, z), -(c3g * div))",
+                                "fma(sL, stencil_sum(st, mu, &g, x, y, z), (c3g * div))"),
+    "Model H gradient of m instead of mu": ("const double gm = central_diff(radius, a, mu, &g, x, y, z);",
+                                            "const double gm = central_diff(radius, a, mc, &g, x, y, z);"),
+    "Model H 4th-order difference weight": ("return fma(8.0, d1, -d2);", "return fma(6.0, d1, -d2);"),
+    "Model H gradient scale": ("1.0 / (2.0 * h) : 1.0 / (12.0 * h)", "1.0 / h : 1.0 / (12.0 * h)"),
+    "Model H flux of j only": ("mj[(size_t)a * n + i] = mc[i] * jcur[a][i];", "mj[(size_t)a * n + i] = jcur[a][i];"),
+    "Model H current noise stream": ("or_u01(seed, (uint64_t)((a + 1) * N + i))", "or_u01(seed, (uint64_t)(a * N + i))"),
     "Model C density noise stream": ("            v[i] = mean + amp * (2.0 * or_u01(seed, (uint64_t)(N + i)) - 1.0);",
                                      "            v[i] = mean + amp * (2.0 * or_u01(seed, (uint64_t)i) - 1.0);"),
 }

@@ -566,3 +566,151 @@ def test_model_c_initial_condition_streams(orc):
     for i in (0, 5, N - 1):
         assert u.ravel()[i] == 0.1 + 0.4 * (2 * O.u01(21, i) - 1)
         assert v.ravel()[i] == 0.1 + 0.4 * (2 * O.u01(21, N + i) - 1)
+
+
+# ------------------------------------------------------------ Model H
+#
+# mu = -lap m - c1 m + c2 m^3;  dm/dt = lap mu - c3 div(m j);  dj/dt = lap j - c3 m grad mu
+# (signs of the paper's EQUATION_OF listing); grad / div by central differences of
+# the stencil's order: radius 1 (f(+1) - f(-1)) / 2h, radius 2 (8 (f(+1) - f(-1)) -
+# (f(+2) - f(-2))) / 12h.
+
+MH_DT = 0.004  # inside the forward-Euler bound of every stencil for these coefficients
+
+
+def diff_symbol(st, theta):
+    """D cos(theta x) = -s sin(theta x) and D sin(theta x) = s cos(theta x), unscaled."""
+    if O.STENCIL_RADIUS[st] == 1:
+        return 2 * math.sin(theta)
+    return 16 * math.sin(theta) - 2 * math.sin(2 * theta)
+
+
+def grad_scale(st, h):
+    return 1 / (2 * h) if O.STENCIL_RADIUS[st] == 1 else 1 / (12 * h)
+
+
+def sin_field(shape, ks, amp=1.0):
+    idx = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")[::-1]
+    ph = sum(2 * np.pi * k * i / n for k, i, n in zip(ks, idx, shape[::-1]))
+    return amp * np.sin(ph)
+
+
+@pytest.mark.parametrize("st", ALL)
+def test_model_h_uncoupled(orc, st):
+    """c3 = 0: m follows Cahn-Hilliard (to rounding: the scaling of the outer
+    Laplacian is folded differently) and each component of j diffuses, a mode
+    decaying exactly as (1 - dt lambda / h^2)^n."""
+    dims = O.STENCIL_DIMS[st]
+    shape = SHAPES[dims]
+    h, n = 1.0, 20
+    m = orc.initial_condition(O.CH, shape, seed=23, amp=0.4)
+    js = []
+    for a in range(dims):
+        f, th = mode_field(shape, tuple((a + 1, 2, 1)[:dims]), amp=0.3)
+        js.append(f)
+    prm = O.params(c1=0.9, c2=1.1, c3=0.0)
+    mo, jo = O.step_h(st, m, js, h=h, dt=MH_DT, prm=prm, nsteps=n)
+    ref = orc.step(O.CH, st, m, h=h, dt=MH_DT, prm=prm, nsteps=n)
+    np.testing.assert_allclose(mo, ref, rtol=0, atol=1e-13)
+    for a in range(dims):
+        _, th = mode_field(shape, tuple((a + 1, 2, 1)[:dims]))
+        lam = symbol(st, th)
+        np.testing.assert_allclose(jo[a], (1 - MH_DT * lam / h ** 2) ** n * js[a], rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("st", ALL)
+def test_model_h_current_from_a_density_mode(orc, st):
+    """m = m0 + eps cos(theta.x), j = 0: one step gives
+    j_a = dt c3 g m0 dmu s_a sin(theta.x)  (from -c3 m grad mu), with
+    dmu = eps (3 c2 m0^2 - c1 + kappa lambda/h^2), s_a the difference symbol, g its
+    scale; m moves by -dt (lambda/h^2) dmu cos(theta.x) (the outer Laplacian)."""
+    dims = O.STENCIL_DIMS[st]
+    shape = SHAPES[dims]
+    h, eps, m0 = 0.9, 1e-6, 0.4
+    c1, c2, kappa, c3 = 0.8, 1.2, 1.0, 0.7
+    ks = (2, 1, 3)[:dims]
+    f, th = mode_field(shape, ks)
+    lam = symbol(st, th) / h ** 2
+    dmu = eps * (3 * c2 * m0 ** 2 - c1 + kappa * lam)
+    prm = O.params(c1=c1, c2=c2, kappa=kappa, c3=c3)
+    m = m0 + eps * f
+    mo, jo = O.step_h(st, m, [np.zeros(shape)] * dims, h=h, dt=MH_DT, prm=prm, nsteps=1)
+    s = sin_field(shape, ks)
+    g = grad_scale(st, h)
+    for a in range(dims):
+        pred = MH_DT * c3 * g * m0 * dmu * diff_symbol(st, th[a]) * s
+        np.testing.assert_allclose(jo[a], pred, rtol=0, atol=1e-3 * eps * MH_DT)
+    # second-order terms (dt lambda 3 c2 m0 eps^2 ~ 1e-13) stay far below the first-order ones (~6e-8)
+    np.testing.assert_allclose(mo - m0, (eps - MH_DT * lam * dmu) * f, rtol=0, atol=1e-6 * eps)
+
+
+@pytest.mark.parametrize("st", ALL)
+def test_model_h_density_from_a_current_mode(orc, st):
+    """m = m0, j_x = eps sin(theta.x): one step moves m by
+    -dt c3 g m0 eps s_x cos(theta.x)  (from -c3 div(m j)) and j_x diffuses."""
+    dims = O.STENCIL_DIMS[st]
+    shape = SHAPES[dims]
+    h, eps, m0 = 1.1, 1e-6, 0.35
+    c3 = 0.6
+    ks = (1, 2, 1)[:dims]
+    f, th = mode_field(shape, ks)
+    s = sin_field(shape, ks)
+    lam = symbol(st, th) / h ** 2
+    js = [eps * s] + [np.zeros(shape)] * (dims - 1)
+    mo, jo = O.step_h(st, np.full(shape, m0), js, h=h, dt=MH_DT, prm=O.params(c3=c3), nsteps=1)
+    g = grad_scale(st, h)
+    np.testing.assert_allclose(mo - m0, -MH_DT * c3 * g * m0 * eps * diff_symbol(st, th[0]) * f, rtol=0,
+                               atol=1e-9 * eps)
+    np.testing.assert_allclose(jo[0], (1 - MH_DT * lam) * eps * s, rtol=0, atol=1e-9 * eps)
+    for a in range(1, dims):
+        assert np.abs(jo[a]).max() == 0.0
+
+
+@pytest.mark.parametrize("st", [O.S1, O.S3, O.S4])
+def test_model_h_conserves_m(orc, st):
+    dims = O.STENCIL_DIMS[st]
+    shape = SHAPES[dims]
+    m, js = O.initial_condition_h(shape, seed=29, mean=0.1, amp=0.5)
+    mo, jo = O.step_h(st, m, js, dt=MH_DT, prm=O.params(c3=1.0), nsteps=100)
+    assert abs(mo.sum() - m.sum()) / (m.size * np.abs(m).max()) < 100 * 1e-15
+    assert abs(jo[0].sum() - js[0].sum()) > 1e-6  # j is not conserved
+
+
+@pytest.mark.parametrize("st", [O.S1, O.S4])
+def test_model_h_free_energy_decreases(orc, st):
+    """With the listing's signs the couplings cancel in dF/dt, so F = Landau(m) +
+    |j|^2/2 decreases at every small step."""
+    dims = O.STENCIL_DIMS[st]
+    shape = SHAPES[dims]
+    m, js = O.initial_condition_h(shape, seed=31, mean=0.1, amp=0.6)
+    prm = O.params(c3=1.5)
+    F = [O.free_energy_h(m, js)]
+    for _ in range(40):
+        m, js = O.step_h(st, m, js, dt=0.002, prm=prm, nsteps=1)
+        F.append(O.free_energy_h(m, js))
+    assert all(b < a for a, b in zip(F, F[1:])), F
+
+
+@pytest.mark.parametrize("st", [O.S2, O.S5, O.S6])
+def test_model_h_shift_equivariance(orc, st):
+    dims = O.STENCIL_DIMS[st]
+    shape = SHAPES[dims]
+    axes = tuple(range(dims))
+    shift = (3, -5, 2)[:dims]
+    m, js = O.initial_condition_h(shape, seed=37, amp=0.3)
+    prm = O.params(c3=0.8)
+    a = O.step_h(st, m, js, dt=MH_DT, prm=prm, nsteps=3)
+    b = O.step_h(st, np.roll(m, shift, axes), [np.roll(c, shift, axes) for c in js], dt=MH_DT, prm=prm, nsteps=3)
+    assert np.array_equal(np.roll(a[0], shift, axes), b[0])
+    for x, y in zip(a[1], b[1]):
+        assert np.array_equal(np.roll(x, shift, axes), y)
+
+
+def test_model_h_initial_condition_streams(orc):
+    shape = (5, 6, 7)
+    m, js = O.initial_condition_h(shape, seed=41, mean=0.2, amp=0.3)
+    N = m.size
+    for i in (0, 17, N - 1):
+        assert m.ravel()[i] == 0.2 + 0.3 * (2 * O.u01(41, i) - 1)
+        for a in range(3):
+            assert js[a].ravel()[i] == 0.3 * (2 * O.u01(41, (a + 1) * N + i) - 1)
