@@ -67,13 +67,18 @@ WORKLOADS = {
     "ac2d-4096-f64-spectral": (0, 2, (4096, 4096), 0.5, 0, 0, 20),
     "ch2d-8192-f32-spectral": (1, 2, (8192, 8192), 0.5, 0, 1, 20),
     "ch3d-256-f64-spectral": (1, 3, (256, 256, 256), 0.5, 3, 0, 10),
+    # Model H (m and the d components of j), c3 = 0.5
+    "mh2d-4096-f64-lap5": (4, 2, (4096, 4096), 0.01, 0, 0, 50),
+    "mh2d-8192-f32-lap5": (4, 2, (8192, 8192), 0.01, 0, 1, 20),
+    "mh3d-256-f64-lap7": (4, 3, (256, 256, 256), 0.005, 3, 0, 10),
+    "mh3d-256-f32-lap7": (4, 3, (256, 256, 256), 0.005, 3, 1, 20),
     # ablation: the unfused Cahn-Hilliard step (mu through a device-memory temporary)
     "ch2d-4096-f64-lap5-unfused": (1, 2, (4096, 4096), 0.01, 0, 0, 100, 1, 3),
     "ch2d-16384-f32-lap5-unfused": (1, 2, (16384, 16384), 0.01, 0, 1, 20, 1, 3),
     "ch3d-1024-f32-lap7-unfused": (1, 3, (1024, 1024, 1024), 0.005, 3, 1, 5, 1, 3),
 }
 DEFAULT = "ch2d-4096-f64-lap5"
-MODEL_NAME = {0: "Allen-Cahn", 1: "Cahn-Hilliard", 2: "Gray-Scott", 3: "Model C"}
+MODEL_NAME = {0: "Allen-Cahn", 1: "Cahn-Hilliard", 2: "Gray-Scott", 3: "Model C", 4: "Model H"}
 STENCIL_NAME = {0: "5-point", 1: "9-point box", 2: "4th-order 9-point cross", 3: "7-point", 4: "27-point",
                 5: "4th-order 13-point cross"}
 DTYPE_NAME = {0: "f64", 1: "f32", 2: "bf16-storage/f32"}
@@ -109,15 +114,30 @@ def spectral_ops_per_lup(npts: int) -> float:
 SPECTRAL_BYTES_PER_LUP_IN_P = 10
 
 
+def model_h_ops_per_lup(st: int) -> int:
+    """Model H, fixed order: mu (s + 4), the m update (s + d (3 + dc) + 2) and each
+    current component (s + dc + 4); dc = 1 or 3 FP64 operations per central
+    difference of radius 1 or 2."""
+    s = STENCIL_OPS[st]
+    d = 3 if st >= 3 else 2
+    dc = 3 if st in (2, 5) else 1
+    return (2 + d) * s + d * (7 + 2 * dc) + 6
+
+
 def fp64_ops_per_lup(model: int, st: int) -> int:
+    if model == 4:
+        return model_h_ops_per_lup(st)
     s = STENCIL_OPS[st]
     # Model C: mu of the density once per point (2), two stencils, the update (7)
     return {0: s + 5, 1: 2 * s + 5, 2: 2 * s + 9, 3: 2 * s + 9}[model]
 
 
-def hbm_bytes_per_lup(model: int, dtype: int) -> int:
-    nf = 2 if model in (2, 3) else 1
-    return 2 * nf * ESIZE[dtype]
+def nfields(model: int, dims: int) -> int:
+    return 1 + dims if model == 4 else (2 if model in (2, 3) else 1)
+
+
+def hbm_bytes_per_lup(model: int, dtype: int, dims: int = 2) -> int:
+    return 2 * nfields(model, dims) * ESIZE[dtype]
 
 
 def load_peaks() -> dict:
@@ -212,18 +232,18 @@ def oracle_rate(model, dims, shape, dt, st, budget_s=15.0, max_steps=2000, spect
         return {"value": npts * n / el / 1e9, "unit": "GLUPS", "cores": 1, "kind": "oracle",
                 "sample": f"{n} FP64 spectral oracle steps (numpy FFT) of the full {'x'.join(map(str, shape[::-1]))} "
                           f"grid ({el:.1f} s)"}
-    if model == 2:
-        u, v = O.initial_condition(O.GS, shape, seed=2, amp=0.01, patches=64, patch=20)
-    elif model == 3:
-        u, v = O.initial_condition(O.MC, shape, seed=1, amp=0.01)
+    if model == 4:
+        m, js = O.initial_condition_h(shape, seed=1, amp=0.01)
+        run = lambda n: O.step_h(st, m, js, dt=dt, prm=prm, nsteps=n)  # noqa: E731
+    elif model in (2, 3):
+        if model == 2:
+            u, v = O.initial_condition(O.GS, shape, seed=2, amp=0.01, patches=64, patch=20)
+        else:
+            u, v = O.initial_condition(O.MC, shape, seed=1, amp=0.01)
+        run = lambda n: O.step(model, st, u, v, dt=dt, prm=prm, nsteps=n)  # noqa: E731
     else:
         u = O.initial_condition(model, shape, seed=1, amp=0.01)
-        v = None
-    def run(n):
-        if v is not None:
-            O.step(model, st, u, v, dt=dt, prm=prm, nsteps=n)
-        else:
-            O.step(model, st, u, dt=dt, prm=prm, nsteps=n)
+        run = lambda n: O.step(model, st, u, dt=dt, prm=prm, nsteps=n)  # noqa: E731
 
     run(1)  # start the OpenMP team
     t0 = time.perf_counter()
@@ -523,9 +543,9 @@ def main():
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "FP64 Gop/s",
                 "frac": achieved / FP64_PEAK_GOPS, "traffic": traffic,
                 "note": f"{ops} FP64 ops/LUP (fixed evaluation order); peak = 152 SMs x 2 FP64 ops/clk x 2.07 GHz; "
-                        f"HBM side {hbm_bytes_per_lup(model, dtype) * npts / (launch_ms * 1e-3) / 1e9:.0f} GB/s"}
+                        f"HBM side {hbm_bytes_per_lup(model, dtype, dims) * npts / (launch_ms * 1e-3) / 1e9:.0f} GB/s"}
     else:
-        bpl = hbm_bytes_per_lup(model, dtype)
+        bpl = hbm_bytes_per_lup(model, dtype, dims)
         achieved = bpl * npts / (launch_ms * 1e-3) / 1e9
         peak = float(peaks.get("hbm_gbs", 6800.0))
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -537,20 +557,17 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        host_in = torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+        n_fields = nfields(model, dims)
+        host_in = [torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy() for _ in range(n_fields)]
         host_out = torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
-        host_in[...] = sim.read(0, stream=stream)
-        host_v = None
-        if model in (2, 3):
-            host_v = torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
-            host_v[...] = sim.read(1, stream=stream)
+        for f in range(n_fields):
+            host_in[f][...] = sim.read(f, stream=stream)
         e2e_steps = max(1, min(args.steps, 5))
         barrier()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            sim.write(0, host_in, stream=stream)
-            if host_v is not None:
-                sim.write(1, host_v, stream=stream)
+            for f in range(n_fields):
+                sim.write(f, host_in[f], stream=stream)
             sim.step(sub, stream=stream)
             sim.reduce(sp.MASS, stream=stream)
             host_out[...] = 0
@@ -559,9 +576,8 @@ def main():
                                     stream.cuda_stream), "sp_read")
         barrier()
         el = reduce_max_over_ranks([time.perf_counter() - t0], device="cuda")[0]
-        nf = 2 if model in (2, 3) else 1
         e2e = {"value": replica_glups(npts * sub * e2e_steps, world, el), "unit": "GLUPS",
-               "h2d_bytes_per_step": npts * 8 * nf, "d2h_bytes_per_step": npts * 8 + 8, "steps": e2e_steps}
+               "h2d_bytes_per_step": npts * 8 * n_fields, "d2h_bytes_per_step": npts * 8 + 8, "steps": e2e_steps}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -58,11 +58,17 @@ typedef enum sp_model {
     SP_ALLEN_CAHN = 0,     /* Model A, Eq. (model-a): dphi/dt = lap phi + c1 phi - c2 phi^3 */
     SP_CAHN_HILLIARD = 1,  /* Model B, Eq. (model-b): dphi/dt = lap(c2 phi^3 - c1 phi - kappa lap phi) */
     SP_GRAY_SCOTT = 2,     /* du/dt = Du lap u - u v^2 + F(1-u); dv/dt = Dv lap v + u v^2 - (F+k) v */
-    SP_MODEL_C = 3         /* Model C (Sec. "Model C"), phi = field 0 (non-conserved), rho = field 1
+    SP_MODEL_C = 3,        /* Model C (Sec. "Model C"), phi = field 0 (non-conserved), rho = field 1
                               (conserved), signs from the paper's free-energy listing
                               F = Landau(phi) + rho^2/2 - c3 phi^2 rho:
                               dphi/dt = lap phi + c1 phi - c2 phi^3 + 2 c3 phi rho;
                               drho/dt = lap(rho - c3 phi^2) */
+    SP_MODEL_H = 4         /* Model H (Sec. "Model H", transverse projector at unity), field 0 = m
+                              (conserved), fields 1..dims = the components of j; coupling signs
+                              from the paper's listing: mu = -kappa lap m - c1 m + c2 m^3,
+                              dm/dt = lap mu - c3 div(m j), dj/dt = lap j - c3 m grad mu, grad/div
+                              by central differences of the stencil's order.  Two passes per step
+                              (mu through a device buffer, as the paper's one temporary). */
 } sp_model;
 
 /* Laplacian stencils (integer weights over a denominator q; L f = sum w f / (q h^2)). */
@@ -92,7 +98,7 @@ typedef enum sp_reduce_what {
     SP_MASS = 0,           /* h^d * sum of the conserved field (field 1, rho, for Model C;
                               field 0 otherwise), compensated FP64 */
     SP_FREE_ENERGY = 1,    /* h^d sum [1/2 |grad+ phi|^2 - c1/2 phi^2 + c2/4 phi^4] (field 0);
-                              Model C adds + rho^2/2 - c3 phi^2 rho */
+                              Model C adds + rho^2/2 - c3 phi^2 rho, Model H + |j|^2/2 */
     SP_SUM_U = 2,          /* sum of field 0 (no h^d) */
     SP_SUM_V = 3,          /* sum of field 1 (Gray-Scott, Model C) */
     SP_MIN_U = 4,          /* minimum of field 0 */

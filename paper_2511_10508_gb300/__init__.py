@@ -15,10 +15,10 @@ import numpy as np
 from . import _native as N
 from ._native import (ALLEN_CAHN, BF16_F32, CAHN_HILLIARD, F32, F64, FLAG_AUTOTUNE, FREE_ENERGY, GRAY_SCOTT, IC_CONSTANT,
                       IC_NOISE, LAP_5, LAP_7, LAP_9BOX, LAP_9CROSS4, LAP_13CROSS4, LAP_27, LAP_DEFAULT, MASS,
-                      MAX_U, MIN_U, MODEL_C, SCHEME_FD, SCHEME_SPECTRAL, SUM_U, SUM_V, SUMSQ_U, SpError)
+                      MAX_U, MIN_U, MODEL_C, MODEL_H, SCHEME_FD, SCHEME_SPECTRAL, SUM_U, SUM_V, SUMSQ_U, SpError)
 
 __all__ = ["Simulation", "Server", "Result", "params", "check_stability", "SpError", "ALLEN_CAHN", "CAHN_HILLIARD", "GRAY_SCOTT",
-           "MODEL_C", "SCHEME_FD", "SCHEME_SPECTRAL",
+           "MODEL_C", "MODEL_H", "SCHEME_FD", "SCHEME_SPECTRAL",
            "LAP_5", "LAP_9BOX", "LAP_9CROSS4", "LAP_7", "LAP_27", "LAP_13CROSS4", "LAP_DEFAULT", "F64", "F32",
            "BF16_F32", "IC_NOISE", "IC_CONSTANT", "FLAG_AUTOTUNE", "MASS", "FREE_ENERGY", "SUM_U", "SUM_V", "MIN_U", "MAX_U",
            "SUMSQ_U"]
@@ -68,7 +68,7 @@ class Simulation:
         N.check(N.lib().sp_create(model, self.dims, xyz, h, dt, ctypes.byref(self.prm), ctypes.byref(h_)),
                 "sp_create")
         self._h = h_
-        self.nfields = 2 if model in (GRAY_SCOTT, MODEL_C) else 1
+        self.nfields = (1 + len(shape)) if model == MODEL_H else (2 if model in (GRAY_SCOTT, MODEL_C) else 1)
         self.dtype = self.prm.dtype
 
     # -- lifecycle

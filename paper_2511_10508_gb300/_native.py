@@ -21,7 +21,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 # enums (mirrors sp.h)
 SP_OK, SP_EINVAL, SP_EUNSTABLE, SP_ENOMEM, SP_EBUDGET, SP_ECUDA, SP_ETIMEOUT, SP_EBUSY, SP_PENDING, SP_ENOTFOUND = range(10)
-ALLEN_CAHN, CAHN_HILLIARD, GRAY_SCOTT, MODEL_C = 0, 1, 2, 3
+ALLEN_CAHN, CAHN_HILLIARD, GRAY_SCOTT, MODEL_C, MODEL_H = 0, 1, 2, 3, 4
 LAP_DEFAULT, LAP_5, LAP_9BOX, LAP_9CROSS4, LAP_7, LAP_27, LAP_13CROSS4 = -1, 0, 1, 2, 3, 4, 5
 F64, F32, BF16_F32 = 0, 1, 2
 IC_NOISE, IC_CONSTANT = 0, 1

@@ -36,7 +36,7 @@
 
 namespace sp {
 
-enum Model : int { AC = 0, CH = 1, GS = 2, MC = 3 };
+enum Model : int { AC = 0, CH = 1, GS = 2, MC = 3, MH = 4 };
 enum Stencil : int { L5 = 0, L9BOX = 1, L9X4 = 2, L7 = 3, L27 = 4, L13X4 = 5 };
 
 template <int ST> struct StencilInfo;

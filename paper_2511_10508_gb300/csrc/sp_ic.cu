@@ -92,3 +92,31 @@ cudaError_t launch_ic(int dtype, void *u, void *v, int model, int dims, int nx, 
 }
 
 }  // namespace sp
+
+namespace sp {
+
+// Model H currents: component a of j at point i is amp (2U - 1) from stream
+// n = (a+1) N + i (mean 0).
+template <typename T>
+__global__ void ic_currents_kernel(T *j0, T *j1, T *j2, int dims, uint64_t N, uint64_t seed, double amp,
+                                   int constant) {
+    T *jc[3] = {j0, j1, j2};
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
+        for (int a = 0; a < dims; ++a)
+            jc[a][i] = round_store<T>(constant ? 0.0 : noise(seed, (uint64_t)(a + 1) * N + i, 0.0, amp));
+}
+
+cudaError_t launch_ic_currents(int dtype, void *const j[3], int dims, uint64_t N, uint64_t seed, int ic_kind, double amp,
+                               cudaStream_t s, int n_sm) {
+    const unsigned blocks = (unsigned)std::min<uint64_t>((N + 255) / 256, (uint64_t)n_sm * 8);
+    const int constant = ic_kind != SP_IC_NOISE;
+    switch (dtype) {
+    case SP_F64: ic_currents_kernel<double><<<blocks, 256, 0, s>>>((double *)j[0], (double *)j[1], (double *)j[2], dims, N, seed, amp, constant); break;
+    case SP_F32: ic_currents_kernel<float><<<blocks, 256, 0, s>>>((float *)j[0], (float *)j[1], (float *)j[2], dims, N, seed, amp, constant); break;
+    default: ic_currents_kernel<bf16><<<blocks, 256, 0, s>>>((bf16 *)j[0], (bf16 *)j[1], (bf16 *)j[2], dims, N, seed, amp, constant); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sp

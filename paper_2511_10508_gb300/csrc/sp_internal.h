@@ -19,6 +19,8 @@ struct ReduceGeom {
     double h, cell_volume, c1, c2;
     double c3 = 0.0;            // Model C free energy: coupling
     const void *rho = nullptr;  // Model C free energy: the density field (else null)
+    const void *jq[3] = {nullptr, nullptr, nullptr};  // Model H free energy: |j|^2/2 terms
+    int nq = 0;
 };
 
 // Step launchers, one per storage type (sp_step_f64.cu, sp_step_f32.cu,
@@ -45,12 +47,20 @@ cudaError_t launch_step_bf16(int model, int stencil, const StepArgs &a, cudaStre
 extern thread_local int g_step_variant;
 
 inline int steps_per_launch(int dims, int dtype, int model, int requested) {
-    if (dims != 2 || dtype == SP_F64) return 1;
+    if (dims != 2 || dtype == SP_F64 || model == SP_MODEL_H) return 1;
     if (requested == 0) return (dtype == SP_F32 && model != CH) ? 2 : 1;
     if (requested >= 4) return 4;
     if (requested >= 2) return 2;
     return 1;
 }
+
+// Model H (sp_model_h.cu): one step from in[0..nf) to out[0..nf) (m, then the
+// components of j; unused entries null) through the mu buffer of N compute-
+// precision values; c3g = c3 times the central-difference scale.
+cudaError_t launch_model_h(int dtype, int stencil, void *const in[4], void *const out[4], void *mu, int nx, int ny,
+                           int nz, const StepConsts &k, double c3g, cudaStream_t s, int n_sm);
+cudaError_t launch_ic_currents(int dtype, void *const j[3], int dims, uint64_t N, uint64_t seed, int ic_kind, double amp,
+                               cudaStream_t s, int n_sm);
 
 // Unfused Cahn-Hilliard step (ablation only, kernel family kUnfusedFamily): mu
 // into the caller's temporary of N compute-precision values, then the update.

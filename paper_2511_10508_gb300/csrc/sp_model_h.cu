@@ -1,0 +1,177 @@
+// sp_model_h.cu -- Model H (Sec. "Model H", transverse projector at unity), a
+// conserved scalar m and a d-vector current j, signs of the paper's listing:
+//   mu    = -kappa lap m - c1 m + c2 m^3
+//   dm/dt = lap mu - c3 div(m j)
+//   dj/dt = lap j - c3 m grad mu
+// grad and div are central differences of the Laplacian stencil's order.
+//
+// Like the paper's solver (one temporary for Model H, Table 2), a step is two
+// passes: mu for every point into a compute-precision buffer, then the update
+// of m and of each component of j, which reads mu, m and j through periodic
+// taps (the flux m j_a is formed at each tap, with the rounding of the product
+// m * j_a).  Fixed order per point (FP64 results equal the oracle's bit for bit):
+//   mu  = fma(m, fma(c2, m*m, -c1), -((kappa/q_h2) * S(m)))
+//   div = (D_x(m j_x) + D_y(m j_y)) [+ D_z(m j_z)]
+//   m'  = fma(dt, fma(1/q_h2, S(mu), -(c3g * div)), m)
+//   j_a' = fma(dt, fma(1/q_h2, S(j_a), -(c3g * (m * D_a mu))), j_a)
+// with D f = f(+1) - f(-1) (radius-1 stencils) or fma(8, f(+1) - f(-1),
+// -(f(+2) - f(-2))) (radius 2) and c3g = c3 / (2h) or c3 / (12h).
+#include "sp_internal.h"
+
+namespace sp {
+
+// Wrapped offsets of the planes and rows within the stencil radius around a
+// 256-point row segment (computed once per segment).
+template <int R>
+struct TapRows {
+    size_t zb[2 * R + 1], yb[2 * R + 1];
+    __device__ __forceinline__ TapRows(int y, int z, int nx, int ny, int nz) {
+#pragma unroll
+        for (int d = -R; d <= R; ++d) {
+            zb[d + R] = (size_t)wrap_idx(z + d, nz) * ny * nx;
+            yb[d + R] = (size_t)wrap_idx(y + d, ny) * nx;
+        }
+    }
+    __device__ __forceinline__ size_t at(int x, int nx, int dx, int dy, int dz) const {
+        return zb[dz + R] + yb[dy + R] + wrap_idx(x + dx, nx);
+    }
+};
+
+struct MhArgs {
+    const void *m, *j[3];
+    void *mo, *jo[3];
+    void *mu;
+    int nx, ny, nz;
+    StepConsts k;
+    StepConstsF kf;
+};
+
+__device__ __forceinline__ void mh_seg(long long u, int segs, const MhArgs &a, int &x, int &y, int &z, size_t &row) {
+    const long long r = u / segs;
+    x = (int)(u - r * segs) * 256 + (int)threadIdx.x;
+    y = (int)(r % a.ny);
+    z = (int)(r / a.ny);
+    row = (size_t)r * a.nx;
+}
+
+// central difference along axis A of f at the tap origin
+template <int R, int A, typename Fn>
+__device__ __forceinline__ auto central(const Fn &f) -> decltype(f(0, 0, 0)) {
+    constexpr int ex = (A == 0), ey = (A == 1), ez = (A == 2);
+    const auto d1 = f(ex, ey, ez) - f(-ex, -ey, -ez);
+    if constexpr (R == 1) {
+        return d1;
+    } else {
+        const auto d2 = f(2 * ex, 2 * ey, 2 * ez) - f(-2 * ex, -2 * ey, -2 * ez);
+        return FMA(decltype(d1)(8), d1, -d2);
+    }
+}
+
+template <int ST, typename T>
+__global__ void __launch_bounds__(256) mh_mu_kernel(MhArgs a, int segs) {
+    typedef typename Cmp<T>::type C;
+    constexpr int R = StencilInfo<ST>::r;
+    const ConstsC<C> k(a.k, a.kf);
+    const T *m = static_cast<const T *>(a.m);
+    C *mu = static_cast<C *>(a.mu);
+    const long long units = (long long)a.ny * a.nz * segs;
+    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+        int x, y, z;
+        size_t row;
+        mh_seg(u, segs, a, x, y, z, row);
+        const TapRows<R> tp(y, z, a.nx, a.ny, a.nz);
+        if (x >= a.nx) continue;
+        auto P = [&](int dx, int dy, int dz) -> C { return to_c(m[tp.at(x, a.nx, dx, dy, dz)]); };
+        mu[row + x] = ch_mu<C>(to_c(m[row + x]), stencil_sum<ST, C>(P), k);
+    }
+}
+
+template <int ST, typename T, int DIMS>
+__global__ void __launch_bounds__(256) mh_update_kernel(MhArgs a, int segs, typename Cmp<T>::type c3g) {
+    typedef typename Cmp<T>::type C;
+    constexpr int R = StencilInfo<ST>::r;
+    const ConstsC<C> k(a.k, a.kf);
+    const T *m = static_cast<const T *>(a.m);
+    const C *mu = static_cast<const C *>(a.mu);
+    const T *j[3] = {static_cast<const T *>(a.j[0]), static_cast<const T *>(a.j[1]), static_cast<const T *>(a.j[2])};
+    T *jo[3] = {static_cast<T *>(a.jo[0]), static_cast<T *>(a.jo[1]), static_cast<T *>(a.jo[2])};
+    const long long units = (long long)a.ny * a.nz * segs;
+    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+        int x, y, z;
+        size_t row;
+        mh_seg(u, segs, a, x, y, z, row);
+        const TapRows<R> tp(y, z, a.nx, a.ny, a.nz);
+        if (x >= a.nx) continue;
+        const size_t i = row + x;
+        auto Pmu = [&](int dx, int dy, int dz) -> C { return mu[tp.at(x, a.nx, dx, dy, dz)]; };
+        auto flux = [&](int ax) {
+            return [&, ax](int dx, int dy, int dz) -> C {
+                const size_t t = tp.at(x, a.nx, dx, dy, dz);
+                return to_c(m[t]) * to_c(j[ax][t]);
+            };
+        };
+        C div = central<R, 0>(flux(0)) + central<R, 1>(flux(1));
+        if constexpr (DIMS == 3) div = div + central<R, 2>(flux(2));
+        const C mi = to_c(m[i]);
+        static_cast<T *>(a.mo)[i] = from_c<T>(FMA(k.dt, FMA(k.sAC, stencil_sum<ST, C>(Pmu), -(c3g * div)), mi));
+#pragma unroll
+        for (int ax = 0; ax < DIMS; ++ax) {
+            C gm;
+            if (ax == 0) gm = central<R, 0>(Pmu);
+            else if (ax == 1) gm = central<R, 1>(Pmu);
+            else gm = central<R, 2>(Pmu);
+            auto Pj = [&](int dx, int dy, int dz) -> C { return to_c(j[ax][tp.at(x, a.nx, dx, dy, dz)]); };
+            jo[ax][i] = from_c<T>(FMA(k.dt, FMA(k.sAC, stencil_sum<ST, C>(Pj), -(c3g * (mi * gm))), to_c(j[ax][i])));
+        }
+    }
+}
+
+template <int ST, typename T>
+static cudaError_t launch_mh_t(const MhArgs &a, double c3g, cudaStream_t s, int n_sm) {
+    const int segs = (a.nx + 255) / 256;
+    const long long units = (long long)a.ny * a.nz * segs;
+    const unsigned blocks = (unsigned)std::min<long long>(units, (long long)n_sm * 8);
+    mh_mu_kernel<ST, T><<<blocks, 256, 0, s>>>(a, segs);
+    typedef typename Cmp<T>::type C;
+    if constexpr (StencilInfo<ST>::dims == 2)
+        mh_update_kernel<ST, T, 2><<<blocks, 256, 0, s>>>(a, segs, (C)c3g);
+    else
+        mh_update_kernel<ST, T, 3><<<blocks, 256, 0, s>>>(a, segs, (C)c3g);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_mh_st(int stencil, const MhArgs &a, double c3g, cudaStream_t s, int n_sm) {
+    switch (stencil) {
+    case L5: return launch_mh_t<L5, T>(a, c3g, s, n_sm);
+    case L9BOX: return launch_mh_t<L9BOX, T>(a, c3g, s, n_sm);
+    case L9X4: return launch_mh_t<L9X4, T>(a, c3g, s, n_sm);
+    case L7: return launch_mh_t<L7, T>(a, c3g, s, n_sm);
+    case L27: return launch_mh_t<L27, T>(a, c3g, s, n_sm);
+    default: return launch_mh_t<L13X4, T>(a, c3g, s, n_sm);
+    }
+}
+
+cudaError_t launch_model_h(int dtype, int stencil, void *const in[4], void *const out[4], void *mu, int nx, int ny,
+                           int nz, const StepConsts &k, double c3g, cudaStream_t s, int n_sm) {
+    MhArgs a;
+    a.m = in[0];
+    a.mo = out[0];
+    for (int c = 0; c < 3; ++c) {
+        a.j[c] = in[1 + c] ? in[1 + c] : in[1];
+        a.jo[c] = out[1 + c] ? out[1 + c] : out[1];
+    }
+    a.mu = mu;
+    a.nx = nx;
+    a.ny = ny;
+    a.nz = nz;
+    a.k = k;
+    a.kf = to_float(k);
+    switch (dtype) {
+    case SP_F64: return launch_mh_st<double>(stencil, a, c3g, s, n_sm);
+    case SP_F32: return launch_mh_st<float>(stencil, a, c3g, s, n_sm);
+    default: return launch_mh_st<bf16>(stencil, a, c3g, s, n_sm);
+    }
+}
+
+}  // namespace sp

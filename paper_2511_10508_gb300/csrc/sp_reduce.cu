@@ -66,10 +66,12 @@ template <int WHAT> __device__ __forceinline__ double point_value(double p) {
 }
 
 // Free-energy density at linear index i (forward differences, periodic).
-// With rho (Model C) the density adds rho^2/2 - c3 phi^2 rho.
+// With rho (Model C) the density adds rho^2/2 - c3 phi^2 rho; with currents
+// (Model H, nq components) it adds (j_x^2 + j_y^2 [+ j_z^2]) / 2.
 template <typename T>
-__device__ __forceinline__ double fe_density(const T *__restrict__ f, const T *__restrict__ rho, uint64_t i, int nx,
-                                             int ny, int nz, int dims, double h, double c1, double c2, double c3) {
+__device__ __forceinline__ double fe_density(const T *__restrict__ f, const T *__restrict__ rho, const T *const *jq,
+                                             int nq, uint64_t i, int nx, int ny, int nz, int dims, double h, double c1,
+                                             double c2, double c3) {
     const double p = (double)to_c(f[i]);
     const int x = (int)(i % (uint64_t)nx);
     const int y = (int)((i / (uint64_t)nx) % (uint64_t)ny);
@@ -88,6 +90,11 @@ __device__ __forceinline__ double fe_density(const T *__restrict__ f, const T *_
         g2 = g2 + gz * gz;
     }
     const double p2 = p * p;
+    if (nq > 0) {
+        double q = (double)to_c(jq[0][i]) * (double)to_c(jq[0][i]) + (double)to_c(jq[1][i]) * (double)to_c(jq[1][i]);
+        if (nq == 3) q = q + (double)to_c(jq[2][i]) * (double)to_c(jq[2][i]);
+        return (0.5 * g2 - 0.5 * c1 * p2 + 0.25 * c2 * p2 * p2) + 0.5 * q;
+    }
     if (rho) {
         const double r = (double)to_c(rho[i]);
         return 0.5 * g2 - 0.5 * c1 * p2 + 0.25 * c2 * p2 * p2 + 0.5 * r * r - c3 * p2 * r;
@@ -103,8 +110,9 @@ __device__ __forceinline__ double fe_density(const T *__restrict__ f, const T *_
 // the compute type.  The free energy keeps a per-point Neumaier update.
 template <typename T, int WHAT>
 __global__ void __launch_bounds__(kReduceThreads)
-reduce_partial_kernel(const T *__restrict__ f, const T *__restrict__ rho, int nx, int ny, int nz, int dims, double h,
-                      double c1, double c2, double c3, double *__restrict__ partials) {
+reduce_partial_kernel(const T *__restrict__ f, const T *__restrict__ rho, const T *j0, const T *j1, const T *j2, int nq,
+                      int nx, int ny, int nz, int dims, double h, double c1, double c2, double c3,
+                      double *__restrict__ partials) {
     typedef typename Cmp<T>::type C;
     constexpr int VE = 16 / sizeof(T);       // values per vector
     constexpr int kBlockVecs = (16 + VE - 1) / VE;
@@ -113,8 +121,9 @@ reduce_partial_kernel(const T *__restrict__ f, const T *__restrict__ rho, int nx
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     if constexpr (WHAT == SP_FREE_ENERGY) {
+        const T *jq[3] = {j0, j1, j2};
         for (uint64_t i = tid; i < N; i += stride)
-            neu_add(s, c, fe_density(f, rho, i, nx, ny, nz, dims, h, c1, c2, c3));
+            neu_add(s, c, fe_density(f, rho, jq, nq, i, nx, ny, nz, dims, h, c1, c2, c3));
     } else {
         // vector part when the base is 16-byte aligned (library buffers always are;
         // a caller's pointer may not be), then the scalar tail
@@ -176,8 +185,9 @@ static cudaError_t launch_reduce_t(const void *f, const ReduceGeom &g, double *p
                                    double *out, cudaStream_t s) {
     const double scale = (WHAT == SP_MASS || WHAT == SP_FREE_ENERGY) ? g.cell_volume : 1.0;
     reduce_partial_kernel<T, WHAT><<<nblocks, kReduceThreads, 0, s>>>(
-        static_cast<const T *>(f), static_cast<const T *>(g.rho), g.nx, g.ny, g.nz, g.dims, g.h, g.c1, g.c2, g.c3,
-        partials);
+        static_cast<const T *>(f), static_cast<const T *>(g.rho), static_cast<const T *>(g.jq[0]),
+        static_cast<const T *>(g.jq[1]), static_cast<const T *>(g.jq[2]), g.nq, g.nx, g.ny, g.nz, g.dims, g.h, g.c1,
+        g.c2, g.c3, partials);
     reduce_final_kernel<WHAT><<<1, kReduceThreads, 0, s>>>(partials, nblocks, scale, out);
     return cudaGetLastError();
 }

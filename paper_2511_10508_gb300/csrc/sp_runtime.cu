@@ -47,6 +47,7 @@ extern "C" int sp_version(void) { return 100; }
 // ---------------------------------------------------- stencil metadata --
 
 static int stencil_dims(int st) { return st >= SP_LAP_7 ? 3 : 2; }
+static int stencil_radius(int st) { return (st == SP_LAP_9CROSS4 || st == SP_LAP_13CROSS4) ? 2 : 1; }
 static int stencil_q(int st) {
     static const int q[6] = {1, 6, 12, 1, 30, 12};
     return q[st];
@@ -110,6 +111,17 @@ static double max_growth(int model, int st, double h, const sp_params &p) {
         }
     } else if (model == SP_GRAY_SCOTT) {
         m = std::fmax(std::fabs(p.Du * lam + p.F), std::fabs(p.Dv * lam + p.F + p.k));
+    } else if (model == SP_MODEL_H) {
+        // Model H: m as Cahn-Hilliard, j diffuses with unit mobility
+        const double as[2] = {3.0 * p.c2 - p.c1, -p.c1};
+        for (double a : as) {
+            m = std::fmax(m, std::fabs(lam * (p.kappa * lam + a)));
+            if (p.kappa > 0) {
+                const double ls = -a / (2.0 * p.kappa);
+                if (ls > 0 && ls < lam) m = std::fmax(m, std::fabs(ls * (p.kappa * ls + a)));
+            }
+        }
+        m = std::fmax(m, lam);
     } else {
         // Model C: phi as Allen-Cahn about rho = 0, rho diffuses with unit mobility
         const double as[2] = {p.c1 - 3.0 * p.c2, p.c1};
@@ -120,7 +132,7 @@ static double max_growth(int model, int st, double h, const sp_params &p) {
 }
 
 static int validate_params(int model, int dims, double h, double dt, const sp_params &p, int *st_out) {
-    if (model < SP_ALLEN_CAHN || model > SP_MODEL_C) return fail(SP_EINVAL, "unknown model %d", model);
+    if (model < SP_ALLEN_CAHN || model > SP_MODEL_H) return fail(SP_EINVAL, "unknown model %d", model);
     if (dims != 2 && dims != 3) return fail(SP_EINVAL, "dims must be 2 or 3 (got %d)", dims);
     const int st = resolve_stencil(p.stencil, dims);
     if (st < SP_LAP_5 || st > SP_LAP_13CROSS4) return fail(SP_EINVAL, "unknown stencil %d", p.stencil);
@@ -176,7 +188,7 @@ struct sp_sim {
     double h, dt;
     sp_params p;
     size_t esize;
-    void *f[2][2];        // [level][field]
+    void *f[2][4];        // [level][field] (Model H: m and up to three components of j)
     int cur;              // current level
     int64_t steps;
     cudaStream_t stream;  // library-owned stream
@@ -224,7 +236,7 @@ static void release(sp_sim *s) {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
     for (int l = 0; l < 2; ++l)
-        for (int f = 0; f < 2; ++f)
+        for (int f = 0; f < 4; ++f)
             if (s->f[l][f]) cudaFree(s->f[l][f]);
     if (s->d_partials) cudaFree(s->d_partials);
     if (s->d_stage) cudaFree(s->d_stage);
@@ -268,7 +280,7 @@ extern "C" int sp_create(int model, int dims, const int64_t shape[3], double h, 
     s->dims = dims;
     s->stencil = st;
     s->dtype = prm.dtype;
-    s->nf = (model == SP_GRAY_SCOTT || model == SP_MODEL_C) ? 2 : 1;
+    s->nf = model == SP_MODEL_H ? 1 + dims : ((model == SP_GRAY_SCOTT || model == SP_MODEL_C) ? 2 : 1);
     s->nx = (int)nx;
     s->ny = (int)ny;
     s->nz = (int)nz;
@@ -308,8 +320,22 @@ extern "C" int sp_create(int model, int dims, const int64_t shape[3], double h, 
         release(s);
         return fail(SP_ENOMEM, "scratch allocation failed: %s", cudaGetErrorString(e));
     }
-    e = launch_ic(s->dtype, s->f[0][0], s->nf > 1 ? s->f[0][1] : nullptr, model, dims, s->nx, s->ny, s->nz,
-                  prm.seed, prm.ic_kind, prm.ic_mean, prm.ic_amp, prm.gs_patches, prm.gs_patch, s->stream, s->n_sm);
+    if (model == SP_MODEL_H) {
+        e = cudaMalloc(&s->mu_tmp, s->N * (s->dtype == SP_F64 ? sizeof(double) : sizeof(float)));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s->mu_tmp = nullptr;
+            release(s);
+            return fail(SP_ENOMEM, "Model H mu buffer: %s", cudaGetErrorString(e));
+        }
+    }
+    e = launch_ic(s->dtype, s->f[0][0], (s->nf > 1 && model != SP_MODEL_H) ? s->f[0][1] : nullptr, model, dims, s->nx,
+                  s->ny, s->nz, prm.seed, prm.ic_kind, prm.ic_mean, prm.ic_amp, prm.gs_patches, prm.gs_patch, s->stream,
+                  s->n_sm);
+    if (e == cudaSuccess && model == SP_MODEL_H) {
+        void *j[3] = {s->f[0][1], s->f[0][2], dims == 3 ? s->f[0][3] : nullptr};
+        e = launch_ic_currents(s->dtype, j, dims, s->N, prm.seed, prm.ic_kind, prm.ic_amp, s->stream, s->n_sm);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
         release(s);
@@ -351,6 +377,15 @@ static cudaError_t launch_one_step_impl(sp_sim *s, cudaStream_t st, int k) {
     a.k = s->k;
     a.kf = to_float(s->k);
     if (s->variant == kUnfusedFamily) return launch_unfused_ch(s->dtype, s->stencil, a, s->mu_tmp, st, s->n_sm);
+    if (s->model == SP_MODEL_H) {
+        void *in[4] = {nullptr, nullptr, nullptr, nullptr}, *out[4] = {nullptr, nullptr, nullptr, nullptr};
+        for (int f = 0; f < s->nf; ++f) {
+            in[f] = s->f[s->cur][f];
+            out[f] = s->f[1 - s->cur][f];
+        }
+        const double c3g = s->p.c3 * (stencil_radius(s->stencil) == 1 ? 1.0 / (2.0 * s->h) : 1.0 / (12.0 * s->h));
+        return launch_model_h(s->dtype, s->stencil, in, out, s->mu_tmp, s->nx, s->ny, s->nz, s->k, c3g, st, s->n_sm);
+    }
     switch (s->dtype) {
     case SP_F64: return launch_step_f64(s->model, s->stencil, a, st, s->n_sm, k);
     case SP_F32: return launch_step_f32(s->model, s->stencil, a, st, s->n_sm, k);
@@ -398,7 +433,7 @@ static TuneKey tune_key(const sp_sim *s) {
 
 static std::vector<TuneChoice> tune_candidates(const sp_sim *s) {
     std::vector<TuneChoice> c;
-    if (s->spec) return {{1, 0}};
+    if (s->spec || s->model == SP_MODEL_H) return {{1, 0}};
     if (s->dims == 2 && s->dtype != SP_F64) {
         c.push_back({1, 1});
         for (int spl : {1, 2, 4}) c.push_back({spl, 0});
@@ -625,6 +660,10 @@ extern "C" int sp_reduce(sp_sim *s, int what, double *out, void *stream) {
     g.c3 = s->p.c3;
     // Model C free energy adds rho^2/2 - c3 phi^2 rho
     g.rho = (what == SP_FREE_ENERGY && s->model == SP_MODEL_C) ? s->f[s->cur][1] : nullptr;
+    if (what == SP_FREE_ENERGY && s->model == SP_MODEL_H) {
+        g.nq = s->nf - 1;
+        for (int c = 0; c < g.nq; ++c) g.jq[c] = s->f[s->cur][1 + c];
+    }
     const cudaStream_t st = pick(s, stream);
     double *d_out = s->d_partials + 2 * (size_t)s->nred;
     SP_CUDA(launch_reduce(s->dtype, what, s->f[s->cur][field], g, s->d_partials, s->nred, d_out, st));

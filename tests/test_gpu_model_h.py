@@ -1,0 +1,134 @@
+"""Model H on the GPU against the FP64 oracle (oracle.step_h): FP64 bit for bit
+(two passes per step in the oracle's order), FP32 / BF16 storage within the
+reduced-precision bounds; reductions, graph replay, field I/O."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+# FP32: per-step relative rounding ~6e-8, relative L2 < 1e-5 over these runs.
+# BF16 storage: every field is rounded to 8 significant bits (2^-9 relative) at
+# every store; over 10 steps the error of the small current components adds up
+# to ~1e-2 (measured 1.2e-2), bounded here by 3e-2 = 10 x 2^-9 plus margin.
+TOL = {1: 1e-5, 2: 3e-2}
+
+
+@pytest.fixture(scope="module")
+def sp():
+    import __graft_entry__
+
+    __graft_entry__._load_builder().build()
+    import paper_2511_10508_gb300 as sp
+
+    return sp
+
+
+def make(sp, shape, st, dtype=0, dt=0.002, **kw):
+    kw.setdefault("ic_amp", 0.4)
+    kw.setdefault("c3", 0.8)
+    return sp.Simulation(sp.MODEL_H, shape, dt=dt, stencil=st, dtype=dtype, seed=kw.pop("seed", 77), **kw)
+
+
+def oracle_prm(sim):
+    p = sim.prm
+    return O.params(c1=p.c1, c2=p.c2, kappa=p.kappa, c3=p.c3)
+
+
+def read_all(sim, as_f64=True):
+    return [sim.read(f, as_f64=as_f64) for f in range(sim.nfields)]
+
+
+@pytest.mark.parametrize("st", [0, 1, 2, 3, 4, 5])
+def test_model_h_fp64_bitwise(sp, st):
+    shape = (70, 301) if O.STENCIL_DIMS[st] == 2 else (20, 24, 36)
+    with make(sp, shape, st) as s:
+        m0, j0 = O.initial_condition_h(shape, seed=77, amp=0.4)
+        got0 = read_all(s)
+        assert np.array_equal(got0[0], m0) and all(np.array_equal(a, b) for a, b in zip(got0[1:], j0))
+        s.step(9)
+        got = read_all(s)
+    m, js = O.step_h(st, m0, j0, dt=0.002, prm=oracle_prm(s), nsteps=9)
+    assert np.array_equal(got[0], m), np.abs(got[0] - m).max()
+    for a, b in zip(got[1:], js):
+        assert np.array_equal(a, b), np.abs(a - b).max()
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (3, 5), (2, 3, 5), (1, 1, 1)])
+def test_model_h_small_and_degenerate(sp, shape):
+    for st in ((0, 2) if len(shape) == 2 else (3, 5)):
+        with make(sp, shape, st) as s:
+            m0, j0 = O.initial_condition_h(shape, seed=77, amp=0.4)
+            s.step(5)
+            got = read_all(s)
+        m, js = O.step_h(st, m0, j0, dt=0.002, prm=oracle_prm(s), nsteps=5)
+        assert np.array_equal(got[0], m) and all(np.array_equal(a, b) for a, b in zip(got[1:], js))
+
+
+def test_model_h_graph_replay_long_run(sp):
+    """40 steps (one captured 32-step graph plus eager steps) bit for bit."""
+    shape = (64, 96)
+    with make(sp, shape, 0) as s:
+        m0, j0 = O.initial_condition_h(shape, seed=77, amp=0.4)
+        s.step(40)
+        got = read_all(s)
+    m, js = O.step_h(0, m0, j0, dt=0.002, prm=oracle_prm(s), nsteps=40)
+    assert np.array_equal(got[0], m) and all(np.array_equal(a, b) for a, b in zip(got[1:], js))
+
+
+@pytest.mark.parametrize("dtype", [1, 2])
+@pytest.mark.parametrize("st", [0, 3])
+def test_model_h_reduced_precision(sp, dtype, st):
+    shape = (60, 400) if st == 0 else (24, 28, 40)
+    with make(sp, shape, st, dtype=dtype) as s:
+        start = read_all(s)  # the rounded initial fields, widened exactly
+        s.step(10)
+        got = read_all(s)
+    m, js = O.step_h(st, start[0], start[1:], dt=0.002, prm=oracle_prm(s), nsteps=10)
+    for a, b in zip(got, [m] + js):
+        e = O.rel_l2(a, b)
+        assert e < TOL[dtype], e
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_model_h_reductions(sp, dtype):
+    shape = (20, 24, 28)
+    with make(sp, shape, 3, dtype=dtype) as s:
+        m0 = s.reduce(sp.MASS)
+        s.step(30)
+        f = read_all(s)
+        scale = np.abs(f[0]).sum() + 1
+        assert abs(s.reduce(sp.MASS) - O.mass(f[0])) <= 1e-13 * scale
+        assert abs(s.reduce(sp.MASS) - m0) <= (1e-12 if dtype == 0 else 1e-4) * scale
+        fe = O.free_energy_h(f[0], f[1:], c1=s.prm.c1, c2=s.prm.c2)
+        assert abs(s.reduce(sp.FREE_ENERGY) - fe) <= 1e-12 * (abs(fe) + scale)
+
+
+def test_model_h_free_energy_decreases_on_gpu(sp):
+    with make(sp, (96, 128), 0, dt=0.002, ic_amp=0.6, c3=1.5) as s:
+        F = [s.reduce(sp.FREE_ENERGY)]
+        for _ in range(25):
+            s.step(2)
+            F.append(s.reduce(sp.FREE_ENERGY))
+    assert all(b < a for a, b in zip(F, F[1:])), F
+
+
+def test_model_h_write_current_then_step(sp):
+    shape = (32, 40)
+    rng = np.random.default_rng(4)
+    with make(sp, shape, 0) as s:
+        jx = rng.uniform(-0.2, 0.2, shape)
+        s.write(1, jx)
+        f = read_all(s)
+        assert np.array_equal(f[1], jx)
+        s.step(6)
+        got = read_all(s)
+    m, js = O.step_h(0, f[0], f[1:], dt=0.002, prm=oracle_prm(s), nsteps=6)
+    assert np.array_equal(got[0], m) and all(np.array_equal(a, b) for a, b in zip(got[1:], js))
+
+
+def test_model_h_not_served(sp):
+    with sp.Server(1 << 30) as srv:
+        with pytest.raises(sp.SpError):
+            srv.submit(sp.MODEL_H, (64, 64), dt=0.002, nsteps=10)
