@@ -75,6 +75,8 @@ def lib():
             L.or_mass.argtypes = [c_int, i64, i64, i64, dbl, ptr]
             L.or_free_energy.restype = dbl
             L.or_free_energy.argtypes = [c_int, i64, i64, i64, dbl, dbl, dbl, ptr]
+            L.or_step_gen.restype = c_int
+            L.or_step_gen.argtypes = [c_int, c_int, c_int, ptr, i64, i64, i64, dbl, dbl, ptr, ptr, ptr, i64]
             L.or_step_h.restype = c_int
             L.or_step_h.argtypes = [c_int, i64, i64, i64, dbl, dbl, ptr, ptr, ptr, ptr, ptr, i64]
             L.or_initial_condition_h.restype = c_int
@@ -271,3 +273,21 @@ def free_energy_h(m, j, h: float = 1.0, c1: float = 1.0, c2: float = 1.0) -> flo
     nx, ny, nz = _shape3(m, dims)
     return lib().or_free_energy_h(dims, nx, ny, nz, h, c1, c2, _p(m), _p(js[0]), _p(js[1]),
                                   _p(js[2]) if dims == 3 else None)
+
+
+def step_gen(model: int, order: int, u, v=None, *, h: float = 1.0, dt: float, prm=None, nsteps: int = 1):
+    """Steps with the generated cross Laplacian of accuracy ``order`` (weights from
+    oracle/stencil_gen.py); returns copies like ``step``."""
+    from .stencil_gen import kernel_weights
+
+    u = np.array(u, dtype=np.float64, copy=True, order="C")
+    vv = None if v is None else np.array(v, dtype=np.float64, copy=True, order="C")
+    prm = params() if prm is None else _f64(prm)
+    dims = u.ndim
+    wk = np.array(kernel_weights(order, dims), dtype=np.float64)
+    nx, ny, nz = _shape3(u, dims)
+    rc = lib().or_step_gen(model, dims, order // 2, _p(wk), nx, ny, nz, h, dt, _p(prm), _p(u),
+                           None if vv is None else _p(vv), int(nsteps))
+    if rc:
+        raise ValueError("or_step_gen: bad arguments or out of memory")
+    return u if model not in TWO_FIELD else (u, vv)

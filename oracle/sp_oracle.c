@@ -93,7 +93,8 @@ enum { OR_AC = 0, OR_CH = 1, OR_GS = 2, OR_MC = 3, OR_MH = 4 };
 /* parameter vector: c1, c2, kappa, Du, Dv, F, k */
 enum { P_C1 = 0, P_C2, P_KAPPA, P_DU, P_DV, P_F, P_K, P_C3, P_COUNT };
 
-#define OR_MAXR 2
+#define OR_MAXR 4
+#define OR_GEN 6 /* generated cross stencil (weights held in the grid) */
 
 int or_num_threads(void) {
 #ifdef _OPENMP
@@ -107,6 +108,7 @@ int or_stencil_dims(int st) { return (st >= OR_S4) ? 3 : 2; }
 int or_stencil_radius(int st) { return (st == OR_S3 || st == OR_S6) ? 2 : 1; }
 int or_stencil_q(int st) {
     switch (st) {
+    case OR_GEN: return 1;
     case OR_S1: return 1;
     case OR_S2: return 6;
     case OR_S3: return 12;
@@ -121,10 +123,13 @@ int or_stencil_q(int st) {
 typedef struct {
     int64_t n[3];
     int64_t *w[3];
+    int gen_dims, gen_r;  /* generated cross stencil: dimensions, radius */
+    double gen_w[5];      /* its kernel weights (d w_0, w_1, ..., w_r) */
 } grid_t;
 
 static int grid_init(grid_t *g, int64_t nx, int64_t ny, int64_t nz) {
     g->n[0] = nx; g->n[1] = ny; g->n[2] = nz;
+    g->gen_dims = 0; g->gen_r = 0;
     for (int a = 0; a < 3; a++) {
         int64_t n = g->n[a];
         g->w[a] = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * OR_MAXR + 1) * (size_t)n);
@@ -154,6 +159,16 @@ static inline double at(const double *f, const grid_t *g, int64_t x, int64_t y, 
 /* Unscaled weighted neighbour sum S = sum_s w_s f(x+s), in the fixed order. */
 static double stencil_sum(int st, const double *f, const grid_t *g, int64_t x, int64_t y, int64_t z) {
 #define P(dx, dy, dz) at(f, g, x, y, z, dx, dy, dz)
+    if (st == OR_GEN) {
+        /* P_j = ((x pair) + (y pair)) [+ (z pair)];  S = fma(d w_0, f_0, w_r P_r (+ ...) fused down to w_1 P_1) */
+        double acc = 0.0;
+        for (int jj = g->gen_r; jj >= 1; jj--) {
+            double pj = (P(jj, 0, 0) + P(-jj, 0, 0)) + (P(0, jj, 0) + P(0, -jj, 0));
+            if (g->gen_dims == 3) pj = pj + (P(0, 0, jj) + P(0, 0, -jj));
+            acc = (jj == g->gen_r) ? g->gen_w[jj] * pj : fma(g->gen_w[jj], pj, acc);
+        }
+        return fma(g->gen_w[0], P(0, 0, 0), acc);
+    }
     switch (st) {
     case OR_S1: {
         double C = (P(-1, 0, 0) + P(1, 0, 0)) + (P(0, -1, 0) + P(0, 1, 0));
@@ -255,13 +270,46 @@ int or_chemical_potential(int st, int64_t nx, int64_t ny, int64_t nz, double h, 
  * rho = v.  prm = {c1, c2, kappa, Du, Dv, F, k, c3}.  Returns 0, or -1 on bad
  * arguments / allocation failure.
  */
+static int step_body(int model, int st, grid_t *gp, double h, double dt, const double *prm, double *u, double *v,
+                     int64_t nsteps);
+
 int or_step(int model, int st, int64_t nx, int64_t ny, int64_t nz, double h, double dt,
             const double *prm, double *u, double *v, int64_t nsteps) {
     grid_t g;
     if (check_grid(st, nx, ny, nz) || model < OR_AC || model > OR_MC || nsteps < 0) return -1;
-    const int two = (model == OR_GS || model == OR_MC);
-    if (two && !v) return -1;
+    if ((model == OR_GS || model == OR_MC) && !v) return -1;
     if (grid_init(&g, nx, ny, nz)) return -1;
+    const int rc = step_body(model, st, &g, h, dt, prm, u, v, nsteps);
+    grid_free(&g);
+    return rc;
+}
+
+/*
+ * The same steps with a generated cross stencil of radius r (1..4) in dims
+ * dimensions: wk = (d w_0, w_1, ..., w_r), the exact weights of the order-2r
+ * central second derivative rounded once to FP64 (oracle/stencil_gen.py); the
+ * Laplacian is S / h^2 with S = fma(d w_0, f_0, ...) as in stencil_sum().
+ */
+int or_step_gen(int model, int dims, int r, const double *wk, int64_t nx, int64_t ny, int64_t nz, double h, double dt,
+                const double *prm, double *u, double *v, int64_t nsteps) {
+    grid_t g;
+    if (model < OR_AC || model > OR_MC || nsteps < 0 || r < 1 || r > OR_MAXR || !wk) return -1;
+    if ((dims != 2 && dims != 3) || nx < 1 || ny < 1 || nz < 1 || (dims == 2 && nz != 1)) return -1;
+    if ((model == OR_GS || model == OR_MC) && !v) return -1;
+    if (grid_init(&g, nx, ny, nz)) return -1;
+    g.gen_dims = dims;
+    g.gen_r = r;
+    for (int j = 0; j <= r; j++) g.gen_w[j] = wk[j];
+    const int rc = step_body(model, OR_GEN, &g, h, dt, prm, u, v, nsteps);
+    grid_free(&g);
+    return rc;
+}
+
+static int step_body(int model, int st, grid_t *gp, double h, double dt, const double *prm, double *u, double *v,
+                     int64_t nsteps) {
+    grid_t g = *gp;
+    const int two = (model == OR_GS || model == OR_MC);
+    const int64_t nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int64_t n = nx * ny * nz;
     const double q_h2 = ((double)or_stencil_q(st) * h) * h;
     const double c1 = prm[P_C1], c2 = prm[P_C2];
@@ -269,7 +317,7 @@ int or_step(int model, int st, int64_t nx, int64_t ny, int64_t nz, double h, dou
     double *vn = two ? (double *)malloc(sizeof(double) * (size_t)n) : NULL;
     double *mu = (model == OR_CH || model == OR_MC) ? (double *)malloc(sizeof(double) * (size_t)n) : NULL;
     if (!un || (two && !vn) || ((model == OR_CH || model == OR_MC) && !mu)) {
-        free(un); free(vn); free(mu); grid_free(&g);
+        free(un); free(vn); free(mu);
         return -1;
     }
     double *uc = u, *vc = v;
@@ -335,7 +383,6 @@ int or_step(int model, int st, int64_t nx, int64_t ny, int64_t nz, double h, dou
     if (uc != u) { memcpy(u, uc, sizeof(double) * (size_t)n); un = uc; }
     if (two && vc != v) { memcpy(v, vc, sizeof(double) * (size_t)n); vn = vc; }
     free(un); free(vn); free(mu);
-    grid_free(&g);
     return 0;
 }
 

@@ -48,6 +48,10 @@ MUTANTS = {
     "Model C density Laplacian of rho only": ("vn[i] = fma(dq, stencil_sum(st, mu, &g, x, y, z), r);",
                                               "vn[i] = fma(dq, stencil_sum(st, vc, &g, x, y, z), r);"),
     "Model C free-energy coupling sign": ("+ 0.5 * r * r - c3 * p2 * r", "+ 0.5 * r * r + c3 * p2 * r"),
+    "generated stencil accumulation sign": ("acc = (jj == g->gen_r) ? g->gen_w[jj] * pj : fma(g->gen_w[jj], pj, acc);",
+                                            "acc = (jj == g->gen_r) ? g->gen_w[jj] * pj : fma(g->gen_w[jj], pj, -acc);"),
+    "generated stencil without z pairs": ("if (g->gen_dims == 3) pj = pj + (P(0, 0, jj) + P(0, 0, -jj));",
+                                          "if (g->gen_dims == 4) pj = pj + (P(0, 0, jj) + P(0, 0, -jj));"),
     "Model H printed coupling sign in j": ("-(c3g * (mc[i] * gm)))", "(c3g * (mc[i] * gm)))"),
     "Model H divergence sign": ("fma(sL, stencil_sum(st, mu, &g, x, y, z), -(c3g * div))",
                                 "fma(sL, stencil_sum(st, mu, &g, x, y, z), (c3g * div))"),
@@ -75,6 +79,7 @@ def test_pins_reject_mutant(name, tmp_path):
                            "-o", str(so), str(csrc), "-lm"])
     env = dict(os.environ, SP_ORACLE_LIB=str(so), OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_stencil_gen.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch mutant {name!r}:\n{r.stdout[-2000:]}"
