@@ -72,6 +72,11 @@ WORKLOADS = {
     "mh2d-8192-f32-lap5": (4, 2, (8192, 8192), 0.01, 0, 1, 20),
     "mh3d-256-f64-lap7": (4, 3, (256, 256, 256), 0.005, 3, 0, 10),
     "mh3d-256-f32-lap7": (4, 3, (256, 256, 256), 0.005, 3, 1, 20),
+    # generated cross Laplacians (accuracy order in the name), stencil entry 6
+    "ch2d-4096-f64-gen8": (1, 2, (4096, 4096), 0.002, 6, 0, 50),
+    "ac2d-4096-f64-gen6": (0, 2, (4096, 4096), 0.05, 6, 0, 50),
+    "ch3d-256-f64-gen6": (1, 3, (256, 256, 256), 0.001, 6, 0, 10),
+    "ch2d-8192-f32-gen8": (1, 2, (8192, 8192), 0.002, 6, 1, 20),
     # ablation: the unfused Cahn-Hilliard step (mu through a device-memory temporary)
     "ch2d-4096-f64-lap5-unfused": (1, 2, (4096, 4096), 0.01, 0, 0, 100, 1, 3),
     "ch2d-16384-f32-lap5-unfused": (1, 2, (16384, 16384), 0.01, 0, 1, 20, 1, 3),
@@ -80,7 +85,7 @@ WORKLOADS = {
 DEFAULT = "ch2d-4096-f64-lap5"
 MODEL_NAME = {0: "Allen-Cahn", 1: "Cahn-Hilliard", 2: "Gray-Scott", 3: "Model C", 4: "Model H"}
 STENCIL_NAME = {0: "5-point", 1: "9-point box", 2: "4th-order 9-point cross", 3: "7-point", 4: "27-point",
-                5: "4th-order 13-point cross"}
+                5: "4th-order 13-point cross", 6: "generated cross"}
 DTYPE_NAME = {0: "f64", 1: "f32", 2: "bf16-storage/f32"}
 ESIZE = {0: 8, 1: 4, 2: 2}
 
@@ -124,10 +129,17 @@ def model_h_ops_per_lup(st: int) -> int:
     return (2 + d) * s + d * (7 + 2 * dc) + 6
 
 
-def fp64_ops_per_lup(model: int, st: int) -> int:
+def generated_stencil_ops(order: int, dims: int) -> int:
+    """Per application: r pair groups of 2d - 1 additions each, r + 1 multiplies /
+    fused multiply-adds."""
+    r = order // 2
+    return r * (2 * dims - 1) + r + 1
+
+
+def fp64_ops_per_lup(model: int, st: int, order: int = 0, dims: int = 2) -> int:
     if model == 4:
         return model_h_ops_per_lup(st)
-    s = STENCIL_OPS[st]
+    s = generated_stencil_ops(order, dims) if st == 6 else STENCIL_OPS[st]
     # Model C: mu of the density once per point (2), two stencils, the update (7)
     return {0: s + 5, 1: 2 * s + 5, 2: 2 * s + 9, 3: 2 * s + 9}[model]
 
@@ -210,7 +222,7 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_rate(model, dims, shape, dt, st, budget_s=15.0, max_steps=2000, spectral=False):
+def oracle_rate(model, dims, shape, dt, st, budget_s=15.0, max_steps=2000, spectral=False, order=0):
     """FP64 oracle GLUPS on the host cores over a bounded sample of the workload."""
     import numpy as np
 
@@ -244,6 +256,8 @@ def oracle_rate(model, dims, shape, dt, st, budget_s=15.0, max_steps=2000, spect
     else:
         u = O.initial_condition(model, shape, seed=1, amp=0.01)
         run = lambda n: O.step(model, st, u, dt=dt, prm=prm, nsteps=n)  # noqa: E731
+    if order and model in (0, 1):
+        run = lambda n: O.step_gen(model, order, u, dt=dt, prm=prm, nsteps=n)  # noqa: E731
 
     run(1)  # start the OpenMP team
     t0 = time.perf_counter()
@@ -426,8 +440,12 @@ def run_reference(args):
 
 def workload_config(name):
     model, dims, shape, dt, st, dtype, sub = WORKLOADS[name][:7]
-    lap = ("semi-implicit Fourier spectral scheme (continuous Laplacian)" if name.endswith("-spectral")
-           else f"{STENCIL_NAME[st]} Laplacian, forward Euler")
+    if name.endswith("-spectral"):
+        lap = "semi-implicit Fourier spectral scheme (continuous Laplacian)"
+    elif "-gen" in name:
+        lap = f"generated cross Laplacian of order {name.rsplit('-gen', 1)[1]}, forward Euler"
+    else:
+        lap = f"{STENCIL_NAME[st]} Laplacian, forward Euler"
     return {"workload": f"{MODEL_NAME[model]} {dims}D {'x'.join(map(str, shape[::-1]))} {DTYPE_NAME[dtype]}, "
                         f"{lap}, dt={dt}, h=1, periodic",
             "model": MODEL_NAME[model], "grid": list(shape[::-1]), "stencil": lap,
@@ -470,8 +488,11 @@ def main():
     spl_req = WORKLOADS[args.workload][7] if len(WORKLOADS[args.workload]) > 7 else 0
     npts = int(np.prod(shape))
     spectral = args.workload.endswith("-spectral")
+    order = int(args.workload.rsplit("-gen", 1)[1]) if "-gen" in args.workload else 0
     kw = dict(stencil=st, dtype=dtype, seed=1 + rank, ic_amp=0.01, steps_per_launch=spl_req,
               scheme=sp.SCHEME_SPECTRAL if spectral else sp.SCHEME_FD)
+    if order:
+        kw.update(stencil_order=order)
     if model == 2:
         kw.update(seed=2 + rank, gs_patches=64, gs_patch=20)
     sim = sp.Simulation(model, shape, dt=dt, **kw)
@@ -538,7 +559,7 @@ def main():
                 "note": f"semi-implicit spectral step, {bpl} bytes/LUP at one pass per stage (cube, forward "
                         "transform, Fourier update, inverse transform)"}
     elif dtype == 0:
-        ops = fp64_ops_per_lup(model, st)
+        ops = fp64_ops_per_lup(model, st, order, dims)
         achieved = ops * npts / (launch_ms * 1e-3) / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "FP64 Gop/s",
                 "frac": achieved / FP64_PEAK_GOPS, "traffic": traffic,
@@ -581,7 +602,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_rate(model, dims, shape, dt, st, spectral=spectral)
+        cpu = oracle_rate(model, dims, shape, dt, st, spectral=spectral, order=order)
 
     served = None
     if rank == 0 and not args.no_served:

@@ -79,7 +79,10 @@ typedef enum sp_stencil {
     SP_LAP_9CROSS4 = 2,    /* 2D, q=12: centre -60, +-1: 16, +-2: -1 per axis (4th order) */
     SP_LAP_7 = 3,          /* 3D, q=1:  centre -6, faces 1 */
     SP_LAP_27 = 4,         /* 3D, q=30: centre -128, faces 14, edges 3, corners 1 (isotropic) */
-    SP_LAP_13CROSS4 = 5    /* 3D, q=12: centre -90, +-1: 16, +-2: -1 per axis (4th order) */
+    SP_LAP_13CROSS4 = 5,   /* 3D, q=12: centre -90, +-1: 16, +-2: -1 per axis (4th order) */
+    SP_LAP_GENERATED = 6   /* 2D or 3D cross stencil of accuracy sp_params.stencil_order (2, 4, 6, 8),
+                              weights generated at sp_create (see sp_stencil_weights); q = 1.
+                              Allen-Cahn, Cahn-Hilliard, Gray-Scott and Model C; not served. */
 } sp_stencil;
 
 /* Storage / arithmetic precision of the fields. */
@@ -139,6 +142,7 @@ typedef struct sp_params {
     int steps_per_launch;  /* time steps fused per kernel launch (temporal blocking);
                               0 = the library's choice, 1 = none */
     int scheme;            /* sp_scheme (default SP_SCHEME_FD) */
+    int stencil_order;     /* accuracy order of SP_LAP_GENERATED (even, 2..8; default 2) */
     int flags;             /* SP_FLAG_* bits; other bits must be 0 */
 } sp_params;
 
@@ -250,6 +254,18 @@ int sp_autotune(sp_sim *sim, void *stream, int64_t *steps_taken);
  * Every available configuration gives bit-identical results.  SP_EINVAL if the
  * pair is not available for this grid; cancels a pending SP_FLAG_AUTOTUNE. */
 int sp_set_launch_config(sp_sim *sim, int steps_per_launch, int variant);
+
+/* Weights of the generated cross Laplacian (SP_LAP_GENERATED; the paper
+ * generates stencils by solving a polynomial-interpolation system, Sec.
+ * "Compile-Time Stencil Generation").  The symmetric weights w_0..w_r (r =
+ * order/2) of the central second derivative exact on polynomials of degree
+ * <= order+1 are found in exact rational arithmetic and rounded once to FP64.
+ * Host only.  w receives order/2 + 1 values (dims * w_0, w_1, ..., w_r), the
+ * kernels' weights: L_h f = (1/h^2) [dims w_0 f_0 + sum_j w_j P_j], P_j the sum
+ * over axes of f(+j e_a) + f(-j e_a); *lambda_max (if not NULL) the largest
+ * eigenvalue of -h^2 L_h.  SP_EINVAL for an odd order or one outside 2..8, or
+ * dims not 2 or 3. */
+int sp_stencil_weights(int order, int dims, double *w, double *lambda_max);
 
 /* Launch configuration in use: steps fused per launch and kernel family
  * (0 = the default for the grid, 1 = the alternative the autotuner may pick). */

@@ -14,12 +14,13 @@ import numpy as np
 
 from . import _native as N
 from ._native import (ALLEN_CAHN, BF16_F32, CAHN_HILLIARD, F32, F64, FLAG_AUTOTUNE, FREE_ENERGY, GRAY_SCOTT, IC_CONSTANT,
-                      IC_NOISE, LAP_5, LAP_7, LAP_9BOX, LAP_9CROSS4, LAP_13CROSS4, LAP_27, LAP_DEFAULT, MASS,
+                      IC_NOISE, LAP_5, LAP_7, LAP_9BOX, LAP_9CROSS4, LAP_13CROSS4, LAP_27, LAP_DEFAULT, LAP_GENERATED, MASS,
                       MAX_U, MIN_U, MODEL_C, MODEL_H, SCHEME_FD, SCHEME_SPECTRAL, SUM_U, SUM_V, SUMSQ_U, SpError)
 
 __all__ = ["Simulation", "Server", "Result", "params", "check_stability", "SpError", "ALLEN_CAHN", "CAHN_HILLIARD", "GRAY_SCOTT",
            "MODEL_C", "MODEL_H", "SCHEME_FD", "SCHEME_SPECTRAL",
-           "LAP_5", "LAP_9BOX", "LAP_9CROSS4", "LAP_7", "LAP_27", "LAP_13CROSS4", "LAP_DEFAULT", "F64", "F32",
+           "LAP_5", "LAP_9BOX", "LAP_9CROSS4", "LAP_7", "LAP_27", "LAP_13CROSS4", "LAP_DEFAULT", "LAP_GENERATED",
+           "stencil_weights", "F64", "F32",
            "BF16_F32", "IC_NOISE", "IC_CONSTANT", "FLAG_AUTOTUNE", "MASS", "FREE_ENERGY", "SUM_U", "SUM_V", "MIN_U", "MAX_U",
            "SUMSQ_U"]
 
@@ -35,6 +36,15 @@ def params(model: int, dims: int, **kw) -> N.sp_params:
             raise AttributeError(f"sp_params has no field {k!r}")
         setattr(p, k, v)
     return p
+
+
+def stencil_weights(order: int, dims: int):
+    """Kernel weights (dims w_0, w_1, ..., w_r) and lambda_max of the generated cross
+    Laplacian of accuracy ``order`` (see sp_stencil_weights)."""
+    w = (ctypes.c_double * 5)()
+    lm = ctypes.c_double(0.0)
+    N.check(N.lib().sp_stencil_weights(int(order), int(dims), w, ctypes.byref(lm)), "sp_stencil_weights")
+    return [w[i] for i in range(order // 2 + 1)], lm.value
 
 
 def check_stability(model: int, dims: int, h: float, dt: float, prm: N.sp_params | None = None):

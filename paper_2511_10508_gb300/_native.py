@@ -22,7 +22,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 # enums (mirrors sp.h)
 SP_OK, SP_EINVAL, SP_EUNSTABLE, SP_ENOMEM, SP_EBUDGET, SP_ECUDA, SP_ETIMEOUT, SP_EBUSY, SP_PENDING, SP_ENOTFOUND = range(10)
 ALLEN_CAHN, CAHN_HILLIARD, GRAY_SCOTT, MODEL_C, MODEL_H = 0, 1, 2, 3, 4
-LAP_DEFAULT, LAP_5, LAP_9BOX, LAP_9CROSS4, LAP_7, LAP_27, LAP_13CROSS4 = -1, 0, 1, 2, 3, 4, 5
+LAP_DEFAULT, LAP_5, LAP_9BOX, LAP_9CROSS4, LAP_7, LAP_27, LAP_13CROSS4, LAP_GENERATED = -1, 0, 1, 2, 3, 4, 5, 6
 F64, F32, BF16_F32 = 0, 1, 2
 IC_NOISE, IC_CONSTANT = 0, 1
 FLAG_AUTOTUNE = 1
@@ -36,7 +36,8 @@ class sp_params(ctypes.Structure):
                 ("c3", ctypes.c_double), ("stencil", ctypes.c_int), ("dtype", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("ic_kind", ctypes.c_int), ("ic_mean", ctypes.c_double), ("ic_amp", ctypes.c_double),
                 ("gs_patches", ctypes.c_int), ("gs_patch", ctypes.c_int),
-                ("steps_per_launch", ctypes.c_int), ("scheme", ctypes.c_int), ("flags", ctypes.c_int)]
+                ("steps_per_launch", ctypes.c_int), ("scheme", ctypes.c_int), ("stencil_order", ctypes.c_int),
+                ("flags", ctypes.c_int)]
 
 
 class sp_request(ctypes.Structure):
@@ -76,6 +77,7 @@ _SIGS = {
     "sp_steps_taken": (ctypes.c_int, [_vp, _P(_i64)]),
     "sp_autotune": (ctypes.c_int, [_vp, _vp, _P(_i64)]),
     "sp_set_launch_config": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "sp_stencil_weights": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P(ctypes.c_double), _P(ctypes.c_double)]),
     "sp_launch_config": (ctypes.c_int, [_vp, _P(ctypes.c_int), _P(ctypes.c_int)]),
     "sp_destroy": (ctypes.c_int, [_vp]),
     "sp_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, _P(_vp)]),

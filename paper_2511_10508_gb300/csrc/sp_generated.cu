@@ -1,0 +1,273 @@
+// sp_generated.cu -- cross Laplacians of any even accuracy order, generated at
+// run time (the paper generates stencils from polynomial interpolation, Sec.
+// "Compile-Time Stencil Generation"), and the step kernels that use them.
+//
+// Weights: on the points -r..r (r = order/2) the symmetric weights w_0..w_r of
+// the central second derivative make it exact on polynomials of degree <= 2r+1:
+//   sum_{j>=1} w_j j^(2m) = [m == 1]  (m = 1..r),   w_0 = -2 sum_{j>=1} w_j.
+// The system is solved exactly in rational arithmetic and each weight is then
+// rounded once to FP64, so the values do not depend on the solver.  In d
+// dimensions the cross Laplacian is (1/h^2) [d w_0 f_0 + sum_j w_j P_j] with
+// P_j = ((f(+j e_x) + f(-j e_x)) + (f(+j e_y) + f(-j e_y))) [+ (z pair)], in the
+// fixed order  acc = w_r P_r; acc = fma(w_j, P_j, acc) for j = r-1..1;
+// S = fma(d w_0, f_0, acc).  The kernels are per point (a block per 256-point
+// row segment, tap offsets computed once per segment); Cahn-Hilliard takes two
+// passes through a mu buffer.
+#include <cstdint>
+#include <cstdlib>
+
+#include "sp_internal.h"
+
+namespace sp {
+
+// ------------------------------------------------------ exact weights --
+
+namespace {
+struct Rat {
+    __int128 p, q;  // q > 0, gcd(p, q) = 1
+};
+__int128 gcd128(__int128 a, __int128 b) {
+    if (a < 0) a = -a;
+    if (b < 0) b = -b;
+    while (b) {
+        const __int128 t = a % b;
+        a = b;
+        b = t;
+    }
+    return a ? a : 1;
+}
+Rat mk(__int128 p, __int128 q) {
+    if (q < 0) p = -p, q = -q;
+    const __int128 g = gcd128(p, q);
+    return {p / g, q / g};
+}
+Rat add(Rat a, Rat b) { return mk(a.p * b.q + b.p * a.q, a.q * b.q); }
+Rat sub(Rat a, Rat b) { return mk(a.p * b.q - b.p * a.q, a.q * b.q); }
+Rat mul(Rat a, Rat b) { return mk(a.p * b.p, a.q * b.q); }
+Rat dvd(Rat a, Rat b) { return mk(a.p * b.q, a.q * b.p); }
+}  // namespace
+
+// Exact weights w_0..w_r of the central second derivative of accuracy `order`
+// (even, 2..8) as numerator / denominator pairs.
+static bool exact_weights(int order, Rat *w) {
+    if (order < 2 || order > 2 * kMaxGenRadius || order % 2) return false;
+    const int r = order / 2;
+    Rat A[kMaxGenRadius][kMaxGenRadius + 1];
+    for (int m = 1; m <= r; ++m) {
+        for (int j = 1; j <= r; ++j) {
+            __int128 v = 1;
+            for (int e = 0; e < 2 * m; ++e) v *= j;
+            A[m - 1][j - 1] = mk(v, 1);
+        }
+        A[m - 1][r] = mk(m == 1 ? 1 : 0, 1);
+    }
+    for (int c = 0; c < r; ++c) {  // Gauss-Jordan elimination
+        int piv = c;
+        while (piv < r && A[piv][c].p == 0) ++piv;
+        if (piv == r) return false;
+        if (piv != c)
+            for (int k = 0; k <= r; ++k) std::swap(A[c][k], A[piv][k]);
+        const Rat pv = A[c][c];
+        for (int k = 0; k <= r; ++k) A[c][k] = dvd(A[c][k], pv);
+        for (int i = 0; i < r; ++i)
+            if (i != c && A[i][c].p != 0) {
+                const Rat f = A[i][c];
+                for (int k = 0; k <= r; ++k) A[i][k] = sub(A[i][k], mul(f, A[c][k]));
+            }
+    }
+    Rat s = mk(0, 1);
+    for (int j = 1; j <= r; ++j) {
+        w[j] = A[j - 1][r];
+        s = add(s, w[j]);
+    }
+    w[0] = mul(mk(-2, 1), s);
+    return true;
+}
+
+// p/q rounded once to FP64 (p and q are far below 2^53 for these orders)
+static double to_double(Rat a) { return (double)(long long)a.p / (double)(long long)a.q; }
+
+int generated_weights(int order, int dims, double *wk, double *lambda_max) {
+    Rat w[kMaxGenRadius + 1];
+    if (!exact_weights(order, w) || (dims != 2 && dims != 3)) return SP_EINVAL;
+    const int r = order / 2;
+    wk[0] = to_double(mul(mk(dims, 1), w[0]));
+    for (int j = 1; j <= r; ++j) wk[j] = to_double(w[j]);
+    if (lambda_max) {  // largest eigenvalue of -h^2 L_h: theta = pi on every axis
+        Rat one = w[0];
+        for (int j = 1; j <= r; ++j) one = add(one, mul(mk(j % 2 ? -2 : 2, 1), w[j]));
+        *lambda_max = to_double(mul(mk(-dims, 1), one));
+    }
+    return SP_OK;
+}
+
+// -------------------------------------------------------------- kernels --
+
+struct GenW {
+    double w[kMaxGenRadius + 1];  // d w_0, w_1, ..., w_r
+    float wf[kMaxGenRadius + 1];
+};
+
+template <int R>
+struct GenTaps {
+    size_t zb[2 * R + 1], yb[2 * R + 1];
+    __device__ __forceinline__ GenTaps(int y, int z, int nx, int ny, int nz) {
+#pragma unroll
+        for (int d = -R; d <= R; ++d) {
+            zb[d + R] = (size_t)wrap_idx(z + d, nz) * ny * nx;
+            yb[d + R] = (size_t)wrap_idx(y + d, ny) * nx;
+        }
+    }
+    __device__ __forceinline__ size_t at(int x, int nx, int dx, int dy, int dz) const {
+        return zb[dz + R] + yb[dy + R] + wrap_idx(x + dx, nx);
+    }
+};
+
+template <typename C> __device__ __forceinline__ C gw(const GenW &W, int j);
+template <> __device__ __forceinline__ double gw<double>(const GenW &W, int j) { return W.w[j]; }
+template <> __device__ __forceinline__ float gw<float>(const GenW &W, int j) { return W.wf[j]; }
+
+// S of the generated cross stencil from an accessor P(dx, dy, dz)
+template <int R, int DIMS, typename C, typename Acc>
+__device__ __forceinline__ C gen_sum(const Acc &P, const GenW &W) {
+    C acc = C(0);
+#pragma unroll
+    for (int j = R; j >= 1; --j) {
+        C pj = (P(j, 0, 0) + P(-j, 0, 0)) + (P(0, j, 0) + P(0, -j, 0));
+        if constexpr (DIMS == 3) pj = pj + (P(0, 0, j) + P(0, 0, -j));
+        acc = (j == R) ? gw<C>(W, j) * pj : FMA(gw<C>(W, j), pj, acc);
+    }
+    return FMA(gw<C>(W, 0), P(0, 0, 0), acc);
+}
+
+struct GenArgs {
+    StepArgs a;
+    GenW W;
+    void *mu;
+};
+
+__device__ __forceinline__ void gen_seg(long long u, int segs, const StepArgs &a, int &x, int &y, int &z,
+                                        size_t &row) {
+    const long long r = u / segs;
+    x = (int)(u - r * segs) * 256 + (int)threadIdx.x;
+    y = (int)(r % a.ny);
+    z = (int)(r / a.ny);
+    row = (size_t)r * a.nx;
+}
+
+// Cahn-Hilliard pass 1: mu of every point
+template <int R, int DIMS, typename T>
+__global__ void __launch_bounds__(256) gen_mu_kernel(GenArgs g, int segs) {
+    typedef typename Cmp<T>::type C;
+    const StepArgs &a = g.a;
+    const ConstsC<C> k(a.k, a.kf);
+    const T *p = static_cast<const T *>(a.in0);
+    C *mu = static_cast<C *>(g.mu);
+    const long long units = (long long)a.ny * a.nz * segs;
+    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+        int x, y, z;
+        size_t row;
+        gen_seg(u, segs, a, x, y, z, row);
+        const GenTaps<R> tp(y, z, a.nx, a.ny, a.nz);
+        if (x >= a.nx) continue;
+        auto P = [&](int dx, int dy, int dz) -> C { return to_c(p[tp.at(x, a.nx, dx, dy, dz)]); };
+        mu[row + x] = ch_mu<C>(to_c(p[row + x]), gen_sum<R, DIMS, C>(P, g.W), k);
+    }
+}
+
+// one step of the model (Cahn-Hilliard: pass 2, from mu)
+template <int MODEL, int R, int DIMS, typename T>
+__global__ void __launch_bounds__(256) gen_step_kernel(GenArgs g, int segs) {
+    typedef typename Cmp<T>::type C;
+    const StepArgs &a = g.a;
+    const ConstsC<C> k(a.k, a.kf);
+    const T *i0 = static_cast<const T *>(a.in0), *i1 = static_cast<const T *>(a.in1);
+    T *o0 = static_cast<T *>(a.out0), *o1 = static_cast<T *>(a.out1);
+    const long long units = (long long)a.ny * a.nz * segs;
+    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+        int x, y, z;
+        size_t row;
+        gen_seg(u, segs, a, x, y, z, row);
+        const GenTaps<R> tp(y, z, a.nx, a.ny, a.nz);
+        if (x >= a.nx) continue;
+        const size_t i = row + x;
+        auto P0 = [&](int dx, int dy, int dz) -> C { return to_c(i0[tp.at(x, a.nx, dx, dy, dz)]); };
+        if constexpr (MODEL == CH) {
+            const C *mu = static_cast<const C *>(g.mu);
+            auto Pm = [&](int dx, int dy, int dz) -> C { return mu[tp.at(x, a.nx, dx, dy, dz)]; };
+            o0[i] = from_c<T>(ch_update<C>(to_c(i0[i]), gen_sum<R, DIMS, C>(Pm, g.W), k));
+        } else if constexpr (MODEL == AC) {
+            o0[i] = from_c<T>(ac_update<C>(to_c(i0[i]), gen_sum<R, DIMS, C>(P0, g.W), k));
+        } else {
+            auto P1 = [&](int dx, int dy, int dz) -> C { return to_c(i1[tp.at(x, a.nx, dx, dy, dz)]); };
+            C S1;
+            if constexpr (MODEL == MC) {
+                auto Pm = [&](int dx, int dy, int dz) -> C { return mc_mu<C>(P0(dx, dy, dz), P1(dx, dy, dz), k); };
+                S1 = gen_sum<R, DIMS, C>(Pm, g.W);
+            } else {
+                S1 = gen_sum<R, DIMS, C>(P1, g.W);
+            }
+            C a0, a1;
+            two_field_update<MODEL, C>(to_c(i0[i]), to_c(i1[i]), gen_sum<R, DIMS, C>(P0, g.W), S1, k, a0, a1);
+            o0[i] = from_c<T>(a0);
+            o1[i] = from_c<T>(a1);
+        }
+    }
+}
+
+template <int MODEL, int R, int DIMS, typename T>
+static cudaError_t launch_gen_t(const GenArgs &g, cudaStream_t s, int n_sm) {
+    const int segs = (g.a.nx + 255) / 256;
+    const long long units = (long long)g.a.ny * g.a.nz * segs;
+    const unsigned blocks = (unsigned)std::min<long long>(units, (long long)n_sm * 8);
+    if constexpr (MODEL == CH) gen_mu_kernel<R, DIMS, T><<<blocks, 256, 0, s>>>(g, segs);
+    gen_step_kernel<MODEL, R, DIMS, T><<<blocks, 256, 0, s>>>(g, segs);
+    return cudaGetLastError();
+}
+
+template <int MODEL, typename T>
+static cudaError_t launch_gen_r(int r, int dims, const GenArgs &g, cudaStream_t s, int n_sm) {
+#define SP_GEN(RR)                                                                            \
+    case RR:                                                                                  \
+        return dims == 2 ? launch_gen_t<MODEL, RR, 2, T>(g, s, n_sm) : launch_gen_t<MODEL, RR, 3, T>(g, s, n_sm);
+    switch (r) {
+        SP_GEN(1) SP_GEN(2) SP_GEN(3) SP_GEN(4)
+    }
+#undef SP_GEN
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+static cudaError_t launch_gen_m(int model, int r, int dims, const GenArgs &g, cudaStream_t s, int n_sm) {
+    switch (model) {
+    case AC: return launch_gen_r<AC, T>(r, dims, g, s, n_sm);
+    case CH: return launch_gen_r<CH, T>(r, dims, g, s, n_sm);
+    case GS: return launch_gen_r<GS, T>(r, dims, g, s, n_sm);
+    case MC: return launch_gen_r<MC, T>(r, dims, g, s, n_sm);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_generated(int model, int dtype, int order, int dims, const double *wk, const StepArgs &a, void *mu,
+                             cudaStream_t s, int n_sm) {
+    GenArgs g;
+    g.a = a;
+    g.mu = mu;
+    const int r = order / 2;
+    for (int j = 0; j <= kMaxGenRadius; ++j) {
+        g.W.w[j] = j <= r ? wk[j] : 0.0;
+        g.W.wf[j] = (float)g.W.w[j];
+    }
+    switch (dtype) {
+    case SP_F64: return launch_gen_m<double>(model, r, dims, g, s, n_sm);
+    case SP_F32: return launch_gen_m<float>(model, r, dims, g, s, n_sm);
+    default: return launch_gen_m<bf16>(model, r, dims, g, s, n_sm);
+    }
+}
+
+}  // namespace sp
+
+extern "C" int sp_stencil_weights(int order, int dims, double *w, double *lambda_max) {
+    if (!w) return SP_EINVAL;
+    return sp::generated_weights(order, dims, w, lambda_max);
+}

@@ -54,6 +54,12 @@ inline int steps_per_launch(int dims, int dtype, int model, int requested) {
     return 1;
 }
 
+// Generated cross stencils (sp_generated.cu), radius up to kMaxGenRadius.
+constexpr int kMaxGenRadius = 4;
+int generated_weights(int order, int dims, double *wk, double *lambda_max);
+cudaError_t launch_generated(int model, int dtype, int order, int dims, const double *wk, const StepArgs &a, void *mu,
+                             cudaStream_t s, int n_sm);
+
 // Model H (sp_model_h.cu): one step from in[0..nf) to out[0..nf) (m, then the
 // components of j; unused entries null) through the mu buffer of N compute-
 // precision values; c3g = c3 times the central-difference scale.

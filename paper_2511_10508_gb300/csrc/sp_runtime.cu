@@ -46,10 +46,10 @@ extern "C" int sp_version(void) { return 100; }
 
 // ---------------------------------------------------- stencil metadata --
 
-static int stencil_dims(int st) { return st >= SP_LAP_7 ? 3 : 2; }
+static int stencil_dims(int st) { return st >= SP_LAP_7 ? 3 : 2; }  // fixed stencils
 static int stencil_radius(int st) { return (st == SP_LAP_9CROSS4 || st == SP_LAP_13CROSS4) ? 2 : 1; }
 static int stencil_q(int st) {
-    static const int q[6] = {1, 6, 12, 1, 30, 12};
+    static const int q[7] = {1, 6, 12, 1, 30, 12, 1};
     return q[st];
 }
 // max over theta of the symbol lambda(theta) (eigenvalue of -h^2 L_h)
@@ -75,6 +75,7 @@ extern "C" void sp_params_default(int model, int dims, sp_params *p) {
     p->k = 0.065;
     p->c3 = 0.5;
     p->stencil = dims == 3 ? SP_LAP_7 : SP_LAP_5;
+    p->stencil_order = 2;
     p->dtype = SP_F64;
     p->seed = 0;
     p->ic_kind = SP_IC_NOISE;
@@ -94,8 +95,15 @@ static bool is_finite(double x) { return std::isfinite(x); }
 //   Cahn-Hilliard: sigma = -lam (kappa lam + a), a in {3 c2 - c1, -c1}
 //   Gray-Scott:    about (u, v) = (1, 0): sigma_u = -Du lam - F, sigma_v = -Dv lam - (F + k)
 // with lam in [0, lambda_max / h^2].  Forward Euler is stable when dt*max|sigma| <= 2.
-static double max_growth(int model, int st, double h, const sp_params &p) {
-    const double lam = stencil_lambda_max(st) / (h * h);
+static double max_growth(int model, int st, double h, const sp_params &p, int dims) {
+    double lm = 0;
+    if (st == SP_LAP_GENERATED) {
+        double wk[kMaxGenRadius + 1];
+        generated_weights(p.stencil_order, dims, wk, &lm);
+    } else {
+        lm = stencil_lambda_max(st);
+    }
+    const double lam = lm / (h * h);
     double m = 0.0;
     if (model == SP_ALLEN_CAHN) {
         const double as[2] = {p.c1 - 3.0 * p.c2, p.c1};
@@ -135,8 +143,16 @@ static int validate_params(int model, int dims, double h, double dt, const sp_pa
     if (model < SP_ALLEN_CAHN || model > SP_MODEL_H) return fail(SP_EINVAL, "unknown model %d", model);
     if (dims != 2 && dims != 3) return fail(SP_EINVAL, "dims must be 2 or 3 (got %d)", dims);
     const int st = resolve_stencil(p.stencil, dims);
-    if (st < SP_LAP_5 || st > SP_LAP_13CROSS4) return fail(SP_EINVAL, "unknown stencil %d", p.stencil);
-    if (stencil_dims(st) != dims) return fail(SP_EINVAL, "stencil %d is %dD but the grid is %dD", st, stencil_dims(st), dims);
+    if (st < SP_LAP_5 || st > SP_LAP_GENERATED) return fail(SP_EINVAL, "unknown stencil %d", p.stencil);
+    if (st == SP_LAP_GENERATED) {
+        double wk[kMaxGenRadius + 1];
+        if (generated_weights(p.stencil_order, dims, wk, nullptr) != SP_OK)
+            return fail(SP_EINVAL, "stencil_order must be even and in [2, %d] (got %d)", 2 * kMaxGenRadius,
+                        p.stencil_order);
+        if (model == SP_MODEL_H) return fail(SP_EINVAL, "Model H uses the fixed stencils");
+    } else if (stencil_dims(st) != dims) {
+        return fail(SP_EINVAL, "stencil %d is %dD but the grid is %dD", st, stencil_dims(st), dims);
+    }
     if (!(is_finite(h) && h > 0)) return fail(SP_EINVAL, "h must be finite and > 0");
     if (!(is_finite(dt) && dt > 0)) return fail(SP_EINVAL, "dt must be finite and > 0");
     const double vals[8] = {p.c1, p.c2, p.kappa, p.Du, p.Dv, p.F, p.k, p.c3};
@@ -173,7 +189,7 @@ extern "C" int sp_check_stability(int model, int dims, double h, double dt, cons
         if (!(f < 1.0)) return fail(SP_EUNSTABLE, "dt max L(k) = %.6g >= 1: the semi-implicit step is undefined", f);
         return SP_OK;
     }
-    const double f = dt * max_growth(model, st, h, *p);
+    const double f = dt * max_growth(model, st, h, *p, dims);
     if (factor) *factor = f;
     if (!(f <= 2.0)) return fail(SP_EUNSTABLE, "dt*max|sigma| = %.6g > 2: forward Euler is unstable", f);
     return SP_OK;
@@ -204,6 +220,7 @@ struct sp_sim {
     int variant;               // kernel family (see g_step_variant)
     void *mu_tmp;              // unfused ablation: mu temporary (allocated on first use)
     bool tune_pending;         // autotune on the next long sp_step
+    double genw[kMaxGenRadius + 1];  // generated stencil: kernel weights (d w_0, w_1, ..., w_r)
     SpectralPlan *spec;        // semi-implicit spectral scheme (else null)
     bool spec_dirty;           // the resident spectrum must be recomputed from phi
 };
@@ -291,7 +308,8 @@ extern "C" int sp_create(int model, int dims, const int64_t shape[3], double h, 
     s->p.stencil = st;
     s->esize = dtype_size(prm.dtype);
     s->k = make_consts(*s);
-    s->spl = steps_per_launch(dims, prm.dtype, model, prm.steps_per_launch);
+    s->spl = st == SP_LAP_GENERATED ? 1 : steps_per_launch(dims, prm.dtype, model, prm.steps_per_launch);
+    if (st == SP_LAP_GENERATED) generated_weights(prm.stencil_order, dims, s->genw, nullptr);
     s->variant = 0;
     s->tune_pending = (prm.flags & SP_FLAG_AUTOTUNE) != 0 && prm.steps_per_launch == 0;
 
@@ -320,7 +338,7 @@ extern "C" int sp_create(int model, int dims, const int64_t shape[3], double h, 
         release(s);
         return fail(SP_ENOMEM, "scratch allocation failed: %s", cudaGetErrorString(e));
     }
-    if (model == SP_MODEL_H) {
+    if (model == SP_MODEL_H || (st == SP_LAP_GENERATED && model == SP_CAHN_HILLIARD)) {
         e = cudaMalloc(&s->mu_tmp, s->N * (s->dtype == SP_F64 ? sizeof(double) : sizeof(float)));
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -376,6 +394,8 @@ static cudaError_t launch_one_step_impl(sp_sim *s, cudaStream_t st, int k) {
     a.nz = s->nz;
     a.k = s->k;
     a.kf = to_float(s->k);
+    if (s->stencil == SP_LAP_GENERATED)
+        return launch_generated(s->model, s->dtype, s->p.stencil_order, s->dims, s->genw, a, s->mu_tmp, st, s->n_sm);
     if (s->variant == kUnfusedFamily) return launch_unfused_ch(s->dtype, s->stencil, a, s->mu_tmp, st, s->n_sm);
     if (s->model == SP_MODEL_H) {
         void *in[4] = {nullptr, nullptr, nullptr, nullptr}, *out[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -433,7 +453,7 @@ static TuneKey tune_key(const sp_sim *s) {
 
 static std::vector<TuneChoice> tune_candidates(const sp_sim *s) {
     std::vector<TuneChoice> c;
-    if (s->spec || s->model == SP_MODEL_H) return {{1, 0}};
+    if (s->spec || s->model == SP_MODEL_H || s->stencil == SP_LAP_GENERATED) return {{1, 0}};
     if (s->dims == 2 && s->dtype != SP_F64) {
         c.push_back({1, 1});
         for (int spl : {1, 2, 4}) c.push_back({spl, 0});
@@ -707,7 +727,8 @@ extern "C" int sp_set_launch_config(sp_sim *s, int steps_per_launch, int variant
         set_launch_config(s, {1, 0});
         return SP_OK;
     }
-    if (steps_per_launch == 1 && variant == kUnfusedFamily && s->model == SP_CAHN_HILLIARD && !s->spec) {
+    if (steps_per_launch == 1 && variant == kUnfusedFamily && s->model == SP_CAHN_HILLIARD && !s->spec &&
+        s->stencil != SP_LAP_GENERATED) {
         if (!s->mu_tmp) {
             const size_t bytes = s->N * (s->dtype == SP_F64 ? sizeof(double) : sizeof(float));
             const cudaError_t e = cudaMalloc(&s->mu_tmp, bytes);

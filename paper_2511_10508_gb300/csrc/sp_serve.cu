@@ -511,6 +511,7 @@ extern "C" int sp_submit(sp_server *S, const sp_request *r, uint64_t *ticket) {
     if (p.dtype != SP_F64 && p.dtype != SP_F32) return SP_EINVAL;  // the serving kernels cover FP64 and FP32
     if (p.scheme != SP_SCHEME_FD) return SP_EINVAL;                 // and the finite-difference scheme
     if (r->model == SP_MODEL_H) return SP_EINVAL;                   // of the one- and two-field models
+    if (st == SP_LAP_GENERATED) return SP_EINVAL;                  // with the fixed stencils
     double factor = 0;
     if (int rc = sp_check_stability(r->model, dims, r->h, r->dt, &p, &factor)) return rc;
     const int64_t nx = r->shape[0], ny = r->shape[1], nz = dims == 2 ? 1 : r->shape[2];

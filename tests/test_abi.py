@@ -162,3 +162,35 @@ def test_spectral_scheme_stability_bound(sp):
     assert not ok
     ok, _ = sp.check_stability(sp.CAHN_HILLIARD, 2, 1.0, 0.5, sp.params(sp.CAHN_HILLIARD, 2))
     assert not ok  # forward Euler with the 5-point stencil is unstable at this dt
+
+
+@pytest.mark.parametrize("order", [2, 4, 6, 8])
+@pytest.mark.parametrize("dims", [2, 3])
+def test_generated_stencil_weights_equal_the_oracles(sp, order, dims):
+    """The library solves the interpolation system in its own exact rational
+    arithmetic; the weights it rounds to FP64 equal the oracle's bit for bit, so
+    FP64 steps with generated stencils can be compared bit for bit."""
+    from oracle import stencil_gen as G
+
+    w, lm = sp.stencil_weights(order, dims)
+    assert w == G.kernel_weights(order, dims)
+    assert lm == G.lambda_max(order, dims)
+
+
+def test_generated_stencil_rejections(sp):
+    from paper_2511_10508_gb300 import _native as N
+
+    w = (ctypes.c_double * 5)()
+    for order, dims in [(3, 2), (0, 2), (10, 3), (4, 4)]:
+        assert N.lib().sp_stencil_weights(order, dims, w, None) == N.SP_EINVAL
+    for order in (1, 5, 12):
+        p = sp.params(sp.CAHN_HILLIARD, 2, stencil=sp.LAP_GENERATED, stencil_order=order)
+        ok = N.lib().sp_check_stability(sp.CAHN_HILLIARD, 2, 1.0, 1e-4, ctypes.byref(p), None)
+        assert ok == N.SP_EINVAL
+    p = sp.params(sp.MODEL_H, 2, stencil=sp.LAP_GENERATED, stencil_order=4)
+    assert N.lib().sp_check_stability(sp.MODEL_H, 2, 1.0, 1e-4, ctypes.byref(p), None) == N.SP_EINVAL
+    # stability uses the generated stencil's lambda_max: order 8 in 3D
+    _, lm = sp.stencil_weights(8, 3)
+    p = sp.params(sp.ALLEN_CAHN, 3, stencil=sp.LAP_GENERATED, stencil_order=8)
+    ok, f = sp.check_stability(sp.ALLEN_CAHN, 3, 1.0, 0.01, p)
+    assert ok and abs(f - 0.01 * max(1.0, abs(1.0 - lm), 2.0, abs(-2.0 - lm))) < 1e-12
