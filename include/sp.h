@@ -246,7 +246,7 @@ int sp_autotune(sp_sim *sim, void *stream, int64_t *steps_taken);
 
 /* Pin a launch configuration (for instance one that sp_autotune chose in an
  * earlier run): steps fused per launch (1, or 2 / 4 for 2D FP32/BF16) and kernel
- * family (0, or 1 / 2 where sp_launch_config documents an alternative).  Family 3
+ * family (0, or 1 / 2 / 4 where sp_launch_config documents an alternative).  Family 3
  * (Cahn-Hilliard only, one step per launch) is an ablation with no use in
  * production: the unfused two-pass step of the paper's solver, which writes mu to
  * a temporary field in device memory (allocated here, N values of the compute
@@ -268,7 +268,10 @@ int sp_set_launch_config(sp_sim *sim, int steps_per_launch, int variant);
 int sp_stencil_weights(int order, int dims, double *w, double *lambda_max);
 
 /* Launch configuration in use: steps fused per launch and kernel family
- * (0 = the default for the grid, 1 = the alternative the autotuner may pick). */
+ * (0 = the default for the grid; alternatives the autotuner may pick: 1 for
+ * every grid of the finite-difference scheme except 3D FP64 with the 7/13/
+ * 19-point stencils; 2 for 3D FP32/BF16; 2 and 4 for 2D FP64, the strip kernel
+ * with 64 threads per CTA and with half the rows per batch). */
 int sp_launch_config(const sp_sim *sim, int *steps_per_launch, int *variant);
 
 /* Number of time steps taken since creation. */

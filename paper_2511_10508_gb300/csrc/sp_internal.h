@@ -39,7 +39,8 @@ cudaError_t launch_step_bf16(int model, int stencil, const StepArgs &a, cudaStre
 // storage are limited by on-chip work, so extra halo work only slows them.
 // Kernel variant chosen per launch: 0 = the default for the grid, 1 (and 2) =
 // alternative families (2D FP64: small tiles instead of strips, or strips instead
-// of small tiles for grids up to 1024^2; 2D FP32/BF16 single steps: shared-
+// of small tiles for grids up to 1024^2, and 2 / 4 = strips of 64 threads / of
+// half the rows per batch; 2D FP32/BF16 single steps: shared-
 // memory tiles instead of warp strips; 3D FP32/BF16: 1 = cp.async plane ring,
 // 2 = register-staged plane rings, instead of warp rows; 3D FP64 27-point:
 // shared-memory plane rings instead of z-streaming).  Set around each launch by

@@ -461,6 +461,10 @@ static std::vector<TuneChoice> tune_candidates(const sp_sim *s) {
         c.push_back({1, 0});
         c.push_back({1, 1});
         if (s->dims == 3 && s->dtype != SP_F64) c.push_back({1, 2});
+        if (s->dims == 2 && s->dtype == SP_F64) {  // two more strip shapes
+            c.push_back({1, 2});
+            c.push_back({1, 4});
+        }
     } else {
         c.push_back({1, 0});
     }

@@ -58,6 +58,29 @@ inline int lockstep_segments(long long tiles, int nz, int halo, long long wave) 
 // Batched persistent 2D kernel (FP64): rows per batch and CTAs per SM.
 template <int MODEL> struct Batch2d { static constexpr int NT = 128, RB = (MODEL == CH) ? 8 : (MODEL == AC ? 4 : 2), CPS = 4; };
 
+// The FP64 2D strip kernel with NT threads, RB rows per batch, at most CPS CTAs
+// per SM; persistent grid with equal rows per CTA.
+template <int MODEL, int ST, typename T, int NT, int RB, int CPS>
+cudaError_t launch_strips(const StepArgs &a, cudaStream_t s, int n_sm) {
+    typedef Step2dBatchShape<MODEL, ST, T, NT, RB> Sh;
+    auto kern = step2d_batch_kernel<MODEL, ST, T, NT, RB>;
+    static const int occ = [&] {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem_bytes);
+        int o = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT, Sh::smem_bytes);
+        return o;
+    }();
+    const int strips = (a.nx + Sh::TW - 1) / Sh::TW;
+    const long long total = (long long)strips * a.ny;
+    // equal rows per CTA; at least 4*RB rows each so that the ring warm-up stays small
+    long long ctas = (long long)n_sm * std::max(1, std::min(occ, CPS));
+    ctas = std::max(1LL, std::min(ctas, total / (4 * RB)));
+    const long long rows = (total + ctas - 1) / ctas;
+    ctas = (total + rows - 1) / rows;
+    kern<<<(unsigned)ctas, NT, Sh::smem_bytes, s>>>(a, strips, rows);
+    return cudaGetLastError();
+}
+
 // Temporally blocked 2D tile kernel (FP32 / BF16): K steps per launch.
 template <int MODEL, int ST, typename T, int K>
 cudaError_t launch_tb(const StepArgs &a, cudaStream_t s) {
@@ -101,7 +124,8 @@ cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
     }
     if constexpr (StencilInfo<ST>::dims == 2 && std::is_same<T, double>::value) {
         const bool small = (long long)a.nx * a.ny <= kSmallGrid2d;
-        if (small != (g_step_variant == 1)) {
+        const bool strip_shape = g_step_variant == 2 || g_step_variant == 4;
+        if (!strip_shape && small != (g_step_variant == 1)) {
             // small grids are latency bound: many small tiles instead of a few long strips
             constexpr int BX = 32, BY = 16, NT = 128;
             typedef Step2dTileShape<MODEL, ST, T, BX, BY> Sh;
@@ -114,23 +138,13 @@ cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
             kern<<<dim3((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY), NT, Sh::smem_bytes, s>>>(a);
             return cudaGetLastError();
         }
+        // strip families: 0 the default shape, 2 narrower CTAs (64 threads), 4 half
+        // the rows per batch; the autotuner picks per grid
         typedef Batch2d<MODEL> B;
-        typedef Step2dBatchShape<MODEL, ST, T, B::NT, B::RB> Sh;
-        auto kern = step2d_batch_kernel<MODEL, ST, T, B::NT, B::RB>;
-        static const int occ = [&] {
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem_bytes);
-            int o = 1;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, B::NT, Sh::smem_bytes);
-            return o;
-        }();
-        const int strips = (a.nx + Sh::TW - 1) / Sh::TW;
-        const long long total = (long long)strips * a.ny;
-        // equal rows per CTA; at least 4*RB rows each so that the ring warm-up stays small
-        long long ctas = (long long)n_sm * std::max(1, std::min(occ, B::CPS));
-        ctas = std::max(1LL, std::min(ctas, total / (4 * B::RB)));
-        const long long rows = (total + ctas - 1) / ctas;
-        ctas = (total + rows - 1) / rows;
-        kern<<<(unsigned)ctas, B::NT, Sh::smem_bytes, s>>>(a, strips, rows);
+        if (g_step_variant == 2) return launch_strips<MODEL, ST, T, 64, B::RB, 2 * B::CPS>(a, s, n_sm);
+        if (g_step_variant == 4)
+            return launch_strips<MODEL, ST, T, B::NT, (B::RB > 1 ? B::RB / 2 : 1), 2 * B::CPS>(a, s, n_sm);
+        return launch_strips<MODEL, ST, T, B::NT, B::RB, B::CPS>(a, s, n_sm);
     } else if constexpr (StencilInfo<ST>::dims == 2) {
         typedef Step2dWarpShape<MODEL, ST, T> WS;
         const bool aligned = ((uintptr_t)a.in0 | (uintptr_t)a.in1 | (uintptr_t)a.out0 | (uintptr_t)a.out1) % 16 == 0;

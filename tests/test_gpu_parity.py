@@ -385,6 +385,31 @@ def test_2d_kernel_families_agree(sp, dtype, model, st, shape):
         assert O.rel_l2(outs[0][0].astype(np.float64), ref) < TOL[1]
 
 
+@pytest.mark.parametrize("shape", [(70, 300), (45, 64), (9, 8), (130, 520)])
+@pytest.mark.parametrize("model,st", CASES_2D)
+def test_2d_fp64_families_equal_oracle(sp, model, st, shape):
+    """2D FP64: the strip kernel in its three shapes (family 0: 128 threads;
+    2: 64 threads; 4: half the rows per batch) and the small-tile kernel
+    (family 1) each equal the oracle bit for bit.  Shapes: strips of 128 and 256
+    columns with a ragged one, a grid narrower than one strip, a grid smaller
+    than the stencil's ring, and rows split over many CTAs."""
+    ref = None
+    for variant in (0, 1, 2, 4):
+        sim, dt = make(sp, model, shape, st)
+        with sim:
+            sim.launch_config = (1, variant)
+            assert sim.launch_config == (1, variant)
+            sim.step(11)
+            got = sim.read(0)
+        if ref is None:
+            ic = oracle_ic(model, shape, sim.prm)
+            if model in TWO:
+                ref = O.step(model, st, ic[0], ic[1], dt=dt, prm=oparams(sim.prm), nsteps=11)[0]
+            else:
+                ref = O.step(model, st, ic, dt=dt, prm=oparams(sim.prm), nsteps=11)
+        assert np.array_equal(got, ref), f"family {variant}"
+
+
 def test_set_launch_config_rejects_unavailable(sp):
     sim, _ = make(sp, 1, (64, 64), 0, dtype=0)
     with sim:
@@ -392,8 +417,15 @@ def test_set_launch_config_rejects_unavailable(sp):
             sim.launch_config = (2, 0)  # FP64 has no temporal blocking
         with pytest.raises(sp.SpError):
             sim.launch_config = (1, 7)
-        sim.launch_config = (1, 1)
-        assert sim.launch_config == (1, 1)
+        with pytest.raises(sp.SpError):
+            sim.launch_config = (1, 5)
+        for fam in (1, 2, 4):
+            sim.launch_config = (1, fam)
+            assert sim.launch_config == (1, fam)
+    sim, _ = make(sp, 1, (64, 64), 0, dtype=1)
+    with sim:
+        with pytest.raises(sp.SpError):
+            sim.launch_config = (1, 4)  # strip shapes are FP64 only
     sim, _ = make(sp, 1, (20, 24, 28), 3, dtype=0)
     with sim:
         with pytest.raises(sp.SpError):
