@@ -97,10 +97,11 @@ STENCIL_OPS = {0: 4, 1: 6, 2: 8, 3: 6, 4: 12, 5: 12}
 
 
 # DRAM bytes (read + write) per step launch of the dominant kernel, from an ncu
-# capture of the same kernel and workload (summaries in profiles/); workloads
-# without a capture of the current kernel report null.
+# capture of the same kernel and workload (summaries in profiles/), keyed by
+# (workload, steps per launch, kernel family); other pairs report null.
 NCU_TRAFFIC = {
-    "ch2d-4096-f64-lap5": (242.47e6, "profiles/step2d_batch_ch_f64_lap5_4096.txt"),
+    ("ch2d-4096-f64-lap5", 1, 0): (242.47e6, "profiles/step2d_batch_ch_f64_lap5_4096.txt"),
+    ("ch2d-4096-f64-lap5", 1, 4): (231.14e6, "profiles/step2d_batch_ch_f64_lap5_4096.txt"),
 }
 
 
@@ -542,7 +543,7 @@ def main():
     launch_ms = step_ms / (args.steps * sub)  # average duration of one step-kernel launch
 
     peaks = load_peaks()
-    traffic = NCU_TRAFFIC[args.workload][0] if (args.workload in NCU_TRAFFIC and spl == 1 and variant == 0) else None
+    traffic = NCU_TRAFFIC.get((args.workload, spl, variant), (None,))[0]
     if spectral and dtype == 0:
         ops = spectral_ops_per_lup(npts)
         achieved = ops * npts / (launch_ms * 1e-3) / 1e9
