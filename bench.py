@@ -563,7 +563,7 @@ def main():
         ops = fp64_ops_per_lup(model, st, order, dims)
         achieved = ops * npts / (launch_ms * 1e-3) / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "FP64 Gop/s",
-                "frac": achieved / FP64_PEAK_GOPS, "traffic": traffic,
+                "frac": achieved / FP64_PEAK_GOPS, "traffic": traffic, "steps_per_launch": spl,
                 "note": f"{ops} FP64 ops/LUP (fixed evaluation order); peak = 152 SMs x 2 FP64 ops/clk x 2.07 GHz; "
                         f"HBM side {hbm_bytes_per_lup(model, dtype, dims) * npts / (launch_ms * 1e-3) / 1e9:.0f} GB/s"}
     else:

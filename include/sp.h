@@ -139,8 +139,8 @@ typedef struct sp_params {
     double ic_mean, ic_amp;/* noise mean and half-width */
     int gs_patches;        /* Gray-Scott: number of seeded patches */
     int gs_patch;          /* Gray-Scott: patch side (points) */
-    int steps_per_launch;  /* time steps fused per kernel launch (temporal blocking);
-                              0 = the library's choice, 1 = none */
+    int steps_per_launch;  /* time steps fused per kernel launch (temporal blocking,
+                              2D grids: 2 or 4); 0 = the library's choice, 1 = none */
     int scheme;            /* sp_scheme (default SP_SCHEME_FD) */
     int stencil_order;     /* accuracy order of SP_LAP_GENERATED (even, 2..8; default 2) */
     int flags;             /* SP_FLAG_* bits; other bits must be 0 */
@@ -148,8 +148,9 @@ typedef struct sp_params {
 
 /* sp_params.flags: with steps_per_launch = 0, SP_FLAG_AUTOTUNE makes the first
  * sp_step call that asks for at least 66 steps autotune as sp_autotune does
- * (steps per launch and kernel family for 2D FP32/BF16; strip or small-tile
- * kernels for 2D FP64; two kernel families for the 3D FP64 27-point stencil),
+ * (steps per launch and kernel family for 2D FP32/BF16; for 2D FP64 the strip
+ * shapes or small tiles, and on grids up to 1024^2 steps fused per launch; the
+ * kernel families of 3D FP32/BF16 and of the 3D FP64 27-point stencil),
  * counting the timed steps among the steps asked for. */
 #define SP_FLAG_AUTOTUNE 1
 
@@ -245,7 +246,7 @@ int sp_field_devptr(sp_sim *sim, int field, void **dptr);
 int sp_autotune(sp_sim *sim, void *stream, int64_t *steps_taken);
 
 /* Pin a launch configuration (for instance one that sp_autotune chose in an
- * earlier run): steps fused per launch (1, or 2 / 4 for 2D FP32/BF16) and kernel
+ * earlier run): steps fused per launch (1, or 2 / 4 for 2D grids) and kernel
  * family (0, or 1 / 2 / 4 where sp_launch_config documents an alternative).  Family 3
  * (Cahn-Hilliard only, one step per launch) is an ablation with no use in
  * production: the unfused two-pass step of the paper's solver, which writes mu to

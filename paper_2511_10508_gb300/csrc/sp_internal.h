@@ -31,12 +31,14 @@ cudaError_t launch_step_f32(int model, int stencil, const StepArgs &a, cudaStrea
 cudaError_t launch_step_bf16(int model, int stencil, const StepArgs &a, cudaStream_t s, int n_sm, int k);
 
 // Steps fused per launch (temporal blocking) for a request of `requested`
-// (0 = the library's choice, 1 = none): 2D FP32 / BF16 grids support 2 and 4;
-// FP64 (bound by the FP64 pipe) and 3D run one step per launch.  The library's
-// choice follows measurement on GB300: blocking pays where the one-step tile
-// kernel is at the HBM bound (FP32 Gray-Scott 32768^2: 1 step 0.99 of the copy
-// bandwidth, 2 steps 1.31 effective, 4 steps 1.19); Cahn-Hilliard and BF16
-// storage are limited by on-chip work, so extra halo work only slows them.
+// (0 = the library's choice, 1 = none): 2D grids support 2 and 4 (FP64 on small
+// tiles, where a launch is short enough for its fixed cost to matter); 3D runs
+// one step per launch.  The library's choice follows measurement on GB300:
+// blocking pays where the one-step tile kernel is at the HBM bound (FP32
+// Gray-Scott 32768^2: 1 step 0.99 of the copy bandwidth, 2 steps 1.31
+// effective, 4 steps 1.19); Cahn-Hilliard and BF16 storage are limited by
+// on-chip work and FP64 by the FP64 pipe, so there extra halo work only slows
+// large grids (the autotuner tries it on small FP64 grids).
 // Kernel variant chosen per launch: 0 = the default for the grid, 1 (and 2) =
 // alternative families (2D FP64: small tiles instead of strips, or strips instead
 // of small tiles for grids up to 1024^2, and 2 / 4 = strips of 64 threads / of
@@ -47,8 +49,11 @@ cudaError_t launch_step_bf16(int model, int stencil, const StepArgs &a, cudaStre
 // the runtime.
 extern thread_local int g_step_variant;
 
+// FP64 2D grids up to 1024^2 use small tiles by default (and may fuse steps).
+constexpr long long kSmallGrid2d = 1LL << 20;
+
 inline int steps_per_launch(int dims, int dtype, int model, int requested) {
-    if (dims != 2 || dtype == SP_F64 || model == SP_MODEL_H) return 1;
+    if (dims != 2 || model == SP_MODEL_H) return 1;
     if (requested == 0) return (dtype == SP_F32 && model != CH) ? 2 : 1;
     if (requested >= 4) return 4;
     if (requested >= 2) return 2;

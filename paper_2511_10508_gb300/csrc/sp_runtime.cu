@@ -461,9 +461,14 @@ static std::vector<TuneChoice> tune_candidates(const sp_sim *s) {
         c.push_back({1, 0});
         c.push_back({1, 1});
         if (s->dims == 3 && s->dtype != SP_F64) c.push_back({1, 2});
-        if (s->dims == 2 && s->dtype == SP_F64) {  // two more strip shapes
-            c.push_back({1, 2});
-            c.push_back({1, 4});
+        if (s->dims == 2 && s->dtype == SP_F64) {
+            if (s->N <= (size_t)kSmallGrid2d) {  // small grids: steps fused per launch
+                c.push_back({2, 0});
+                c.push_back({4, 0});
+            } else {  // two more strip shapes
+                c.push_back({1, 2});
+                c.push_back({1, 4});
+            }
         }
     } else {
         c.push_back({1, 0});
@@ -726,6 +731,16 @@ extern "C" int sp_set_launch_config(sp_sim *s, int steps_per_launch, int variant
             set_launch_config(s, c);
             return SP_OK;
         }
+    // 2D FP64 finite differences: every strip shape and fused-step count runs on
+    // any grid (the autotuner tries only the likely winners of the size class)
+    const bool fd2d64 = s->dims == 2 && s->dtype == SP_F64 && !s->spec && s->model != SP_MODEL_H &&
+                        s->stencil != SP_LAP_GENERATED;
+    if (fd2d64 && ((steps_per_launch == 1 && (variant == 2 || variant == 4)) ||
+                   ((steps_per_launch == 2 || steps_per_launch == 4) && variant == 0))) {
+        s->tune_pending = false;
+        set_launch_config(s, {steps_per_launch, variant});
+        return SP_OK;
+    }
     if (steps_per_launch == 1 && variant == 0) {  // the default is always available
         s->tune_pending = false;
         set_launch_config(s, {1, 0});

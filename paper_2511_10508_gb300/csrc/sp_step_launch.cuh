@@ -28,7 +28,6 @@ template <> struct Tiles<bf16> {
 };
 
 constexpr int kMinRun = 32;
-constexpr long long kSmallGrid2d = 1LL << 20;  // FP64 2D grids up to 1024^2 use small tiles
 
 // Persistent grids: one resident wave of CTAs (SMs x occupancy), each owning an
 // equal share of the flattened (tile, slow-axis) work, but at least kMinRun
@@ -81,10 +80,13 @@ cudaError_t launch_strips(const StepArgs &a, cudaStream_t s, int n_sm) {
     return cudaGetLastError();
 }
 
-// Temporally blocked 2D tile kernel (FP32 / BF16): K steps per launch.
+// Temporally blocked 2D tile kernel: K steps per launch.  FP32 / BF16 tiles of
+// 128 x 16; FP64 (small grids, where the fixed cost of a launch matters) tiles
+// of 32 x 16, so that a 256^2 grid still spreads over 128 SMs.
 template <int MODEL, int ST, typename T, int K>
 cudaError_t launch_tb(const StepArgs &a, cudaStream_t s) {
-    constexpr int BX = 128, BY = 16, NT = 256;
+    constexpr bool f64 = std::is_same<T, double>::value;
+    constexpr int BX = f64 ? 32 : 128, BY = 16, NT = f64 ? 128 : 256;
     typedef Step2dTbShape<MODEL, ST, T, BX, BY, K> Sh;
     auto kern = step2d_tb_kernel<MODEL, ST, T, BX, BY, K, NT>;
     static const bool attr = [&] {
@@ -118,7 +120,7 @@ cudaError_t launch_zreg(const StepArgs &a, cudaStream_t s, int n_sm) {
 
 template <int MODEL, int ST, typename T>
 cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
-    if constexpr (StencilInfo<ST>::dims == 2 && !std::is_same<T, double>::value) {
+    if constexpr (StencilInfo<ST>::dims == 2) {
         if (k == 4) return launch_tb<MODEL, ST, T, 4>(a, s);
         if (k == 2) return launch_tb<MODEL, ST, T, 2>(a, s);
     }

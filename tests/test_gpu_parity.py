@@ -299,22 +299,56 @@ def test_graph_replay_equals_eager(sp, model, shape, dtype):
         assert a.steps_taken == b.steps_taken == 133
 
 
-@pytest.mark.parametrize("dtype", [1, 2])
+@pytest.mark.parametrize("dtype", [0, 1, 2])
 @pytest.mark.parametrize("model,st", [(m, s) for m in (0, 1, 2, 3) for s in (0, 1, 2)])
 def test_temporal_blocking_equals_single_steps(sp, dtype, model, st):
     """K steps fused in one launch (intermediate values rounded to the storage type
-    in shared memory) equal K single-step launches bit for bit."""
+    in shared memory) equal K single-step launches bit for bit; FP64 equals the
+    oracle bit for bit."""
     shape = (70, 301)
     outs = []
     for spl in (1, 2, 4):
         sim, dt = make(sp, model, shape, st, dtype=dtype, steps_per_launch=spl)
         with sim:
+            assert sim.launch_config[0] == spl
             sim.step(1)       # first step of a handle is a single-step launch
             sim.step(12)      # blocked launches (and single steps for the rest)
             outs.append([sim.read(f, as_f64=False) for f in range(2 if model in TWO else 1)])
     for o in outs[1:]:
         for a, b in zip(outs[0], o):
             assert np.array_equal(a, b)
+    if dtype == 0:
+        ic = oracle_ic(model, shape, sim.prm)
+        if model in TWO:
+            ref = O.step(model, st, ic[0], ic[1], dt=dt, prm=oparams(sim.prm), nsteps=13)
+        else:
+            ref = (O.step(model, st, ic, dt=dt, prm=oparams(sim.prm), nsteps=13),)
+        for a, b in zip(outs[-1], ref):
+            assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("shape", [(256, 256), (9, 8), (45, 70)])
+@pytest.mark.parametrize("model,st", [(0, 0), (1, 2), (2, 0), (3, 1)])
+def test_fp64_fused_steps_small_grids(sp, model, st, shape):
+    """2D FP64 with 2 and 4 steps per launch on small grids (the grid a few tiles
+    wide, one ragged tile, a grid smaller than the fused halo) equals the oracle
+    bit for bit, including graph replays (64 steps)."""
+    ref = None
+    for cfg in ((2, 0), (4, 0)):
+        sim, dt = make(sp, model, shape, st)
+        with sim:
+            sim.launch_config = cfg
+            sim.step(1)
+            sim.step(64)
+            got = [sim.read(f) for f in range(2 if model in TWO else 1)]
+        if ref is None:
+            ic = oracle_ic(model, shape, sim.prm)
+            if model in TWO:
+                ref = O.step(model, st, ic[0], ic[1], dt=dt, prm=oparams(sim.prm), nsteps=65)
+            else:
+                ref = (O.step(model, st, ic, dt=dt, prm=oparams(sim.prm), nsteps=65),)
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b), cfg
 
 
 @pytest.mark.parametrize("model,shape,dtype,st", [(2, (520, 777), 1, 0), (1, (300, 270), 0, 0),
@@ -341,10 +375,12 @@ def test_autotune_keeps_results(sp, model, shape, dtype, st):
         assert b.launch_config == c.launch_config  # the second tuning came from the cache
         if len(shape) == 3:
             assert spl == 1 and var in ((0, 1, 2) if dtype != 0 else (0, 1) if st == 4 else (0,))
+        elif dtype == 0 and shape[0] * shape[1] <= 1 << 20:
+            assert (spl, var) in ((1, 0), (1, 1), (2, 0), (4, 0))
         elif dtype == 0:
-            assert spl == 1 and var in (0, 1)
+            assert (spl, var) in ((1, 0), (1, 1), (1, 2), (1, 4))
         else:
-            assert spl in (1, 2, 4) and var == 0
+            assert (spl, var) in ((1, 0), (1, 1), (2, 0), (4, 0))
         for f in range(2 if model in TWO else 1):
             ra = a.read(f, as_f64=False)
             assert np.array_equal(ra, b.read(f, as_f64=False)) and np.array_equal(ra, c.read(f, as_f64=False))
@@ -413,15 +449,12 @@ def test_2d_fp64_families_equal_oracle(sp, model, st, shape):
 def test_set_launch_config_rejects_unavailable(sp):
     sim, _ = make(sp, 1, (64, 64), 0, dtype=0)
     with sim:
-        with pytest.raises(sp.SpError):
-            sim.launch_config = (2, 0)  # FP64 has no temporal blocking
-        with pytest.raises(sp.SpError):
-            sim.launch_config = (1, 7)
-        with pytest.raises(sp.SpError):
-            sim.launch_config = (1, 5)
-        for fam in (1, 2, 4):
-            sim.launch_config = (1, fam)
-            assert sim.launch_config == (1, fam)
+        for bad in ((8, 0), (2, 1), (1, 7), (1, 5)):
+            with pytest.raises(sp.SpError):
+                sim.launch_config = bad
+        for cfg in ((1, 1), (1, 2), (1, 4), (2, 0), (4, 0), (1, 0)):
+            sim.launch_config = cfg
+            assert sim.launch_config == cfg
     sim, _ = make(sp, 1, (64, 64), 0, dtype=1)
     with sim:
         with pytest.raises(sp.SpError):
