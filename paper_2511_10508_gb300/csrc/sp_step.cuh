@@ -1179,10 +1179,17 @@ __global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT)
     const bool mu_row = (MODEL == CH) && w >= r && w < HIN - r;
     const bool out_row = w >= R && w < HIN - R;
 
-    // chunk of row `row` (this lane's column) in the input ring slot, widened
-    auto ring_chunk = [&](int slot, int f, int row, float *dst) {
+    // this lane's chunk of its own row in ring slot 0 (field 0); other slots,
+    // fields and rows lie at fixed offsets, so each plane needs one base pointer
+    constexpr int D = P + 1;  // ring slots
+    static_assert((D & (D - 1)) == 0, "ring slots must be a power of two");
+    constexpr size_t SLOT = (size_t)NF * HIN * 32, FLD = (size_t)HIN * 32;
+    W *const s_own = s_in + (size_t)w * 32 + lane;
+    float *const mu_own = s_mu + ((size_t)w * 32 + lane) * V;
+    // chunk at row offset dy of field f in the slot starting at `base`, widened
+    auto ring_chunk = [&](const W *base, int f, int dy, float *dst) {
         union { W q; T t[V]; } u;
-        u.q = s_in[((size_t)(slot * NF + f) * HIN + row) * 32 + lane];
+        u.q = base[f * FLD + dy * 32];
 #pragma unroll
         for (int i = 0; i < V; ++i) dst[i] = to_c(u.t[i]);
     };
@@ -1205,21 +1212,30 @@ __global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT)
         const size_t goff = (size_t)wrap_idx(y0 - R + w, ny) * nx + wrap_idx(col, nx);
         const int yo = y0 - R + w;                                 // output row (if out_row)
         const bool store = out_row && lane >= 1 && lane <= 30 && col < nx && yo < ny;
+        // element offsets: next plane to fetch (plane jn, wrapped z zn) and next output
+        int jn = 0, zn = wrap_idx(z0 - R, nz);
+        size_t src = (size_t)zn * plane + goff;
+        size_t dst_off = (size_t)z0 * plane + (size_t)yo * nx + col;
 
-        auto issue = [&](int j) {
-            if (j < n) {
-                const size_t zoff = (size_t)wrap_idx(z0 - R + j, nz) * plane;
+        auto issue = [&]() {
+            if (jn < n) {
+                W *dst = s_own + (size_t)(jn & (D - 1)) * SLOT;
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
-                    W *dst = &s_in[((size_t)((j % (P + 1)) * NF + f) * HIN + w) * 32 + lane];
-                    if constexpr (CB == 16) cp_async16(dst, in[f] + zoff + goff);
-                    else cp_async8(dst, in[f] + zoff + goff);
+                    if constexpr (CB == 16) cp_async16(dst + f * FLD, in[f] + src);
+                    else cp_async8(dst + f * FLD, in[f] + src);
+                }
+                src += plane;
+                if (++zn == nz) {
+                    zn = 0;
+                    src -= (size_t)nz * plane;
                 }
             }
+            ++jn;
             cp_async_commit();
         };
 #pragma unroll
-        for (int j = 0; j < P; ++j) issue(j);
+        for (int j = 0; j < P; ++j) issue();
 
         // queues, slot (j % Q) holds plane j: values and partial sums
         float qf[NF][Q][V], qp[NF][Q][NP][V];
@@ -1233,19 +1249,19 @@ __global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT)
                 if (j < n) {
                     cp_async_wait<P - 1>();
                     __syncthreads();  // plane j published; plane j-1's slot and the mu plane are free
-                    issue(j + P);
-                    const int slot = j % (P + 1);
+                    issue();          // plane j + P into plane j-1's slot
+                    const W *cur = s_own + (size_t)(j & (D - 1)) * SLOT;
 #define QS(m) ((u - (m) + 4 * Q) % Q)   /* queue slot of plane j - m */
                     if ((MODEL == CH && mu_row) || (MODEL != CH && out_row)) {
 #pragma unroll
                         for (int f = 0; f < NF; ++f) {
                             float ext[2 * r + 1][XW];
-                            ring_chunk(slot, f, w, ext[r] + r);
+                            ring_chunk(cur, f, 0, ext[r] + r);
                             extend(ext[r]);
 #pragma unroll
                             for (int dy = 1; dy <= r; ++dy) {
-                                ring_chunk(slot, f, w - dy, ext[r - dy] + r);
-                                ring_chunk(slot, f, w + dy, ext[r + dy] + r);
+                                ring_chunk(cur, f, -dy, ext[r - dy] + r);
+                                ring_chunk(cur, f, dy, ext[r + dy] + r);
                                 if constexpr (ST == L27) {
                                     extend(ext[r - dy]);
                                     extend(ext[r + dy]);
@@ -1271,8 +1287,7 @@ __global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT)
                                 mu[c] = ch_mu<C>(qf[0][QS(r)][c], planar_combine<ST>(f0q, p0q, c), k);
 #pragma unroll
                             for (int i = 0; i < V; i += 4)
-                                *reinterpret_cast<float4 *>(&s_mu[((size_t)w * 32 + lane) * V + i]) =
-                                    make_float4(mu[i], mu[i + 1], mu[i + 2], mu[i + 3]);
+                                *reinterpret_cast<float4 *>(mu_own + i) = make_float4(mu[i], mu[i + 1], mu[i + 2], mu[i + 3]);
                         }
                         __syncthreads();  // mu plane j - r published
                         if (out_row && j >= 2 * r) {
@@ -1283,10 +1298,10 @@ __global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT)
 #pragma unroll
                             for (int dy = -r; dy <= r; ++dy) {
                                 if (dy == 0) continue;
-                                const float *src = &s_mu[((size_t)(w + dy) * 32 + lane) * V];
+                                const float *src_mu = mu_own + dy * 32 * V;
 #pragma unroll
                                 for (int i = 0; i < V; i += 4) {
-                                    const float4 v4 = *reinterpret_cast<const float4 *>(src + i);
+                                    const float4 v4 = *reinterpret_cast<const float4 *>(src_mu + i);
                                     ext[r + dy][r + i] = v4.x;
                                     ext[r + dy][r + i + 1] = v4.y;
                                     ext[r + dy][r + i + 2] = v4.z;
@@ -1307,8 +1322,8 @@ __global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT)
 #pragma unroll
                                 for (int c = 0; c < V; ++c)
                                     o[c] = ch_update<C>(qf[0][QS(2 * r)][c], planar_combine<ST>(mf, mp, c), k);
-                                if (store)
-                                    store_vec<T, V>(out[0] + (size_t)(z0 - 4 * r + j) * plane + (size_t)yo * nx + col, o);
+                                if (store) store_vec<T, V>(out[0] + dst_off, o);
+                                dst_off += plane;
                             }
                         }
                     } else {
@@ -1326,10 +1341,10 @@ __global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT)
                                 }
                             }
                             if (store) {
-                                const size_t o = (size_t)(z0 - 2 * r + j) * plane + (size_t)yo * nx + col;
-                                store_vec<T, V>(out[0] + o, o0);
-                                if constexpr (num_fields<MODEL>() == 2) store_vec<T, V>(out[NF - 1] + o, o1);
+                                store_vec<T, V>(out[0] + dst_off, o0);
+                                if constexpr (num_fields<MODEL>() == 2) store_vec<T, V>(out[NF - 1] + dst_off, o1);
                             }
+                            dst_off += plane;
                         }
                     }
 #undef QS

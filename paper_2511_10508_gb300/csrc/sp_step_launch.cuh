@@ -206,9 +206,10 @@ cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
         typedef Step3dWrShape<MODEL, ST, T, WTY> WS;
         auto wkern = step3d_wr_kernel<MODEL, ST, T, WTY>;
         // the warp-row kernel is the default unless its register queues spill
+        // (a spill of a few words outside the queues costs nothing measurable)
         static const bool wr_spills = [&] {
             cudaFuncAttributes fa{};
-            return cudaFuncGetAttributes(&fa, wkern) != cudaSuccess || fa.localSizeBytes > 0;
+            return cudaFuncGetAttributes(&fa, wkern) != cudaSuccess || fa.localSizeBytes > 16;
         }();
         const int fam = (g_step_variant == 0 && wr_spills) ? 1 : g_step_variant;
         if (fam == 0 && a.nx % WS::V == 0 && aligned) {
