@@ -10,11 +10,14 @@
 // dimensions the cross Laplacian is (1/h^2) [d w_0 f_0 + sum_j w_j P_j] with
 // P_j = ((f(+j e_x) + f(-j e_x)) + (f(+j e_y) + f(-j e_y))) [+ (z pair)], in the
 // fixed order  acc = w_r P_r; acc = fma(w_j, P_j, acc) for j = r-1..1;
-// S = fma(d w_0, f_0, acc).  The kernels are per point (a block per 256-point
-// row segment, tap offsets computed once per segment); Cahn-Hilliard takes two
-// passes through a mu buffer.
+// S = fma(d w_0, f_0, acc).  2D FP32 / BF16 grids use shared-memory tiles (one
+// pass, mu in shared memory); FP64 (bound by the FP64 pipe, where the halo mu
+// of a tile would cost more than it saves) and 3D grids use per-point kernels
+// (a block per 256-point row segment, tap offsets computed once per segment;
+// Cahn-Hilliard takes two passes through a mu buffer).
 #include <cstdint>
 #include <cstdlib>
+#include <type_traits>
 
 #include "sp_internal.h"
 
@@ -215,8 +218,122 @@ __global__ void __launch_bounds__(256) gen_step_kernel(GenArgs g, int segs) {
     }
 }
 
+// 2D tiles (FP32 / BF16 storage): one BX x BY output tile per CTA; the tile and
+// its halo (2R for Cahn-Hilliard, whose mu is evaluated on the tile grown by R,
+// else R; x padded to whole 16-byte chunks) are fetched once into shared
+// memory, and mu stays in shared memory, so the step is one pass over HBM.  The
+// same expressions as the per-point kernels, so the results are identical.
+template <int MODEL, int R, typename T, int BX, int BY>
+struct GenTile2dShape {
+    typedef typename Cmp<T>::type C;
+    static constexpr int RIN = (MODEL == CH) ? 2 * R : R;
+    static constexpr int CK = 16 / sizeof(T);
+    static constexpr int HC = (RIN + CK - 1) / CK;
+    static constexpr int NCK = BX / CK + 2 * HC;
+    static constexpr int SW = NCK * CK, X0 = HC * CK;
+    static constexpr int HIN = BY + 2 * RIN;
+    static constexpr int NF = num_fields<MODEL>();
+    static constexpr int WMU = (MODEL == CH) ? BX + 2 * R : 0, HMU = (MODEL == CH) ? BY + 2 * R : 0;
+    static constexpr size_t bytes_in = sizeof(T) * (size_t)NF * HIN * SW;
+    static constexpr size_t smem_bytes = bytes_in + sizeof(C) * (size_t)WMU * HMU;
+    static_assert(bytes_in % 16 == 0, "mu array alignment");
+};
+
+template <int MODEL, int R, typename T, int BX, int BY, int NT>
+__global__ void __launch_bounds__(NT) gen_tile2d_kernel(GenArgs g) {
+    typedef GenTile2dShape<MODEL, R, T, BX, BY> Sh;
+    typedef typename Sh::C C;
+    constexpr int RIN = Sh::RIN, CK = Sh::CK, NCK = Sh::NCK, SW = Sh::SW, X0 = Sh::X0, HIN = Sh::HIN;
+    constexpr int NF = Sh::NF, WMU = Sh::WMU, HMU = Sh::HMU;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s_in = reinterpret_cast<T *>(smem_raw);                 // [NF][HIN][SW]
+    C *s_mu = reinterpret_cast<C *>(smem_raw + Sh::bytes_in);  // [HMU][WMU]
+    const StepArgs &a = g.a;
+    const ConstsC<C> k(a.k, a.kf);
+    const int nx = a.nx, ny = a.ny, t = threadIdx.x;
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    const bool vec_ok = (nx % CK) == 0;
+    const T *in[2] = {static_cast<const T *>(a.in0), static_cast<const T *>(a.in1)};
+    T *out[2] = {static_cast<T *>(a.out0), static_cast<T *>(a.out1)};
+
+    // chunk c of shared row i holds columns x0 - X0 + c*CK .. +CK-1 of grid row y0 - RIN + i
+    for (int q = t; q < HIN * NCK; q += NT) {
+        const int i = q / NCK, c = q - i * NCK;
+        const int y = wrap_idx(y0 - RIN + i, ny);
+        const int x = x0 - X0 + c * CK;
+        const size_t row = (size_t)y * (size_t)nx;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            T *dst = s_in + ((size_t)f * HIN + i) * SW + c * CK;
+            if (vec_ok && x >= 0 && x + CK <= nx) {
+                cp_async16(dst, in[f] + row + x);
+            } else {
+#pragma unroll
+                for (int j = 0; j < CK; ++j) dst[j] = in[f][row + wrap_idx(x + j, nx)];
+            }
+        }
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+
+    // value of field f at tile coordinates (i, j), -RIN <= i < BY + RIN, -X0 <= j < BX + X0
+    auto phi = [&](int f, int i, int j) -> C { return to_c(s_in[((size_t)f * HIN + i + RIN) * SW + j + X0]); };
+    if constexpr (MODEL == CH) {
+        for (int q = t; q < HMU * WMU; q += NT) {
+            const int i = q / WMU - R, j = q % WMU - R;
+            auto P = [&](int dx, int dy, int) -> C { return phi(0, i + dy, j + dx); };
+            s_mu[q] = ch_mu<C>(phi(0, i, j), gen_sum<R, 2, C>(P, g.W), k);
+        }
+        __syncthreads();
+    }
+    for (int q = t; q < BY * BX; q += NT) {
+        const int i = q / BX, j = q - i * BX;
+        const int y = y0 + i, x = x0 + j;
+        if (y >= ny || x >= nx) continue;
+        const size_t o = (size_t)y * (size_t)nx + x;
+        if constexpr (MODEL == CH) {
+            auto Pm = [&](int dx, int dy, int) -> C { return s_mu[(i + R + dy) * WMU + (j + R + dx)]; };
+            out[0][o] = from_c<T>(ch_update<C>(phi(0, i, j), gen_sum<R, 2, C>(Pm, g.W), k));
+        } else {
+            auto P0 = [&](int dx, int dy, int) -> C { return phi(0, i + dy, j + dx); };
+            if constexpr (MODEL == AC) {
+                out[0][o] = from_c<T>(ac_update<C>(phi(0, i, j), gen_sum<R, 2, C>(P0, g.W), k));
+            } else {
+                auto P1 = [&](int dx, int dy, int) -> C { return phi(NF - 1, i + dy, j + dx); };
+                C S1;
+                if constexpr (MODEL == MC) {
+                    auto Pm = [&](int dx, int dy, int dz) -> C { return mc_mu<C>(P0(dx, dy, dz), P1(dx, dy, dz), k); };
+                    S1 = gen_sum<R, 2, C>(Pm, g.W);
+                } else {
+                    S1 = gen_sum<R, 2, C>(P1, g.W);
+                }
+                C a0, a1;
+                two_field_update<MODEL, C>(phi(0, i, j), phi(NF - 1, i, j), gen_sum<R, 2, C>(P0, g.W), S1, k, a0, a1);
+                out[0][o] = from_c<T>(a0);
+                out[NF - 1][o] = from_c<T>(a1);
+            }
+        }
+    }
+}
+
 template <int MODEL, int R, int DIMS, typename T>
 static cudaError_t launch_gen_t(const GenArgs &g, cudaStream_t s, int n_sm) {
+    if constexpr (DIMS == 2 && !std::is_same<T, double>::value) {
+        // family 0: shared-memory tiles; family 1: the per-point kernels
+        if (g_step_variant != 1) {
+            constexpr int BX = 128, BY = 32, NT = 256;
+            typedef GenTile2dShape<MODEL, R, T, BX, BY> Sh;
+            auto kern = gen_tile2d_kernel<MODEL, R, T, BX, BY, NT>;
+            static const bool attr = [&] {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem_bytes);
+                return true;
+            }();
+            (void)attr;
+            kern<<<dim3((g.a.nx + BX - 1) / BX, (g.a.ny + BY - 1) / BY), NT, Sh::smem_bytes, s>>>(g);
+            return cudaGetLastError();
+        }
+    }
     const int segs = (g.a.nx + 255) / 256;
     const long long units = (long long)g.a.ny * g.a.nz * segs;
     const unsigned blocks = (unsigned)std::min<long long>(units, (long long)n_sm * 8);
