@@ -5,17 +5,21 @@
 //   dj/dt = lap j - c3 m grad mu
 // grad and div are central differences of the Laplacian stencil's order.
 //
-// Like the paper's solver (one temporary for Model H, Table 2), a step is two
-// passes: mu for every point into a compute-precision buffer, then the update
-// of m and of each component of j, which reads mu, m and j through periodic
-// taps (the flux m j_a is formed at each tap, with the rounding of the product
-// m * j_a).  Fixed order per point (FP64 results equal the oracle's bit for bit):
+// Like the paper's solver (one temporary for Model H, Table 2), the per-point
+// kernels take two passes: mu for every point into a compute-precision buffer,
+// then the update of m and of each component of j, which reads mu, m and j
+// through periodic taps (the flux m j_a is formed at each tap, with the
+// rounding of the product m * j_a).  2D FP32 / BF16 grids instead use one
+// shared-memory tile pass with mu kept on chip (FP64 is bound by the FP64
+// pipe, where the halo mu of a tile costs more than the buffer).  Fixed order per point (FP64 results equal the oracle's bit for bit):
 //   mu  = fma(m, fma(c2, m*m, -c1), -((kappa/q_h2) * S(m)))
 //   div = (D_x(m j_x) + D_y(m j_y)) [+ D_z(m j_z)]
 //   m'  = fma(dt, fma(1/q_h2, S(mu), -(c3g * div)), m)
 //   j_a' = fma(dt, fma(1/q_h2, S(j_a), -(c3g * (m * D_a mu))), j_a)
 // with D f = f(+1) - f(-1) (radius-1 stencils) or fma(8, f(+1) - f(-1),
 // -(f(+2) - f(-2))) (radius 2) and c3g = c3 / (2h) or c3 / (12h).
+#include <type_traits>
+
 #include "sp_internal.h"
 
 namespace sp {
@@ -126,13 +130,117 @@ __global__ void __launch_bounds__(256) mh_update_kernel(MhArgs a, int segs, type
     }
 }
 
+// 2D tiles (FP32 / BF16 storage): one BX x BY output tile per CTA.  m and the
+// components of j are fetched once with a 2R halo (x padded to whole 16-byte
+// chunks), mu is evaluated on the tile grown by R into shared memory, and the
+// update reads everything from shared memory: one pass over HBM instead of two
+// plus the mu buffer.  The same expressions as the per-point kernels, so the
+// results are identical to theirs.
+template <int ST, typename T, int BX, int BY>
+struct MhTile2dShape {
+    typedef typename Cmp<T>::type C;
+    static constexpr int R = StencilInfo<ST>::r;
+    static constexpr int RIN = 2 * R;
+    static constexpr int CK = 16 / sizeof(T);
+    static constexpr int HC = (RIN + CK - 1) / CK;
+    static constexpr int NCK = BX / CK + 2 * HC;
+    static constexpr int SW = NCK * CK, X0 = HC * CK;
+    static constexpr int HIN = BY + 2 * RIN;
+    static constexpr int NF = 3;  // m, j_x, j_y
+    static constexpr int WMU = BX + 2 * R, HMU = BY + 2 * R;
+    static constexpr size_t bytes_in = sizeof(T) * (size_t)NF * HIN * SW;
+    static constexpr size_t smem_bytes = bytes_in + sizeof(C) * (size_t)WMU * HMU;
+    static_assert(bytes_in % 16 == 0, "mu array alignment");
+};
+
+template <int ST, typename T, int BX, int BY, int NT>
+__global__ void __launch_bounds__(NT) mh_tile2d_kernel(MhArgs a, typename Cmp<T>::type c3g) {
+    typedef MhTile2dShape<ST, T, BX, BY> Sh;
+    typedef typename Sh::C C;
+    constexpr int R = Sh::R, RIN = Sh::RIN, CK = Sh::CK, NCK = Sh::NCK, SW = Sh::SW, X0 = Sh::X0;
+    constexpr int HIN = Sh::HIN, NF = Sh::NF, WMU = Sh::WMU, HMU = Sh::HMU;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s_in = reinterpret_cast<T *>(smem_raw);                 // [NF][HIN][SW]: m, j_x, j_y
+    C *s_mu = reinterpret_cast<C *>(smem_raw + Sh::bytes_in);  // [HMU][WMU]
+    const ConstsC<C> k(a.k, a.kf);
+    const int nx = a.nx, ny = a.ny, t = threadIdx.x;
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    const bool vec_ok = (nx % CK) == 0;
+    const T *in[NF] = {static_cast<const T *>(a.m), static_cast<const T *>(a.j[0]), static_cast<const T *>(a.j[1])};
+    T *out[NF] = {static_cast<T *>(a.mo), static_cast<T *>(a.jo[0]), static_cast<T *>(a.jo[1])};
+
+    // chunk c of shared row i holds columns x0 - X0 + c*CK .. +CK-1 of grid row y0 - RIN + i
+    for (int q = t; q < HIN * NCK; q += NT) {
+        const int i = q / NCK, c = q - i * NCK;
+        const int y = wrap_idx(y0 - RIN + i, ny);
+        const int x = x0 - X0 + c * CK;
+        const size_t row = (size_t)y * (size_t)nx;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            T *dst = s_in + ((size_t)f * HIN + i) * SW + c * CK;
+            if (vec_ok && x >= 0 && x + CK <= nx) {
+                cp_async16(dst, in[f] + row + x);
+            } else {
+#pragma unroll
+                for (int jj = 0; jj < CK; ++jj) dst[jj] = in[f][row + wrap_idx(x + jj, nx)];
+            }
+        }
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+
+    // field f at tile coordinates (i, j), -RIN <= i < BY + RIN, -X0 <= j < BX + X0
+    auto fld = [&](int f, int i, int j) -> C { return to_c(s_in[((size_t)f * HIN + i + RIN) * SW + j + X0]); };
+    for (int q = t; q < HMU * WMU; q += NT) {
+        const int i = q / WMU - R, j = q % WMU - R;
+        auto P = [&](int dx, int dy, int) -> C { return fld(0, i + dy, j + dx); };
+        s_mu[q] = ch_mu<C>(fld(0, i, j), stencil_sum<ST, C>(P), k);
+    }
+    __syncthreads();
+    for (int q = t; q < BY * BX; q += NT) {
+        const int i = q / BX, j = q - i * BX;
+        const int y = y0 + i, x = x0 + j;
+        if (y >= ny || x >= nx) continue;
+        const size_t o = (size_t)y * (size_t)nx + x;
+        auto Pmu = [&](int dx, int dy, int) -> C { return s_mu[(i + R + dy) * WMU + (j + R + dx)]; };
+        auto flux = [&](int ax) {
+            return [&, ax](int dx, int dy, int) -> C { return fld(0, i + dy, j + dx) * fld(1 + ax, i + dy, j + dx); };
+        };
+        const C div = central<R, 0>(flux(0)) + central<R, 1>(flux(1));
+        const C mi = fld(0, i, j);
+        out[0][o] = from_c<T>(FMA(k.dt, FMA(k.sAC, stencil_sum<ST, C>(Pmu), -(c3g * div)), mi));
+#pragma unroll
+        for (int ax = 0; ax < 2; ++ax) {
+            const C gm = (ax == 0) ? central<R, 0>(Pmu) : central<R, 1>(Pmu);
+            auto Pj = [&](int dx, int dy, int) -> C { return fld(1 + ax, i + dy, j + dx); };
+            out[1 + ax][o] = from_c<T>(FMA(k.dt, FMA(k.sAC, stencil_sum<ST, C>(Pj), -(c3g * (mi * gm))), fld(1 + ax, i, j)));
+        }
+    }
+}
+
 template <int ST, typename T>
 static cudaError_t launch_mh_t(const MhArgs &a, double c3g, cudaStream_t s, int n_sm) {
+    typedef typename Cmp<T>::type C;
+    if constexpr (StencilInfo<ST>::dims == 2 && !std::is_same<T, double>::value) {
+        // family 0: shared-memory tiles; family 1: the two per-point passes
+        if (g_step_variant != 1) {
+            constexpr int BX = 128, BY = 16, NT = 256;
+            typedef MhTile2dShape<ST, T, BX, BY> Sh;
+            auto kern = mh_tile2d_kernel<ST, T, BX, BY, NT>;
+            static const bool attr = [&] {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem_bytes);
+                return true;
+            }();
+            (void)attr;
+            kern<<<dim3((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY), NT, Sh::smem_bytes, s>>>(a, (C)c3g);
+            return cudaGetLastError();
+        }
+    }
     const int segs = (a.nx + 255) / 256;
     const long long units = (long long)a.ny * a.nz * segs;
     const unsigned blocks = (unsigned)std::min<long long>(units, (long long)n_sm * 8);
     mh_mu_kernel<ST, T><<<blocks, 256, 0, s>>>(a, segs);
-    typedef typename Cmp<T>::type C;
     if constexpr (StencilInfo<ST>::dims == 2)
         mh_update_kernel<ST, T, 2><<<blocks, 256, 0, s>>>(a, segs, (C)c3g);
     else
