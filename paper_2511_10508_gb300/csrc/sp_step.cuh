@@ -46,11 +46,14 @@ struct Step2dBatchShape {
     // has 2*RB + 2r slots (row differences lie in [1, 2RB+2r-1]).
     static constexpr int DIN = 2 * RB + 2 * r;
     static constexpr int NF = num_fields<MODEL>();
+    // Model C: the density's chemical potential of every committed point, kept
+    // in the ring as one more field (evaluated once per point, not per tap)
+    static constexpr int NRING = NF + (MODEL == MC ? 1 : 0);
     // mu ring: a batch reads mu rows [yb-r, yb+RB+r); the next batch's rows are
     // written only after a barrier that follows this batch's output.
     static constexpr int WMU = (MODEL == CH) ? TW + 2 * r : 0;
     static constexpr int DMU = (MODEL == CH) ? RB + 2 * r : 0;
-    static constexpr size_t smem_bytes = sizeof(C) * ((size_t)NF * DIN * WIN + (size_t)DMU * WMU);
+    static constexpr size_t smem_bytes = sizeof(C) * ((size_t)NRING * DIN * WIN + (size_t)DMU * WMU);
 };
 
 template <int MODEL, int ST, typename T, int NT, int RB>
@@ -60,9 +63,9 @@ __global__ void __launch_bounds__(NT) step2d_batch_kernel(StepArgs a, int strips
     constexpr int r = Sh::r, RIN = Sh::RIN, TW = Sh::TW, WIN = Sh::WIN, DIN = Sh::DIN, NF = Sh::NF;
     constexpr int WMU = Sh::WMU, DMU = Sh::DMU;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C (*s_in)[DIN][WIN] = reinterpret_cast<C (*)[DIN][WIN]>(smem_raw);                  // [NF][DIN][WIN]
+    C (*s_in)[DIN][WIN] = reinterpret_cast<C (*)[DIN][WIN]>(smem_raw);                  // [NRING][DIN][WIN]
     C (*s_mu)[WMU > 0 ? WMU : 1] =
-        reinterpret_cast<C (*)[WMU > 0 ? WMU : 1]>(smem_raw + sizeof(C) * (size_t)NF * DIN * WIN);  // [DMU][WMU]
+        reinterpret_cast<C (*)[WMU > 0 ? WMU : 1]>(smem_raw + sizeof(C) * (size_t)Sh::NRING * DIN * WIN);  // [DMU][WMU]
 
     const ConstsC<C> k(a.k, a.kf);
     const int nx = a.nx, ny = a.ny;
@@ -115,6 +118,11 @@ __global__ void __launch_bounds__(NT) step2d_batch_kernel(StepArgs a, int strips
                         s_in[f][sl][RIN + t + NT] = pb[f][i];
                         if (has_halo) s_in[f][sl][hxi] = ph[f][i];
                     }
+                    if constexpr (MODEL == MC) {
+                        s_in[NF][sl][RIN + t] = mc_mu<C>(pa[0][i], pa[1][i], k);
+                        s_in[NF][sl][RIN + t + NT] = mc_mu<C>(pb[0][i], pb[1][i], k);
+                        if (has_halo) s_in[NF][sl][hxi] = mc_mu<C>(ph[0][i], ph[1][i], k);
+                    }
                 }
             }
         };
@@ -155,8 +163,16 @@ __global__ void __launch_bounds__(NT) step2d_batch_kernel(StepArgs a, int strips
                                 auto P1 = [&](int dx, int dy, int) -> C {
                                     return s_in[NF - 1][slot_in(y + dy)][c + RIN + dx];
                                 };
-                                two_field_update<MODEL, C>(p0, s_in[NF - 1][slot_in(y)][c + RIN], S0,
-                                                           second_sum<MODEL, ST, C>(P0, P1, k), k, o0, o1);
+                                C S1;
+                                if constexpr (MODEL == MC) {
+                                    auto Pr = [&](int dx, int dy, int) -> C {
+                                        return s_in[NF][slot_in(y + dy)][c + RIN + dx];
+                                    };
+                                    S1 = stencil_sum<ST, C>(Pr);  // = second_sum, mu_rho read, not re-evaluated
+                                } else {
+                                    S1 = second_sum<MODEL, ST, C>(P0, P1, k);
+                                }
+                                two_field_update<MODEL, C>(p0, s_in[NF - 1][slot_in(y)][c + RIN], S0, S1, k, o0, o1);
                             }
                         }
                         if (x < nx) {
