@@ -745,10 +745,13 @@ struct Step3dShape {
     static constexpr int WIN = TX + 2 * RIN, HIN = TY + 2 * RIN, AIN = WIN * HIN;
     static constexpr int DIN = 2 * r + 2;
     static constexpr int NF = num_fields<MODEL>();
+    // Model C: the density's chemical potential of every loaded point, kept in
+    // the ring as one more field (evaluated once per point, not per tap)
+    static constexpr int NRING = NF + (MODEL == MC ? 1 : 0);
     static constexpr int WMU = TX + 2 * r, HMU = TY + 2 * r, AMU = WMU * HMU;
     static constexpr int DMU = (MODEL == CH) ? 2 * r + 1 : 0;
     static constexpr int EPT = (AIN + NT - 1) / NT;  // loaded cells per thread per field
-    static constexpr size_t smem_bytes = sizeof(C) * ((size_t)NF * DIN * AIN + (size_t)DMU * AMU);
+    static constexpr size_t smem_bytes = sizeof(C) * ((size_t)NRING * DIN * AIN + (size_t)DMU * AMU);
 };
 
 template <int MODEL, int ST, typename T, int TX, int TY, int NT>
@@ -758,8 +761,8 @@ __global__ void __launch_bounds__(NT) step3d_kernel(StepArgs a, int tiles_x, int
     constexpr int r = Sh::r, RIN = Sh::RIN, WIN = Sh::WIN, AIN = Sh::AIN, DIN = Sh::DIN, NF = Sh::NF;
     constexpr int WMU = Sh::WMU, AMU = Sh::AMU, DMU = Sh::DMU, EPT = Sh::EPT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *s_in = reinterpret_cast<C *>(smem_raw);            // [NF][DIN][AIN]
-    C *s_mu = s_in + (size_t)NF * DIN * AIN;               // [DMU][AMU]
+    C *s_in = reinterpret_cast<C *>(smem_raw);            // [NRING][DIN][AIN]
+    C *s_mu = s_in + (size_t)Sh::NRING * DIN * AIN;        // [DMU][AMU]
 
     const ConstsC<C> k(a.k, a.kf);
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -807,6 +810,11 @@ __global__ void __launch_bounds__(NT) step3d_kernel(StepArgs a, int tiles_x, int
 #pragma unroll
             for (int e = 0; e < EPT; ++e)
                 if (loff[e] >= 0) s_in[((size_t)f * DIN + slot) * AIN + t + e * NT] = pf[f][e];
+        if constexpr (MODEL == MC) {
+#pragma unroll
+            for (int e = 0; e < EPT; ++e)
+                if (loff[e] >= 0) s_in[((size_t)NF * DIN + slot) * AIN + t + e * NT] = mc_mu<C>(pf[0][e], pf[1][e], k);
+        }
     };
     auto S_in = [&](int f, int slot) -> const C * { return s_in + ((size_t)f * DIN + slot) * AIN; };
 
@@ -867,7 +875,15 @@ __global__ void __launch_bounds__(NT) step3d_kernel(StepArgs a, int tiles_x, int
                         auto P1 = [&](int dx, int dy, int dz) -> C {
                             return S_in(NF - 1, (j - r + dz) % DIN)[b + dy * WIN + dx];
                         };
-                        const C S1 = second_sum<MODEL, ST, C>(P0, P1, k);
+                        C S1;
+                        if constexpr (MODEL == MC) {
+                            auto Pr = [&](int dx, int dy, int dz) -> C {
+                                return S_in(NF, (j - r + dz) % DIN)[b + dy * WIN + dx];
+                            };
+                            S1 = stencil_sum<ST, C>(Pr);  // = second_sum, mu_rho read, not re-evaluated
+                        } else {
+                            S1 = second_sum<MODEL, ST, C>(P0, P1, k);
+                        }
                         const C p1 = S_in(NF - 1, (j - r) % DIN)[b];
                         C un, vn;
                         two_field_update<MODEL, C>(p0, p1, S0, S1, k, un, vn);
