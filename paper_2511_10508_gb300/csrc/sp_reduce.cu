@@ -12,6 +12,8 @@
 // blocks through shared memory, and each block writes its pair to a scratch
 // array; a single block then combines the block pairs in index order and
 // writes the scaled result.
+#include <type_traits>
+
 #include "sp_internal.h"
 
 namespace sp {
@@ -102,12 +104,59 @@ __device__ __forceinline__ double fe_density(const T *__restrict__ f, const T *_
     return 0.5 * g2 - 0.5 * c1 * p2 + 0.25 * c2 * p2 * p2;
 }
 
+// Sum of a block of 32 FP32 values (BF16 values widen to FP32 exactly) in
+// fixed point, with integer arithmetic only.  A value with biased exponent e
+// and 24-bit significand m is m * 2^(max(e,1) - 150).  With E the largest
+// exponent of the block, every value is expressed in units of 2^(E - 150 - K),
+// K = 33: v = floor(m * 2^(K - (E - max(e,1)))), so the block's largest values
+// keep every bit and values more than 2^33 times smaller lose the bits below
+// the unit (an error below 2^-56 max|x| each, at most 2^-51 max|x| per block).
+// 32 values of at most 24 + 33 bits sum exactly in 62 bits.  The integer sum is
+// converted to FP64 once (one rounding) and scaled by the exact power of two.
+// A block holding an infinity or a NaN (E = 255) is summed in FP64 instead, so
+// that those propagate as in plain summation.
+__device__ __forceinline__ double fixed_block_sum32(const float *x) {
+    constexpr int K = 33;
+    uint32_t b[32];
+    int emax = 0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        b[j] = __float_as_uint(x[j]);
+        emax = max(emax, (int)((b[j] >> 23) & 0xffu));
+    }
+    if (emax == 255) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) s += (double)x[j];
+        return s;
+    }
+    const int em = max(emax, 1);
+    long long acc = 0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const int e = (int)((b[j] >> 23) & 0xffu);
+        const unsigned long long m = (unsigned long long)((b[j] & 0x7fffffu) | (e ? 0x800000u : 0u));
+        const int sh = min(em - max(e, 1), 63);
+        const long long v = (long long)((m << K) >> sh);
+        const long long sgn = -(long long)(b[j] >> 31);  // 0 or -1
+        acc += (v ^ sgn) - sgn;
+    }
+    // 2^(em - 150 - K) as an FP64 power of two (em - 183 >= -182: a normal number)
+    const double unit = __longlong_as_double((long long)(em - 150 - K + 1023) << 52);
+    return __ll2double_rn(acc) * unit;
+}
+
 // Block partials.  Sums: each thread reads 16-byte vectors in a grid-stride
-// loop, adds every kBlockVecs vectors (16 values for FP32) with plain FP64
-// additions and folds that block sum into its Neumaier pair, so the FP64 pipe
-// (slow on this part) sees ~2 operations per value instead of ~7; the error
-// bound becomes u|S| + 15u sum|x| per thread instead of u|S|.  Min / max run in
-// the compute type.  The free energy keeps a per-point Neumaier update.
+// loop.  FP32 / BF16 mass and plain sums: the vectors are taken in groups of
+// 32 values per thread (a warp's group interleaves its lanes, so every load
+// instruction is coalesced), each group is summed exactly in fixed point
+// (fixed_block_sum32) and folded into the thread's Neumaier pair, so the FP64
+// pipe (slow on this part) sees ~0.3 operations per value; error bound u|S| +
+// 5u sum|x| per thread (truncation 4u, conversion u).  FP64 fields and sums of
+// squares: plain FP64 additions over blocks of 16 values folded into the
+// Neumaier pair, ~2 FP64 operations per value, bound u|S| + 15u sum|x|.  The
+// remaining vectors and the scalar tail take the FP64 block path.  Min / max run
+// in the compute type.  The free energy keeps a per-point Neumaier update.
 template <typename T, int WHAT>
 __global__ void __launch_bounds__(kReduceThreads)
 reduce_partial_kernel(const T *__restrict__ f, const T *__restrict__ rho, const T *j0, const T *j1, const T *j2, int nq,
@@ -132,7 +181,26 @@ reduce_partial_kernel(const T *__restrict__ f, const T *__restrict__ rho, const 
         C mn = C(INFINITY), mx = C(-INFINITY);
         double blk = 0.0;
         int nb = 0;
-        for (uint64_t v = tid; v < NV; v += stride) {
+        uint64_t v0 = 0;  // first vector of the FP64 block path
+        if constexpr (!std::is_same<T, double>::value && (WHAT == SP_MASS || WHAT == SP_SUM_U)) {
+            constexpr int G = 32 / VE;  // vectors per thread per group
+            const uint64_t lane = threadIdx.x & 31u, warp = tid >> 5;
+            const uint64_t nwarps = stride >> 5;
+            const uint64_t ngroups = NV / (32u * G);
+            for (uint64_t gi = warp; gi < ngroups; gi += nwarps) {
+                float x[32];
+#pragma unroll
+                for (int j = 0; j < G; ++j) {
+                    C xv[VE];
+                    load_vec<T, VE>(f + ((gi * G + j) * 32u + lane) * VE, xv);
+#pragma unroll
+                    for (int q = 0; q < VE; ++q) x[j * VE + q] = xv[q];
+                }
+                neu_add(s, c, fixed_block_sum32(x));
+            }
+            v0 = ngroups * 32u * G;
+        }
+        for (uint64_t v = v0 + tid; v < NV; v += stride) {
             C x[VE];
             load_vec<T, VE>(f + v * VE, x);
             if constexpr (WHAT == SP_MIN_U) {
@@ -176,7 +244,7 @@ reduce_final_kernel(const double *__restrict__ partials, int nblocks, double sca
     block_combine<WHAT>(s, c);
     if (threadIdx.x == 0) {
         if constexpr (WHAT == SP_MIN_U || WHAT == SP_MAX_U) out[0] = s;
-        else out[0] = scale * (s + c);
+        else out[0] = scale * (isfinite(s) ? s + c : s);  // an infinite sum keeps its sign (c is NaN then)
     }
 }
 

@@ -175,6 +175,41 @@ def test_reductions(sp, dtype):
                 assert abs(sim.reduce(sp.SUM_V) - O.kahan_sum(v)) <= 1e-13 * (np.abs(v).sum() + 1)
 
 
+@pytest.mark.parametrize("dtype", [1, 2])
+def test_fixed_point_sums_adversarial(sp, dtype):
+    """FP32 / BF16 mass and sums take exact fixed-point block sums: against the
+    exact sum of the stored values (math.fsum, correctly rounded) the error stays
+    within u|S| + 5u sum|x| (u = 2^-53) on values spanning 60 decades, with
+    denormals, zeros of both signs, cancelling pairs and a ragged tail; an
+    infinity propagates."""
+    import math
+
+    rng = np.random.default_rng(3)
+    shape = (37, 64, 65)
+    n = int(np.prod(shape))
+    mag = 10.0 ** rng.uniform(-30, 30, n)
+    vals = np.where(rng.random(n) < 0.5, -mag, mag)
+    vals[rng.random(n) < 0.02] = 1e-40 if dtype == 1 else 1e-38   # denormal in FP32
+    vals[rng.random(n) < 0.02] = 0.0
+    vals[rng.random(n) < 0.01] = -0.0
+    half = n // 4
+    vals[half:2 * half] = -vals[:half]                              # exact cancellation
+    vals = vals.reshape(shape)
+    u = 2.0 ** -53
+    with sp.Simulation(sp.ALLEN_CAHN, shape, dt=0.01, dtype=dtype, stencil=3) as sim:
+        sim.write(0, vals)
+        stored = sim.read(0)                                        # the values as rounded to storage
+        exact = math.fsum(stored.ravel().tolist())
+        bound = u * abs(exact) + 5 * u * np.abs(stored).sum()
+        for what in (sp.MASS, sp.SUM_U):
+            got = sim.reduce(what)
+            assert abs(got - exact) <= bound, (what, got, exact, bound)
+        inf_vals = stored.copy()
+        inf_vals[5, 7, 9] = np.inf
+        sim.write(0, inf_vals)
+        assert sim.reduce(sp.MASS) == np.inf
+
+
 def test_reductions_with_h(sp):
     """Cell volume h^d and the 1/h of the gradient enter mass and free energy."""
     shape = (48, 80)
