@@ -270,6 +270,44 @@ __device__ __forceinline__ void two_field_update(C p0, C p1, C S0, C S1, const C
     else gs_update<C>(p0, p1, S0, S1, k, o0, o1);
 }
 
+// ------------------------------------------------- packed FP32 pairs --
+//
+// Two cells per instruction (f32x2 arithmetic of sm_100 and later): each lane
+// of __fadd2_rn / __fmul2_rn / __ffma2_rn rounds like the scalar operation, so
+// the pair forms below give the scalar helpers' results bit for bit (a negated
+// operand is exact, so -(a*b) == (-a)*b and x - y == x + (-y)).
+__device__ __forceinline__ float2 splat2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+struct ConstsF2 {
+    float2 c1, negc1, c2, negc2, sAC, negkq, dq, duq, dvq, F, negFk, dt, one;
+    __device__ __forceinline__ explicit ConstsF2(const ConstsC<float> &k)
+        : c1(splat2(k.c1)), negc1(splat2(-k.c1)), c2(splat2(k.c2)), negc2(splat2(-k.c2)), sAC(splat2(k.sAC)),
+          negkq(splat2(-k.kq)), dq(splat2(k.dq)), duq(splat2(k.duq)), dvq(splat2(k.dvq)), F(splat2(k.F)),
+          negFk(splat2(-k.Fk)), dt(splat2(k.dt)), one(splat2(1.f)) {}
+};
+
+// ac_update, ch_mu, ch_update and gs_update on pairs of cells
+__device__ __forceinline__ float2 ac_update2(float2 p, float2 S, const ConstsF2 &k) {
+    const float2 rhs = fma2(p, fma2(k.negc2, mul2(p, p), k.c1), mul2(k.sAC, S));
+    return fma2(k.dt, rhs, p);
+}
+__device__ __forceinline__ float2 ch_mu2(float2 p, float2 S, const ConstsF2 &k) {
+    return fma2(p, fma2(k.c2, mul2(p, p), k.negc1), mul2(k.negkq, S));
+}
+__device__ __forceinline__ float2 ch_update2(float2 p, float2 Smu, const ConstsF2 &k) { return fma2(k.dq, Smu, p); }
+__device__ __forceinline__ void gs_update2(float2 u, float2 v, float2 Su, float2 Sv, const ConstsF2 &k, float2 &un,
+                                           float2 &vn) {
+    const float2 uvv = mul2(mul2(u, v), v);
+    const float2 ru = fma2(k.F, add2(k.one, neg2(u)), fma2(k.duq, Su, neg2(uvv)));
+    const float2 rv = fma2(k.negFk, v, fma2(k.dvq, Sv, uvv));
+    un = fma2(k.dt, ru, u);
+    vn = fma2(k.dt, rv, v);
+}
+
 // ------------------------------------------------------- launch records --
 
 struct StepArgs {

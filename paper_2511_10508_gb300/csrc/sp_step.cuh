@@ -1148,20 +1148,21 @@ __device__ __forceinline__ void planar_sums(const RowFn &row, float (&ps)[Planar
 }
 
 // Stencil sum at the centre plane from the values f[k] and partial sums p[k]
-// of planes k = 0 .. 2r (z offsets -r .. r), cell c.
+// of planes k = 0 .. 2r (z offsets -r .. r), for the pair of cells q (cells 2q
+// and 2q+1), two cells per instruction.
 template <int ST, typename FA, typename PA>
-__device__ __forceinline__ float planar_combine(const FA &f, const PA &p, int c) {
+__device__ __forceinline__ float2 planar_combine2(const FA &f, const PA &p, int q) {
     if constexpr (ST == L7) {
-        return FMA(-6.f, f(1)[c], p(1)[0][c] + (f(0)[c] + f(2)[c]));
+        return fma2(splat2(-6.f), f(1)[q], add2(p(1)[0][q], add2(f(0)[q], f(2)[q])));
     } else if constexpr (ST == L27) {
-        const float F = p(1)[0][c] + (f(0)[c] + f(2)[c]);
-        const float E = p(1)[1][c] + (p(0)[0][c] + p(2)[0][c]);
-        const float K = p(0)[1][c] + p(2)[1][c];
-        return FMA(-128.f, f(1)[c], FMA(14.f, F, FMA(3.f, E, K)));
+        const float2 F = add2(p(1)[0][q], add2(f(0)[q], f(2)[q]));
+        const float2 E = add2(p(1)[1][q], add2(p(0)[0][q], p(2)[0][q]));
+        const float2 K = add2(p(0)[1][q], p(2)[1][q]);
+        return fma2(splat2(-128.f), f(1)[q], fma2(splat2(14.f), F, fma2(splat2(3.f), E, K)));
     } else {  // L13X4
-        const float F1 = p(2)[0][c] + (f(1)[c] + f(3)[c]);
-        const float F2 = p(2)[1][c] + (f(0)[c] + f(4)[c]);
-        return FMA(-90.f, f(2)[c], FMA(16.f, F1, -F2));
+        const float2 F1 = add2(p(2)[0][q], add2(f(1)[q], f(3)[q]));
+        const float2 F2 = add2(p(2)[1][q], add2(f(0)[q], f(4)[q]));
+        return fma2(splat2(-90.f), f(2)[q], fma2(splat2(16.f), F1, neg2(F2)));
     }
 }
 
@@ -1202,7 +1203,7 @@ __global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT)
     W *s_in = reinterpret_cast<W *>(smem_raw);                              // [P+1][NF][HIN][32]
     float *s_mu = reinterpret_cast<float *>(smem_raw + Sh::in_bytes);      // [HIN][32][V]
 
-    const ConstsC<C> k(a.k, a.kf);
+    const ConstsF2 k2(ConstsC<C>(a.k, a.kf));
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const size_t plane = (size_t)nx * (size_t)ny;
@@ -1269,10 +1270,21 @@ __global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT)
 #pragma unroll
         for (int j = 0; j < P; ++j) issue();
 
-        // queues, slot (j % Q) holds plane j: values and partial sums
-        float qf[NF][Q][V], qp[NF][Q][NP][V];
-        float qm[MODEL == CH ? Q : 1][V], qmp[MODEL == CH ? Q : 1][NP][V];
+        // queues, slot (j % Q) holds plane j: values and partial sums, as pairs of cells
+        constexpr int V2 = V / 2;
+        float2 qf[NF][Q][V2], qp[NF][Q][NP][V2];
+        float2 qm[MODEL == CH ? Q : 1][V2], qmp[MODEL == CH ? Q : 1][NP][V2];
         (void)qm; (void)qmp;
+        // in-plane partial sums of a row triple into queue slot dst
+        auto sums_into = [&](const float (*ext)[XW], float2 (&dst)[NP][V2]) {
+            float ps[NP][V];
+            auto row = [&](int dy) -> const float * { return ext[r + dy]; };
+            planar_sums<ST, V, XW>(row, ps);
+#pragma unroll
+            for (int n2 = 0; n2 < NP; ++n2)
+#pragma unroll
+                for (int q = 0; q < V2; ++q) dst[n2][q] = make_float2(ps[n2][2 * q], ps[n2][2 * q + 1]);
+        };
 
         for (int j0 = 0; j0 < n; j0 += Q) {
 #pragma unroll
@@ -1299,33 +1311,37 @@ __global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT)
                                     extend(ext[r + dy]);
                                 }
                             }
-                            auto row = [&](int dy) -> const float * { return ext[r + dy]; };
-                            planar_sums<ST, V, XW>(row, qp[f][QS(0)]);
+                            sums_into(ext, qp[f][QS(0)]);
 #pragma unroll
-                            for (int c = 0; c < V; ++c) qf[f][QS(0)][c] = ext[r][r + c];
+                            for (int q = 0; q < V2; ++q)
+                                qf[f][QS(0)][q] = make_float2(ext[r][r + 2 * q], ext[r][r + 2 * q + 1]);
                         }
                     }
                     // stencil of plane j - r from the queues (planes j - 2r .. j)
-                    auto f0q = [&](int kk) -> const float * { return qf[0][QS(2 * r - kk)]; };
-                    auto p0q = [&](int kk) -> const float(*)[V] { return qp[0][QS(2 * r - kk)]; };
-                    auto f1q = [&](int kk) -> const float * { return qf[NF - 1][QS(2 * r - kk)]; };
-                    auto p1q = [&](int kk) -> const float(*)[V] { return qp[NF - 1][QS(2 * r - kk)]; };
+                    auto f0q = [&](int kk) -> const float2 * { return qf[0][QS(2 * r - kk)]; };
+                    auto p0q = [&](int kk) -> const float2(*)[V2] { return qp[0][QS(2 * r - kk)]; };
+                    auto f1q = [&](int kk) -> const float2 * { return qf[NF - 1][QS(2 * r - kk)]; };
+                    auto p1q = [&](int kk) -> const float2(*)[V2] { return qp[NF - 1][QS(2 * r - kk)]; };
                     (void)f1q; (void)p1q;
                     if constexpr (MODEL == CH) {
-                        float mu[V];
+                        float2 mu[V2];
                         if (mu_row && j >= 2 * r) {
 #pragma unroll
-                            for (int c = 0; c < V; ++c)
-                                mu[c] = ch_mu<C>(qf[0][QS(r)][c], planar_combine<ST>(f0q, p0q, c), k);
+                            for (int q = 0; q < V2; ++q)
+                                mu[q] = ch_mu2(qf[0][QS(r)][q], planar_combine2<ST>(f0q, p0q, q), k2);
 #pragma unroll
-                            for (int i = 0; i < V; i += 4)
-                                *reinterpret_cast<float4 *>(mu_own + i) = make_float4(mu[i], mu[i + 1], mu[i + 2], mu[i + 3]);
+                            for (int q = 0; q < V2; q += 2)
+                                *reinterpret_cast<float4 *>(mu_own + 2 * q) =
+                                    make_float4(mu[q].x, mu[q].y, mu[q + 1].x, mu[q + 1].y);
                         }
                         __syncthreads();  // mu plane j - r published
                         if (out_row && j >= 2 * r) {
                             float ext[2 * r + 1][XW];
 #pragma unroll
-                            for (int c = 0; c < V; ++c) ext[r][r + c] = mu[c];
+                            for (int q = 0; q < V2; ++q) {
+                                ext[r][r + 2 * q] = mu[q].x;
+                                ext[r][r + 2 * q + 1] = mu[q].y;
+                            }
                             extend(ext[r]);
 #pragma unroll
                             for (int dy = -r; dy <= r; ++dy) {
@@ -1341,19 +1357,21 @@ __global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT)
                                 }
                                 if constexpr (ST == L27) extend(ext[r + dy]);
                             }
-                            auto row = [&](int dy) -> const float * { return ext[r + dy]; };
-                            planar_sums<ST, V, XW>(row, qmp[QS(0)]);
+                            sums_into(ext, qmp[QS(0)]);
 #pragma unroll
-                            for (int c = 0; c < V; ++c) qm[QS(0)][c] = mu[c];
+                            for (int q = 0; q < V2; ++q) qm[QS(0)][q] = mu[q];
                             if (j >= 4 * r) {
                                 // output plane j - 2r: mu planes j - 3r .. j - r sit in mu queue
                                 // slots of iterations j - 2r .. j; phi of plane j - 2r in qf
-                                auto mf = [&](int kk) -> const float * { return qm[QS(2 * r - kk)]; };
-                                auto mp = [&](int kk) -> const float(*)[V] { return qmp[QS(2 * r - kk)]; };
+                                auto mf = [&](int kk) -> const float2 * { return qm[QS(2 * r - kk)]; };
+                                auto mp = [&](int kk) -> const float2(*)[V2] { return qmp[QS(2 * r - kk)]; };
                                 float o[V];
 #pragma unroll
-                                for (int c = 0; c < V; ++c)
-                                    o[c] = ch_update<C>(qf[0][QS(2 * r)][c], planar_combine<ST>(mf, mp, c), k);
+                                for (int q = 0; q < V2; ++q) {
+                                    const float2 o2 = ch_update2(qf[0][QS(2 * r)][q], planar_combine2<ST>(mf, mp, q), k2);
+                                    o[2 * q] = o2.x;
+                                    o[2 * q + 1] = o2.y;
+                                }
                                 if (store) store_vec<T, V>(out[0] + dst_off, o);
                                 dst_off += plane;
                             }
@@ -1362,15 +1380,20 @@ __global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT)
                         if (out_row && j >= 2 * r) {
                             float o0[V], o1[V];
 #pragma unroll
-                            for (int c = 0; c < V; ++c) {
-                                const float S0 = planar_combine<ST>(f0q, p0q, c);
-                                const float p0 = qf[0][QS(r)][c];
+                            for (int q = 0; q < V2; ++q) {
+                                const float2 S0 = planar_combine2<ST>(f0q, p0q, q);
+                                const float2 p0 = qf[0][QS(r)][q];
+                                float2 a0, a1 = make_float2(0.f, 0.f);
                                 if constexpr (MODEL == AC) {
-                                    o0[c] = ac_update<C>(p0, S0, k);
+                                    a0 = ac_update2(p0, S0, k2);
                                 } else {
-                                    gs_update<C>(p0, qf[NF - 1][QS(r)][c], S0, planar_combine<ST>(f1q, p1q, c),
-                                                 k, o0[c], o1[c]);
+                                    gs_update2(p0, qf[NF - 1][QS(r)][q], S0, planar_combine2<ST>(f1q, p1q, q), k2, a0,
+                                               a1);
                                 }
+                                o0[2 * q] = a0.x;
+                                o0[2 * q + 1] = a0.y;
+                                o1[2 * q] = a1.x;
+                                o1[2 * q + 1] = a1.y;
                             }
                             if (store) {
                                 store_vec<T, V>(out[0] + dst_off, o0);
