@@ -1185,12 +1185,19 @@ struct Step3dWrShape {
     static constexpr int NF = num_fields<MODEL>();
     static constexpr size_t plane_bytes = (size_t)HIN * 32 * CB;
     static constexpr size_t in_bytes = (size_t)(P + 1) * NF * plane_bytes;
-    static constexpr size_t mu_bytes = (MODEL == CH) ? (size_t)HIN * 32 * V * sizeof(float) : 0;
+    // Cahn-Hilliard: two mu planes (plane j - r is written while the output stage
+    // reads plane j - 1 - r), so one barrier per plane suffices
+    static constexpr size_t mu_plane = (size_t)HIN * 32 * V;
+    static constexpr size_t mu_bytes = (MODEL == CH) ? 2 * mu_plane * sizeof(float) : 0;
     static constexpr size_t smem_bytes = in_bytes + mu_bytes;
+    // resident CTAs per SM asked of the register allocator (measured on GB300:
+    // Allen-Cahn with radius-1 stencils gains from a third CTA; Cahn-Hilliard
+    // 7-point needs two; elsewhere a bound would make the queues spill)
+    static constexpr int MINB = (MODEL == AC && r == 1) ? 3 : ((MODEL == CH && ST == L7) ? 2 : 1);
 };
 
 template <int MODEL, int ST, typename T, int TY>
-__global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT)
+__global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT, Step3dWrShape<MODEL, ST, T, TY>::MINB)
     step3d_wr_kernel(StepArgs a, int tiles_x, int tiles_y, int segs) {
     static_assert(MODEL != MC, "Model C runs on the accessor-based kernels");
     typedef Step3dWrShape<MODEL, ST, T, TY> Sh;
@@ -1201,7 +1208,7 @@ __global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT)
     typedef typename VecT<CB>::type W;                                      // one chunk
     extern __shared__ __align__(16) unsigned char smem_raw[];
     W *s_in = reinterpret_cast<W *>(smem_raw);                              // [P+1][NF][HIN][32]
-    float *s_mu = reinterpret_cast<float *>(smem_raw + Sh::in_bytes);      // [HIN][32][V]
+    float *s_mu = reinterpret_cast<float *>(smem_raw + Sh::in_bytes);      // [2][HIN][32][V]
 
     const ConstsF2 k2(ConstsC<C>(a.k, a.kf));
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -1240,7 +1247,8 @@ __global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT)
         const int seg = (int)(it / tiles), tile = (int)(it - (long long)seg * tiles);
         const int z0 = (int)((long long)seg * nz / segs), z1 = (int)((long long)(seg + 1) * nz / segs);
         const int x0 = (tile % tiles_x) * Sh::TX, y0 = (tile / tiles_x) * TY;
-        const int n = (z1 - z0) + 2 * R;
+        const int n = (z1 - z0) + 2 * R;                           // planes fetched
+        const int niter = n + (MODEL == CH ? 1 : 0);              // CH: the output stage lags one plane
         const int col = x0 + (lane - 1) * V;                       // first cell of this lane's chunk
         const size_t goff = (size_t)wrap_idx(y0 - R + w, ny) * nx + wrap_idx(col, nx);
         const int yo = y0 - R + w;                                 // output row (if out_row)
@@ -1286,17 +1294,69 @@ __global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT)
                 for (int q = 0; q < V2; ++q) dst[n2][q] = make_float2(ps[n2][2 * q], ps[n2][2 * q + 1]);
         };
 
-        for (int j0 = 0; j0 < n; j0 += Q) {
+        for (int j0 = 0; j0 < niter; j0 += Q) {
 #pragma unroll
             for (int u = 0; u < Q; ++u) {
                 const int j = j0 + u;
-                if (j < n) {
+                if (j < niter) {
                     cp_async_wait<P - 1>();
-                    __syncthreads();  // plane j published; plane j-1's slot and the mu plane are free
+                    // plane j published; plane j-1's slot is free; CH: mu plane j-1-r
+                    // published and the mu buffer of plane j-2-r free
+                    __syncthreads();
                     issue();          // plane j + P into plane j-1's slot
                     const W *cur = s_own + (size_t)(j & (D - 1)) * SLOT;
 #define QS(m) ((u - (m) + 4 * Q) % Q)   /* queue slot of plane j - m */
-                    if ((MODEL == CH && mu_row) || (MODEL != CH && out_row)) {
+                    if constexpr (MODEL == CH) {
+                        // output stage on mu plane j - 1 - r (written in the previous
+                        // iteration, published by this iteration's barrier); it runs
+                        // first because phi of its output plane j - 1 - 2r and the mu
+                        // of plane j - 1 - 3r sit in the queue slots that plane j and
+                        // mu plane j - r take below
+                        if (out_row && j >= 2 * r + 1) {
+                            const float2 *mu = qm[QS(1)];
+                            const float *mu_prev = mu_own + (size_t)((j - 1) & 1) * Sh::mu_plane;
+                            float ext[2 * r + 1][XW];
+#pragma unroll
+                            for (int q = 0; q < V2; ++q) {
+                                ext[r][r + 2 * q] = mu[q].x;
+                                ext[r][r + 2 * q + 1] = mu[q].y;
+                            }
+                            extend(ext[r]);
+#pragma unroll
+                            for (int dy = -r; dy <= r; ++dy) {
+                                if (dy == 0) continue;
+                                const float *src_mu = mu_prev + dy * 32 * V;
+#pragma unroll
+                                for (int i = 0; i < V; i += 4) {
+                                    const float4 v4 = *reinterpret_cast<const float4 *>(src_mu + i);
+                                    ext[r + dy][r + i] = v4.x;
+                                    ext[r + dy][r + i + 1] = v4.y;
+                                    ext[r + dy][r + i + 2] = v4.z;
+                                    ext[r + dy][r + i + 3] = v4.w;
+                                }
+                                if constexpr (ST == L27) extend(ext[r + dy]);
+                            }
+                            sums_into(ext, qmp[QS(0)]);
+                            if (j >= 4 * r + 1) {
+                                // output plane j - 1 - 2r: mu planes j - 1 - 3r .. j - 1 - r in mu
+                                // queue slots of iterations j - 2r - 1 .. j - 1 (values) and
+                                // j - 2r .. j (partial sums); its phi in the slot of iteration j - 1 - 2r
+                                auto mf = [&](int kk) -> const float2 * { return qm[QS(2 * r + 1 - kk)]; };
+                                auto mp = [&](int kk) -> const float2(*)[V2] { return qmp[QS(2 * r - kk)]; };
+                                float o[V];
+#pragma unroll
+                                for (int q = 0; q < V2; ++q) {
+                                    const float2 o2 =
+                                        ch_update2(qf[0][QS(2 * r + 1)][q], planar_combine2<ST>(mf, mp, q), k2);
+                                    o[2 * q] = o2.x;
+                                    o[2 * q + 1] = o2.y;
+                                }
+                                if (store) store_vec<T, V>(out[0] + dst_off, o);
+                                dst_off += plane;
+                            }
+                        }
+                    }
+                    if (j < n && ((MODEL == CH && mu_row) || (MODEL != CH && out_row))) {
 #pragma unroll
                         for (int f = 0; f < NF; ++f) {
                             float ext[2 * r + 1][XW];
@@ -1324,57 +1384,17 @@ __global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT)
                     auto p1q = [&](int kk) -> const float2(*)[V2] { return qp[NF - 1][QS(2 * r - kk)]; };
                     (void)f1q; (void)p1q;
                     if constexpr (MODEL == CH) {
-                        float2 mu[V2];
-                        if (mu_row && j >= 2 * r) {
+                        // mu of plane j - r into the queue and the mu buffer of this iteration
+                        if (mu_row && j >= 2 * r && j < n) {
+                            float2 *mu = qm[QS(0)];
 #pragma unroll
                             for (int q = 0; q < V2; ++q)
                                 mu[q] = ch_mu2(qf[0][QS(r)][q], planar_combine2<ST>(f0q, p0q, q), k2);
+                            float *dst_mu = mu_own + (size_t)(j & 1) * Sh::mu_plane;
 #pragma unroll
                             for (int q = 0; q < V2; q += 2)
-                                *reinterpret_cast<float4 *>(mu_own + 2 * q) =
+                                *reinterpret_cast<float4 *>(dst_mu + 2 * q) =
                                     make_float4(mu[q].x, mu[q].y, mu[q + 1].x, mu[q + 1].y);
-                        }
-                        __syncthreads();  // mu plane j - r published
-                        if (out_row && j >= 2 * r) {
-                            float ext[2 * r + 1][XW];
-#pragma unroll
-                            for (int q = 0; q < V2; ++q) {
-                                ext[r][r + 2 * q] = mu[q].x;
-                                ext[r][r + 2 * q + 1] = mu[q].y;
-                            }
-                            extend(ext[r]);
-#pragma unroll
-                            for (int dy = -r; dy <= r; ++dy) {
-                                if (dy == 0) continue;
-                                const float *src_mu = mu_own + dy * 32 * V;
-#pragma unroll
-                                for (int i = 0; i < V; i += 4) {
-                                    const float4 v4 = *reinterpret_cast<const float4 *>(src_mu + i);
-                                    ext[r + dy][r + i] = v4.x;
-                                    ext[r + dy][r + i + 1] = v4.y;
-                                    ext[r + dy][r + i + 2] = v4.z;
-                                    ext[r + dy][r + i + 3] = v4.w;
-                                }
-                                if constexpr (ST == L27) extend(ext[r + dy]);
-                            }
-                            sums_into(ext, qmp[QS(0)]);
-#pragma unroll
-                            for (int q = 0; q < V2; ++q) qm[QS(0)][q] = mu[q];
-                            if (j >= 4 * r) {
-                                // output plane j - 2r: mu planes j - 3r .. j - r sit in mu queue
-                                // slots of iterations j - 2r .. j; phi of plane j - 2r in qf
-                                auto mf = [&](int kk) -> const float2 * { return qm[QS(2 * r - kk)]; };
-                                auto mp = [&](int kk) -> const float2(*)[V2] { return qmp[QS(2 * r - kk)]; };
-                                float o[V];
-#pragma unroll
-                                for (int q = 0; q < V2; ++q) {
-                                    const float2 o2 = ch_update2(qf[0][QS(2 * r)][q], planar_combine2<ST>(mf, mp, q), k2);
-                                    o[2 * q] = o2.x;
-                                    o[2 * q + 1] = o2.y;
-                                }
-                                if (store) store_vec<T, V>(out[0] + dst_off, o);
-                                dst_off += plane;
-                            }
                         }
                     } else {
                         if (out_row && j >= 2 * r) {
