@@ -219,6 +219,133 @@ __global__ void __launch_bounds__(NT) mh_tile2d_kernel(MhArgs a, typename Cmp<T>
     }
 }
 
+// 3D FP32 / BF16: xy tiles streamed along z.  Each loaded plane (tile plus a 2R
+// halo, all four fields, widened to FP32) enters a ring of D = 3R + 2 planes in
+// shared memory; mu of plane i - R (tile grown by R) goes to a ring of 2R + 1
+// planes; the update of plane i - 2R then reads m and j on planes i - 3R .. i - R
+// and mu from the rings.  The ring depth keeps the plane committed at iteration i
+// clear of every plane a thread still in iteration i - 1 may read.  Persistent
+// grid: CTA c owns an equal share of the flattened (tile, z) space.  The same
+// expressions as the per-point kernels, so the results are identical to theirs.
+template <int ST, typename T, int TX, int TY>
+struct MhRing3dShape {
+    static constexpr int R = StencilInfo<ST>::r;
+    static constexpr int RIN = 2 * R;
+    static constexpr int WIN = TX + 2 * RIN, HIN = TY + 2 * RIN, AIN = WIN * HIN;
+    static constexpr int D = 3 * R + 2;
+    static constexpr int NF = 4;  // m, j_x, j_y, j_z
+    static constexpr int WMU = TX + 2 * R, HMU = TY + 2 * R, AMU = WMU * HMU, DMU = 2 * R + 1;
+    static constexpr size_t smem_bytes = sizeof(float) * ((size_t)NF * D * AIN + (size_t)DMU * AMU);
+};
+
+template <int ST, typename T, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT) mh_ring3d_kernel(MhArgs a, float c3g, int tiles_x, int tiles_y,
+                                                      long long planes_per_cta) {
+    typedef float C;
+    typedef MhRing3dShape<ST, T, TX, TY> Sh;
+    constexpr int R = Sh::R, RIN = Sh::RIN, WIN = Sh::WIN, HIN = Sh::HIN, AIN = Sh::AIN, D = Sh::D, NF = Sh::NF;
+    constexpr int WMU = Sh::WMU, AMU = Sh::AMU, DMU = Sh::DMU;
+    constexpr int EPT = (AIN + NT - 1) / NT;  // loaded cells per thread per field
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *s_in = reinterpret_cast<C *>(smem_raw);  // [NF][D][AIN]
+    C *s_mu = s_in + (size_t)NF * D * AIN;      // [DMU][AMU]
+    const ConstsC<C> k(a.k, a.kf);
+    const int nx = a.nx, ny = a.ny, nz = a.nz, t = threadIdx.x;
+    const size_t plane = (size_t)nx * (size_t)ny;
+    const T *in[NF] = {static_cast<const T *>(a.m), static_cast<const T *>(a.j[0]), static_cast<const T *>(a.j[1]),
+                       static_cast<const T *>(a.j[2])};
+    T *out[NF] = {static_cast<T *>(a.mo), static_cast<T *>(a.jo[0]), static_cast<T *>(a.jo[1]),
+                  static_cast<T *>(a.jo[2])};
+    auto S_in = [&](int f, int i) -> const C * { return s_in + ((size_t)f * D + (i % D)) * AIN; };
+
+    long long g0 = (long long)blockIdx.x * planes_per_cta;
+    const long long gend = min(g0 + planes_per_cta, (long long)tiles_x * tiles_y * nz);
+    while (g0 < gend) {
+        const int tile = (int)(g0 / nz);
+        const int z0 = (int)(g0 - (long long)tile * nz);
+        const int z1 = (int)min((long long)nz, (long long)z0 + (gend - g0));
+        g0 += z1 - z0;
+        const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+        const int nplanes = (z1 - z0) + 2 * RIN;  // loaded plane i is z = z0 - RIN + i
+
+        int loff[EPT];
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            const int c = t + e * NT;
+            if (c < AIN) {
+                const int yi = c / WIN, xi = c - yi * WIN;
+                loff[e] = wrap_idx(y0 - RIN + yi, ny) * nx + wrap_idx(x0 - RIN + xi, nx);
+            } else {
+                loff[e] = -1;
+            }
+        }
+        C pf[NF][EPT];
+        auto fetch = [&](int i) {
+            const size_t zoff = (size_t)wrap_idx(z0 - RIN + i, nz) * plane;
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+#pragma unroll
+                for (int e = 0; e < EPT; ++e)
+                    if (loff[e] >= 0) pf[f][e] = to_c(in[f][zoff + loff[e]]);
+        };
+        auto commit = [&](int i) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+#pragma unroll
+                for (int e = 0; e < EPT; ++e)
+                    if (loff[e] >= 0) s_in[((size_t)f * D + (i % D)) * AIN + t + e * NT] = pf[f][e];
+        };
+
+        fetch(0);
+        for (int i = 0; i < nplanes; ++i) {
+            commit(i);
+            if (i + 1 < nplanes) fetch(i + 1);
+            __syncthreads();
+            if (i >= 2 * R) {
+                // mu of plane i - R over the tile grown by R
+                C *mu = s_mu + (size_t)((i - R) % DMU) * AMU;
+                for (int c = t; c < AMU; c += NT) {
+                    const int ym = c / WMU, xm = c - ym * WMU;
+                    const int base = (ym + R) * WIN + (xm + R);
+                    auto P = [&](int dx, int dy, int dz) -> C { return S_in(0, i - R + dz)[base + dy * WIN + dx]; };
+                    mu[c] = ch_mu<C>(S_in(0, i - R)[base], stencil_sum<ST, C>(P), k);
+                }
+            }
+            __syncthreads();
+            if (i >= 4 * R) {
+                const int o = i - 2 * R;  // loaded index of the output plane
+                const size_t zo = (size_t)(z0 + o - RIN) * plane;
+                for (int c = t; c < TX * TY; c += NT) {
+                    const int yy = c / TX, xx = c - yy * TX;
+                    const int x = x0 + xx, y = y0 + yy;
+                    if (x >= nx || y >= ny) continue;
+                    const int b = (yy + RIN) * WIN + xx + RIN;
+                    const int mb = (yy + R) * WMU + (xx + R);
+                    auto Pmu = [&](int dx, int dy, int dz) -> C {
+                        return s_mu[(size_t)((o + dz) % DMU) * AMU + mb + dy * WMU + dx];
+                    };
+                    auto fld = [&](int f, int dx, int dy, int dz) -> C { return S_in(f, o + dz)[b + dy * WIN + dx]; };
+                    auto flux = [&](int ax) {
+                        return [&, ax](int dx, int dy, int dz) -> C { return fld(0, dx, dy, dz) * fld(1 + ax, dx, dy, dz); };
+                    };
+                    const C div = (central<R, 0>(flux(0)) + central<R, 1>(flux(1))) + central<R, 2>(flux(2));
+                    const C mi = fld(0, 0, 0, 0);
+                    const size_t oi = zo + (size_t)y * nx + x;
+                    out[0][oi] = from_c<T>(FMA(k.dt, FMA(k.sAC, stencil_sum<ST, C>(Pmu), -(c3g * div)), mi));
+#pragma unroll
+                    for (int ax = 0; ax < 3; ++ax) {
+                        const C gm = (ax == 0) ? central<R, 0>(Pmu) : (ax == 1 ? central<R, 1>(Pmu) : central<R, 2>(Pmu));
+                        auto Pj = [&](int dx, int dy, int dz) -> C { return fld(1 + ax, dx, dy, dz); };
+                        out[1 + ax][oi] =
+                            from_c<T>(FMA(k.dt, FMA(k.sAC, stencil_sum<ST, C>(Pj), -(c3g * (mi * gm))), fld(1 + ax, 0, 0, 0)));
+                    }
+                }
+            }
+        }
+        __syncthreads();  // the rings are reused by the next segment
+    }
+}
+
 template <int ST, typename T>
 static cudaError_t launch_mh_t(const MhArgs &a, double c3g, cudaStream_t s, int n_sm) {
     typedef typename Cmp<T>::type C;
@@ -234,6 +361,28 @@ static cudaError_t launch_mh_t(const MhArgs &a, double c3g, cudaStream_t s, int 
             }();
             (void)attr;
             kern<<<dim3((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY), NT, Sh::smem_bytes, s>>>(a, (C)c3g);
+            return cudaGetLastError();
+        }
+    }
+    if constexpr (StencilInfo<ST>::dims == 3 && !std::is_same<T, double>::value) {
+        // family 0: z-streaming tiles; family 1: the two per-point passes
+        if (g_step_variant != 1) {
+            constexpr int TX = 32, TY = 16, NT = 256;
+            typedef MhRing3dShape<ST, T, TX, TY> Sh;
+            auto kern = mh_ring3d_kernel<ST, T, TX, TY, NT>;
+            static const int occ = [&] {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem_bytes);
+                int o = 1;
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT, Sh::smem_bytes);
+                return o;
+            }();
+            const int tx = (a.nx + TX - 1) / TX, ty = (a.ny + TY - 1) / TY;
+            const long long total = (long long)tx * ty * a.nz;
+            // one resident wave, at least 32 planes per CTA so that the ring warm-up stays small
+            long long ctas = std::max(1LL, std::min((long long)n_sm * std::max(occ, 1), total / 32));
+            const long long per = (total + ctas - 1) / ctas;
+            ctas = (total + per - 1) / per;
+            kern<<<(unsigned)ctas, NT, Sh::smem_bytes, s>>>(a, (C)c3g, tx, ty, per);
             return cudaGetLastError();
         }
     }

@@ -741,10 +741,11 @@ extern "C" int sp_set_launch_config(sp_sim *s, int steps_per_launch, int variant
         set_launch_config(s, {steps_per_launch, variant});
         return SP_OK;
     }
-    // generated stencils and Model H, 2D FP32 / BF16: the per-point kernels
-    // instead of tiles
-    if (steps_per_launch == 1 && variant == 1 && (s->stencil == SP_LAP_GENERATED || s->model == SP_MODEL_H) &&
-        s->dims == 2 && s->dtype != SP_F64 && !s->spec) {
+    // generated stencils (2D) and Model H (2D and 3D), FP32 / BF16: the
+    // per-point kernels instead of tiles
+    if (steps_per_launch == 1 && variant == 1 &&
+        ((s->stencil == SP_LAP_GENERATED && s->dims == 2) || s->model == SP_MODEL_H) && s->dtype != SP_F64 &&
+        !s->spec) {
         s->tune_pending = false;
         set_launch_config(s, {1, 1});
         return SP_OK;
