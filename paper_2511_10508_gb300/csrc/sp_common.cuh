@@ -270,6 +270,18 @@ __device__ __forceinline__ void two_field_update(C p0, C p1, C S0, C S1, const C
     else gs_update<C>(p0, p1, S0, S1, k, o0, o1);
 }
 
+// --------------------------------------- programmatic dependent launch --
+//
+// A step kernel launched with programmatic stream serialisation may be launched
+// as soon as every CTA of the previous kernel in the stream has exited, before
+// that grid has completed and flushed; it waits, before its first global-memory
+// access, until its predecessor has completed and its writes are visible
+// (griddepcontrol.wait, sm_90 and later).  Without that launch attribute the
+// wait is a no-op, so every launch path may use these kernels.  (Triggering the
+// dependents at the start of the kernel instead measured slower on GB300: the
+// waiting CTAs of the next grid took issue slots and SM space.)
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ------------------------------------------------- packed FP32 pairs --
 //
 // Two cells per instruction (f32x2 arithmetic of sm_100 and later): each lane

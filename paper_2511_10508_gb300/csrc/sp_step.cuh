@@ -323,6 +323,7 @@ __device__ __forceinline__ void tile2d(const T *in0, const T *in1, T *out0, T *o
 template <int MODEL, int ST, typename T, int BX, int BY, int NT>
 __global__ void __launch_bounds__(NT) step2d_tile_kernel(StepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_enter();
     const ConstsC<typename Cmp<T>::type> k(a.k, a.kf);
     tile2d<MODEL, ST, T, BX, BY, NT>(static_cast<const T *>(a.in0), static_cast<const T *>(a.in1),
                                      static_cast<T *>(a.out0), static_cast<T *>(a.out1), a.nx, a.ny, k,
@@ -369,6 +370,7 @@ __global__ void __launch_bounds__(NT) step2d_tb_kernel(StepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);                  // [2 levels][NF][HIN][SW]
     C *s_mu = reinterpret_cast<C *>(smem_raw + Sh::bytes_in);  // [HMU][WMU]
+    pdl_enter();
     const ConstsC<C> k(a.k, a.kf);
     const int nx = a.nx, ny = a.ny;
     const int t = threadIdx.x;

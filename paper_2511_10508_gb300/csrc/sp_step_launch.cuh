@@ -54,6 +54,25 @@ inline int lockstep_segments(long long tiles, int nz, int halo, long long wave) 
     return best;
 }
 
+// Launch with programmatic stream serialisation (the kernel calls pdl_enter()
+// before touching global memory): used where a launch is a few microseconds
+// long, so that the next step's CTAs are resident when this one completes.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Batched persistent 2D kernel (FP64): rows per batch and CTAs per SM.
 template <int MODEL> struct Batch2d { static constexpr int NT = 128, RB = (MODEL == CH) ? 8 : (MODEL == AC ? 4 : 2), CPS = 4; };
 
@@ -95,6 +114,7 @@ cudaError_t launch_tb(const StepArgs &a, cudaStream_t s) {
     }();
     (void)attr;
     dim3 grid((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY);
+    if constexpr (f64) return launch_pdl(kern, grid, dim3(NT), Sh::smem_bytes, s, a);  // small grids
     kern<<<grid, NT, Sh::smem_bytes, s>>>(a);
     return cudaGetLastError();
 }
@@ -137,8 +157,7 @@ cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
                 return true;
             }();
             (void)attr;
-            kern<<<dim3((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY), NT, Sh::smem_bytes, s>>>(a);
-            return cudaGetLastError();
+            return launch_pdl(kern, dim3((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY), dim3(NT), Sh::smem_bytes, s, a);
         }
         // strip families: 0 the default shape, 2 narrower CTAs (64 threads), 4 half
         // the rows per batch; the autotuner picks per grid
