@@ -320,6 +320,30 @@ __device__ __forceinline__ void gs_update2(float2 u, float2 v, float2 Su, float2
     vn = fma2(k.dt, rv, v);
 }
 
+// S of the 2D stencils for the pair of cells (c0, c0 + 1), the fixed order of
+// stencil_sum: the x-direction pair sums are formed per cell (the shifted
+// neighbours are not register pairs), everything else two cells per
+// instruction.  P(dx, dy, c) is the value at offset (dx, dy) of cell c.
+template <int ST, typename Acc>
+__device__ __forceinline__ float2 stencil_sum2_2d(const Acc &P, int c0) {
+    const int c1 = c0 + 1;
+    auto pr = [&](int dx, int dy) { return make_float2(P(dx, dy, c0), P(dx, dy, c1)); };
+    auto xs = [&](int d, int dy) {
+        return make_float2(P(-d, dy, c0) + P(d, dy, c0), P(-d, dy, c1) + P(d, dy, c1));
+    };
+    if constexpr (ST == L5) {
+        return fma2(splat2(-4.f), pr(0, 0), add2(xs(1, 0), add2(pr(0, -1), pr(0, 1))));
+    } else if constexpr (ST == L9BOX) {
+        const float2 Cs = add2(xs(1, 0), add2(pr(0, -1), pr(0, 1)));
+        const float2 D = add2(xs(1, -1), xs(1, 1));
+        return fma2(splat2(-20.f), pr(0, 0), fma2(splat2(4.f), Cs, D));
+    } else {  // L9X4
+        const float2 F1 = add2(xs(1, 0), add2(pr(0, -1), pr(0, 1)));
+        const float2 F2 = add2(xs(2, 0), add2(pr(0, -2), pr(0, 2)));
+        return fma2(splat2(-60.f), pr(0, 0), fma2(splat2(16.f), F1, neg2(F2)));
+    }
+}
+
 // ------------------------------------------------------- launch records --
 
 struct StepArgs {
