@@ -268,6 +268,14 @@ int sp_set_launch_config(sp_sim *sim, int steps_per_launch, int variant);
  * dims not 2 or 3. */
 int sp_stencil_weights(int order, int dims, double *w, double *lambda_max);
 
+/* Measurement aid (no counterpart in the paper): the sustained FP64 fused
+ * multiply-add rate of the current device in Gop/s (one operation per FMA),
+ * from a kernel of independent FMA chains on every SM timed with CUDA events on
+ * `stream` (about 10 ms; the first launch warms up).  FP64 step kernels are
+ * bound by this rate.  Blocks until done; allocates 8 bytes of device memory.
+ * SP_EINVAL if gops is NULL, SP_ENOMEM / SP_ECUDA on failure. */
+int sp_probe_fp64_rate(void *stream, double *gops);
+
 /* Launch configuration in use: steps fused per launch and kernel family
  * (0 = the default for the grid; alternatives the autotuner may pick: 1 for
  * every grid of the finite-difference scheme except 3D FP64 with the 7/13/

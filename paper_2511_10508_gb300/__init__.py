@@ -57,6 +57,13 @@ def check_stability(model: int, dims: int, h: float, dt: float, prm: N.sp_params
     return rc == N.SP_OK, f.value
 
 
+def probe_fp64_rate(stream=None) -> float:
+    """Sustained FP64 FMA rate of the current device in Gop/s (sp_probe_fp64_rate)."""
+    g = ctypes.c_double(0.0)
+    N.check(N.lib().sp_probe_fp64_rate(_stream_ptr(stream), ctypes.byref(g)), "sp_probe_fp64_rate")
+    return g.value
+
+
 def _stream_ptr(stream) -> int | None:
     if stream is None:
         return None

@@ -620,3 +620,11 @@ def test_model_c_free_energy_decreases_on_gpu(sp):
             sim.step(2)
             F.append(sim.reduce(sp.FREE_ENERGY))
     assert all(b < a for a, b in zip(F, F[1:])), F
+
+
+def test_fp64_probe_rate(sp):
+    """The FP64 throughput probe returns a plausible sustained rate (Gop/s, one op per
+    FMA): below the nominal 2 FP64 ops per clock per SM at the maximum clock and far
+    above a serial rate."""
+    g = sp.probe_fp64_rate()
+    assert 100.0 < g <= 152 * 2 * 2.07 * 1.02
