@@ -1,6 +1,10 @@
 """Parity at the benchmark configurations' full sizes, in the launch configuration
-that bench.py times (library defaults: persistent kernels, graph replay, FP32
-Gray-Scott with two steps per launch).
+that bench.py times: bench.py autotunes, so the long runs here autotune too
+(SP_FLAG_AUTOTUNE: the tuner's timed steps are ordinary steps of the run, and every
+candidate it times is checked along the way), and the short sampled runs pin the
+kernel family the autotuner picks for that workload on GB300 (all families are bit
+for bit identical, which other tests check).  Graph replay and persistent kernels as
+in the library's defaults.
 
 Where the oracle finishes in seconds to about a minute the whole run is compared
 (256^2 Allen-Cahn x 1000 steps, 4096^2 Cahn-Hilliard x 10000 steps, 2048^2
@@ -90,10 +94,10 @@ def test_allen_cahn_256_full_run(sp):
     shape, dt = (256, 256), 0.05
     ic = O.initial_condition(O.AC, shape, seed=0, amp=0.1)
     ref = O.step(O.AC, O.S1, ic, dt=dt, nsteps=1000)
-    with sp.Simulation(sp.ALLEN_CAHN, shape, dt=dt, seed=0, ic_amp=0.1) as s:
+    with sp.Simulation(sp.ALLEN_CAHN, shape, dt=dt, seed=0, ic_amp=0.1, flags=sp.FLAG_AUTOTUNE) as s:
         s.step(1000)
         assert np.array_equal(s.read(0), ref)
-    with sp.Simulation(sp.ALLEN_CAHN, shape, dt=dt, seed=0, ic_amp=0.1, dtype=sp.F32) as s:
+    with sp.Simulation(sp.ALLEN_CAHN, shape, dt=dt, seed=0, ic_amp=0.1, dtype=sp.F32, flags=sp.FLAG_AUTOTUNE) as s:
         s.step(1000)
         e = O.rel_l2(s.read(0), ref)
     assert e < 1e-5, e  # FP32 storage: measured ~1e-7
@@ -105,7 +109,7 @@ def test_cahn_hilliard_4096_lap5_full_run(sp):
     shape, dt, n = (4096, 4096), 0.01, 10000
     ic = O.initial_condition(O.CH, shape, seed=1, amp=0.01)
     ref = O.step(O.CH, O.S1, ic, dt=dt, nsteps=n)
-    with sp.Simulation(sp.CAHN_HILLIARD, shape, dt=dt, seed=1, ic_amp=0.01) as s:
+    with sp.Simulation(sp.CAHN_HILLIARD, shape, dt=dt, seed=1, ic_amp=0.01, flags=sp.FLAG_AUTOTUNE) as s:
         m0 = s.reduce(sp.MASS)
         s.step(n)
         got = s.read(0)
@@ -118,6 +122,7 @@ def test_cahn_hilliard_4096_lap5_full_run(sp):
 def test_cahn_hilliard_4096_lap9x4_sampled(sp):
     shape, dt, n = (4096, 4096), 0.01, 5
     with sp.Simulation(sp.CAHN_HILLIARD, shape, dt=dt, seed=1, ic_amp=0.01, stencil=sp.LAP_9CROSS4) as s:
+        s.launch_config = (1, 2)  # the autotuner's choice for this workload (64-thread strips)
         s.step(n)
         check_windows(s, O.CH, O.S3, shape, dt, n, dict(seed=1, amp=0.01), O.params(),
                       sample_points(shape, 24, 11), exact=True)
@@ -141,6 +146,9 @@ def test_gray_scott_32768_sampled(sp, dtype):
     kw = dict(seed=2, ic_amp=0.01, gs_patches=64, gs_patch=20, dtype=dtype)
     pts = sample_points(shape, 16, 12, extra=gs_patch_centres(shape, 2, 8))
     with sp.Simulation(sp.GRAY_SCOTT, shape, dt=dt, **kw) as s:
+        # the autotuner's choices: FP64 the 32x16 tile kernel (family 1 on a grid this size),
+        # FP32 two steps per launch
+        s.launch_config = (1, 1) if dtype == 0 else (2, 0)
         s.step(n)
         check_windows(s, O.GS, O.S1, shape, dt, n, dict(seed=2, amp=0.01, patches=64, patch=20),
                       O.params(**GS_PRM), pts, exact=(dtype == 0), atol=2e-6)
@@ -151,7 +159,8 @@ def test_gray_scott_2048_full_run(sp):
     shape, dt, n = (2048, 2048), 1.0, 5000
     u, v = O.initial_condition(O.GS, shape, seed=2, amp=0.01, patches=16, patch=20)
     ru, rv = O.step(O.GS, O.S1, u, v, dt=dt, prm=O.params(**GS_PRM), nsteps=n)
-    with sp.Simulation(sp.GRAY_SCOTT, shape, dt=dt, seed=2, ic_amp=0.01, gs_patches=16, gs_patch=20) as s:
+    with sp.Simulation(sp.GRAY_SCOTT, shape, dt=dt, seed=2, ic_amp=0.01, gs_patches=16, gs_patch=20,
+                       flags=sp.FLAG_AUTOTUNE) as s:
         s.step(n)
         assert np.array_equal(s.read(0), ru) and np.array_equal(s.read(1), rv)
 
@@ -171,7 +180,8 @@ def test_cahn_hilliard_128_cubed_full_run(sp, st):
     ref = O.step(O.CH, st, ic, dt=dt, nsteps=n)
     errs = {}
     for dtype in (0, 1, 2):
-        with sp.Simulation(sp.CAHN_HILLIARD, shape, dt=dt, seed=3, ic_amp=0.01, stencil=st, dtype=dtype) as s:
+        with sp.Simulation(sp.CAHN_HILLIARD, shape, dt=dt, seed=3, ic_amp=0.01, stencil=st, dtype=dtype,
+                           flags=sp.FLAG_AUTOTUNE) as s:
             s.step(n)
             got = s.read(0)
         if dtype == 0:
