@@ -218,6 +218,26 @@ __global__ void __launch_bounds__(256) gen_step_kernel(GenArgs g, int segs) {
     }
 }
 
+// Stencil sums of RY cells of one column (rows i0 .. i0+RY-1, column j) of the
+// field read by Vf(i, j): the column's values on rows i0-R .. i0+RY-1+R are read
+// once into registers (rows outside [lo, hi] are clamped there: their sums are
+// not used), the x taps per cell.  Each sum is gen_sum's, with the same taps in
+// the same order.
+template <int R, int RY, typename Val>
+__device__ __forceinline__ void gen_column_sums(const Val &Vf, int i0, int j, int lo, int hi, const GenW &W,
+                                                float (&S)[RY], float (&ctr)[RY]) {
+    float col[RY + 2 * R];
+#pragma unroll
+    for (int a = 0; a < RY + 2 * R; ++a) col[a] = Vf(min(max(i0 - R + a, lo), hi), j);
+#pragma unroll
+    for (int b = 0; b < RY; ++b) {
+        const int i = min(max(i0 + b, lo), hi);
+        auto P = [&](int dx, int dy, int) -> float { return dx == 0 ? col[b + R + dy] : Vf(i, j + dx); };
+        S[b] = gen_sum<R, 2, float>(P, W);
+        ctr[b] = col[b + R];
+    }
+}
+
 // 2D tiles (FP32 / BF16 storage): one BX x BY output tile per CTA; the tile and
 // its halo (2R for Cahn-Hilliard, whose mu is evaluated on the tile grown by R,
 // else R; x padded to whole 16-byte chunks) are fetched once into shared
@@ -279,39 +299,66 @@ __global__ void __launch_bounds__(NT) gen_tile2d_kernel(GenArgs g) {
 
     // value of field f at tile coordinates (i, j), -RIN <= i < BY + RIN, -X0 <= j < BX + X0
     auto phi = [&](int f, int i, int j) -> C { return to_c(s_in[((size_t)f * HIN + i + RIN) * SW + j + X0]); };
+    // Each work item is a column of RY cells (register-blocked along y, see
+    // gen_column_sums); consecutive threads take consecutive columns.
+    constexpr int RY = 8;
     if constexpr (MODEL == CH) {
-        for (int q = t; q < HMU * WMU; q += NT) {
-            const int i = q / WMU - R, j = q % WMU - R;
-            auto P = [&](int dx, int dy, int) -> C { return phi(0, i + dy, j + dx); };
-            s_mu[q] = ch_mu<C>(phi(0, i, j), gen_sum<R, 2, C>(P, g.W), k);
+        constexpr int NB = (HMU + RY - 1) / RY;  // row blocks of the mu region
+        auto phi0 = [&](int i, int j) -> C { return phi(0, i, j); };
+        for (int q = t; q < NB * WMU; q += NT) {
+            const int b = q / WMU, j = q - b * WMU - R;
+            const int i0 = b * RY - R;
+            float S[RY], p[RY];
+            gen_column_sums<R, RY>(phi0, i0, j, -RIN, BY + RIN - 1, g.W, S, p);
+#pragma unroll
+            for (int c = 0; c < RY; ++c)
+                if (i0 + c < BY + R) s_mu[(i0 + c + R) * WMU + (j + R)] = ch_mu<C>(p[c], S[c], k);
         }
         __syncthreads();
     }
-    for (int q = t; q < BY * BX; q += NT) {
-        const int i = q / BX, j = q - i * BX;
-        const int y = y0 + i, x = x0 + j;
-        if (y >= ny || x >= nx) continue;
-        const size_t o = (size_t)y * (size_t)nx + x;
+    constexpr int NBO = (BY + RY - 1) / RY;  // row blocks of the output tile
+    for (int q = t; q < NBO * BX; q += NT) {
+        const int b = q / BX, j = q - b * BX;
+        const int i0 = b * RY;
+        const int x = x0 + j;
+        float o0[RY], o1[RY];
         if constexpr (MODEL == CH) {
-            auto Pm = [&](int dx, int dy, int) -> C { return s_mu[(i + R + dy) * WMU + (j + R + dx)]; };
-            out[0][o] = from_c<T>(ch_update<C>(phi(0, i, j), gen_sum<R, 2, C>(Pm, g.W), k));
+            auto mu = [&](int i, int jj) -> C { return s_mu[(i + R) * WMU + (jj + R)]; };
+            float S[RY], dummy[RY];
+            gen_column_sums<R, RY>(mu, i0, j, -R, BY + R - 1, g.W, S, dummy);
+#pragma unroll
+            for (int c = 0; c < RY; ++c) o0[c] = ch_update<C>(phi(0, min(i0 + c, BY - 1), j), S[c], k);
         } else {
-            auto P0 = [&](int dx, int dy, int) -> C { return phi(0, i + dy, j + dx); };
+            auto phi0 = [&](int i, int jj) -> C { return phi(0, i, jj); };
+            float S0[RY], p0[RY];
+            gen_column_sums<R, RY>(phi0, i0, j, -RIN, BY + RIN - 1, g.W, S0, p0);
             if constexpr (MODEL == AC) {
-                out[0][o] = from_c<T>(ac_update<C>(phi(0, i, j), gen_sum<R, 2, C>(P0, g.W), k));
+#pragma unroll
+                for (int c = 0; c < RY; ++c) o0[c] = ac_update<C>(p0[c], S0[c], k);
             } else {
-                auto P1 = [&](int dx, int dy, int) -> C { return phi(NF - 1, i + dy, j + dx); };
-                C S1;
+                float S1[RY], p1[RY];
                 if constexpr (MODEL == MC) {
-                    auto Pm = [&](int dx, int dy, int dz) -> C { return mc_mu<C>(P0(dx, dy, dz), P1(dx, dy, dz), k); };
-                    S1 = gen_sum<R, 2, C>(Pm, g.W);
+                    auto m = [&](int i, int jj) -> C { return mc_mu<C>(phi(0, i, jj), phi(NF - 1, i, jj), k); };
+                    gen_column_sums<R, RY>(m, i0, j, -RIN, BY + RIN - 1, g.W, S1, p1);
                 } else {
-                    S1 = gen_sum<R, 2, C>(P1, g.W);
+                    auto phi1 = [&](int i, int jj) -> C { return phi(NF - 1, i, jj); };
+                    gen_column_sums<R, RY>(phi1, i0, j, -RIN, BY + RIN - 1, g.W, S1, p1);
                 }
-                C a0, a1;
-                two_field_update<MODEL, C>(phi(0, i, j), phi(NF - 1, i, j), gen_sum<R, 2, C>(P0, g.W), S1, k, a0, a1);
-                out[0][o] = from_c<T>(a0);
-                out[NF - 1][o] = from_c<T>(a1);
+#pragma unroll
+                for (int c = 0; c < RY; ++c)
+                    two_field_update<MODEL, C>(p0[c], phi(NF - 1, min(i0 + c, BY - 1), j), S0[c], S1[c], k, o0[c],
+                                               o1[c]);
+            }
+        }
+        if (x < nx) {
+#pragma unroll
+            for (int c = 0; c < RY; ++c) {
+                const int y = y0 + i0 + c;
+                if (i0 + c < BY && y < ny) {
+                    const size_t o = (size_t)y * (size_t)nx + x;
+                    out[0][o] = from_c<T>(o0[c]);
+                    if constexpr (NF == 2) out[NF - 1][o] = from_c<T>(o1[c]);
+                }
             }
         }
     }
