@@ -1,5 +1,6 @@
 // sp_step.cuh -- fused explicit time-step kernels (one forward-Euler step per
-// launch) for Allen-Cahn, Cahn-Hilliard and Gray-Scott on periodic grids.
+// launch, or K steps for the temporally blocked 2D tiles) for Allen-Cahn,
+// Cahn-Hilliard, Gray-Scott and Model C on periodic grids.
 //
 // One pass per step (the paper, Sec. "Benchmarks", stores phi^3 in a temporary
 // field for conserved dynamics; here the chemical potential never leaves the
@@ -7,7 +8,9 @@
 // 3D) and keeps the slices it still needs on chip, so HBM traffic per point and
 // step is one read and one write of each field:
 //   step2d_batch_kernel  2D, FP64: shared-memory rings, batches of rows
-//   step2d_tile_kernel   2D, FP32/BF16: one CTA per tile, tile + halo fetched with cp.async
+//   step2d_tile_kernel   2D: one CTA per tile, tile + halo fetched with cp.async
+//                        (FP64 small grids, FP32/BF16 alternative family, serving)
+//   step2d_tb_kernel     2D: K steps per launch on a tile grown by the K-step halo
 //   step2d_warp_kernel   2D, FP32/BF16: one warp per column strip, rows in registers
 //   step3d_kernel        3D, FP64: shared-memory plane rings
 //   step3d_zreg_kernel   3D, FP64, 27-point: z-streaming with register queues
