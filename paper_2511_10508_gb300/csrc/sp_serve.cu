@@ -6,7 +6,7 @@
 // of tiles that spans every resident grid of that kind; each CTA reads its
 // tile's grid descriptor (model, stencil, sizes, buffers, coefficients) and
 // runs the same tile code as the single-grid kernels (2D: 128 x 32 tiles, 3D:
-// 32 x 8 x 8 boxes), so a grid's result does not depend on what else is
+// 32 x 16 x 8 boxes), so a grid's result does not depend on what else is
 // resident.  A scheduling quantum is Q time steps = Q launches per kind,
 // captured once into a CUDA graph and replayed while the set of resident grids
 // is unchanged; grids that finish inside a quantum skip the remaining steps.
@@ -47,7 +47,7 @@ struct TileDesc {
     int grid, x0, y0, z0;
 };
 
-constexpr int kB2X = 128, kB2Y = 32, kB3X = 32, kB3Y = 8, kB3Z = 8, kBatchNT = 256;
+constexpr int kB2X = 128, kB2Y = 32, kB3X = 32, kB3Y = 16, kB3Z = 8, kBatchNT = 256;
 
 template <typename T> constexpr size_t batch2d_smem() {
     size_t m = 0;
