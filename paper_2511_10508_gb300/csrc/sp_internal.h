@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "sp.h"
 #include "sp_common.cuh"
 
@@ -48,6 +50,23 @@ cudaError_t launch_step_bf16(int model, int stencil, const StepArgs &a, cudaStre
 // shared-memory plane rings instead of z-streaming).  Set around each launch by
 // the runtime.
 extern thread_local int g_step_variant;
+
+// Number of equal z segments for a lockstep schedule of `tiles` x segments work
+// items over `wave` resident CTAs: minimises rounds x (planes per segment +
+// halo planes), the time of the slowest CTA.
+inline int lockstep_segments(long long tiles, int nz, int halo, long long wave) {
+    int best = 1;
+    double best_cost = 0;
+    for (int sgs = 1; sgs <= std::min(nz, 64); ++sgs) {
+        const long long rounds = (tiles * sgs + wave - 1) / wave;
+        const double cost = (double)rounds * ((double)nz / sgs + halo);
+        if (sgs == 1 || cost < best_cost * 0.999) {
+            best = sgs;
+            best_cost = cost;
+        }
+    }
+    return best;
+}
 
 // FP64 2D grids up to 1024^2 use small tiles by default (and may fuse steps).
 constexpr long long kSmallGrid2d = 1LL << 20;

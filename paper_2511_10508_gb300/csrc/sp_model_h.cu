@@ -224,9 +224,11 @@ __global__ void __launch_bounds__(NT) mh_tile2d_kernel(MhArgs a, typename Cmp<T>
 // shared memory; mu of plane i - R (tile grown by R) goes to a ring of 2R + 1
 // planes; the update of plane i - 2R then reads m and j on planes i - 3R .. i - R
 // and mu from the rings.  The ring depth keeps the plane committed at iteration i
-// clear of every plane a thread still in iteration i - 1 may read.  Persistent
-// grid: CTA c owns an equal share of the flattened (tile, z) space.  The same
-// expressions as the per-point kernels, so the results are identical to theirs.
+// clear of every plane a thread still in iteration i - 1 may read.  Work items
+// are (z segment, tile) pairs handed out round by round, segment-major, so the
+// resident CTAs stream the same z range together and the halo rows and columns
+// that neighbouring tiles share are still in L2 when the second tile reads them.
+// The same expressions as the per-point kernels, so the results are identical.
 template <int ST, typename T, int TX, int TY>
 struct MhRing3dShape {
     static constexpr int R = StencilInfo<ST>::r;
@@ -239,8 +241,7 @@ struct MhRing3dShape {
 };
 
 template <int ST, typename T, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT) mh_ring3d_kernel(MhArgs a, float c3g, int tiles_x, int tiles_y,
-                                                      long long planes_per_cta) {
+__global__ void __launch_bounds__(NT) mh_ring3d_kernel(MhArgs a, float c3g, int tiles_x, int tiles_y, int segs) {
     typedef float C;
     typedef MhRing3dShape<ST, T, TX, TY> Sh;
     constexpr int R = Sh::R, RIN = Sh::RIN, WIN = Sh::WIN, HIN = Sh::HIN, AIN = Sh::AIN, D = Sh::D, NF = Sh::NF;
@@ -258,13 +259,10 @@ __global__ void __launch_bounds__(NT) mh_ring3d_kernel(MhArgs a, float c3g, int 
                   static_cast<T *>(a.jo[2])};
     auto S_in = [&](int f, int i) -> const C * { return s_in + ((size_t)f * D + (i % D)) * AIN; };
 
-    long long g0 = (long long)blockIdx.x * planes_per_cta;
-    const long long gend = min(g0 + planes_per_cta, (long long)tiles_x * tiles_y * nz);
-    while (g0 < gend) {
-        const int tile = (int)(g0 / nz);
-        const int z0 = (int)(g0 - (long long)tile * nz);
-        const int z1 = (int)min((long long)nz, (long long)z0 + (gend - g0));
-        g0 += z1 - z0;
+    const int tiles = tiles_x * tiles_y;
+    for (long long it = blockIdx.x; it < (long long)tiles * segs; it += gridDim.x) {
+        const int seg = (int)(it / tiles), tile = (int)(it - (long long)seg * tiles);
+        const int z0 = (int)((long long)seg * nz / segs), z1 = (int)((long long)(seg + 1) * nz / segs);
         const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
         const int nplanes = (z1 - z0) + 2 * RIN;  // loaded plane i is z = z0 - RIN + i
 
@@ -377,12 +375,10 @@ static cudaError_t launch_mh_t(const MhArgs &a, double c3g, cudaStream_t s, int 
                 return o;
             }();
             const int tx = (a.nx + TX - 1) / TX, ty = (a.ny + TY - 1) / TY;
-            const long long total = (long long)tx * ty * a.nz;
-            // one resident wave, at least 32 planes per CTA so that the ring warm-up stays small
-            long long ctas = std::max(1LL, std::min((long long)n_sm * std::max(occ, 1), total / 32));
-            const long long per = (total + ctas - 1) / ctas;
-            ctas = (total + per - 1) / per;
-            kern<<<(unsigned)ctas, NT, Sh::smem_bytes, s>>>(a, (C)c3g, tx, ty, per);
+            const long long wave = (long long)n_sm * std::max(occ, 1);
+            const int segs = lockstep_segments((long long)tx * ty, a.nz, 2 * Sh::RIN, wave);
+            const long long items = (long long)tx * ty * segs;
+            kern<<<(unsigned)std::min(items, wave), NT, Sh::smem_bytes, s>>>(a, (C)c3g, tx, ty, segs);
             return cudaGetLastError();
         }
     }

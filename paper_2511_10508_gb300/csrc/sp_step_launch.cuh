@@ -37,23 +37,6 @@ inline long long persistent_ctas(long long total_slices, int ctas_per_sm, int n_
     return std::max(1LL, std::min(wave, total_slices / kMinRun));
 }
 
-// Number of equal z segments for a lockstep schedule of `tiles` x segments work
-// items over `wave` resident CTAs: minimises rounds x (planes per segment +
-// halo planes), the time of the slowest CTA.
-inline int lockstep_segments(long long tiles, int nz, int halo, long long wave) {
-    int best = 1;
-    double best_cost = 0;
-    for (int sgs = 1; sgs <= std::min(nz, 64); ++sgs) {
-        const long long rounds = (tiles * sgs + wave - 1) / wave;
-        const double cost = (double)rounds * ((double)nz / sgs + halo);
-        if (sgs == 1 || cost < best_cost * 0.999) {
-            best = sgs;
-            best_cost = cost;
-        }
-    }
-    return best;
-}
-
 // Launch with programmatic stream serialisation (the kernel calls pdl_enter()
 // before touching global memory): used where a launch is a few microseconds
 // long, so that the next step's CTAs are resident when this one completes.
