@@ -165,6 +165,44 @@ def load_peaks() -> dict:
 FP64_PEAK_GOPS = 152 * 2 * 2.070
 
 
+def roofline(model: int, dims: int, st: int, dtype: int, order: int, spectral: bool, npts: int, launch_ms: float,
+             spl: int, traffic, peaks: dict) -> dict:
+    """The roofline object of the dominant kernel: algorithmic work of one time step
+    over the grid divided by the average step-kernel time (launch_ms per time step).
+    FP64 kernels are bound by the FP64 pipe (ops against the derived peak), FP32/BF16
+    kernels by HBM (algorithmic bytes against the measured copy bandwidth)."""
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    per_s = 1.0 / (launch_ms * 1e-3) / 1e9
+    if spectral and dtype == 0:
+        ops = spectral_ops_per_lup(npts)
+        achieved = ops * npts * per_s
+        return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "FP64 Gop/s",
+                "frac": achieved / FP64_PEAK_GOPS, "traffic": None,
+                "note": f"semi-implicit spectral step, {ops:.1f} FP64 ops/LUP by the model 5 log2 N + 9.5 "
+                        "(two real cuFFT transforms at 2.5 log2 N each, cube, Fourier update)"}
+    if spectral:
+        bpl = SPECTRAL_BYTES_PER_LUP_IN_P * ESIZE[dtype]
+        achieved = bpl * npts * per_s
+        return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "traffic": None,
+                "note": f"semi-implicit spectral step, {bpl} bytes/LUP at one pass per stage (cube, forward "
+                        "transform, Fourier update, inverse transform)"}
+    if dtype == 0:
+        ops = fp64_ops_per_lup(model, st, order, dims)
+        achieved = ops * npts * per_s
+        return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "FP64 Gop/s",
+                "frac": achieved / FP64_PEAK_GOPS, "traffic": traffic, "steps_per_launch": spl,
+                "note": f"{ops} FP64 ops/LUP (fixed evaluation order); peak = 152 SMs x 2 FP64 ops/clk x 2.07 GHz; "
+                        f"HBM side {hbm_bytes_per_lup(model, dtype, dims) * npts * per_s:.0f} GB/s"}
+    bpl = hbm_bytes_per_lup(model, dtype, dims)
+    achieved = bpl * npts * per_s
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+            "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "traffic": traffic, "steps_per_launch": spl,
+            "note": f"{bpl} algorithmic bytes/LUP at one step per pass; peak = measured copy bandwidth"
+                    + ("" if "hbm_gbs" in peaks else " (fallback)")
+                    + (f"; {spl} steps per HBM pass, so this is an effective rate" if spl > 1 else "")}
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -542,40 +580,9 @@ def main():
     value = replica_glups(lups, world, total_ms * 1e-3)
     launch_ms = step_ms / (args.steps * sub)  # average duration of one step-kernel launch
 
-    peaks = load_peaks()
-    traffic = NCU_TRAFFIC.get((args.workload, spl, variant), (None,))[0]
-    if spectral and dtype == 0:
-        ops = spectral_ops_per_lup(npts)
-        achieved = ops * npts / (launch_ms * 1e-3) / 1e9
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "FP64 Gop/s",
-                "frac": achieved / FP64_PEAK_GOPS, "traffic": None,
-                "note": f"semi-implicit spectral step, {ops:.1f} FP64 ops/LUP by the model 5 log2 N + 9.5 "
-                        "(two real cuFFT transforms at 2.5 log2 N each, cube, Fourier update)"}
-    elif spectral:
-        bpl = SPECTRAL_BYTES_PER_LUP_IN_P * ESIZE[dtype]
-        achieved = bpl * npts / (launch_ms * 1e-3) / 1e9
-        peak = float(peaks.get("hbm_gbs", 6800.0))
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "traffic": None,
-                "note": f"semi-implicit spectral step, {bpl} bytes/LUP at one pass per stage (cube, forward "
-                        "transform, Fourier update, inverse transform)"}
-    elif dtype == 0:
-        ops = fp64_ops_per_lup(model, st, order, dims)
-        achieved = ops * npts / (launch_ms * 1e-3) / 1e9
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "FP64 Gop/s",
-                "frac": achieved / FP64_PEAK_GOPS, "traffic": traffic, "steps_per_launch": spl,
-                "note": f"{ops} FP64 ops/LUP (fixed evaluation order); peak = 152 SMs x 2 FP64 ops/clk x 2.07 GHz; "
-                        f"HBM side {hbm_bytes_per_lup(model, dtype, dims) * npts / (launch_ms * 1e-3) / 1e9:.0f} GB/s"}
-    else:
-        bpl = hbm_bytes_per_lup(model, dtype, dims)
-        achieved = bpl * npts / (launch_ms * 1e-3) / 1e9
-        peak = float(peaks.get("hbm_gbs", 6800.0))
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
-                "traffic": traffic, "steps_per_launch": spl,
-                "note": f"{bpl} algorithmic bytes/LUP at one step per pass; peak = measured copy bandwidth"
-                        + ("" if "hbm_gbs" in peaks else " (fallback)")
-                        + (f"; {spl} steps per HBM pass, so this is an effective rate" if spl > 1 else "")}
+    roof = roofline(model, dims, st, dtype, order, spectral, npts, launch_ms, spl,
+                    NCU_TRAFFIC.get((args.workload, spl, variant), (None,))[0], load_peaks())
+    achieved = roof["achieved"]
     if roof["unit"] == "FP64 Gop/s":
         # the device's sustained FP64 FMA rate (independent chains on every SM),
         # measured after the timed region: the attainable ceiling beside the nominal one

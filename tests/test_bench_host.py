@@ -83,3 +83,25 @@ def test_served_request_stream():
     s2 = np.array([sh[0] for _, sh, *_ in reqs if len(sh) == 2])
     assert 250 < np.median(s2) < 520
     assert bench.served_requests(400, 4) == reqs  # seeded
+
+
+@pytest.mark.parametrize("workload", sorted(bench.WORKLOADS))
+def test_roofline_object_of_every_workload(workload):
+    """The roofline object of every bench workload (host arithmetic only): FP64 lines
+    are bound by the FP64 pipe against the derived peak, FP32/BF16 lines by HBM
+    against the measured copy bandwidth; achieved = algorithmic work / time."""
+    w = bench.WORKLOADS[workload]
+    model, dims, shape, st, dtype = w[0], w[1], w[2], w[4], w[5]
+    order = int(workload.split("-gen", 1)[1].split("-")[0]) if "-gen" in workload else 0
+    spectral = "spectral" in workload
+    npts = int(np.prod(shape))
+    roof = bench.roofline(model, dims, st, dtype, order, spectral, npts, 1.0, 1, None, {"hbm_gbs": 6800.0})
+    assert set(("bound", "achieved", "peak", "unit", "frac", "traffic")) <= set(roof)
+    if dtype == 0:
+        assert roof["bound"] == "alu" and roof["unit"] == "FP64 Gop/s" and roof["peak"] == bench.FP64_PEAK_GOPS
+    else:
+        assert roof["bound"] == "hbm" and roof["unit"] == "GB/s" and roof["peak"] == 6800.0
+        if not spectral:
+            # bytes per update: one read and one write of every field
+            assert roof["achieved"] == pytest.approx(bench.hbm_bytes_per_lup(model, dtype, dims) * npts / 1e-3 / 1e9)
+    assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
