@@ -84,11 +84,11 @@ cudaError_t launch_strips(const StepArgs &a, cudaStream_t s, int n_sm) {
 
 // Temporally blocked 2D tile kernel: K steps per launch.  FP32 / BF16 tiles of
 // 128 x 16; FP64 (small grids, where the fixed cost of a launch matters) tiles
-// of 32 x 16, so that a 256^2 grid still spreads over 128 SMs.
+// of 32 x 14, so that a 256^2 grid spreads over 8 x 19 = 152 CTAs, one per SM.
 template <int MODEL, int ST, typename T, int K>
 cudaError_t launch_tb(const StepArgs &a, cudaStream_t s) {
     constexpr bool f64 = std::is_same<T, double>::value;
-    constexpr int BX = f64 ? 32 : 128, BY = 16, NT = f64 ? 128 : 256;
+    constexpr int BX = f64 ? 32 : 128, BY = f64 ? 14 : 16, NT = f64 ? 128 : 256;
     typedef Step2dTbShape<MODEL, ST, T, BX, BY, K> Sh;
     auto kern = step2d_tb_kernel<MODEL, ST, T, BX, BY, K, NT>;
     static const bool attr = [&] {
