@@ -1124,16 +1124,21 @@ __global__ void __launch_bounds__(NT) step3d_zreg_kernel(StepArgs a, int tiles_x
 // FP32 / BF16-storage 3D kernel built like the 2D warp-strip kernel.  Warp w
 // of a CTA owns input row w of a tile (TY output rows plus R halo rows on each
 // side) and lane l the chunk l of 4 cells of that row (16 bytes FP32, 8 bytes
-// BF16): lanes 1..30 are the tile's 30 chunks, lanes 0 and 31 halo chunks.  Planes stream along z through a ring
-// of P+1 planes in shared memory filled by cp.async (each thread copies its own
-// chunk).  Neighbours: x from the adjacent lanes (warp shuffles), y from the
-// rows above and below in shared memory, z from per-thread register queues of
-// the previous planes' values and in-plane partial sums (the stencil's fixed
-// order is a sum over planes of in-plane partial sums, see sp_common.cuh).  A
-// Cahn-Hilliard thread keeps the mu of its own chunk in registers and shares
-// it through one mu plane in shared memory.  The plane loop is unrolled by the
-// queue length so that queues rotate by renaming registers.  Same expressions
-// in the same order as the other FP32 kernels: identical results bit for bit.
+// BF16): lanes 1..30 are the tile's 30 chunks, lanes 0 and 31 halo chunks.
+// Planes stream along z through a ring of P+1 planes in shared memory filled by
+// cp.async (each thread copies its own chunk; one base pointer per plane, the
+// global source and destination offsets advance by a plane each step).
+// Neighbours: x from the adjacent lanes (warp shuffles), y from the rows above
+// and below in shared memory, z from per-thread register queues of the previous
+// planes' values and in-plane partial sums, held as pairs of cells (the
+// stencil's fixed order is a sum over planes of in-plane partial sums, see
+// sp_common.cuh); the combine, mu and the updates run two cells per instruction
+// (packed f32x2).  Cahn-Hilliard keeps mu in the register queues and shares each
+// mu plane through one of two mu buffers in shared memory; its output stage runs
+// one plane behind mu, so one barrier per plane suffices.  The plane loop is
+// unrolled by the queue length so that queues rotate by renaming registers.
+// Same expressions in the same order as the other FP32 kernels: identical
+// results bit for bit.
 //
 // Requirements (checked by the launcher): nx a multiple of 4 and 16-byte
 // aligned field pointers.
