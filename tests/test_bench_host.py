@@ -105,3 +105,25 @@ def test_roofline_object_of_every_workload(workload):
             # bytes per update: one read and one write of every field
             assert roof["achieved"] == pytest.approx(bench.hbm_bytes_per_lup(model, dtype, dims) * npts / 1e-3 / 1e9)
     assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
+
+
+def test_reference_arm_line():
+    """The reference arm (the oracle timed on the host cores) prints the benchmark
+    line with the same metric and config as the GPU arm, an e2e equal to its value
+    with no host transfers, and a cpu_baseline describing the run."""
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload",
+                        "ac2d-256-f64-lap5", "--steps", "1", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == "GLUPS" and line["unit"] == "GLUPS"
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["warmup"] >= 3
+    assert line["config"]["workload"].startswith("Allen-Cahn 2D 256x256 f64")
+    assert line["e2e"] == {"value": line["value"], "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
