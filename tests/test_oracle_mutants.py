@@ -61,6 +61,11 @@ MUTANTS = {
     "Model H gradient scale": ("1.0 / (2.0 * h) : 1.0 / (12.0 * h)", "1.0 / h : 1.0 / (12.0 * h)"),
     "Model H flux of j only": ("mj[(size_t)a * n + i] = mc[i] * jcur[a][i];", "mj[(size_t)a * n + i] = jcur[a][i];"),
     "Model H current noise stream": ("or_u01(seed, (uint64_t)((a + 1) * N + i))", "or_u01(seed, (uint64_t)(a * N + i))"),
+    "relative L2 without the square root": ("return den > 0 ? sqrt(num / den) : sqrt(num);",
+                                            "return den > 0 ? num / den : num;"),
+    "relative L2 normalised by the first argument": ("r[i] = b[i] * b[i];", "r[i] = a[i] * a[i];"),
+    "relative L2 of absolute differences": ("d[i] = (a[i] - b[i]) * (a[i] - b[i]);",
+                                            "d[i] = fabs(a[i] - b[i]);"),
     "Model C density noise stream": ("            v[i] = mean + amp * (2.0 * or_u01(seed, (uint64_t)(N + i)) - 1.0);",
                                      "            v[i] = mean + amp * (2.0 * or_u01(seed, (uint64_t)i) - 1.0);"),
 }

@@ -349,6 +349,33 @@ def test_compensated_sum_matches_exact(orc):
     assert abs(s - exact) <= 2 * np.spacing(abs(exact)) + 4 * x.size * 2.0 ** -106 * np.abs(x).sum()
 
 
+def test_rel_l2_closed_forms(orc):
+    """Relative L2 distance ||a - b||_2 / ||b||_2 on cases worked by hand: the
+    denominator is the norm of the second argument, both norms are square roots
+    of sums of squares, and an all-zero reference gives the absolute norm."""
+    # ||(3, -1)|| / ||(0, 5)|| = sqrt(10) / 5
+    assert orc.rel_l2([3.0, 4.0], [0.0, 5.0]) == pytest.approx(math.sqrt(10.0) / 5.0, rel=1e-15)
+    # the reference decides the scale: ||(1, 0)|| / ||(1, 0)|| = 1 against ||(1, 0)|| / ||(2, 0)|| = 1/2
+    assert orc.rel_l2([2.0, 0.0], [1.0, 0.0]) == 1.0
+    assert orc.rel_l2([1.0, 0.0], [2.0, 0.0]) == 0.5
+    # 3-4-5 triangles: ||(3, 4)|| = 5 over ||(0, 0, 5, 12)|| = 13
+    assert orc.rel_l2([3.0, 4.0, 5.0, 12.0], [0.0, 0.0, 5.0, 12.0]) == pytest.approx(5.0 / 13.0, rel=1e-15)
+    # all-zero reference: the absolute norm ||a||
+    assert orc.rel_l2([3.0, -4.0], [0.0, 0.0]) == 5.0
+    assert orc.rel_l2([0.0, 0.0], [0.0, 0.0]) == 0.0
+    # identical arrays are at distance 0; a scaled copy (1 + e) b is at |e| for any b
+    rng = np.random.default_rng(11)
+    b = rng.standard_normal(1001)
+    assert orc.rel_l2(b, b) == 0.0
+    for e in (0.5, -0.25, 2.0 ** -20):
+        assert orc.rel_l2((1.0 + e) * b, b) == pytest.approx(abs(e), rel=1e-12)
+    # a single perturbed entry of a constant field: sqrt(d^2 / (n c^2))
+    n, c, d = 400, 0.5, 0.03
+    a = np.full(n, c)
+    a[17] += d
+    assert orc.rel_l2(a, np.full(n, c)) == pytest.approx(math.sqrt(d * d / (n * c * c)), rel=1e-13)
+
+
 def test_mass_is_cell_volume_times_sum(orc):
     f = orc.initial_condition(O.CH, (6, 7, 8), seed=1, mean=0.3, amp=0.2)
     assert orc.mass(f, h=0.5) == pytest.approx(0.125 * math.fsum(f.ravel()), rel=1e-15)
