@@ -223,10 +223,14 @@ int sp_reduce(sp_sim *sim, int what, double *out, void *stream);
  * partials, 8 KiB, held on every GPU that loads the library until exit); a
  * grid needing more partials than that fails with SP_ETOOLARGE.  The array is
  * shared by all calls and keeps the last call's contents; calls that overlap
- * on the GPU race on it.  The first call on a device looks up the array's
- * device address: make it before any stream capture.  No cudaMalloc, cudaFree
- * or allocating routine is called; on failure only the status code is
- * returned and sp_last_error() is not updated.
+ * on the GPU race on it.  The first call in a CUDA context looks up the
+ * array's device address (again after cudaDeviceReset re-creates the
+ * context): make it before any stream capture.  The call cannot be used on a
+ * stream that is being captured (SP_EINVAL: it copies the result to the host
+ * and synchronises).  SP_EINVAL also for a field not aligned to its element
+ * size and for grids beyond sp_create's limits.  No cudaMalloc, cudaFree or
+ * allocating routine is called; on failure only the status code is returned
+ * and sp_last_error() is not updated.
  */
 int sp_reduce_field_noalloc(int what, int dtype, const void *field, int dims, const int64_t shape[3], double h,
                             double c1, double c2, double *out, void *stream);
@@ -275,6 +279,13 @@ int sp_stencil_weights(int order, int dims, double *w, double *lambda_max);
  * bound by this rate.  Blocks until done; allocates 8 bytes of device memory.
  * SP_EINVAL if gops is NULL, SP_ENOMEM / SP_ECUDA on failure. */
 int sp_probe_fp64_rate(void *stream, double *gops);
+
+/* Build check (no counterpart in the paper): the compute capability the
+ * library's device code was compiled for, as major*10 + minor of the binary the
+ * runtime loaded for the current device (103 for sm_103a, GB300).  Needs a
+ * device; SP_EINVAL if version is NULL, SP_ECUDA when no binary in the library
+ * runs on the current device. */
+int sp_binary_version(int *version);
 
 /* Launch configuration in use: steps fused per launch and kernel family
  * (0 = the default for the grid; alternatives the autotuner may pick: 1 for

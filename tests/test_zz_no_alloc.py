@@ -92,3 +92,43 @@ def test_noalloc_rejects_bad_arguments(sp):
         assert f(sp.MASS, 0, ptr, 2, shape, 0.0, 1.0, 1.0, ctypes.byref(out), None) == N.SP_EINVAL
         assert f(sp.MASS, 0, ptr, 2, (ctypes.c_int64 * 3)(16, 16, 2), 1.0, 1.0, 1.0, ctypes.byref(out),
                  None) == N.SP_EINVAL
+        # an FP64 field must be 8-byte aligned (checked on the host, nothing is launched)
+        assert f(sp.MASS, 0, ptr + 4, 2, (ctypes.c_int64 * 3)(8, 8, 1), 1.0, 1.0, 1.0, ctypes.byref(out),
+                 None) == N.SP_EINVAL
+        # a 3D plane beyond sp_create's limit
+        assert f(sp.MASS, 0, ptr, 3, (ctypes.c_int64 * 3)(1 << 20, 1 << 20, 1 << 20), 1.0, 1.0, 1.0,
+                 ctypes.byref(out), None) == N.SP_EINVAL
+        assert f(sp.MASS, 0, ptr, 2, shape, 1.0, 1.0, 1.0, ctypes.byref(out), None) == N.SP_OK
+
+
+def test_noalloc_rejects_a_capturing_stream(sp):
+    """The result is copied to the host and the stream synchronised, which a
+    stream under capture does not allow: the call must refuse before touching it,
+    and the capture must still end cleanly."""
+    import torch
+    from paper_2511_10508_gb300 import _native as N
+
+    with sp.Simulation(sp.ALLEN_CAHN, (32, 32), dt=0.01, seed=3) as sim:
+        f = N.lib().sp_reduce_field_noalloc
+        f.restype = ctypes.c_int
+        f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                      ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                      ctypes.c_void_p]
+        shape = (ctypes.c_int64 * 3)(32, 32, 1)
+        out = ctypes.c_double(0)
+        expect = noalloc(sp, sp.MASS, sim)  # first call in this context, outside any capture
+        ptr = sim.devptr(0)
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        x = torch.zeros(4, device="cuda")
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            g.capture_begin()
+            x += 1.0
+            rc = f(sp.MASS, 0, ptr, 2, shape, 1.0, 1.0, 1.0, ctypes.byref(out), s.cuda_stream)
+            g.capture_end()
+        assert rc == N.SP_EINVAL
+        g.replay()
+        torch.cuda.synchronize()
+        assert x.tolist() == [1.0] * 4
+        assert noalloc(sp, sp.MASS, sim) == expect
