@@ -53,3 +53,15 @@ extern "C" int sp_probe_fp64_rate(void *stream, double *gops) {
     cudaFree(sink);
     return rc;
 }
+
+extern "C" int sp_binary_version(int *version) {
+    if (!version) return SP_EINVAL;
+    *version = 0;
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, sp::fp64_probe_kernel) != cudaSuccess) {
+        cudaGetLastError();
+        return SP_ECUDA;
+    }
+    *version = a.binaryVersion;
+    return SP_OK;
+}

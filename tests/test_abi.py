@@ -37,13 +37,14 @@ def test_library_exports_every_declared_function(sp):
     assert set(names) <= exported
 
 
+@pytest.mark.gpu
 def test_library_is_built_for_sm103a(sp):
+    """The library reports the architecture of the device code the runtime loaded."""
     from paper_2511_10508_gb300 import _native as N
 
-    out = subprocess.run(["cuobjdump", "--list-elf", N.LIB_PATH], capture_output=True, text=True)
-    if out.returncode != 0:
-        pytest.skip("cuobjdump unavailable")
-    assert "sm_103a" in out.stdout
+    v = ctypes.c_int(0)
+    assert N.lib().sp_binary_version(ctypes.byref(v)) == N.SP_OK
+    assert v.value == 103
 
 
 def test_params_default(sp):

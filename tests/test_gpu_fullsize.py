@@ -119,6 +119,25 @@ def test_cahn_hilliard_4096_lap5_full_run(sp):
     assert drift < 1e-13, drift
 
 
+def test_cahn_hilliard_4096_lap9x4_full_run(sp):
+    """The same configuration with the 4th-order 9-point cross (S3) for every
+    Laplacian: 4096^2, dt = 0.01, 10000 steps from +-0.01 noise, autotuned as bench.py
+    runs it; bitwise equal to the oracle, mass drift stated."""
+    shape, dt, n = (4096, 4096), 0.01, 10000
+    ic = O.initial_condition(O.CH, shape, seed=1, amp=0.01)
+    ref = O.step(O.CH, O.S3, ic, dt=dt, nsteps=n)
+    with sp.Simulation(sp.CAHN_HILLIARD, shape, dt=dt, seed=1, ic_amp=0.01, stencil=sp.LAP_9CROSS4,
+                       flags=sp.FLAG_AUTOTUNE) as s:
+        m0 = s.reduce(sp.MASS)
+        s.step(n)
+        got = s.read(0)
+        m1 = s.reduce(sp.MASS)
+    assert np.array_equal(got, ref)
+    drift = abs(m1 - m0) / (got.size * np.abs(got).max())
+    assert drift < 1e-13, drift
+    print(f"CH 4096^2 S3 10000 steps: bitwise; mass drift {drift:.2e} of N max|phi|")
+
+
 def test_cahn_hilliard_4096_lap9x4_sampled(sp):
     shape, dt, n = (4096, 4096), 0.01, 5
     with sp.Simulation(sp.CAHN_HILLIARD, shape, dt=dt, seed=1, ic_amp=0.01, stencil=sp.LAP_9CROSS4) as s:
