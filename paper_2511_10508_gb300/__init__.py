@@ -13,7 +13,7 @@ import ctypes
 import numpy as np
 
 from . import _native as N
-from ._native import (ALLEN_CAHN, BF16_F32, CAHN_HILLIARD, F32, F64, FLAG_AUTOTUNE, FREE_ENERGY, GRAY_SCOTT, IC_CONSTANT,
+from ._native import (ALLEN_CAHN, BF16_F32, CAHN_HILLIARD, F32, F64, FLAG_AUTOTUNE, FLAG_BF16_NO_BOUND, FREE_ENERGY, GRAY_SCOTT, IC_CONSTANT,
                       IC_NOISE, LAP_5, LAP_7, LAP_9BOX, LAP_9CROSS4, LAP_13CROSS4, LAP_27, LAP_DEFAULT, LAP_GENERATED, MASS,
                       MAX_U, MIN_U, MODEL_C, MODEL_H, SCHEME_FD, SCHEME_SPECTRAL, SUM_U, SUM_V, SUMSQ_U, SpError)
 
@@ -21,7 +21,7 @@ __all__ = ["Simulation", "Server", "Result", "params", "check_stability", "SpErr
            "MODEL_C", "MODEL_H", "SCHEME_FD", "SCHEME_SPECTRAL",
            "LAP_5", "LAP_9BOX", "LAP_9CROSS4", "LAP_7", "LAP_27", "LAP_13CROSS4", "LAP_DEFAULT", "LAP_GENERATED",
            "stencil_weights", "F64", "F32",
-           "BF16_F32", "IC_NOISE", "IC_CONSTANT", "FLAG_AUTOTUNE", "MASS", "FREE_ENERGY", "SUM_U", "SUM_V", "MIN_U", "MAX_U",
+           "BF16_F32", "IC_NOISE", "IC_CONSTANT", "FLAG_AUTOTUNE", "FLAG_BF16_NO_BOUND", "MASS", "FREE_ENERGY", "SUM_U", "SUM_V", "MIN_U", "MAX_U",
            "SUMSQ_U"]
 
 _STORAGE = {F64: np.float64, F32: np.float32, BF16_F32: np.uint16}

@@ -26,6 +26,7 @@ LAP_DEFAULT, LAP_5, LAP_9BOX, LAP_9CROSS4, LAP_7, LAP_27, LAP_13CROSS4, LAP_GENE
 F64, F32, BF16_F32 = 0, 1, 2
 IC_NOISE, IC_CONSTANT = 0, 1
 FLAG_AUTOTUNE = 1
+FLAG_BF16_NO_BOUND = 2
 SCHEME_FD, SCHEME_SPECTRAL = 0, 1
 MASS, FREE_ENERGY, SUM_U, SUM_V, MIN_U, MAX_U, SUMSQ_U = range(7)
 

@@ -34,8 +34,8 @@ cudaError_t launch_step_bf16(int model, int stencil, const StepArgs &a, cudaStre
 
 // Steps fused per launch (temporal blocking) for a request of `requested`
 // (0 = the library's choice, 1 = none): 2D grids support 2 and 4 (FP64 on small
-// tiles, where a launch is short enough for its fixed cost to matter); 3D runs
-// one step per launch.  The library's choice follows measurement on GB300:
+// tiles, where a launch is short enough for its fixed cost to matter); 3D grids
+// see steps_per_launch_3d.  The library's choice follows measurement on GB300:
 // blocking pays where the one-step tile kernel is at the HBM bound (FP32
 // Gray-Scott 32768^2: 1 step 0.99 of the copy bandwidth, 2 steps 1.31
 // effective, 4 steps 1.19); Cahn-Hilliard and BF16 storage are limited by
@@ -70,6 +70,13 @@ inline int lockstep_segments(long long tiles, int nz, int halo, long long wave) 
 
 // FP64 2D grids up to 1024^2 use small tiles by default (and may fuse steps).
 constexpr long long kSmallGrid2d = 1LL << 20;
+
+// 3D: two steps per launch for FP32 / BF16 Allen-Cahn and Gray-Scott (warp-row
+// plane queues, grids with nx a multiple of 4), when asked for or autotuned.
+inline int steps_per_launch_3d(int dtype, int model, int nx, int requested) {
+    const bool ok = dtype != SP_F64 && (model == SP_ALLEN_CAHN || model == SP_GRAY_SCOTT) && nx % 4 == 0;
+    return (ok && requested >= 2) ? 2 : 1;
+}
 
 inline int steps_per_launch(int dims, int dtype, int model, int requested) {
     if (dims != 2 || model == SP_MODEL_H) return 1;

@@ -102,6 +102,29 @@ cudaError_t launch_tb(const StepArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// 3D FP32 / BF16 temporal blocking (Allen-Cahn, Gray-Scott): K steps per pass
+// on warp-row tiles of 120 x 8 outputs; lockstep z segments like the one-step
+// warp-row kernel.  Needs nx a multiple of 4 and 16-byte aligned fields (the
+// runtime offers K > 1 in 3D only then).
+template <int MODEL, int ST, typename T, int K>
+cudaError_t launch_tbw(const StepArgs &a, cudaStream_t s, int n_sm) {
+    constexpr int TY = 8;
+    typedef Step3dTbwShape<MODEL, ST, T, TY, K> Sh;
+    auto kern = step3d_tbw_kernel<MODEL, ST, T, TY, K>;
+    static const int occ = [&] {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem_bytes);
+        int o = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, Sh::NT, Sh::smem_bytes);
+        return o;
+    }();
+    const int tx = (a.nx + Sh::TX - 1) / Sh::TX, ty = (a.ny + TY - 1) / TY;
+    const long long wave = (long long)n_sm * std::max(occ, 1);
+    const int segs = lockstep_segments((long long)tx * ty, a.nz, 2 * K * Sh::r, wave);
+    const long long items = (long long)tx * ty * segs;
+    kern<<<(unsigned)std::min(items, wave), Sh::NT, Sh::smem_bytes, s>>>(a, tx, ty, segs);
+    return cudaGetLastError();
+}
+
 // FP64 27-point: z-streaming kernel with per-plane partial sums in registers.
 template <int MODEL, typename T>
 cudaError_t launch_zreg(const StepArgs &a, cudaStream_t s, int n_sm) {
@@ -201,6 +224,9 @@ cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
         const int bx = (a.nx + BX - 1) / BX, by = (a.ny + BY - 1) / BY, bz = (a.nz + BZ - 1) / BZ;
         kern<<<dim3((unsigned)bx, (unsigned)by, (unsigned)bz), NT, Sh::smem_bytes, s>>>(a);
     } else if constexpr (!std::is_same<T, double>::value) {
+        if constexpr (MODEL == AC || MODEL == GS) {
+            if (k == 2) return launch_tbw<MODEL, ST, T, 2>(a, s, n_sm);
+        }
         constexpr int ATX = 16, ATY = 16;
         typedef Step3dAsyncShape<MODEL, ST, T, ATX, ATY> AS;
         const bool aligned = ((uintptr_t)a.in0 | (uintptr_t)a.in1 | (uintptr_t)a.out0 | (uintptr_t)a.out1) % 16 == 0;

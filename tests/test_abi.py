@@ -58,7 +58,8 @@ def test_params_default(sp):
 
 @pytest.mark.parametrize("bad", [
     dict(model=7), dict(dims=4), dict(stencil=9),
-    dict(h=0.0), dict(dt=-1.0), dict(h=float("nan")), dict(dtype=5), dict(flags=2), dict(scheme=2),
+    dict(h=0.0), dict(dt=-1.0), dict(h=float("nan")), dict(dtype=5), dict(flags=4), dict(scheme=2),
+    dict(dtype=2),  # BF16 storage without SP_FLAG_BF16_NO_BOUND
     dict(scheme=1, model=2), dict(scheme=1, model=3), dict(scheme=1, dtype=2),
     dict(stencil=3),  # 3D stencil on a 2D grid
 ])

@@ -100,7 +100,16 @@ def test_allen_cahn_256_full_run(sp):
     with sp.Simulation(sp.ALLEN_CAHN, shape, dt=dt, seed=0, ic_amp=0.1, dtype=sp.F32, flags=sp.FLAG_AUTOTUNE) as s:
         s.step(1000)
         e = O.rel_l2(s.read(0), ref)
-    assert e < 1e-5, e  # FP32 storage: measured ~1e-7
+    assert e < 1e-6, e  # FP32 storage: measured 1.8e-7
+    # BF16 storage is refused unless asked for without a bound; asked for, it misses 1e-2
+    with pytest.raises(sp.SpError):
+        sp.Simulation(sp.ALLEN_CAHN, shape, dt=dt, seed=0, ic_amp=0.1, dtype=sp.BF16_F32)
+    with sp.Simulation(sp.ALLEN_CAHN, shape, dt=dt, seed=0, ic_amp=0.1, dtype=sp.BF16_F32,
+                       flags=sp.FLAG_BF16_NO_BOUND) as s:
+        s.step(1000)
+        eb = O.rel_l2(s.read(0), ref)
+    assert 1e-2 < eb < 0.2, eb  # measured 8.7e-2
+    print(f"AC 256^2 1000 steps: rel-L2 vs FP64 oracle FP32 {e:.2e}, BF16 {eb:.2e}")
 
 
 def test_cahn_hilliard_4096_lap5_full_run(sp):
@@ -117,6 +126,12 @@ def test_cahn_hilliard_4096_lap5_full_run(sp):
     assert np.array_equal(got, ref)
     drift = abs(m1 - m0) / (got.size * np.abs(got).max())
     assert drift < 1e-13, drift
+    with sp.Simulation(sp.CAHN_HILLIARD, shape, dt=dt, seed=1, ic_amp=0.01, dtype=sp.F32,
+                       flags=sp.FLAG_AUTOTUNE) as s:
+        s.step(n)
+        e = O.rel_l2(s.read(0), ref)
+    assert e < 1e-5, e  # FP32 storage: measured 4.1e-6
+    print(f"CH 4096^2 S1 10000 steps: bitwise; mass drift {drift:.2e}; FP32 rel-L2 {e:.2e}")
 
 
 def test_cahn_hilliard_4096_lap9x4_full_run(sp):
@@ -135,7 +150,12 @@ def test_cahn_hilliard_4096_lap9x4_full_run(sp):
     assert np.array_equal(got, ref)
     drift = abs(m1 - m0) / (got.size * np.abs(got).max())
     assert drift < 1e-13, drift
-    print(f"CH 4096^2 S3 10000 steps: bitwise; mass drift {drift:.2e} of N max|phi|")
+    with sp.Simulation(sp.CAHN_HILLIARD, shape, dt=dt, seed=1, ic_amp=0.01, stencil=sp.LAP_9CROSS4, dtype=sp.F32,
+                       flags=sp.FLAG_AUTOTUNE) as s:
+        s.step(n)
+        e = O.rel_l2(s.read(0), ref)
+    assert e < 1e-5, e  # FP32 storage: measured 2.3e-6
+    print(f"CH 4096^2 S3 10000 steps: bitwise; mass drift {drift:.2e} of N max|phi|; FP32 rel-L2 {e:.2e}")
 
 
 def test_cahn_hilliard_4096_lap9x4_sampled(sp):
@@ -182,32 +202,44 @@ def test_gray_scott_2048_full_run(sp):
                        flags=sp.FLAG_AUTOTUNE) as s:
         s.step(n)
         assert np.array_equal(s.read(0), ru) and np.array_equal(s.read(1), rv)
+    # FP32 storage: the error of v (the growing spots) rises over the run: measured
+    # u 3.3e-6 and v 1.0e-4 after 5000 steps (v 2.5e-5 after 2000); stated bound 2e-4
+    with sp.Simulation(sp.GRAY_SCOTT, shape, dt=dt, seed=2, ic_amp=0.01, gs_patches=16, gs_patch=20, dtype=sp.F32,
+                       flags=sp.FLAG_AUTOTUNE) as s:
+        s.step(n)
+        eu, ev = O.rel_l2(s.read(0), ru), O.rel_l2(s.read(1), rv)
+    assert eu < 1e-5 and ev < 2e-4, (eu, ev)
+    print(f"GS 2048^2 5000 steps: bitwise; FP32 rel-L2 u {eu:.2e}, v {ev:.2e}")
 
 
 # ---------------------------------------------------------------- 3D ----
 
 
-@pytest.mark.parametrize("st", [O.S4, O.S5])
+@pytest.mark.parametrize("st", [O.S4, O.S5, O.S6])
 def test_cahn_hilliard_128_cubed_full_run(sp, st):
     """128^3 Cahn-Hilliard, dt = 0.005, 2000 steps from +-0.01 noise: FP64 bitwise.
-    FP32 storage within relative L2 1e-5 of the FP64 oracle.  BF16 storage: the
+    FP32 storage within relative L2 1e-6 of the FP64 oracle (measured 4.1e-7 with
+    the 7-point and 2.4e-7 with the 27-point stencil).  BF16 storage: the
     increments (~1e-6) are far below half an ulp of BF16 at |phi| ~ 0.01 (~2e-5),
-    so stored values barely move; its error is measured and bounded here only to
-    show it does not meet the FP32 bound (BF16 is not offered for this case)."""
+    so stored values barely move (measured 0.84): sp_create refuses BF16 unless
+    SP_FLAG_BF16_NO_BOUND accepts an unbounded error, and with it the run misses
+    even a 0.5 bound."""
     shape, dt, n = (128, 128, 128), 0.005, 2000
     ic = O.initial_condition(O.CH, shape, seed=3, amp=0.01)
     ref = O.step(O.CH, st, ic, dt=dt, nsteps=n)
     errs = {}
+    with pytest.raises(sp.SpError):
+        sp.Simulation(sp.CAHN_HILLIARD, shape, dt=dt, seed=3, ic_amp=0.01, stencil=st, dtype=2)
     for dtype in (0, 1, 2):
         with sp.Simulation(sp.CAHN_HILLIARD, shape, dt=dt, seed=3, ic_amp=0.01, stencil=st, dtype=dtype,
-                           flags=sp.FLAG_AUTOTUNE) as s:
+                           flags=sp.FLAG_AUTOTUNE | (sp.FLAG_BF16_NO_BOUND if dtype == 2 else 0)) as s:
             s.step(n)
             got = s.read(0)
         if dtype == 0:
             assert np.array_equal(got, ref)
         errs[dtype] = O.rel_l2(got, ref)
-    assert errs[1] < 1e-5, errs
-    assert errs[2] > errs[1] and math.isfinite(errs[2]), errs
+    assert errs[1] < 1e-6, errs
+    assert errs[2] > 0.5 and math.isfinite(errs[2]), errs
     print(f"stencil {st}: rel-L2 vs FP64 oracle after {n} steps: FP32 {errs[1]:.3e}, BF16 {errs[2]:.3e}")
 
 

@@ -28,6 +28,8 @@ def make(sp, model, shape, order, dtype=0, **kw):
     else:
         base.update(ic_amp=0.4)
     base.update(kw)
+    if dtype == 2:  # BF16 storage has no accuracy bound and must be asked for explicitly
+        base["flags"] = base.get("flags", 0) | sp.FLAG_BF16_NO_BOUND
     return sp.Simulation(model, shape, dt=DT[model], **base)
 
 

@@ -28,6 +28,8 @@ def sp():
 def make(sp, shape, st, dtype=0, dt=0.002, **kw):
     kw.setdefault("ic_amp", 0.4)
     kw.setdefault("c3", 0.8)
+    if dtype == 2:  # BF16 storage has no accuracy bound and must be asked for explicitly
+        kw["flags"] = kw.get("flags", 0) | sp.FLAG_BF16_NO_BOUND
     return sp.Simulation(sp.MODEL_H, shape, dt=dt, stencil=st, dtype=dtype, seed=kw.pop("seed", 77), **kw)
 
 

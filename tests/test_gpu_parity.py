@@ -39,6 +39,8 @@ def make(sp, model, shape, st, dtype=0, dt=None, **kw):
     else:
         base.update(ic_amp=kw.pop("ic_amp", 0.5))
     base.update(kw)
+    if dtype == 2:  # BF16 storage has no accuracy bound and must be asked for explicitly
+        base["flags"] = base.get("flags", 0) | sp.FLAG_BF16_NO_BOUND
     return sp.Simulation(model, shape, dt=dt, **base), dt
 
 
@@ -196,7 +198,7 @@ def test_fixed_point_sums_adversarial(sp, dtype):
     vals[half:2 * half] = -vals[:half]                              # exact cancellation
     vals = vals.reshape(shape)
     u = 2.0 ** -53
-    with sp.Simulation(sp.ALLEN_CAHN, shape, dt=0.01, dtype=dtype, stencil=3) as sim:
+    with sp.Simulation(sp.ALLEN_CAHN, shape, dt=0.01, dtype=dtype, flags=sp.FLAG_BF16_NO_BOUND if dtype == 2 else 0, stencil=3) as sim:
         sim.write(0, vals)
         stored = sim.read(0)                                        # the values as rounded to storage
         exact = math.fsum(stored.ravel().tolist())
@@ -249,7 +251,7 @@ def test_write_rounds_to_storage(sp, dtype):
     shape = (16, 40)
     rng = np.random.default_rng(0)
     x = rng.standard_normal(shape)
-    with sp.Simulation(sp.ALLEN_CAHN, shape, dt=0.01, dtype=dtype) as s:
+    with sp.Simulation(sp.ALLEN_CAHN, shape, dt=0.01, dtype=dtype, flags=sp.FLAG_BF16_NO_BOUND if dtype == 2 else 0) as s:
         s.write(0, x)
         y = s.read(0)
         if dtype == 1:
@@ -360,6 +362,27 @@ def test_temporal_blocking_equals_single_steps(sp, dtype, model, st):
             ref = (O.step(model, st, ic, dt=dt, prm=oparams(sim.prm), nsteps=13),)
         for a, b in zip(outs[-1], ref):
             assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("dtype", [1, 2])
+@pytest.mark.parametrize("model,st", [(m, s) for m in (0, 2) for s in (3, 4, 5)])
+@pytest.mark.parametrize("shape", [(37, 45, 124), (6, 5, 8), (20, 17, 244)])
+def test_temporal_blocking_3d_equals_single_steps(sp, dtype, model, st, shape):
+    """3D FP32 / BF16 Allen-Cahn and Gray-Scott with two steps per launch (the
+    warp-row plane queues, intermediate planes rounded to the storage type) equal
+    single-step launches bit for bit: two tiles in x (one ragged), ragged y tiles,
+    z segments, a grid smaller than the two-step halo in every direction, and
+    graph replays (45 steps)."""
+    outs = []
+    for spl in (1, 2):
+        sim, dt = make(sp, model, shape, st, dtype=dtype, steps_per_launch=spl)
+        with sim:
+            assert sim.launch_config[0] == spl
+            sim.step(1)
+            sim.step(44)
+            outs.append([sim.read(f, as_f64=False) for f in range(2 if model in TWO else 1)])
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
 
 
 @pytest.mark.parametrize("shape", [(256, 256), (9, 8), (45, 70)])

@@ -148,3 +148,45 @@ def test_bounded_wait_and_poll(sp):
         r = srv.wait(t, timeout=600)
         assert r.steps_done == 3000 and r.t_admit >= r.t_submit and r.t_finish > r.t_admit
         srv.release(t)
+
+
+def test_served_fp32_requests_against_fp64_oracle(sp):
+    """The FP32 form of the served stream: requests drawn by bench.py's generator of
+    the served mix (models, sides, steps and coefficients), run by the server in
+    FP32 storage, against the FP64 oracle started from the same seeded field.  For
+    each (model, dims) the longest run the oracle finishes quickly is taken.  Stated
+    bound: relative L2 <= 2e-4 per field (the Gray-Scott v field after thousands of
+    steps is the largest; Allen-Cahn and Cahn-Hilliard stay near 1e-6)."""
+    import bench
+
+    reqs = bench.served_requests(400, 4)
+    picked = {}
+    for m, sh, dt, n, kw in reqs:
+        cost = int(np.prod(sh)) * n
+        if cost > 4e8:
+            continue
+        key = (m, len(sh))
+        if key not in picked or n > picked[key][3]:
+            picked[key] = (m, sh, dt, n, kw)
+    assert len(picked) == 6, sorted(picked)
+    worst = {}
+    with sp.Server(8 << 30, max_slots=16, quantum_steps=50) as srv:
+        tickets = {key: srv.submit(m, sh, dt=dt, nsteps=n, return_fields=True, **dict(kw, dtype=sp.F32))
+                   for key, (m, sh, dt, n, kw) in picked.items()}
+        for key, t in tickets.items():
+            m, sh, dt, n, kw = picked[key]
+            got = srv.wait(t, timeout=600).fields
+            dims = len(sh)
+            st = O.S1 if dims == 2 else O.S4
+            prm = O.params(**{k: v for k, v in kw.items() if k in ("c1", "c2", "kappa", "F", "k")})
+            if m == 2:
+                u, v = O.initial_condition(O.GS, sh, seed=kw["seed"], amp=kw["ic_amp"], patches=kw["gs_patches"],
+                                           patch=kw["gs_patch"])
+                ref = O.step(O.GS, st, u, v, dt=dt, prm=prm, nsteps=n)
+            else:
+                ref = (O.step(m, st, O.initial_condition(m, sh, seed=kw["seed"], amp=kw["ic_amp"]), dt=dt, prm=prm,
+                              nsteps=n),)
+            errs = [O.rel_l2(got[f], ref[f]) for f in range(len(ref))]
+            worst[key] = (n, sh, errs)
+            assert max(errs) <= 2e-4, (key, n, sh, errs)
+    print({k: (n, sh[0], [f"{e:.1e}" for e in errs]) for k, (n, sh, errs) in worst.items()})

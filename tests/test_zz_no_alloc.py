@@ -52,7 +52,8 @@ def noalloc(sp, what, sim, field=0):
 ])
 def test_noalloc_reduction_matches_sp_reduce(sp, model, shape, stencil, dtype, h):
     dt = {0: 0.01, 1: 0.002, 2: 0.5}[model]
-    kw = dict(stencil=stencil, dtype=dtype, seed=21, ic_amp=0.3 if model != 2 else 0.01)
+    kw = dict(stencil=stencil, dtype=dtype, seed=21, ic_amp=0.3 if model != 2 else 0.01,
+              flags=sp.FLAG_BF16_NO_BOUND if dtype == 2 else 0)
     if model == 2:
         kw.update(gs_patches=4, gs_patch=5)
     with sp.Simulation(model, shape, h=h, dt=dt, **kw) as sim:
@@ -109,6 +110,7 @@ def test_noalloc_rejects_a_capturing_stream(sp):
     from paper_2511_10508_gb300 import _native as N
 
     with sp.Simulation(sp.ALLEN_CAHN, (32, 32), dt=0.01, seed=3) as sim:
+        sim.h = 1.0
         f = N.lib().sp_reduce_field_noalloc
         f.restype = ctypes.c_int
         f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
