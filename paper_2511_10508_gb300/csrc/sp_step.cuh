@@ -15,8 +15,10 @@
 //   step3d_kernel        3D, FP64: shared-memory plane rings
 //   step3d_zreg_kernel   3D, FP64, 27-point: z-streaming with register queues
 //   step3d_wr_kernel     3D, FP32/BF16: warp per tile row, z in register queues
-//   step3d_tbw_kernel    3D, FP32/BF16 Allen-Cahn / Gray-Scott: K steps per pass
-//                        (warp rows, one register queue and plane buffer per level)
+//   step3d_tbw_kernel    3D, FP32/BF16 Allen-Cahn / Gray-Scott, 27-point: K steps
+//                        per pass (warp rows, a register queue and plane buffer per level)
+//   step3d_tbs_kernel    3D, FP32/BF16 Allen-Cahn / Gray-Scott, cross stencils: K
+//                        steps per pass (warp rows, a plane ring per level)
 //   step3d_async_kernel  3D, FP32/BF16: cp.async plane ring, planes in flight
 //   step3d_vec_kernel    3D, FP32/BF16: plane rings of 16-byte chunks (any nx)
 //   step3d_box_kernel    3D, FP32/BF16 Model C: one CTA per box
@@ -1676,6 +1678,209 @@ __global__ void __launch_bounds__(Step3dTbwShape<MODEL, ST, T, TY, K>::NT, 1)
         }
         cp_async_wait<0>();
         __syncthreads();  // the ring and level buffers are reused by the next item
+    }
+}
+
+// ====================================== 3D, plane rings, K steps per pass ==
+//
+// Temporal blocking in 3D for the cross stencils (7-point, 4th-order 13-point):
+// K forward-Euler steps of Allen-Cahn or Gray-Scott per HBM round trip, with
+// every time level kept as a ring of planes in shared memory instead of
+// register queues, so that a thread holds no per-level state and more warps fit
+// on an SM.  Warp w owns row w of a tile (TY output rows plus K*r halo rows on
+// each side), lane l the chunk of 4 cells l (lanes 1..30 the tile's 120 cells,
+// lanes 0 and 31 halo chunks covering the K*r halo cells).  Input planes stream
+// along z through a cp.async ring.  Level s (1..K) produces plane j-(s-1)-s*r
+// at iteration j from planes of level s-1 that earlier iterations published
+// (the x neighbours by warp shuffles, y and z neighbours from the ring of level
+// s-1); levels 1..K-1 write their plane into their own ring, level K to global
+// memory.  One barrier per iteration.  Level s is valid on the rows and cells of
+// level s-1 shrunk by r, so after K levels exactly the tile remains.
+// Intermediate planes are rounded to the storage type as a global store would
+// round them, and every level evaluates the single-step expressions in the same
+// order, so K blocked steps equal K single steps bit for bit.
+//
+// Requirements (checked by the launcher): nx a multiple of 4 and 16-byte
+// aligned field pointers.
+template <int MODEL, int ST, typename T, int TY, int K>
+struct Step3dTbsShape {
+    static constexpr int V = 4;
+    static constexpr int CB = V * (int)sizeof(T);
+    static constexpr int r = StencilInfo<ST>::r;
+    static_assert(ST == L7 || ST == L13X4, "cross stencils");
+    static_assert(K * r <= V, "the halo lanes must cover K*r cells");
+    static constexpr int TXC = 30;
+    static constexpr int TX = TXC * V;
+    static constexpr int HIN = TY + 2 * K * r;
+    static constexpr int NT = 32 * HIN;
+    static constexpr int NF = num_fields<MODEL>();
+    static constexpr int P = 2;                        // input planes in flight
+    static constexpr int D0 = 2 * r + 1 + P;           // input ring: planes read by level 1, plus in flight
+    static constexpr int DL = 2 * r + 2;               // level ring: planes read by the next level, plus the new one
+    static constexpr size_t in_plane = (size_t)HIN * 32 * CB;              // bytes, one field
+    static constexpr size_t lv_plane = (size_t)HIN * 32 * V * sizeof(float);
+    static constexpr size_t in_bytes = (size_t)D0 * NF * in_plane;
+    static constexpr size_t smem_bytes = in_bytes + (size_t)(K - 1) * DL * NF * lv_plane;
+};
+
+template <int MODEL, int ST, typename T, int TY, int K>
+__global__ void __launch_bounds__(Step3dTbsShape<MODEL, ST, T, TY, K>::NT)
+    step3d_tbs_kernel(StepArgs a, int tiles_x, int tiles_y, int segs) {
+    static_assert(MODEL == AC || MODEL == GS, "temporal blocking in 3D covers Allen-Cahn and Gray-Scott");
+    typedef Step3dTbsShape<MODEL, ST, T, TY, K> Sh;
+    constexpr int V = Sh::V, r = Sh::r, HIN = Sh::HIN, NF = Sh::NF, CB = Sh::CB, V2 = V / 2;
+    constexpr int D0 = Sh::D0, DL = Sh::DL, P = Sh::P;
+    constexpr int XW = V + 2 * r;
+    constexpr unsigned FULL = 0xffffffffu;
+    typedef typename VecT<CB>::type W;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+
+    const ConstsF2 k2(ConstsC<float>(a.k, a.kf));
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const size_t plane = (size_t)nx * (size_t)ny;
+    const T *in[2] = {static_cast<const T *>(a.in0), static_cast<const T *>(a.in1)};
+    T *out[2] = {static_cast<T *>(a.out0), static_cast<T *>(a.out1)};
+    // this lane's chunk of its own row: input ring [D0][NF][HIN][32] chunks,
+    // level rings [K-1][DL][NF][HIN][32][V] floats
+    W *const in_own = reinterpret_cast<W *>(smem_raw) + (size_t)w * 32 + lane;
+    float *const lv_own = reinterpret_cast<float *>(smem_raw + Sh::in_bytes) + ((size_t)w * 32 + lane) * V;
+    constexpr size_t IN_FLD = (size_t)HIN * 32, IN_SLOT = NF * IN_FLD;   // chunks
+    constexpr size_t LV_FLD = (size_t)HIN * 32 * V, LV_SLOT = NF * LV_FLD, LV_LEVEL = DL * LV_SLOT;  // floats
+    auto extend = [&](float *ext) {
+#pragma unroll
+        for (int h = 0; h < r; ++h) {
+            ext[h] = __shfl_up_sync(FULL, ext[V + h], 1);
+            ext[r + V + h] = __shfl_down_sync(FULL, ext[r + h], 1);
+        }
+    };
+    // V cells of field f at row offset dy of level-s plane q (s = 0: the input ring)
+    auto chunk = [&](int s, int q, int f, int dy, float *dst) {
+        if (s == 0) {
+            union { W c; T t[V]; } u;
+            u.c = in_own[(size_t)(q % D0) * IN_SLOT + f * IN_FLD + dy * 32];
+#pragma unroll
+            for (int i = 0; i < V; ++i) dst[i] = to_c(u.t[i]);
+        } else {
+            const float4 v4 = *reinterpret_cast<const float4 *>(
+                lv_own + (size_t)(s - 1) * LV_LEVEL + (size_t)(q % DL) * LV_SLOT + f * LV_FLD + dy * 32 * V);
+            dst[0] = v4.x;
+            dst[1] = v4.y;
+            dst[2] = v4.z;
+            dst[3] = v4.w;
+        }
+    };
+
+    const int tiles = tiles_x * tiles_y;
+    for (long long it = blockIdx.x; it < (long long)tiles * segs; it += gridDim.x) {
+        const int seg = (int)(it / tiles), tile = (int)(it - (long long)seg * tiles);
+        const int z0 = (int)((long long)seg * nz / segs), z1 = (int)((long long)(seg + 1) * nz / segs);
+        const int x0 = (tile % tiles_x) * Sh::TX, y0 = (tile / tiles_x) * TY;
+        const int n = (z1 - z0) + 2 * K * r;
+        const int niter = n + K - 1;
+        const int col = x0 + (lane - 1) * V;
+        const size_t goff = (size_t)wrap_idx(y0 - K * r + w, ny) * nx + wrap_idx(col, nx);
+        const int yo = y0 - K * r + w;
+        const bool store = w >= K * r && w < HIN - K * r && lane >= 1 && lane <= 30 && col < nx && yo < ny;
+        int jn = 0, zn = wrap_idx(z0 - K * r, nz);
+        size_t src = (size_t)zn * plane + goff;
+        size_t dst_off = (size_t)z0 * plane + (size_t)yo * nx + col;
+        auto issue = [&]() {
+            if (jn < n) {
+                W *dst = in_own + (size_t)(jn % D0) * IN_SLOT;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    if constexpr (CB == 16) cp_async16(dst + f * IN_FLD, in[f] + src);
+                    else cp_async8(dst + f * IN_FLD, in[f] + src);
+                }
+                src += plane;
+                if (++zn == nz) {
+                    zn = 0;
+                    src -= (size_t)nz * plane;
+                }
+            }
+            ++jn;
+            cp_async_commit();
+        };
+#pragma unroll
+        for (int j = 0; j < P; ++j) issue();
+
+        for (int j = 0; j < niter; ++j) {
+            cp_async_wait<P - 1>();
+            // input plane j and the level planes of iteration j-1 published; the
+            // slots written below are no longer read
+            __syncthreads();
+            issue();
+#pragma unroll
+            for (int s = 1; s <= K; ++s) {
+                const int t = j - (s - 1) - s * r;                 // plane of level s produced now
+                if (w >= s * r && w < HIN - s * r && t >= s * r && t < n - s * r) {
+                    float S[NF][V], cen[NF][V], res[NF][V];
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        float ext[XW], ym[r][V], yp[r][V], zm[r][V], zp[r][V];
+                        chunk(s - 1, t, f, 0, ext + r);
+                        extend(ext);
+#pragma unroll
+                        for (int d = 1; d <= r; ++d) {
+                            chunk(s - 1, t, f, -d, ym[d - 1]);
+                            chunk(s - 1, t, f, d, yp[d - 1]);
+                            chunk(s - 1, t - d, f, 0, zm[d - 1]);
+                            chunk(s - 1, t + d, f, 0, zp[d - 1]);
+                        }
+                        // stencil sum in the fixed order (sp_common.cuh), two cells per instruction
+#pragma unroll
+                        for (int q = 0; q < V2; ++q) {
+                            const int c0 = 2 * q, x = r + c0;
+                            auto pr = [&](const float *a) { return make_float2(a[c0], a[c0 + 1]); };
+                            const float2 xs1 = make_float2(ext[x - 1] + ext[x + 1], ext[x] + ext[x + 2]);
+                            const float2 F1 = add2(add2(xs1, add2(pr(ym[0]), pr(yp[0]))), add2(pr(zm[0]), pr(zp[0])));
+                            float2 s2;
+                            if constexpr (ST == L7) {
+                                s2 = fma2(splat2(-6.f), make_float2(ext[x], ext[x + 1]), F1);
+                            } else {
+                                const float2 xs2 = make_float2(ext[x - 2] + ext[x + 2], ext[x - 1] + ext[x + 3]);
+                                const float2 F2 =
+                                    add2(add2(xs2, add2(pr(ym[r - 1]), pr(yp[r - 1]))), add2(pr(zm[r - 1]), pr(zp[r - 1])));
+                                s2 = fma2(splat2(-90.f), make_float2(ext[x], ext[x + 1]), fma2(splat2(16.f), F1, neg2(F2)));
+                            }
+                            S[f][c0] = s2.x;
+                            S[f][c0 + 1] = s2.y;
+                            cen[f][c0] = ext[x];
+                            cen[f][c0 + 1] = ext[x + 1];
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < V2; ++q) {
+                        const int c0 = 2 * q;
+                        auto pr = [&](const float *a) { return make_float2(a[c0], a[c0 + 1]); };
+                        float2 a0, a1 = make_float2(0.f, 0.f);
+                        if constexpr (MODEL == AC) a0 = ac_update2(pr(cen[0]), pr(S[0]), k2);
+                        else gs_update2(pr(cen[0]), pr(cen[NF - 1]), pr(S[0]), pr(S[NF - 1]), k2, a0, a1);
+                        res[0][c0] = a0.x;
+                        res[0][c0 + 1] = a0.y;
+                        res[NF - 1][c0] = NF == 2 ? a1.x : a0.x;
+                        res[NF - 1][c0 + 1] = NF == 2 ? a1.y : a0.y;
+                    }
+                    if (s < K) {
+#pragma unroll
+                        for (int f = 0; f < NF; ++f)
+                            *reinterpret_cast<float4 *>(lv_own + (size_t)(s - 1) * LV_LEVEL +
+                                                        (size_t)(t % DL) * LV_SLOT + f * LV_FLD) =
+                                make_float4(to_c(from_c<T>(res[f][0])), to_c(from_c<T>(res[f][1])),
+                                            to_c(from_c<T>(res[f][2])), to_c(from_c<T>(res[f][3])));
+                    } else {
+                        if (store) {
+                            store_vec<T, V>(out[0] + dst_off, res[0]);
+                            if constexpr (NF == 2) store_vec<T, V>(out[NF - 1] + dst_off, res[NF - 1]);
+                        }
+                        dst_off += plane;
+                    }
+                }
+            }
+        }
+        cp_async_wait<0>();
+        __syncthreads();
     }
 }
 

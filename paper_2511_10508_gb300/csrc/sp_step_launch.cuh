@@ -28,6 +28,7 @@ template <> struct Tiles<bf16> {
 };
 
 constexpr int kMinRun = 32;
+constexpr size_t kMaxSmemPerCta = 227 * 1024;  // opt-in maximum of dynamic shared memory per CTA
 
 // Persistent grids: one resident wave of CTAs (SMs x occupancy), each owning an
 // equal share of the flattened (tile, slow-axis) work, but at least kMinRun
@@ -111,6 +112,25 @@ cudaError_t launch_tbw(const StepArgs &a, cudaStream_t s, int n_sm) {
     constexpr int TY = 8;
     typedef Step3dTbwShape<MODEL, ST, T, TY, K> Sh;
     auto kern = step3d_tbw_kernel<MODEL, ST, T, TY, K>;
+    static const int occ = [&] {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem_bytes);
+        int o = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, Sh::NT, Sh::smem_bytes);
+        return o;
+    }();
+    const int tx = (a.nx + Sh::TX - 1) / Sh::TX, ty = (a.ny + TY - 1) / TY;
+    const long long wave = (long long)n_sm * std::max(occ, 1);
+    const int segs = lockstep_segments((long long)tx * ty, a.nz, 2 * K * Sh::r, wave);
+    const long long items = (long long)tx * ty * segs;
+    kern<<<(unsigned)std::min(items, wave), Sh::NT, Sh::smem_bytes, s>>>(a, tx, ty, segs);
+    return cudaGetLastError();
+}
+
+// The same for the cross stencils with a plane ring per level (tiles of 120 x TY).
+template <int MODEL, int ST, typename T, int TY, int K>
+cudaError_t launch_tbs(const StepArgs &a, cudaStream_t s, int n_sm) {
+    typedef Step3dTbsShape<MODEL, ST, T, TY, K> Sh;
+    auto kern = step3d_tbs_kernel<MODEL, ST, T, TY, K>;
     static const int occ = [&] {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem_bytes);
         int o = 1;
@@ -225,7 +245,14 @@ cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
         kern<<<dim3((unsigned)bx, (unsigned)by, (unsigned)bz), NT, Sh::smem_bytes, s>>>(a);
     } else if constexpr (!std::is_same<T, double>::value) {
         if constexpr (MODEL == AC || MODEL == GS) {
-            if (k == 2) return launch_tbw<MODEL, ST, T, 2>(a, s, n_sm);
+            if constexpr (ST == L27) {
+                if (k == 2) return launch_tbw<MODEL, ST, T, 2>(a, s, n_sm);
+            } else {
+                // taller tiles where their rings fit in shared memory (not Gray-Scott radius 2)
+                constexpr bool tall_fits = Step3dTbsShape<MODEL, ST, T, 16, 2>::smem_bytes <= kMaxSmemPerCta;
+                if (k == 2 && g_step_variant == 1 && tall_fits) return launch_tbs<MODEL, ST, T, (tall_fits ? 16 : 8), 2>(a, s, n_sm);
+                if (k == 2) return launch_tbs<MODEL, ST, T, 8, 2>(a, s, n_sm);
+            }
         }
         constexpr int ATX = 16, ATY = 16;
         typedef Step3dAsyncShape<MODEL, ST, T, ATX, ATY> AS;

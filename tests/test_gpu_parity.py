@@ -374,15 +374,18 @@ def test_temporal_blocking_3d_equals_single_steps(sp, dtype, model, st, shape):
     z segments, a grid smaller than the two-step halo in every direction, and
     graph replays (45 steps)."""
     outs = []
-    for spl in (1, 2):
+    configs = [(1, 0), (2, 0)] + ([(2, 1)] if st != 4 else [])  # family 1: taller tiles (cross stencils)
+    for spl, fam in configs:
         sim, dt = make(sp, model, shape, st, dtype=dtype, steps_per_launch=spl)
         with sim:
-            assert sim.launch_config[0] == spl
+            sim.launch_config = (spl, fam)
             sim.step(1)
             sim.step(44)
+            assert sim.launch_config == (spl, fam)
             outs.append([sim.read(f, as_f64=False) for f in range(2 if model in TWO else 1)])
-    for a, b in zip(outs[0], outs[1]):
-        assert np.array_equal(a, b)
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(a, b)
 
 
 @pytest.mark.parametrize("shape", [(256, 256), (9, 8), (45, 70)])
