@@ -69,7 +69,7 @@ WORKLOADS = {
     "mc2d-16384-f32-lap5": (3, 2, (16384, 16384), 0.02, 0, 1, 20),
     "mc3d-512-f64-lap7": (3, 3, (512, 512, 512), 0.02, 3, 0, 4),
     "mc3d-512-f32-lap7": (3, 3, (512, 512, 512), 0.02, 3, 1, 10),
-    # semi-implicit Fourier spectral scheme (cuFFT transforms), the stencil entry unused
+    # semi-implicit Fourier spectral scheme (the library's own FFTs), the stencil entry unused
     "ch2d-4096-f64-spectral": (1, 2, (4096, 4096), 0.5, 0, 0, 20),
     "ac2d-4096-f64-spectral": (0, 2, (4096, 4096), 0.5, 0, 0, 20),
     "ch2d-8192-f32-spectral": (1, 2, (8192, 8192), 0.5, 0, 1, 20),
@@ -121,10 +121,14 @@ def spectral_ops_per_lup(npts: int) -> float:
     return 5.0 * math.log2(npts) + 9.5
 
 
-# bytes per update of the spectral step at one pass per stage: cube 2P, forward
-# transform 2P, update 4P (resident spectrum and the transform's output in, both
-# copies out, each half-spectrum ~ P per point), inverse transform 2P
-SPECTRAL_BYTES_PER_LUP_IN_P = 10
+def spectral_bytes_per_lup_in_p(dims: int) -> int:
+    """Algorithmic bytes per update of the spectral step, in units of the storage
+    size P (a half spectrum holds about one P per real point): the x pass reads the
+    spectrum and writes phi and the next step's transformed cubic term (3P); the
+    last axis pass reads the transform and the resident spectrum and writes both
+    (4P); in 3D the y passes before and after it read and write the transform
+    (2P each)."""
+    return 7 if dims == 2 else 11
 
 
 def model_h_ops_per_lup(st: int) -> int:
@@ -186,14 +190,15 @@ def roofline(model: int, dims: int, st: int, dtype: int, order: int, spectral: b
         return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "FP64 Gop/s",
                 "frac": achieved / FP64_PEAK_GOPS, "traffic": None,
                 "note": f"semi-implicit spectral step, {ops:.1f} FP64 ops/LUP by the model 5 log2 N + 9.5 "
-                        "(two real cuFFT transforms at 2.5 log2 N each, cube, Fourier update)"}
+                        "(two real transforms at 2.5 log2 N each, cube, Fourier update)"}
     if spectral:
-        bpl = SPECTRAL_BYTES_PER_LUP_IN_P * ESIZE[dtype]
+        bpl = spectral_bytes_per_lup_in_p(dims) * ESIZE[dtype]
         achieved = bpl * npts * per_s
         return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "traffic": None,
-                "note": f"semi-implicit spectral step, {bpl} bytes/LUP at one pass per stage (cube, forward "
-                        "transform, Fourier update, inverse transform)"}
+                "note": f"semi-implicit spectral step, {bpl} bytes/LUP: one pass per transform axis (x pass "
+                        "fused with the cube and the next step's forward transform, the last axis pass fused "
+                        "with the Fourier update)"}
     if dtype == 0:
         ops = fp64_ops_per_lup(model, st, order, dims)
         achieved = ops * npts * per_s

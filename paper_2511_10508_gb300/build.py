@@ -66,7 +66,7 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
     if todo or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         libdir = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
         cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", LIB + ".tmp"] + objs + \
-            ["-ldl", "-Xlinker", "-rpath=" + libdir]  # cuFFT is dlopen-ed on first spectral use
+            ["-Xlinker", "-rpath=" + libdir]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")

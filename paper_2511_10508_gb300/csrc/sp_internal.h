@@ -105,15 +105,17 @@ cudaError_t launch_ic_currents(int dtype, void *const j[3], int dims, uint64_t N
 constexpr int kUnfusedFamily = 3;
 cudaError_t launch_unfused_ch(int dtype, int stencil, const StepArgs &a, void *mu, cudaStream_t s, int n_sm);
 
-// Semi-implicit Fourier spectral scheme (sp_spectral.cu): a plan holds the cuFFT
-// plans and the resident spectrum.  Functions return SP_* status codes.
+// Semi-implicit Fourier spectral scheme (sp_spectral.cu, with its own FFTs): a
+// plan holds the twiddle tables, the resident spectrum and the transform
+// buffer.  Functions return SP_* status codes.  spectral_step with `more` set
+// also transforms the cubic term of the new field for the step that follows.
 struct SpectralPlan;
 int spectral_create(int dtype, int dims, int nx, int ny, int nz, SpectralPlan **out);
 void spectral_destroy(SpectralPlan *P);
 size_t spectral_bytes(const SpectralPlan *P);
 int spectral_load(SpectralPlan *P, const void *phi, cudaStream_t s);
 int spectral_step(SpectralPlan *P, int model, void *phi, void *nbuf, double h, double dt, double c1, double c2,
-                  double kappa, cudaStream_t s, int n_sm);
+                  double kappa, cudaStream_t s, int n_sm, bool more);
 const char *spectral_last_error();
 
 cudaError_t launch_ic(int dtype, void *u, void *v, int model, int dims, int nx, int ny, int nz,

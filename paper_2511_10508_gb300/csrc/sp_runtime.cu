@@ -578,7 +578,7 @@ extern "C" int sp_step(sp_sim *s, int64_t nsteps, void *stream) {
                 s->spec_dirty = false;
             }
             if (int rc = spectral_step(s->spec, s->model, s->f[0][0], s->f[1][0], s->h, s->dt, s->p.c1, s->p.c2,
-                                       s->p.kappa, st, s->n_sm))
+                                       s->p.kappa, st, s->n_sm, i + 1 < nsteps))
                 return fail(rc, "spectral step: %s", spectral_last_error());
             s->steps += 1;
         }

@@ -1,8 +1,8 @@
 """Semi-implicit Fourier spectral scheme on the GPU against the numpy oracle
-(oracle/spectral.py).  The transforms differ (cuFFT vs numpy's), so results are
-compared with bounds: FP64 to 1e-12 of the field scale after the stated steps,
-FP32 storage and arithmetic to relative L2 1e-5 against the FP64 oracle started
-from the same (rounded) field."""
+(oracle/spectral.py).  The transforms differ (the library's own mixed-radix FFTs
+vs numpy's), so results are compared with bounds: FP64 to 1e-12 of the field
+scale after the stated steps, FP32 storage and arithmetic to relative L2 1e-5
+against the FP64 oracle started from the same (rounded) field."""
 import numpy as np
 import pytest
 
@@ -26,7 +26,10 @@ def sim_of(sp, model, shape, dtype=0, dt=0.1, **kw):
     return sp.Simulation(model, shape, dt=dt, dtype=dtype, scheme=sp.SCHEME_SPECTRAL, seed=31, **kw)
 
 
-CASES = [(0, (64, 96)), (1, (64, 96)), (0, (24, 20, 30)), (1, (24, 20, 30)), (1, (63, 45)), (0, (7, 9, 5))]
+# sides with every radix (8, 4, 2, 3, 5, 7), odd sides (no Nyquist bin), powers of two
+# (the radix-8/4/2 kernels), 2D and 3D, an odd number of rows (one row transformed alone)
+CASES = [(0, (64, 96)), (1, (64, 96)), (0, (24, 20, 30)), (1, (24, 20, 30)), (1, (63, 45)), (0, (7, 9, 5)),
+         (1, (64, 128)), (0, (16, 32, 64)), (1, (8, 16, 4)), (1, (1, 32)), (0, (5, 7, 1)), (1, (35, 56))]
 
 
 @pytest.mark.parametrize("model,shape", CASES)
@@ -51,6 +54,31 @@ def test_spectral_fp32_against_fp64_oracle(sp, model, shape):
     ref = SO.step(model, u0, dt=dt, nsteps=n)
     e = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert e < 1e-5, e
+
+
+@pytest.mark.parametrize("model,shape,dtype", [(1, (128, 4096), 0), (0, (96, 2048), 0), (1, (64, 8192), 1),
+                                               (0, (40, 4096), 1), (1, (64, 64, 64), 0)])
+def test_spectral_largest_sides(sp, model, shape, dtype):
+    """The longest lines one CTA transforms: 4096 points in FP64 and 8192 in FP32
+    (powers of two), 2048 / 4096 otherwise."""
+    dt, n = 0.1, 6
+    with sim_of(sp, model, shape, dtype=dtype, dt=dt) as s:
+        u0 = s.read(0)
+        s.step(n)
+        got = s.read(0)
+    ref = SO.step(model, u0, dt=dt, nsteps=n)
+    if dtype == 0:
+        assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+    else:
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-5
+
+
+@pytest.mark.parametrize("shape,dtype", [((11, 16), 0), ((16, 8192), 0), ((16, 6144), 1), ((22, 4, 4), 1)])
+def test_spectral_rejects_unsupported_sides(sp, shape, dtype):
+    """Prime factors beyond 7, or lines longer than one CTA transforms: SP_EINVAL."""
+    with pytest.raises(sp.SpError) as e:
+        sim_of(sp, 1, shape, dtype=dtype)
+    assert e.value.code == 1
 
 
 def test_spectral_cahn_hilliard_conserves_mass_at_large_dt(sp):
