@@ -49,6 +49,9 @@ struct FftLen {
     int n, nst;
     int rad[kFftMaxStages];
     int tw_off;  // offset (complex entries) of exp(-2 pi i t / n), t < n, in the plan's table
+    // powers of two: log2 n, and the two-level table w(t) = lo[t mod 2^ls] * hi[t >> ls]
+    // (lo[t] = exp(-2 pi i t / n), hi[u] = exp(-2 pi i u 2^ls / n)) at lo_off / hi_off
+    int log2n, ls, lo_off, hi_off;
 };
 
 template <typename R> struct Cplx;
@@ -151,9 +154,14 @@ template <int RAD, int DIR, typename C> __device__ __forceinline__ void dft(C (&
 // the product of the radices of the earlier stages.  Butterfly b of a line
 // (b < n/RAD) reads its inputs at stride n/RAD and writes them at stride p
 // from ((b - k) * RAD + k), k = b mod p.  Each thread keeps at most QMAX
-// butterflies in registers; the launch has at least G*n/8 threads.
-template <int RAD, int QMAX, int DIR, typename C>
-__device__ __forceinline__ void fft_stage(C *buf, int n, int G, int p, const C *tw, const C *roots) {
+// butterflies in registers.  POW2 (every length a power of two): index
+// arithmetic by shifts.  TWS: twiddles from the two-level table in shared
+// memory (lo, hi), one extra complex product each (FP32, where the kernels are
+// latency-bound); otherwise from the full table in global memory (FP64, where
+// the FP64 pipe is the bound and the table stays in L1/L2).
+template <int RAD, int QMAX, int DIR, bool POW2, bool TWS, typename C>
+__device__ __forceinline__ void fft_stage(C *buf, int n, int G, int p, const C *tw, const C *roots, const C *lo,
+                                          const C *hi, int lg_m, int lg_p, int ls) {
     const int m = n / RAD, step = n / (p * RAD), total = G * m;
     C u[QMAX][RAD];
     int ob[QMAX];
@@ -162,14 +170,26 @@ __device__ __forceinline__ void fft_stage(C *buf, int n, int G, int p, const C *
         const int b = threadIdx.x + q * blockDim.x;
         ob[q] = -1;
         if (b < total) {
-            const int line = b / m, i = b - line * m, k = i % p;
+            int line, i, k;
+            if constexpr (POW2) {
+                line = b >> lg_m;
+                i = b & (m - 1);
+                k = i & (p - 1);
+            } else {
+                line = b / m;
+                i = b - line * m;
+                k = i % p;
+            }
             const C *src = buf + (size_t)line * n + i;
 #pragma unroll
             for (int j = 0; j < RAD; ++j) u[q][j] = src[j * m];
             if (p > 1) {
 #pragma unroll
                 for (int j = 1; j < RAD; ++j) {
-                    C w = __ldg(tw + j * k * step);
+                    const int t = j * k * step;
+                    C w;
+                    if constexpr (TWS) w = cmul(lo[t & ((1 << ls) - 1)], hi[t >> ls]);
+                    else w = __ldg(tw + t);
                     if (DIR > 0) w.y = -w.y;
                     u[q][j] = cmul(u[q][j], w);
                 }
@@ -178,6 +198,7 @@ __device__ __forceinline__ void fft_stage(C *buf, int n, int G, int p, const C *
             ob[q] = line * n + (i - k) * RAD + k;
         }
     }
+    (void)lg_p;
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < QMAX; ++q)
@@ -188,37 +209,76 @@ __device__ __forceinline__ void fft_stage(C *buf, int n, int G, int p, const C *
     __syncthreads();
 }
 
+// Work split of the transforms: at most NT threads per CTA (512 FP64, 1024
+// FP32: the registers of one CTA fill the SM), VPT values of a line per thread
+// (each thread holds at most VPT values of a stage: QMAX = VPT / RAD
+// butterflies): 8 for powers of two, 4 for other lengths (every radix); TWS as
+// above.  (16 values per thread at two FP32 CTAs per SM spilled registers.)
+template <typename R, bool POW2> struct FftCfg {
+    static constexpr bool f64 = sizeof(R) == 8;
+    static constexpr int NT = f64 ? 512 : 1024, MINB = 1;
+    static constexpr int VPT = POW2 ? 8 : 4;
+    static constexpr bool TWS = POW2 && !f64;
+};
+
 // Transform G lines of L.n points in place (DIR = -1 forward, +1 inverse,
-// unnormalised).  Call with every thread of the CTA, after a barrier.  POW2:
-// radices 8, 4, 2 only, at least G*n/8 threads; otherwise every radix, at least
-// G*n/4 threads (each thread then holds at most 8 values of one stage).
-template <int DIR, bool POW2, typename C>
-__device__ void fft_lines(C *buf, const FftLen &L, int G, const C *tw_all, const C *roots) {
+// unnormalised).  Call with every thread of the CTA (at least G*n/VPT), after
+// a barrier.
+template <int DIR, bool POW2, typename R, typename C>
+__device__ __forceinline__ void fft_lines_t(C *buf, const FftLen &L, int G, const C *tw_all, const C *roots, const C *lo, const C *hi) {
+    typedef FftCfg<R, POW2> Cf;
+    constexpr int V = Cf::VPT;
+    constexpr bool T = Cf::TWS;
     const C *tw = tw_all + L.tw_off;
-    int p = 1;
+    int p = 1, lg_p = 0, lg_m = L.log2n;
     for (int s = 0; s < L.nst; ++s) {
         const int R_ = L.rad[s];
         if constexpr (POW2) {
-            if (R_ == 8) fft_stage<8, 1, DIR>(buf, L.n, G, p, tw, roots);
-            else if (R_ == 4) fft_stage<4, 2, DIR>(buf, L.n, G, p, tw, roots);
-            else fft_stage<2, 4, DIR>(buf, L.n, G, p, tw, roots);
+            if (R_ == 8) fft_stage<8, V / 8, DIR, true, T>(buf, L.n, G, p, tw, roots, lo, hi, lg_m - 3, lg_p, L.ls);
+            else if (R_ == 4) fft_stage<4, V / 4, DIR, true, T>(buf, L.n, G, p, tw, roots, lo, hi, lg_m - 2, lg_p, L.ls);
+            else fft_stage<2, V / 2, DIR, true, T>(buf, L.n, G, p, tw, roots, lo, hi, lg_m - 1, lg_p, L.ls);
+            lg_p += R_ == 8 ? 3 : R_ == 4 ? 2 : 1;
         } else {
             switch (R_) {
-            case 8: fft_stage<8, 1, DIR>(buf, L.n, G, p, tw, roots); break;
-            case 4: fft_stage<4, 1, DIR>(buf, L.n, G, p, tw, roots); break;
-            case 2: fft_stage<2, 2, DIR>(buf, L.n, G, p, tw, roots); break;
-            case 3: fft_stage<3, 2, DIR>(buf, L.n, G, p, tw, roots); break;
-            case 5: fft_stage<5, 1, DIR>(buf, L.n, G, p, tw, roots); break;
-            default: fft_stage<7, 1, DIR>(buf, L.n, G, p, tw, roots); break;
+            case 8: fft_stage<8, 1, DIR, false, false>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
+            case 4: fft_stage<4, 1, DIR, false, false>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
+            case 2: fft_stage<2, 2, DIR, false, false>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
+            case 3: fft_stage<3, 2, DIR, false, false>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
+            case 5: fft_stage<5, 1, DIR, false, false>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
+            default: fft_stage<7, 1, DIR, false, false>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
             }
         }
         p *= R_;
     }
 }
 
-// Threads per CTA of every FFT kernel: at most 512 (FP64) or 1024 (FP32), so
-// that the registers of the launch fit the SM.
-template <typename R> struct FftBounds { static constexpr int NT = sizeof(R) == 8 ? 512 : 1024; };
+template <int DIR, bool POW2, typename C>
+__device__ __forceinline__ void fft_lines(C *buf, const FftLen &L, int G, const C *tw_all, const C *roots,
+                                          const C *lo, const C *hi) {
+    typedef decltype(C{}.x) R;
+    fft_lines_t<DIR, POW2, R>(buf, L, G, tw_all, roots, lo, hi);
+}
+
+// Copy the two-level twiddle table of L into shared memory at dst (when the
+// transforms use it); returns the (lo, hi) pointers.  The caller's next barrier
+// publishes it.
+template <bool TWS, typename C>
+__device__ __forceinline__ void load_twiddles(const FftLen &L, const C *tw_all, C *dst, const C **lo, const C **hi) {
+    if constexpr (TWS) {
+        const int nlo = 1 << L.ls, nhi = L.n >> L.ls;
+        for (int t = threadIdx.x; t < nlo + nhi; t += blockDim.x)
+            dst[t] = t < nlo ? tw_all[L.lo_off + t] : tw_all[L.hi_off + (t - nlo)];
+        *lo = dst;
+        *hi = dst + nlo;
+    } else {
+        *lo = *hi = nullptr;
+    }
+}
+
+// complex entries of shared memory the two-level table of a length needs
+__host__ __device__ __forceinline__ int twiddle_smem(const FftLen &L, bool tws) {
+    return tws ? (1 << L.ls) + (L.n >> L.ls) : 0;
+}
 
 // ------------------------------------------------------------ row passes --
 
@@ -227,7 +287,8 @@ template <typename R> struct FftBounds { static constexpr int NT = sizeof(R) == 
 template <typename R, bool CUBE, bool POW2>
 __device__ void rows_forward_body(typename Cplx<R>::type *buf, const R *f, typename Cplx<R>::type *Z, int nx,
                                   int nrows, int ra, R coef, const FftLen &L, const typename Cplx<R>::type *tw,
-                                  const typename Cplx<R>::type *roots, bool load) {
+                                  const typename Cplx<R>::type *roots, const typename Cplx<R>::type *lo,
+                                  const typename Cplx<R>::type *hi, bool load) {
     typedef typename Cplx<R>::type C;
     const int rb = ra + 1;
     const bool has_b = rb < nrows;
@@ -242,7 +303,7 @@ __device__ void rows_forward_body(typename Cplx<R>::type *buf, const R *f, typen
         }
     }
     __syncthreads();
-    fft_lines<-1, POW2>(buf, L, 1, tw, roots);
+    fft_lines<-1, POW2>(buf, L, 1, tw, roots, lo, hi);
     const int nxh = nx / 2 + 1;
     for (int k = threadIdx.x; k < nxh; k += blockDim.x) {
         const C zk = buf[k], zc = buf[k == 0 ? 0 : nx - k];
@@ -255,23 +316,27 @@ __device__ void rows_forward_body(typename Cplx<R>::type *buf, const R *f, typen
 }
 
 template <typename R, bool CUBE, bool POW2>
-__global__ void __launch_bounds__(FftBounds<R>::NT)
+__global__ void __launch_bounds__(FftCfg<R, POW2>::NT, FftCfg<R, POW2>::MINB)
     rows_forward_kernel(const R *f, typename Cplx<R>::type *Z, int nx, int nrows, R coef, FftLen L,
                         const typename Cplx<R>::type *tw, const typename Cplx<R>::type *roots) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     typedef typename Cplx<R>::type C;
-    rows_forward_body<R, CUBE, POW2>(reinterpret_cast<C *>(smem_raw), f, Z, nx, nrows, 2 * blockIdx.x, coef, L, tw, roots,
-                               true);
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    const C *lo, *hi;
+    load_twiddles<FftCfg<R, POW2>::TWS>(L, tw, buf + nx, &lo, &hi);
+    rows_forward_body<R, CUBE, POW2>(buf, f, Z, nx, nrows, 2 * blockIdx.x, coef, L, tw, roots, lo, hi, true);
 }
 
 // Inverse x transforms of rows 2c, 2c+1 from Z into phi; with NEXT, the cubic
 // term of the new rows is transformed forward into Z for the next step.
 template <typename R, bool NEXT, bool POW2>
-__global__ void __launch_bounds__(FftBounds<R>::NT) rows_inverse_kernel(typename Cplx<R>::type *Z, R *phi, int nx, int nrows, R coef, FftLen L,
+__global__ void __launch_bounds__(FftCfg<R, POW2>::NT, FftCfg<R, POW2>::MINB) rows_inverse_kernel(typename Cplx<R>::type *Z, R *phi, int nx, int nrows, R coef, FftLen L,
                                     const typename Cplx<R>::type *tw, const typename Cplx<R>::type *roots) {
     typedef typename Cplx<R>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
+    const C *lo, *hi;
+    load_twiddles<FftCfg<R, POW2>::TWS>(L, tw, buf + nx, &lo, &hi);
     const int ra = 2 * blockIdx.x, rb = ra + 1;
     const bool has_b = rb < nrows;
     const int half = nx / 2;
@@ -291,14 +356,14 @@ __global__ void __launch_bounds__(FftBounds<R>::NT) rows_inverse_kernel(typename
         buf[k] = C{A.x - B.y, A.y + B.x};  // A + i B
     }
     __syncthreads();
-    fft_lines<1, POW2>(buf, L, 1, tw, roots);
+    fft_lines<1, POW2>(buf, L, 1, tw, roots, lo, hi);
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
         const C v = buf[i];
         phi[(size_t)ra * nx + i] = v.x;
         if (has_b) phi[(size_t)rb * nx + i] = v.y;
         if (NEXT) buf[i] = C{coef * ((v.x * v.x) * v.x), has_b ? coef * ((v.y * v.y) * v.y) : R(0)};
     }
-    if (NEXT) rows_forward_body<R, false, POW2>(buf, nullptr, Z, nx, nrows, ra, coef, L, tw, roots, false);
+    if (NEXT) rows_forward_body<R, false, POW2>(buf, nullptr, Z, nx, nrows, ra, coef, L, tw, roots, lo, hi, false);
 }
 
 // ----------------------------------------------------------- line passes --
@@ -338,12 +403,14 @@ __device__ __forceinline__ typename Cplx<R>::type update_mode(typename Cplx<R>::
 }
 
 template <typename R, int MODE, int MODEL, bool POW2>
-__global__ void __launch_bounds__(FftBounds<R>::NT) lines_kernel(typename Cplx<R>::type *Z, typename Cplx<R>::type *uh, LineGeom g, FftLen L,
+__global__ void __launch_bounds__(FftCfg<R, POW2>::NT, FftCfg<R, POW2>::MINB) lines_kernel(typename Cplx<R>::type *Z, typename Cplx<R>::type *uh, LineGeom g, FftLen L,
                              const typename Cplx<R>::type *tw, const typename Cplx<R>::type *roots, R tx, R ty, R tz,
                              R c1, R kappa, R dt, R inv_n) {
     typedef typename Cplx<R>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
+    const C *lo, *hi;
+    load_twiddles<FftCfg<R, POW2>::TWS>(L, tw, buf + (size_t)g.G * g.n, &lo, &hi);
     const int n = g.n;
     // first line of this CTA's group and its line count
     const int gi = blockIdx.x;
@@ -362,17 +429,23 @@ __global__ void __launch_bounds__(FftBounds<R>::NT) lines_kernel(typename Cplx<R
     }
     for (int e = threadIdx.x; e < nl * n; e += blockDim.x) {
         int l, i;
-        if (g.estride == 1) { l = e / n; i = e - l * n; }
+        if (g.estride == 1) {
+            if (POW2) { l = e >> L.log2n; i = e & (n - 1); }
+            else { l = e / n; i = e - l * n; }
+        }
         else { i = e / nl; l = e - i * nl; }   // adjacent lines first: coalesced
         buf[l * n + i] = Z[base + (size_t)l * g.lstride + (size_t)i * g.estride];
     }
     __syncthreads();
-    if (MODE == kLineInverse) fft_lines<1, POW2>(buf, L, nl, tw, roots);
-    else fft_lines<-1, POW2>(buf, L, nl, tw, roots);
+    if (MODE == kLineInverse) fft_lines<1, POW2>(buf, L, nl, tw, roots, lo, hi);
+    else fft_lines<-1, POW2>(buf, L, nl, tw, roots, lo, hi);
     if (MODE == kLineUpdate) {
         for (int e = threadIdx.x; e < nl * n; e += blockDim.x) {
             int l, i;
-            if (g.estride == 1) { l = e / n; i = e - l * n; }
+            if (g.estride == 1) {
+            if (POW2) { l = e >> L.log2n; i = e & (n - 1); }
+            else { l = e / n; i = e - l * n; }
+        }
             else { i = e / nl; l = e - i * nl; }
             const size_t at = base + (size_t)l * g.lstride + (size_t)i * g.estride;
             int mx, my, mz;
@@ -389,11 +462,14 @@ __global__ void __launch_bounds__(FftBounds<R>::NT) lines_kernel(typename Cplx<R
                                                    inv_n);
         }
         __syncthreads();
-        fft_lines<1, POW2>(buf, L, nl, tw, roots);
+        fft_lines<1, POW2>(buf, L, nl, tw, roots, lo, hi);
     }
     for (int e = threadIdx.x; e < nl * n; e += blockDim.x) {
         int l, i;
-        if (g.estride == 1) { l = e / n; i = e - l * n; }
+        if (g.estride == 1) {
+            if (POW2) { l = e >> L.log2n; i = e & (n - 1); }
+            else { l = e / n; i = e - l * n; }
+        }
         else { i = e / nl; l = e - i * nl; }
         Z[base + (size_t)l * g.lstride + (size_t)i * g.estride] = buf[l * n + i];
     }
@@ -416,10 +492,11 @@ static bool factor_len(int n, FftLen *L) {
 
 static bool is_pow2(int n) { return (n & (n - 1)) == 0; }
 
-// threads for G lines of n points: G*n/8 (radices 8, 4, 2) or G*n/4 (any radix),
-// so that no thread holds more butterflies than a stage's QMAX; whole warps
-static int fft_threads(int n, int G, bool pow2) {
-    const int t = (G * n + (pow2 ? 7 : 3)) / (pow2 ? 8 : 4);
+// threads for G lines of n points: G*n/VPT (so that no thread holds more
+// butterflies than a stage's QMAX), whole warps
+template <typename R> static int fft_threads(int n, int G, bool pow2) {
+    const int vpt = pow2 ? FftCfg<R, true>::VPT : FftCfg<R, false>::VPT;
+    const int t = (G * n + vpt - 1) / vpt;
     return std::max(32, (t + 31) / 32 * 32);
 }
 
@@ -428,17 +505,14 @@ template <typename R> static size_t csize() { return 2 * sizeof(R); }
 // lines per CTA for a pass of n-point lines: within the thread limit of the
 // launch and 64 KB of shared memory (at least one line)
 template <typename R> static int lines_per_cta(int n, bool pow2, int cap) {
-    const int by_threads = FftBounds<R>::NT * (pow2 ? 8 : 4) / n;
+    const int vpt = pow2 ? FftCfg<R, true>::VPT : FftCfg<R, false>::VPT;
+    const int by_threads = FftCfg<R, true>::NT * vpt / n;
     const int by_smem = (int)(64 * 1024 / (csize<R>() * (size_t)n));
     return std::max(1, std::min(std::min(by_threads, by_smem), cap));
 }
 
-struct PlanCfg {
-    bool pow2;
-};
-
 template <typename R> static bool fits(int n, bool pow2) {
-    return n <= kFftMaxN && fft_threads(n, 1, pow2) <= FftBounds<R>::NT;
+    return n <= kFftMaxN && fft_threads<R>(n, 1, pow2) <= FftCfg<R, true>::NT;
 }
 
 int spectral_create(int dtype, int dims, int nx, int ny, int nz, SpectralPlan **out) {
@@ -462,7 +536,7 @@ int spectral_create(int dtype, int dims, int nx, int ny, int nz, SpectralPlan **
                         (f64 ? fits<double>(sides[a], P->pow2) : fits<float>(sides[a], P->pow2));
         if (!ok) {
             g_fft_err = std::string("the spectral scheme needs sides with prime factors 2, 3, 5, 7 of at most ") +
-                        (f64 ? "4096 (FP64, powers of two; 2048 otherwise)" : "8192 (FP32, powers of two; 4096 otherwise)") +
+                        (f64 ? "4096 (FP64, powers of two; 2048 otherwise)" : "8192 (FP32, powers of two; 2048 otherwise)") +
                         " points (got " + std::to_string(sides[a]) + ")";
             delete P;
             return SP_EINVAL;
@@ -491,6 +565,28 @@ int spectral_create(int dtype, int dims, int nx, int ny, int nz, SpectralPlan **
     P->lx.tw_off = offs[0];
     P->ly.tw_off = offs[1];
     P->lz.tw_off = offs[2];
+    // two-level tables of the power-of-two lengths: lo[t] = w^t (t < 2^ls), hi[u] = w^(u 2^ls)
+    for (int a = 0; a < 3; ++a) {
+        FftLen &L = *ls[a];
+        int lg = 0;
+        while ((1 << lg) < L.n) ++lg;
+        L.log2n = lg;
+        L.ls = (lg + 1) / 2;
+        L.lo_off = L.hi_off = 0;
+        if (!P->pow2) continue;
+        L.lo_off = (int)re.size();
+        for (int t = 0; t < (1 << L.ls); ++t) {
+            const long double ang = two_pi * (long double)t / (long double)L.n;
+            re.push_back(cosl(ang));
+            im.push_back(-sinl(ang));
+        }
+        L.hi_off = (int)re.size();
+        for (int u = 0; u < (L.n >> L.ls); ++u) {
+            const long double ang = two_pi * (long double)u * (long double)(1 << L.ls) / (long double)L.n;
+            re.push_back(cosl(ang));
+            im.push_back(-sinl(ang));
+        }
+    }
     P->roots_off = (int)re.size();
     for (int R_ : {3, 5, 7})
         for (int t = 0; t < R_; ++t) {
@@ -566,12 +662,12 @@ static cudaError_t run_lines_t(SpectralPlan *P, int axis, cudaStream_t s, R tx, 
     const FftLen &L = axis == 1 ? P->ly : P->lz;
     const unsigned blocks = axis == 1 ? (unsigned)((P->nxh * P->nz + g.G - 1) / g.G)
                                       : (unsigned)(P->nxh * g.groups_per_kx);
-    const size_t smem = (size_t)g.G * g.n * csize<R>();
+    const size_t smem = ((size_t)g.G * g.n + twiddle_smem(L, FftCfg<R, POW2>::TWS)) * csize<R>();
     auto kern = lines_kernel<R, MODE, MODEL, POW2>;
     cudaError_t e = prepare(kern, smem);
     if (e != cudaSuccess) return e;
     const C *tw = static_cast<const C *>(P->tw);
-    kern<<<blocks, fft_threads(g.n, g.G, POW2), smem, s>>>(Z, static_cast<C *>(P->uh), g, L, tw, tw + P->roots_off,
+    kern<<<blocks, fft_threads<R>(g.n, g.G, POW2), smem, s>>>(Z, static_cast<C *>(P->uh), g, L, tw, tw + P->roots_off,
                                                            tx, ty, tz, c1, kappa, dt, inv_n);
     return cudaGetLastError();
 }
@@ -587,12 +683,12 @@ template <typename R, bool CUBE, bool POW2>
 static cudaError_t run_rows_forward_t(SpectralPlan *P, const R *f, typename Cplx<R>::type *Z, R coef, cudaStream_t s) {
     typedef typename Cplx<R>::type C;
     const int nrows = P->ny * P->nz;
-    const size_t smem = (size_t)P->nx * csize<R>();
+    const size_t smem = ((size_t)P->nx + twiddle_smem(P->lx, FftCfg<R, POW2>::TWS)) * csize<R>();
     auto kern = rows_forward_kernel<R, CUBE, POW2>;
     cudaError_t e = prepare(kern, smem);
     if (e != cudaSuccess) return e;
     const C *tw = static_cast<const C *>(P->tw);
-    kern<<<(unsigned)((nrows + 1) / 2), fft_threads(P->nx, 1, POW2), smem, s>>>(f, Z, P->nx, nrows, coef, P->lx, tw,
+    kern<<<(unsigned)((nrows + 1) / 2), fft_threads<R>(P->nx, 1, POW2), smem, s>>>(f, Z, P->nx, nrows, coef, P->lx, tw,
                                                                                 tw + P->roots_off);
     return cudaGetLastError();
 }
@@ -607,12 +703,12 @@ template <typename R, bool NEXT, bool POW2>
 static cudaError_t run_rows_inverse_t(SpectralPlan *P, R *phi, R coef, cudaStream_t s) {
     typedef typename Cplx<R>::type C;
     const int nrows = P->ny * P->nz;
-    const size_t smem = (size_t)P->nx * csize<R>();
+    const size_t smem = ((size_t)P->nx + twiddle_smem(P->lx, FftCfg<R, POW2>::TWS)) * csize<R>();
     auto kern = rows_inverse_kernel<R, NEXT, POW2>;
     cudaError_t e = prepare(kern, smem);
     if (e != cudaSuccess) return e;
     const C *tw = static_cast<const C *>(P->tw);
-    kern<<<(unsigned)((nrows + 1) / 2), fft_threads(P->nx, 1, POW2), smem, s>>>(
+    kern<<<(unsigned)((nrows + 1) / 2), fft_threads<R>(P->nx, 1, POW2), smem, s>>>(
         static_cast<C *>(P->z), phi, P->nx, nrows, coef, P->lx, tw, tw + P->roots_off);
     return cudaGetLastError();
 }
