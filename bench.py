@@ -395,9 +395,46 @@ def run_one_at_a_time_fp64(sp, reqs):
     return lups / el / 1e9, el
 
 
+def served_summary_large(sp, n_req: int, seed=4, calib=100, baseline_sample=200):
+    """The served stream at its stated size: capacities (burst GLUPS of the mixed
+    stream and of its FP32 form) calibrated on the first `calib` requests, then
+    all `n_req` requests arrive as a Poisson stream at 0.7 of the calibrated
+    capacity, in both forms; the one-at-a-time FP64 baseline runs a seeded sample
+    of `baseline_sample` requests of the same stream."""
+    import numpy as np
+
+    reqs = served_requests(n_req, seed)
+    mean_lups = float(np.mean([np.prod(sh) * n for _, sh, _, n, _ in reqs]))
+    cal = reqs[:calib]
+    cal32 = [(m, sh, dt, n, dict(kw, dtype=1)) for m, sh, dt, n, kw in cal]
+    burst_glups, _, burst_s = run_served(sp, cal)
+    b32_glups, _, b32_s = run_served(sp, cal32)
+    rate = 0.7 * burst_glups * 1e9 / mean_lups
+    glups, lat, el = run_served(sp, reqs, rate=rate)
+    reqs32 = [(m, sh, dt, n, dict(kw, dtype=1)) for m, sh, dt, n, kw in reqs]
+    rate32 = 0.7 * b32_glups * 1e9 / mean_lups
+    g32, lat32, el32 = run_served(sp, reqs32, rate=rate32)
+    rng = np.random.default_rng(seed + 1)
+    pick = sorted(rng.choice(n_req, size=min(baseline_sample, n_req), replace=False))
+    fp64_glups, fp64_s = run_one_at_a_time_fp64(sp, [reqs[i] for i in pick])
+    return {"requests": n_req, "mix": "AC/CH/GS x 2D (64^2-2048^2) / 3D (32^3-256^3) x FP32/FP64, 100-5000 steps",
+            "budget_bytes": 120 << 30, "arrivals": "Poisson at 0.7 of the burst capacity of the first "
+            f"{calib} requests", "calibration": {"burst_glups": burst_glups, "burst_makespan_s": burst_s,
+                                                 "fp32_burst_glups": b32_glups, "fp32_burst_makespan_s": b32_s},
+            "poisson_rate_per_s": rate, "glups": glups, "makespan_s": el,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "fp32_form": {"poisson_rate_per_s": rate32, "glups": g32, "makespan_s": el32,
+                          "p50_s": float(np.percentile(lat32, 50)), "p99_s": float(np.percentile(lat32, 99))},
+            "fp64_one_at_a_time_glups": fp64_glups, "fp64_one_at_a_time_s": fp64_s,
+            "fp64_one_at_a_time_sample": f"{len(pick)} requests drawn without replacement (seed {seed + 1})",
+            "served_vs_fp64": glups / fp64_glups, "served_fp32_vs_fp64": g32 / fp64_glups}
+
+
 def served_summary(sp, n_req=100, seed=4):
     import numpy as np
 
+    if n_req > 1000:
+        return served_summary_large(sp, n_req, seed)
     reqs = served_requests(n_req, seed)
     mean_lups = float(np.mean([np.prod(sh) * n for _, sh, _, n, _ in reqs]))
     burst_glups, _, burst_s = run_served(sp, reqs)

@@ -325,8 +325,9 @@ int sp_destroy(sp_sim *sim);
  * Continuous-batching server (the paper has no serving layer; it benchmarks
  * one grid at a time, Sec. "Benchmarks").  Requests of any model, dimension,
  * size and precision (FP64 or FP32 storage) arrive at any time; a scheduler
- * thread admits them in arrival order whenever a slot and enough of the HBM
- * budget are free (a request that does not fit yet lets smaller ones pass),
+ * thread admits them by priority, in arrival order within a priority, whenever
+ * a slot and enough of the HBM budget are free (a request that does not fit yet
+ * lets later ones that fit pass; sp_admission_order states the rule),
  * keeps their fields resident, and advances all resident grids together in
  * quanta of `quantum_steps` time steps: one batched launch per (dims, dtype)
  * per step covers the tiles of every resident grid, and the quantum's launches
@@ -345,6 +346,7 @@ typedef struct sp_request {
     int64_t nsteps;         /* time steps to run (>= 1) */
     int return_fields;      /* nonzero: keep an FP64 host copy of the final fields */
     int fault;              /* fault injection for tests: 0 none, 1 the allocation fails */
+    int priority;           /* admission priority: higher first (see sp_admission_order) */
 } sp_request;
 
 typedef struct sp_result {
@@ -364,6 +366,17 @@ typedef struct sp_server_stats {
     double lups;            /* lattice-site updates done (points x steps) */
     double busy_s;          /* seconds the scheduler spent running quanta */
 } sp_server_stats;
+
+/* The server's admission rule as a pure host function (no device work; the
+ * scheduler calls the same code): n pending requests in arrival order, with
+ * their field bytes and priorities, `free_bytes` of the budget and `free_slots`
+ * slots free.  Requests are taken by priority (higher first), in arrival order
+ * within a priority; each one that fits the remaining bytes and slots is
+ * admitted, one that does not lets later ones pass.  The indices of the
+ * admitted requests, in admission order, go to order[] (room for n); returns
+ * their number, or -1 if an array is NULL while n > 0. */
+int sp_admission_order(int n, const size_t bytes[], const int priority[], size_t free_bytes, int free_slots,
+                       int order[]);
 
 /* Create a server on the current device with an HBM budget for field buffers,
  * at most max_slots resident grids, and quanta of quantum_steps steps. */

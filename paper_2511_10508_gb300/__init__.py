@@ -17,7 +17,7 @@ from ._native import (ALLEN_CAHN, BF16_F32, CAHN_HILLIARD, F32, F64, FLAG_AUTOTU
                       IC_NOISE, LAP_5, LAP_7, LAP_9BOX, LAP_9CROSS4, LAP_13CROSS4, LAP_27, LAP_DEFAULT, LAP_GENERATED, MASS,
                       MAX_U, MIN_U, MODEL_C, MODEL_H, SCHEME_FD, SCHEME_SPECTRAL, SUM_U, SUM_V, SUMSQ_U, SpError)
 
-__all__ = ["Simulation", "Server", "Result", "params", "check_stability", "SpError", "ALLEN_CAHN", "CAHN_HILLIARD", "GRAY_SCOTT",
+__all__ = ["Simulation", "Server", "Result", "params", "admission_order", "check_stability", "SpError", "ALLEN_CAHN", "CAHN_HILLIARD", "GRAY_SCOTT",
            "MODEL_C", "MODEL_H", "SCHEME_FD", "SCHEME_SPECTRAL",
            "LAP_5", "LAP_9BOX", "LAP_9CROSS4", "LAP_7", "LAP_27", "LAP_13CROSS4", "LAP_DEFAULT", "LAP_GENERATED",
            "stencil_weights", "F64", "F32",
@@ -211,6 +211,19 @@ class Result:
         return self.t_finish - self.t_submit
 
 
+def admission_order(bytes_, priorities, free_bytes: int, free_slots: int) -> list[int]:
+    """The server's admission rule (sp_admission_order): indices of the pending
+    requests admitted now, in admission order."""
+    n = len(bytes_)
+    b = (ctypes.c_size_t * max(n, 1))(*[int(x) for x in bytes_])
+    p = (ctypes.c_int * max(n, 1))(*[int(x) for x in priorities])
+    o = (ctypes.c_int * max(n, 1))()
+    k = N.lib().sp_admission_order(n, b, p, int(free_bytes), int(free_slots), o)
+    if k < 0:
+        raise SpError(N.SP_EINVAL, "sp_admission_order")
+    return [o[i] for i in range(k)]
+
+
 class Server:
     """Continuous-batching server (``sp_server_*``): submit grids at any time,
     collect results by ticket."""
@@ -223,7 +236,7 @@ class Server:
         self._meta = {}
 
     def submit(self, model: int, shape, *, dt: float, nsteps: int, h: float = 1.0, prm: N.sp_params | None = None,
-               return_fields: bool = False, fault: int = 0, **kw) -> int:
+               return_fields: bool = False, fault: int = 0, priority: int = 0, **kw) -> int:
         shape = tuple(int(s) for s in shape)
         dims = len(shape)
         r = N.sp_request()
@@ -236,6 +249,7 @@ class Server:
         r.nsteps = int(nsteps)
         r.return_fields = int(bool(return_fields))
         r.fault = int(fault)
+        r.priority = int(priority)
         t = ctypes.c_uint64(0)
         N.check(N.lib().sp_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "sp_submit")
         self._meta[t.value] = (shape, 2 if model in (GRAY_SCOTT, MODEL_C) else 1)

@@ -44,7 +44,8 @@ class sp_params(ctypes.Structure):
 class sp_request(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int), ("dims", ctypes.c_int), ("shape", ctypes.c_int64 * 3),
                 ("h", ctypes.c_double), ("dt", ctypes.c_double), ("params", sp_params),
-                ("nsteps", ctypes.c_int64), ("return_fields", ctypes.c_int), ("fault", ctypes.c_int)]
+                ("nsteps", ctypes.c_int64), ("return_fields", ctypes.c_int), ("fault", ctypes.c_int),
+                ("priority", ctypes.c_int)]
 
 
 class sp_result(ctypes.Structure):
@@ -88,6 +89,8 @@ _SIGS = {
     "sp_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, _P(sp_result)]),
     "sp_wait": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_double, _P(sp_result)]),
     "sp_release": (ctypes.c_int, [_vp, ctypes.c_uint64]),
+    "sp_admission_order": (ctypes.c_int, [ctypes.c_int, _P(ctypes.c_size_t), _P(ctypes.c_int), ctypes.c_size_t,
+                                          ctypes.c_int, _P(ctypes.c_int)]),
     "sp_server_get_stats": (ctypes.c_int, [_vp, _P(sp_server_stats)]),
     "sp_server_destroy": (ctypes.c_int, [_vp]),
     "sp_last_error": (ctypes.c_char_p, []),

@@ -11,8 +11,9 @@
 // captured once into a CUDA graph and replayed while the set of resident grids
 // is unchanged; grids that finish inside a quantum skip the remaining steps.
 //
-// Host side: a scheduler thread admits pending requests in arrival order
-// (smaller requests may pass a large one that does not fit yet), allocates
+// Host side: a scheduler thread admits pending requests by priority, in
+// arrival order within a priority (later requests may pass one that does not
+// fit yet; sp_admission_order), allocates
 // their buffers stream-ordered, writes the seeded initial condition, runs
 // quanta, and retires finished grids: FP64 mass, optional FP64 copy of the
 // fields to host memory, buffers freed, waiters notified.
@@ -382,19 +383,29 @@ static void scheduler(sp_server *S) {
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv_work.wait(lk, [&] { return S->stop || !S->pending.empty() || !S->resident.empty(); });
             if (S->stop) break;
-            // admission in arrival order; a request that does not fit yet lets smaller ones pass
-            size_t slots = S->resident.size();
-            for (auto it = S->pending.begin(); it != S->pending.end();) {
-                Req *q = *it;
-                if (slots < (size_t)S->max_slots && S->used + q->bytes <= S->budget) {
-                    S->used += q->bytes;
-                    ++slots;
-                    admit.push_back(q);
-                    it = S->pending.erase(it);
-                } else {
-                    ++it;
-                }
+            // admission by priority, arrival order within a priority; a request that
+            // does not fit yet lets later ones pass (sp_admission_order)
+            const int np = (int)S->pending.size();
+            std::vector<size_t> bytes(np);
+            std::vector<int> prio(np), order(np);
+            for (int i = 0; i < np; ++i) {
+                bytes[i] = S->pending[i]->bytes;
+                prio[i] = S->pending[i]->r.priority;
             }
+            const int free_slots = std::max(0, S->max_slots - (int)S->resident.size());
+            const int na = sp_admission_order(np, bytes.data(), prio.data(), S->budget - S->used, free_slots,
+                                              order.data());
+            std::vector<bool> taken(np, false);
+            for (int a = 0; a < na; ++a) {
+                Req *q = S->pending[order[a]];
+                S->used += q->bytes;
+                admit.push_back(q);
+                taken[order[a]] = true;
+            }
+            std::deque<Req *> rest;
+            for (int i = 0; i < np; ++i)
+                if (!taken[i]) rest.push_back(S->pending[i]);
+            S->pending.swap(rest);
         }
         // allocate and initialise outside the lock
         for (Req *q : admit) {
@@ -465,6 +476,24 @@ static void scheduler(sp_server *S) {
             cudaGetLastError();
         }
     }
+}
+
+extern "C" int sp_admission_order(int n, const size_t bytes[], const int priority[], size_t free_bytes,
+                                  int free_slots, int order[]) {
+    if (n <= 0) return 0;
+    if (!bytes || !priority || !order) return -1;
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return priority[a] > priority[b]; });
+    int na = 0;
+    for (int i : idx) {
+        if (na >= free_slots) break;
+        if (bytes[i] <= free_bytes) {
+            free_bytes -= bytes[i];
+            order[na++] = i;
+        }
+    }
+    return na;
 }
 
 extern "C" int sp_server_create(size_t hbm_budget_bytes, int max_slots, int quantum_steps, sp_server **out) {

@@ -196,3 +196,22 @@ def test_generated_stencil_rejections(sp):
     p = sp.params(sp.ALLEN_CAHN, 3, stencil=sp.LAP_GENERATED, stencil_order=8)
     ok, f = sp.check_stability(sp.ALLEN_CAHN, 3, 1.0, 0.01, p)
     assert ok and abs(f - 0.01 * max(1.0, abs(1.0 - lm), 2.0, abs(-2.0 - lm))) < 1e-12
+
+
+def test_admission_order_by_priority(sp):
+    """The server's admission rule on the host: higher priority first, arrival
+    order within a priority, requests that do not fit let later ones pass, and
+    the slot limit stops admission."""
+    order = sp.admission_order
+    # everything fits: priority, then arrival
+    assert order([10, 10, 10, 10], [0, 2, 1, 2], 100, 10) == [1, 3, 2, 0]
+    # the high-priority request is too large for now: smaller ones pass it
+    assert order([80, 30, 30, 30], [5, 0, 1, 0], 70, 10) == [2, 1]
+    # the budget is consumed in admission order
+    assert order([40, 40, 40], [0, 0, 9], 90, 10) == [2, 0]
+    # slots
+    assert order([1, 1, 1, 1], [3, 2, 1, 0], 100, 2) == [0, 1]
+    assert order([1, 1], [0, 0], 100, 0) == []
+    assert order([], [], 100, 4) == []
+    # negative priorities come after the default 0
+    assert order([1, 1, 1], [-1, 0, -5], 100, 10) == [1, 0, 2]

@@ -190,3 +190,19 @@ def test_served_fp32_requests_against_fp64_oracle(sp):
             worst[key] = (n, sh, errs)
             assert max(errs) <= 2e-4, (key, n, sh, errs)
     print({k: (n, sh[0], [f"{e:.1e}" for e in errs]) for k, (n, sh, errs) in worst.items()})
+
+
+def test_admission_follows_priority(sp):
+    """With room for one resident grid, queued requests are admitted by priority
+    (arrival order within a priority), whatever their arrival order."""
+    shape = (256, 256)
+    one = 2 * 256 * 256 * 8  # bytes of one FP64 single-field grid (two levels)
+    with sp.Server(one, max_slots=4, quantum_steps=20) as srv:
+        blocker = srv.submit(0, shape, dt=0.05, nsteps=4000, seed=1, ic_amp=0.1)
+        prios = [0, 2, 1, 2, -1]
+        tickets = [srv.submit(0, shape, dt=0.05, nsteps=20, seed=10 + i, ic_amp=0.1, priority=p)
+                   for i, p in enumerate(prios)]
+        res = [srv.wait(t, timeout=120) for t in tickets]
+        srv.wait(blocker, timeout=120)
+    admitted = sorted(range(len(prios)), key=lambda i: res[i].t_admit)
+    assert admitted == [1, 3, 2, 0, 4], [(prios[i], res[i].t_admit) for i in admitted]
