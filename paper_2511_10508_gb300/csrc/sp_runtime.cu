@@ -469,8 +469,8 @@ static std::vector<TuneChoice> tune_candidates(const sp_sim *s) {
         c.push_back({1, 1});
         if (s->dims == 3 && s->dtype != SP_F64) c.push_back({1, 2});
         if (s->dims == 3 && steps_per_launch_3d(s->dtype, s->model, s->nx, 2) == 2) {
-            c.push_back({2, 0});
-            if (s->stencil != SP_LAP_27) c.push_back({2, 1});  // taller tiles
+            c.push_back({2, 0});  // two steps per pass, 8 rows
+            c.push_back({2, 1});  // 16 rows
         }
         if (s->dims == 2 && s->dtype == SP_F64) {
             if (s->N <= (size_t)kSmallGrid2d) {  // small grids: steps fused per launch

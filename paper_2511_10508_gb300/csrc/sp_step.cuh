@@ -15,10 +15,8 @@
 //   step3d_kernel        3D, FP64: shared-memory plane rings
 //   step3d_zreg_kernel   3D, FP64, 27-point: z-streaming with register queues
 //   step3d_wr_kernel     3D, FP32/BF16: warp per tile row, z in register queues
-//   step3d_tbw_kernel    3D, FP32/BF16 Allen-Cahn / Gray-Scott, 27-point: K steps
-//                        per pass (warp rows, a register queue and plane buffer per level)
-//   step3d_tbs_kernel    3D, FP32/BF16 Allen-Cahn / Gray-Scott, cross stencils: K
-//                        steps per pass (warp rows, a plane ring per level)
+//   step3d_tbs_kernel    3D, FP32/BF16 Allen-Cahn / Gray-Scott: 2 steps per pass
+//                        (warp rows, a plane ring per time level)
 //   step3d_async_kernel  3D, FP32/BF16: cp.async plane ring, planes in flight
 //   step3d_vec_kernel    3D, FP32/BF16: plane rings of 16-byte chunks (any nx)
 //   step3d_box_kernel    3D, FP32/BF16 Model C: one CTA per box
@@ -1455,236 +1453,89 @@ __global__ void __launch_bounds__(Step3dWrShape<MODEL, ST, T, TY>::NT, Step3dWrS
     }
 }
 
-// ========================================== 3D, warp rows, K steps per pass ==
-//
-// Temporal blocking in 3D (the plane-queue form of z-streaming): K forward-Euler
-// steps of Allen-Cahn or Gray-Scott per HBM round trip.  The layout is the warp-
-// row kernel's: warp w owns input row w of a tile (TY output rows plus K*r halo
-// rows on each side), lane l the chunk of 4 cells l (lanes 1..30 the tile's 120
-// cells, lanes 0 and 31 halo chunks, which covers the K*r halo cells when
-// K*r <= 4), and planes of the input stream along z through a cp.async ring.
-// Time level s (0 = the input, K = the output) is produced plane by plane, one
-// plane behind level s-1 per loop iteration: at iteration j the newest plane of
-// level s (published by this iteration's barrier) is turned into its in-plane
-// partial sums and pushed onto level s's register queues, and the queues give
-// level s+1's plane r behind it.  Levels 1..K-1 publish each new plane (rows
-// y-r..y+r of other warps are its in-plane neighbours) through one of two plane
-// buffers in shared memory; level K goes to global memory.  One barrier per
-// iteration.  Level s+1 is valid on the rows and cells of level s shrunk by r,
-// so after K levels exactly the tile remains.  Intermediate planes are rounded to
-// the storage type as a global store would round them, and every level uses the
-// single-step expressions in the same order, so K blocked steps equal K single
-// steps bit for bit.  HBM traffic: one read and one write of each field per K
-// steps (plus halo planes at the ends of each z segment).
-//
-// Requirements (checked by the launcher): nx a multiple of 4 and 16-byte
-// aligned field pointers.
-template <int MODEL, int ST, typename T, int TY, int K>
-struct Step3dTbwShape {
-    static constexpr int V = 4;                       // cells per lane
-    static constexpr int CB = V * (int)sizeof(T);     // chunk bytes
-    static constexpr int r = StencilInfo<ST>::r;
-    static_assert(K * r <= V, "the halo lanes must cover K*r cells");
-    static constexpr int TXC = 30;
-    static constexpr int TX = TXC * V;
-    static constexpr int HIN = TY + 2 * K * r;        // warps = input rows
-    static constexpr int NT = 32 * HIN;
-    static constexpr int XW = V + 2 * r;
-    static constexpr int NP = Planar<ST>::NP;
-    static constexpr int Q = 2 * r + 1;
-    static constexpr int P = 3;                       // input planes in flight
-    static constexpr int NF = num_fields<MODEL>();
-    static constexpr size_t plane_bytes = (size_t)HIN * 32 * CB;
-    static constexpr size_t in_bytes = (size_t)(P + 1) * NF * plane_bytes;
-    static constexpr size_t lv_plane = (size_t)HIN * 32 * V;   // floats of one level plane of one field
-    static constexpr size_t lv_bytes = (size_t)(K - 1) * 2 * NF * lv_plane * sizeof(float);
-    static constexpr size_t smem_bytes = in_bytes + lv_bytes;
-};
-
-template <int MODEL, int ST, typename T, int TY, int K>
-__global__ void __launch_bounds__(Step3dTbwShape<MODEL, ST, T, TY, K>::NT, 1)
-    step3d_tbw_kernel(StepArgs a, int tiles_x, int tiles_y, int segs) {
-    static_assert(MODEL == AC || MODEL == GS, "temporal blocking in 3D covers Allen-Cahn and Gray-Scott");
-    static_assert(K >= 2, "K steps per pass");
-    typedef Step3dTbwShape<MODEL, ST, T, TY, K> Sh;
-    constexpr int V = Sh::V, r = Sh::r, HIN = Sh::HIN, XW = Sh::XW, NP = Sh::NP, Q = Sh::Q;
-    constexpr int P = Sh::P, NF = Sh::NF, CB = Sh::CB, V2 = V / 2;
-    constexpr unsigned FULL = 0xffffffffu;
-    typedef typename VecT<CB>::type W;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    W *s_in = reinterpret_cast<W *>(smem_raw);                              // [P+1][NF][HIN][32]
-    float *s_lv = reinterpret_cast<float *>(smem_raw + Sh::in_bytes);      // [K-1][2][NF][HIN][32][V]
-
-    const ConstsF2 k2(ConstsC<float>(a.k, a.kf));
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const size_t plane = (size_t)nx * (size_t)ny;
-    const T *in[2] = {static_cast<const T *>(a.in0), static_cast<const T *>(a.in1)};
-    T *out[2] = {static_cast<T *>(a.out0), static_cast<T *>(a.out1)};
-
-    constexpr int D = P + 1;
-    static_assert((D & (D - 1)) == 0, "ring slots must be a power of two");
-    constexpr size_t SLOT = (size_t)NF * HIN * 32, FLD = (size_t)HIN * 32;
-    W *const s_own = s_in + (size_t)w * 32 + lane;
-    // this lane's chunk of its own row in level buffer (level 1, slot 0, field 0)
-    float *const lv_own = s_lv + ((size_t)w * 32 + lane) * V;
-    auto lv_chunk = [&](int level, int slot, int f) -> float * {  // level 1 .. K-1
-        return lv_own + ((size_t)((level - 1) * 2 + slot) * NF + f) * Sh::lv_plane;
-    };
-    auto extend = [&](float *ext) {
+// Stencil sum of the 4 cells of this lane's chunk, two cells per instruction,
+// in the fixed order of stencil_sum (sp_common.cuh).  row(dz, dy, dst) loads
+// the chunk at plane offset dz and row offset dy; `ext` helpers shuffle in the
+// x halo.
+template <int ST, typename RowFn, typename ExtFn>
+__device__ __forceinline__ void ring_stencil(const RowFn &row, const ExtFn &extend, float (&S)[4], float (&cen)[4]) {
+    constexpr int r = StencilInfo<ST>::r, V = 4, XW = V + 2 * r;
+    auto pr = [](const float *a, int c0) { return make_float2(a[c0], a[c0 + 1]); };
+    if constexpr (ST == L27) {
+        // per plane dz: cross C and diagonal D sums of the 3 x 3 in-plane neighbourhood
+        float2 Cz[3][2], Dz[3][2];
+        float ctr[3][V];
 #pragma unroll
-        for (int h = 0; h < r; ++h) {
-            ext[h] = __shfl_up_sync(FULL, ext[V + h], 1);
-            ext[r + V + h] = __shfl_down_sync(FULL, ext[r + h], 1);
-        }
-    };
-
-    const int tiles = tiles_x * tiles_y;
-    for (long long it = blockIdx.x; it < (long long)tiles * segs; it += gridDim.x) {
-        const int seg = (int)(it / tiles), tile = (int)(it - (long long)seg * tiles);
-        const int z0 = (int)((long long)seg * nz / segs), z1 = (int)((long long)(seg + 1) * nz / segs);
-        const int x0 = (tile % tiles_x) * Sh::TX, y0 = (tile / tiles_x) * TY;
-        const int n = (z1 - z0) + 2 * K * r;                      // input planes
-        const int niter = n + K - 1;                               // level K lags K-1 iterations
-        const int col = x0 + (lane - 1) * V;
-        const size_t goff = (size_t)wrap_idx(y0 - K * r + w, ny) * nx + wrap_idx(col, nx);
-        const int yo = y0 - K * r + w;
-        const bool out_row = w >= K * r && w < HIN - K * r;
-        const bool store = out_row && lane >= 1 && lane <= 30 && col < nx && yo < ny;
-        int jn = 0, zn = wrap_idx(z0 - K * r, nz);
-        size_t src = (size_t)zn * plane + goff;
-        size_t dst_off = (size_t)z0 * plane + (size_t)yo * nx + col;
-
-        auto issue = [&]() {
-            if (jn < n) {
-                W *dst = s_own + (size_t)(jn & (D - 1)) * SLOT;
+        for (int dz = -1; dz <= 1; ++dz) {
+            float e[3][XW];
 #pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    if constexpr (CB == 16) cp_async16(dst + f * FLD, in[f] + src);
-                    else cp_async8(dst + f * FLD, in[f] + src);
-                }
-                src += plane;
-                if (++zn == nz) {
-                    zn = 0;
-                    src -= (size_t)nz * plane;
-                }
+            for (int dy = -1; dy <= 1; ++dy) {
+                row(dz, dy, e[dy + 1] + r);
+                extend(e[dy + 1]);
             }
-            ++jn;
-            cp_async_commit();
-        };
 #pragma unroll
-        for (int j = 0; j < P; ++j) issue();
-
-        // register queues of levels 0 .. K-1, slot (j % Q) for the plane pushed at iteration j
-        float2 qf[K][NF][Q][V2], qp[K][NF][Q][NP][V2];
-        auto sums_into = [&](const float (*ext)[XW], float2 (&dst)[NP][V2]) {
-            float ps[NP][V];
-            auto row = [&](int dy) -> const float * { return ext[r + dy]; };
-            planar_sums<ST, V, XW>(row, ps);
-#pragma unroll
-            for (int n2 = 0; n2 < NP; ++n2)
-#pragma unroll
-                for (int q = 0; q < V2; ++q) dst[n2][q] = make_float2(ps[n2][2 * q], ps[n2][2 * q + 1]);
-        };
-
-        for (int j0 = 0; j0 < niter; j0 += Q) {
-#pragma unroll
-            for (int u = 0; u < Q; ++u) {
-                const int j = j0 + u;
-                if (j < niter) {
-                    cp_async_wait<P - 1>();
-                    // input plane j published; level planes written at iteration j-1
-                    // published; the slots overwritten below are no longer read
-                    __syncthreads();
-                    issue();
-                    const W *cur = s_own + (size_t)(j & (D - 1)) * SLOT;
-#define QS(m) ((u - (m) + 4 * Q) % Q)
-#pragma unroll
-                    for (int s = 0; s < K; ++s) {
-                        const int ps = j - s * (1 + r);              // newest plane of level s
-                        const bool rows = w >= (s + 1) * r && w < HIN - (s + 1) * r;
-                        if (rows && ps >= s * r && ps < n - s * r) {
-#pragma unroll
-                            for (int f = 0; f < NF; ++f) {
-                                float ext[2 * r + 1][XW];
-#pragma unroll
-                                for (int dy = -r; dy <= r; ++dy) {
-                                    if (s == 0) {
-                                        union { W q; T t[V]; } cv;
-                                        cv.q = cur[f * FLD + dy * 32];
-#pragma unroll
-                                        for (int i = 0; i < V; ++i) ext[r + dy][r + i] = to_c(cv.t[i]);
-                                    } else {
-                                        const float4 v4 = *reinterpret_cast<const float4 *>(
-                                            lv_chunk(s, (j - 1) & 1, f) + dy * 32 * V);
-                                        ext[r + dy][r] = v4.x;
-                                        ext[r + dy][r + 1] = v4.y;
-                                        ext[r + dy][r + 2] = v4.z;
-                                        ext[r + dy][r + 3] = v4.w;
-                                    }
-                                    if (dy == 0 || ST == L27) extend(ext[r + dy]);
-                                }
-                                sums_into(ext, qp[s][f][QS(0)]);
-#pragma unroll
-                                for (int q = 0; q < V2; ++q)
-                                    qf[s][f][QS(0)][q] = make_float2(ext[r][r + 2 * q], ext[r][r + 2 * q + 1]);
-                            }
-                        }
-                        // level s+1, plane ps - r, from planes ps - 2r .. ps of level s
-                        if (rows && ps >= (s + 2) * r && ps < n - s * r) {
-                            auto f0q = [&](int kk) -> const float2 * { return qf[s][0][QS(2 * r - kk)]; };
-                            auto p0q = [&](int kk) -> const float2(*)[V2] { return qp[s][0][QS(2 * r - kk)]; };
-                            auto f1q = [&](int kk) -> const float2 * { return qf[s][NF - 1][QS(2 * r - kk)]; };
-                            auto p1q = [&](int kk) -> const float2(*)[V2] { return qp[s][NF - 1][QS(2 * r - kk)]; };
-                            (void)f1q; (void)p1q;
-                            float o0[V], o1[V];
-#pragma unroll
-                            for (int q = 0; q < V2; ++q) {
-                                const float2 S0 = planar_combine2<ST>(f0q, p0q, q);
-                                const float2 p0 = qf[s][0][QS(r)][q];
-                                float2 a0, a1 = make_float2(0.f, 0.f);
-                                if constexpr (MODEL == AC) {
-                                    a0 = ac_update2(p0, S0, k2);
-                                } else {
-                                    gs_update2(p0, qf[s][NF - 1][QS(r)][q], S0, planar_combine2<ST>(f1q, p1q, q), k2,
-                                               a0, a1);
-                                }
-                                o0[2 * q] = a0.x;
-                                o0[2 * q + 1] = a0.y;
-                                o1[2 * q] = a1.x;
-                                o1[2 * q + 1] = a1.y;
-                            }
-                            if (s + 1 < K) {
-                                // publish level s+1's plane, rounded as a store to T would round it
-#pragma unroll
-                                for (int f = 0; f < NF; ++f) {
-                                    const float *o = f == 0 ? o0 : o1;
-                                    *reinterpret_cast<float4 *>(lv_chunk(s + 1, j & 1, f)) =
-                                        make_float4(to_c(from_c<T>(o[0])), to_c(from_c<T>(o[1])),
-                                                    to_c(from_c<T>(o[2])), to_c(from_c<T>(o[3])));
-                                }
-                            } else {
-                                if (store) {
-                                    store_vec<T, V>(out[0] + dst_off, o0);
-                                    if constexpr (NF == 2) store_vec<T, V>(out[NF - 1] + dst_off, o1);
-                                }
-                                dst_off += plane;
-                            }
-                        }
-                    }
-#undef QS
-                }
+            for (int q = 0; q < 2; ++q) {
+                const int c0 = 2 * q, x = r + c0;
+                const float2 xs = make_float2(e[1][x - 1] + e[1][x + 1], e[1][x] + e[1][x + 2]);
+                Cz[dz + 1][q] = add2(xs, add2(pr(e[0] + r, c0), pr(e[2] + r, c0)));
+                const float2 dm = make_float2(e[0][x - 1] + e[0][x + 1], e[0][x] + e[0][x + 2]);
+                const float2 dp = make_float2(e[2][x - 1] + e[2][x + 1], e[2][x] + e[2][x + 2]);
+                Dz[dz + 1][q] = add2(dm, dp);
             }
+#pragma unroll
+            for (int c = 0; c < V; ++c) ctr[dz + 1][c] = e[1][r + c];
         }
-        cp_async_wait<0>();
-        __syncthreads();  // the ring and level buffers are reused by the next item
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int c0 = 2 * q;
+            const float2 F = add2(Cz[1][q], add2(pr(ctr[0], c0), pr(ctr[2], c0)));
+            const float2 E = add2(Dz[1][q], add2(Cz[0][q], Cz[2][q]));
+            const float2 K = add2(Dz[0][q], Dz[2][q]);
+            const float2 s2 =
+                fma2(splat2(-128.f), pr(ctr[1], c0), fma2(splat2(14.f), F, fma2(splat2(3.f), E, K)));
+            S[c0] = s2.x;
+            S[c0 + 1] = s2.y;
+            cen[c0] = ctr[1][c0];
+            cen[c0 + 1] = ctr[1][c0 + 1];
+        }
+    } else {
+        float ext[XW], ym[r][V], yp[r][V], zm[r][V], zp[r][V];
+        row(0, 0, ext + r);
+        extend(ext);
+#pragma unroll
+        for (int d = 1; d <= r; ++d) {
+            row(0, -d, ym[d - 1]);
+            row(0, d, yp[d - 1]);
+            row(-d, 0, zm[d - 1]);
+            row(d, 0, zp[d - 1]);
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int c0 = 2 * q, x = r + c0;
+            const float2 xs1 = make_float2(ext[x - 1] + ext[x + 1], ext[x] + ext[x + 2]);
+            const float2 F1 =
+                add2(add2(xs1, add2(pr(ym[0], c0), pr(yp[0], c0))), add2(pr(zm[0], c0), pr(zp[0], c0)));
+            float2 s2;
+            if constexpr (ST == L7) {
+                s2 = fma2(splat2(-6.f), make_float2(ext[x], ext[x + 1]), F1);
+            } else {
+                const float2 xs2 = make_float2(ext[x - 2] + ext[x + 2], ext[x - 1] + ext[x + 3]);
+                const float2 F2 = add2(add2(xs2, add2(pr(ym[r - 1], c0), pr(yp[r - 1], c0))),
+                                       add2(pr(zm[r - 1], c0), pr(zp[r - 1], c0)));
+                s2 = fma2(splat2(-90.f), make_float2(ext[x], ext[x + 1]), fma2(splat2(16.f), F1, neg2(F2)));
+            }
+            S[c0] = s2.x;
+            S[c0 + 1] = s2.y;
+            cen[c0] = ext[x];
+            cen[c0 + 1] = ext[x + 1];
+        }
     }
 }
 
 // ====================================== 3D, plane rings, K steps per pass ==
 //
-// Temporal blocking in 3D for the cross stencils (7-point, 4th-order 13-point):
-// K forward-Euler steps of Allen-Cahn or Gray-Scott per HBM round trip, with
+// Temporal blocking in 3D: K forward-Euler steps of Allen-Cahn or Gray-Scott
+// per HBM round trip, with
 // every time level kept as a ring of planes in shared memory instead of
 // register queues, so that a thread holds no per-level state and more warps fit
 // on an SM.  Warp w owns row w of a tile (TY output rows plus K*r halo rows on
@@ -1707,7 +1558,6 @@ struct Step3dTbsShape {
     static constexpr int V = 4;
     static constexpr int CB = V * (int)sizeof(T);
     static constexpr int r = StencilInfo<ST>::r;
-    static_assert(ST == L7 || ST == L13X4, "cross stencils");
     static_assert(K * r <= V, "the halo lanes must cover K*r cells");
     static constexpr int TXC = 30;
     static constexpr int TX = TXC * V;
@@ -1730,7 +1580,6 @@ __global__ void __launch_bounds__(Step3dTbsShape<MODEL, ST, T, TY, K>::NT)
     typedef Step3dTbsShape<MODEL, ST, T, TY, K> Sh;
     constexpr int V = Sh::V, r = Sh::r, HIN = Sh::HIN, NF = Sh::NF, CB = Sh::CB, V2 = V / 2;
     constexpr int D0 = Sh::D0, DL = Sh::DL, P = Sh::P;
-    constexpr int XW = V + 2 * r;
     constexpr unsigned FULL = 0xffffffffu;
     typedef typename VecT<CB>::type W;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1818,37 +1667,8 @@ __global__ void __launch_bounds__(Step3dTbsShape<MODEL, ST, T, TY, K>::NT)
                     float S[NF][V], cen[NF][V], res[NF][V];
 #pragma unroll
                     for (int f = 0; f < NF; ++f) {
-                        float ext[XW], ym[r][V], yp[r][V], zm[r][V], zp[r][V];
-                        chunk(s - 1, t, f, 0, ext + r);
-                        extend(ext);
-#pragma unroll
-                        for (int d = 1; d <= r; ++d) {
-                            chunk(s - 1, t, f, -d, ym[d - 1]);
-                            chunk(s - 1, t, f, d, yp[d - 1]);
-                            chunk(s - 1, t - d, f, 0, zm[d - 1]);
-                            chunk(s - 1, t + d, f, 0, zp[d - 1]);
-                        }
-                        // stencil sum in the fixed order (sp_common.cuh), two cells per instruction
-#pragma unroll
-                        for (int q = 0; q < V2; ++q) {
-                            const int c0 = 2 * q, x = r + c0;
-                            auto pr = [&](const float *a) { return make_float2(a[c0], a[c0 + 1]); };
-                            const float2 xs1 = make_float2(ext[x - 1] + ext[x + 1], ext[x] + ext[x + 2]);
-                            const float2 F1 = add2(add2(xs1, add2(pr(ym[0]), pr(yp[0]))), add2(pr(zm[0]), pr(zp[0])));
-                            float2 s2;
-                            if constexpr (ST == L7) {
-                                s2 = fma2(splat2(-6.f), make_float2(ext[x], ext[x + 1]), F1);
-                            } else {
-                                const float2 xs2 = make_float2(ext[x - 2] + ext[x + 2], ext[x - 1] + ext[x + 3]);
-                                const float2 F2 =
-                                    add2(add2(xs2, add2(pr(ym[r - 1]), pr(yp[r - 1]))), add2(pr(zm[r - 1]), pr(zp[r - 1])));
-                                s2 = fma2(splat2(-90.f), make_float2(ext[x], ext[x + 1]), fma2(splat2(16.f), F1, neg2(F2)));
-                            }
-                            S[f][c0] = s2.x;
-                            S[f][c0 + 1] = s2.y;
-                            cen[f][c0] = ext[x];
-                            cen[f][c0 + 1] = ext[x + 1];
-                        }
+                        auto row = [&](int dz, int dy, float *dst) { chunk(s - 1, t + dz, f, dy, dst); };
+                        ring_stencil<ST>(row, extend, S[f], cen[f]);
                     }
 #pragma unroll
                     for (int q = 0; q < V2; ++q) {

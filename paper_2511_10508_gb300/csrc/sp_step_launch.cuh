@@ -103,30 +103,10 @@ cudaError_t launch_tb(const StepArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// 3D FP32 / BF16 temporal blocking (Allen-Cahn, Gray-Scott): K steps per pass
-// on warp-row tiles of 120 x 8 outputs; lockstep z segments like the one-step
-// warp-row kernel.  Needs nx a multiple of 4 and 16-byte aligned fields (the
-// runtime offers K > 1 in 3D only then).
-template <int MODEL, int ST, typename T, int K>
-cudaError_t launch_tbw(const StepArgs &a, cudaStream_t s, int n_sm) {
-    constexpr int TY = 8;
-    typedef Step3dTbwShape<MODEL, ST, T, TY, K> Sh;
-    auto kern = step3d_tbw_kernel<MODEL, ST, T, TY, K>;
-    static const int occ = [&] {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem_bytes);
-        int o = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, Sh::NT, Sh::smem_bytes);
-        return o;
-    }();
-    const int tx = (a.nx + Sh::TX - 1) / Sh::TX, ty = (a.ny + TY - 1) / TY;
-    const long long wave = (long long)n_sm * std::max(occ, 1);
-    const int segs = lockstep_segments((long long)tx * ty, a.nz, 2 * K * Sh::r, wave);
-    const long long items = (long long)tx * ty * segs;
-    kern<<<(unsigned)std::min(items, wave), Sh::NT, Sh::smem_bytes, s>>>(a, tx, ty, segs);
-    return cudaGetLastError();
-}
-
-// The same for the cross stencils with a plane ring per level (tiles of 120 x TY).
+// 3D FP32 / BF16 Allen-Cahn and Gray-Scott with a plane ring per time level: K
+// steps per pass (temporal blocking for K = 2) on warp-row tiles of 120 x TY
+// outputs; lockstep z segments.  Needs nx a multiple of 4 and 16-byte aligned
+// fields (the runtime offers these families only then).
 template <int MODEL, int ST, typename T, int TY, int K>
 cudaError_t launch_tbs(const StepArgs &a, cudaStream_t s, int n_sm) {
     typedef Step3dTbsShape<MODEL, ST, T, TY, K> Sh;
@@ -245,14 +225,11 @@ cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
         kern<<<dim3((unsigned)bx, (unsigned)by, (unsigned)bz), NT, Sh::smem_bytes, s>>>(a);
     } else if constexpr (!std::is_same<T, double>::value) {
         if constexpr (MODEL == AC || MODEL == GS) {
-            if constexpr (ST == L27) {
-                if (k == 2) return launch_tbw<MODEL, ST, T, 2>(a, s, n_sm);
-            } else {
-                // taller tiles where their rings fit in shared memory (not Gray-Scott radius 2)
-                constexpr bool tall_fits = Step3dTbsShape<MODEL, ST, T, 16, 2>::smem_bytes <= kMaxSmemPerCta;
-                if (k == 2 && g_step_variant == 1 && tall_fits) return launch_tbs<MODEL, ST, T, (tall_fits ? 16 : 8), 2>(a, s, n_sm);
-                if (k == 2) return launch_tbs<MODEL, ST, T, 8, 2>(a, s, n_sm);
-            }
+            // two steps per launch with a plane ring per time level (families 0 and 1:
+            // tiles of 8 and 16 rows; the taller ones only where their rings fit)
+            constexpr bool tall2 = Step3dTbsShape<MODEL, ST, T, 16, 2>::smem_bytes <= kMaxSmemPerCta;
+            if (k == 2 && g_step_variant == 1 && tall2) return launch_tbs<MODEL, ST, T, (tall2 ? 16 : 8), 2>(a, s, n_sm);
+            if (k == 2) return launch_tbs<MODEL, ST, T, 8, 2>(a, s, n_sm);
         }
         constexpr int ATX = 16, ATY = 16;
         typedef Step3dAsyncShape<MODEL, ST, T, ATX, ATY> AS;

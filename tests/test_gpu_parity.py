@@ -374,7 +374,7 @@ def test_temporal_blocking_3d_equals_single_steps(sp, dtype, model, st, shape):
     z segments, a grid smaller than the two-step halo in every direction, and
     graph replays (45 steps)."""
     outs = []
-    configs = [(1, 0), (2, 0)] + ([(2, 1)] if st != 4 else [])  # family 1: taller tiles (cross stencils)
+    configs = [(1, 0), (2, 0), (2, 1)]  # family 1: taller tiles
     for spl, fam in configs:
         sim, dt = make(sp, model, shape, st, dtype=dtype, steps_per_launch=spl)
         with sim:
@@ -531,10 +531,10 @@ def test_set_launch_config_rejects_unavailable(sp):
 @pytest.mark.parametrize("dtype", [1, 2])
 def test_3d_kernel_families_agree(sp, dtype, model, st, shape):
     """3D FP32 / BF16: the warp-row kernel (family 0), the cp.async plane-ring
-    kernel (family 1; both need nx a multiple of the chunk) and the
-    register-staged ring kernel (family 2) agree bit for bit.  Shapes: ragged
-    tiles in y and z, several x tiles with a ragged one, a grid smaller than one
-    tile in every axis (neighbours wrap), and a long z axis split across CTAs."""
+    kernel (family 1; both need nx a multiple of the chunk), the
+    register-staged ring kernel (family 2) agree bit for bit.  Shapes: ragged tiles in y and z, several x tiles with a ragged one, a
+    grid smaller than one tile in every axis (neighbours wrap), and a long z
+    axis split across CTAs."""
     outs = []
     for variant in (0, 1, 2):
         sim, dt = make(sp, model, shape, st, dtype=dtype)
