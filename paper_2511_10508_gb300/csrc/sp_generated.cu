@@ -218,56 +218,91 @@ __global__ void __launch_bounds__(256) gen_step_kernel(GenArgs g, int segs) {
     }
 }
 
-// Stencil sums of RY cells of one column (rows i0 .. i0+RY-1, column j) of the
-// field read by Vf(i, j): the column's values on rows i0-R .. i0+RY-1+R are read
-// once into registers (rows outside [lo, hi] are clamped there: their sums are
-// not used), the x taps per cell.  Each sum is gen_sum's, with the same taps in
-// the same order.
-template <int R, int RY, typename Val>
-__device__ __forceinline__ void gen_column_sums(const Val &Vf, int i0, int j, int lo, int hi, const GenW &W,
-                                                float (&S)[RY], float (&ctr)[RY]) {
-    float col[RY + 2 * R];
+// Stencil sums of a block of 4 columns x RY rows (columns j .. j+3, j a
+// multiple of 4; rows i0 .. i0+RY-1) of the field read by L(i, jc, dst), which
+// loads the 4 values of row i at columns jc .. jc+3 (jc a multiple of 4; the
+// caller's L clamps rows outside its region, whose sums are then not used).
+// The block's columns are read once over rows i0-R .. i0+RY-1+R (the y taps),
+// and each output row once more 4 columns to the left and to the right (the x
+// taps): 16-byte reads, about 1.25 per cell for RY = 4.  Each sum is gen_sum's,
+// with the same taps in the same order, evaluated two cells per instruction.
+template <int R, int RY, typename Ld>
+__device__ __forceinline__ void gen_block_sums(const Ld &L, int i0, int j, const GenW &W, float (&S)[RY][4],
+                                               float (&ctr)[RY][4]) {
+    static_assert(R <= 4, "the x taps reach at most 4 columns beyond the block");
+    float col[RY + 2 * R][4];
 #pragma unroll
-    for (int a = 0; a < RY + 2 * R; ++a) col[a] = Vf(min(max(i0 - R + a, lo), hi), j);
+    for (int a = 0; a < RY + 2 * R; ++a) L(i0 - R + a, j, col[a]);
 #pragma unroll
     for (int b = 0; b < RY; ++b) {
-        const int i = min(max(i0 + b, lo), hi);
-        auto P = [&](int dx, int dy, int) -> float { return dx == 0 ? col[b + R + dy] : Vf(i, j + dx); };
-        S[b] = gen_sum<R, 2, float>(P, W);
-        ctr[b] = col[b + R];
+        float row[12];
+        L(i0 + b, j - 4, row);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) row[4 + c] = col[b + R][c];
+        L(i0 + b, j + 4, row + 8);
+        // two cells per instruction (each lane rounds as the scalar operation):
+        // y pairs always, x pairs where the shifted cells form a register pair
+#pragma unroll
+        for (int c = 0; c < 4; c += 2) {
+            const int x = 4 + c;
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int jj = R; jj >= 1; --jj) {
+                float2 xp;
+                if (jj % 2 == 0) xp = add2(make_float2(row[x + jj], row[x + 1 + jj]), make_float2(row[x - jj], row[x + 1 - jj]));
+                else xp = make_float2(row[x + jj] + row[x - jj], row[x + 1 + jj] + row[x + 1 - jj]);
+                const float2 yp = add2(make_float2(col[b + R + jj][c], col[b + R + jj][c + 1]),
+                                       make_float2(col[b + R - jj][c], col[b + R - jj][c + 1]));
+                const float2 pj = add2(xp, yp);
+                const float2 w = splat2(W.wf[jj]);
+                acc = (jj == R) ? mul2(w, pj) : fma2(w, pj, acc);
+            }
+            const float2 s2 = fma2(splat2(W.wf[0]), make_float2(row[x], row[x + 1]), acc);
+            S[b][c] = s2.x;
+            S[b][c + 1] = s2.y;
+            ctr[b][c] = row[x];
+            ctr[b][c + 1] = row[x + 1];
+        }
     }
 }
 
 // 2D tiles (FP32 / BF16 storage): one BX x BY output tile per CTA; the tile and
-// its halo (2R for Cahn-Hilliard, whose mu is evaluated on the tile grown by R,
-// else R; x padded to whole 16-byte chunks) are fetched once into shared
-// memory, and mu stays in shared memory, so the step is one pass over HBM.  The
-// same expressions as the per-point kernels, so the results are identical.
+// its halo (2R rows for Cahn-Hilliard, whose mu is evaluated on the tile grown
+// by R, else R; 8 or 4 columns, so that every 4-column block can read 4 columns
+// beyond itself) are fetched once into shared memory, and mu stays in shared
+// memory (columns -4 .. BX+3), so the step is one pass over HBM.  Each thread
+// takes blocks of 4 columns x 4 rows (gen_block_sums); consecutive threads take
+// consecutive column blocks.  The same expressions as the per-point kernels, so
+// the results are identical.
 template <int MODEL, int R, typename T, int BX, int BY>
 struct GenTile2dShape {
     typedef typename Cmp<T>::type C;
     static constexpr int RIN = (MODEL == CH) ? 2 * R : R;
     static constexpr int CK = 16 / sizeof(T);
-    static constexpr int HC = (RIN + CK - 1) / CK;
+    static constexpr int XH = (MODEL == CH) ? 8 : 4;  // halo columns in shared memory
+    static constexpr int HC = (XH + CK - 1) / CK;
     static constexpr int NCK = BX / CK + 2 * HC;
     static constexpr int SW = NCK * CK, X0 = HC * CK;
     static constexpr int HIN = BY + 2 * RIN;
     static constexpr int NF = num_fields<MODEL>();
-    static constexpr int WMU = (MODEL == CH) ? BX + 2 * R : 0, HMU = (MODEL == CH) ? BY + 2 * R : 0;
+    static constexpr int RY = 4;   // rows per block of the output stage
+    static constexpr int RYM = 5;  // rows per block of the mu stage (Cahn-Hilliard)
+    static constexpr int WMU = (MODEL == CH) ? BX + 8 : 0, HMU = (MODEL == CH) ? BY + 2 * R : 0;
     static constexpr size_t bytes_in = sizeof(T) * (size_t)NF * HIN * SW;
     static constexpr size_t smem_bytes = bytes_in + sizeof(C) * (size_t)WMU * HMU;
-    static_assert(bytes_in % 16 == 0, "mu array alignment");
+    static_assert(bytes_in % 16 == 0 && BX % 4 == 0 && BY % RY == 0, "aligned rows and whole blocks");
 };
 
+// three CTAs per SM where the registers allow it without spills (one-field models)
 template <int MODEL, int R, typename T, int BX, int BY, int NT>
-__global__ void __launch_bounds__(NT) gen_tile2d_kernel(GenArgs g) {
+__global__ void __launch_bounds__(NT, (MODEL == GS || MODEL == MC) ? 2 : 3) gen_tile2d_kernel(GenArgs g) {
     typedef GenTile2dShape<MODEL, R, T, BX, BY> Sh;
     typedef typename Sh::C C;
     constexpr int RIN = Sh::RIN, CK = Sh::CK, NCK = Sh::NCK, SW = Sh::SW, X0 = Sh::X0, HIN = Sh::HIN;
-    constexpr int NF = Sh::NF, WMU = Sh::WMU, HMU = Sh::HMU;
+    constexpr int NF = Sh::NF, WMU = Sh::WMU, RY = Sh::RY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *s_in = reinterpret_cast<T *>(smem_raw);                 // [NF][HIN][SW]
-    C *s_mu = reinterpret_cast<C *>(smem_raw + Sh::bytes_in);  // [HMU][WMU]
+    C *s_mu = reinterpret_cast<C *>(smem_raw + Sh::bytes_in);  // [HMU][WMU], columns -4 .. BX+3
     const StepArgs &a = g.a;
     const ConstsC<C> k(a.k, a.kf);
     const int nx = a.nx, ny = a.ny, t = threadIdx.x;
@@ -297,68 +332,106 @@ __global__ void __launch_bounds__(NT) gen_tile2d_kernel(GenArgs g) {
     cp_async_wait<0>();
     __syncthreads();
 
-    // value of field f at tile coordinates (i, j), -RIN <= i < BY + RIN, -X0 <= j < BX + X0
-    auto phi = [&](int f, int i, int j) -> C { return to_c(s_in[((size_t)f * HIN + i + RIN) * SW + j + X0]); };
-    // Each work item is a column of RY cells (register-blocked along y, see
-    // gen_column_sums); consecutive threads take consecutive columns.
-    constexpr int RY = 8;
-    if constexpr (MODEL == CH) {
-        constexpr int NB = (HMU + RY - 1) / RY;  // row blocks of the mu region
-        auto phi0 = [&](int i, int j) -> C { return phi(0, i, j); };
-        for (int q = t; q < NB * WMU; q += NT) {
-            const int b = q / WMU, j = q - b * WMU - R;
-            const int i0 = b * RY - R;
-            float S[RY], p[RY];
-            gen_column_sums<R, RY>(phi0, i0, j, -RIN, BY + RIN - 1, g.W, S, p);
+    // 4 values of field f at tile row i (clamped to the fetched rows), columns jc .. jc+3
+    auto ld_phi = [&](int f, int i, int jc, float *dst) {
+        i = min(max(i, -RIN), BY + RIN - 1);
+        const T *src = s_in + ((size_t)f * HIN + i + RIN) * SW + jc + X0;
+        if constexpr (sizeof(T) == 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(src);
+            dst[0] = v.x, dst[1] = v.y, dst[2] = v.z, dst[3] = v.w;
+        } else {
+            union { uint2 w; T t[4]; } u;
+            u.w = *reinterpret_cast<const uint2 *>(src);
 #pragma unroll
-            for (int c = 0; c < RY; ++c)
-                if (i0 + c < BY + R) s_mu[(i0 + c + R) * WMU + (j + R)] = ch_mu<C>(p[c], S[c], k);
+            for (int c = 0; c < 4; ++c) dst[c] = to_c(u.t[c]);
+        }
+    };
+    auto L0 = [&](int i, int jc, float *dst) { ld_phi(0, i, jc, dst); };
+    auto L1 = [&](int i, int jc, float *dst) {
+        if constexpr (MODEL == MC) {  // the density's chemical potential at every tap
+            float p[4], q[4];
+            ld_phi(0, i, jc, p);
+            ld_phi(NF - 1, i, jc, q);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) dst[c] = mc_mu<C>(p[c], q[c], k);
+        } else {
+            ld_phi(NF - 1, i, jc, dst);
+        }
+    };
+    if constexpr (MODEL == CH) {
+        constexpr int RYM = Sh::RYM;
+        constexpr int NBM = (BY + 2 * R + RYM - 1) / RYM, NGM = WMU / 4;  // mu row blocks and column blocks
+        for (int q = t; q < NBM * NGM; q += NT) {
+            const int b = q / NGM, gc = q - b * NGM;
+            const int i0 = b * RYM - R, j = gc * 4 - 4;
+            float S[RYM][4], p[RYM][4];
+            gen_block_sums<R, RYM>(L0, i0, j, g.W, S, p);
+#pragma unroll
+            for (int bb = 0; bb < RYM; ++bb)
+                if (i0 + bb < BY + R)
+                    *reinterpret_cast<float4 *>(s_mu + (size_t)(i0 + bb + R) * WMU + (j + 4)) =
+                        make_float4(ch_mu<C>(p[bb][0], S[bb][0], k), ch_mu<C>(p[bb][1], S[bb][1], k),
+                                    ch_mu<C>(p[bb][2], S[bb][2], k), ch_mu<C>(p[bb][3], S[bb][3], k));
         }
         __syncthreads();
     }
-    constexpr int NBO = (BY + RY - 1) / RY;  // row blocks of the output tile
-    for (int q = t; q < NBO * BX; q += NT) {
-        const int b = q / BX, j = q - b * BX;
-        const int i0 = b * RY;
-        const int x = x0 + j;
-        float o0[RY], o1[RY];
+    constexpr int NBO = BY / RY, NGO = BX / 4;
+    for (int q = t; q < NBO * NGO; q += NT) {
+        const int b = q / NGO, gc = q - b * NGO;
+        const int i0 = b * RY, j = gc * 4;
+        float o0[RY][4], o1[RY][4];
         if constexpr (MODEL == CH) {
-            auto mu = [&](int i, int jj) -> C { return s_mu[(i + R) * WMU + (jj + R)]; };
-            float S[RY], dummy[RY];
-            gen_column_sums<R, RY>(mu, i0, j, -R, BY + R - 1, g.W, S, dummy);
+            auto Lmu = [&](int i, int jc, float *dst) {
+                i = min(max(i, -R), BY + R - 1);
+                const float4 v = *reinterpret_cast<const float4 *>(s_mu + (size_t)(i + R) * WMU + jc + 4);
+                dst[0] = v.x, dst[1] = v.y, dst[2] = v.z, dst[3] = v.w;
+            };
+            float S[RY][4], dummy[RY][4];
+            gen_block_sums<R, RY>(Lmu, i0, j, g.W, S, dummy);
 #pragma unroll
-            for (int c = 0; c < RY; ++c) o0[c] = ch_update<C>(phi(0, min(i0 + c, BY - 1), j), S[c], k);
+            for (int bb = 0; bb < RY; ++bb) {
+                float p[4];
+                ld_phi(0, i0 + bb, j, p);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) o0[bb][c] = ch_update<C>(p[c], S[bb][c], k);
+            }
         } else {
-            auto phi0 = [&](int i, int jj) -> C { return phi(0, i, jj); };
-            float S0[RY], p0[RY];
-            gen_column_sums<R, RY>(phi0, i0, j, -RIN, BY + RIN - 1, g.W, S0, p0);
+            float S0[RY][4], p0[RY][4];
+            gen_block_sums<R, RY>(L0, i0, j, g.W, S0, p0);
             if constexpr (MODEL == AC) {
 #pragma unroll
-                for (int c = 0; c < RY; ++c) o0[c] = ac_update<C>(p0[c], S0[c], k);
-            } else {
-                float S1[RY], p1[RY];
-                if constexpr (MODEL == MC) {
-                    auto m = [&](int i, int jj) -> C { return mc_mu<C>(phi(0, i, jj), phi(NF - 1, i, jj), k); };
-                    gen_column_sums<R, RY>(m, i0, j, -RIN, BY + RIN - 1, g.W, S1, p1);
-                } else {
-                    auto phi1 = [&](int i, int jj) -> C { return phi(NF - 1, i, jj); };
-                    gen_column_sums<R, RY>(phi1, i0, j, -RIN, BY + RIN - 1, g.W, S1, p1);
-                }
+                for (int bb = 0; bb < RY; ++bb)
 #pragma unroll
-                for (int c = 0; c < RY; ++c)
-                    two_field_update<MODEL, C>(p0[c], phi(NF - 1, min(i0 + c, BY - 1), j), S0[c], S1[c], k, o0[c],
-                                               o1[c]);
+                    for (int c = 0; c < 4; ++c) o0[bb][c] = ac_update<C>(p0[bb][c], S0[bb][c], k);
+            } else {
+                float S1[RY][4], p1[RY][4];
+                gen_block_sums<R, RY>(L1, i0, j, g.W, S1, p1);
+#pragma unroll
+                for (int bb = 0; bb < RY; ++bb) {
+                    float r1[4];
+                    ld_phi(NF - 1, i0 + bb, j, r1);  // rho or v itself at the centre
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        two_field_update<MODEL, C>(p0[bb][c], r1[c], S0[bb][c], S1[bb][c], k, o0[bb][c], o1[bb][c]);
+                }
             }
         }
-        if (x < nx) {
+        const int x = x0 + j;
 #pragma unroll
-            for (int c = 0; c < RY; ++c) {
-                const int y = y0 + i0 + c;
-                if (i0 + c < BY && y < ny) {
-                    const size_t o = (size_t)y * (size_t)nx + x;
-                    out[0][o] = from_c<T>(o0[c]);
-                    if constexpr (NF == 2) out[NF - 1][o] = from_c<T>(o1[c]);
-                }
+        for (int bb = 0; bb < RY; ++bb) {
+            const int y = y0 + i0 + bb;
+            if (y >= ny) continue;
+            const size_t o = (size_t)y * (size_t)nx + x;
+            if (vec_ok && x + 4 <= nx) {
+                store_vec<T, 4>(out[0] + o, o0[bb]);
+                if constexpr (NF == 2) store_vec<T, 4>(out[NF - 1] + o, o1[bb]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (x + c < nx) {
+                        out[0][o + c] = from_c<T>(o0[bb][c]);
+                        if constexpr (NF == 2) out[NF - 1][o + c] = from_c<T>(o1[bb][c]);
+                    }
             }
         }
     }
@@ -369,11 +442,16 @@ static cudaError_t launch_gen_t(const GenArgs &g, cudaStream_t s, int n_sm) {
     if constexpr (DIMS == 2 && !std::is_same<T, double>::value) {
         // family 0: shared-memory tiles; family 1: the per-point kernels
         if (g_step_variant != 1) {
-            constexpr int BX = 128, BY = 32, NT = 256;
+            // Cahn-Hilliard: 288 threads take the (BY + 2R) / 5 x (BX + 8) / 4 mu blocks
+            // (up to 272) in one round and the 8 x 32 output blocks; 256 otherwise
+            constexpr int BX = 128, BY = 32, NT = MODEL == CH ? 288 : 256;
             typedef GenTile2dShape<MODEL, R, T, BX, BY> Sh;
             auto kern = gen_tile2d_kernel<MODEL, R, T, BX, BY, NT>;
             static const bool attr = [&] {
                 cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem_bytes);
+                // several tiles per SM overlap one tile's loads with another's arithmetic
+                cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
                 return true;
             }();
             (void)attr;
