@@ -71,10 +71,11 @@ inline int lockstep_segments(long long tiles, int nz, int halo, long long wave) 
 // FP64 2D grids up to 1024^2 use small tiles by default (and may fuse steps).
 constexpr long long kSmallGrid2d = 1LL << 20;
 
-// 3D: two steps per launch for FP32 / BF16 Allen-Cahn and Gray-Scott (warp-row
-// plane queues, grids with nx a multiple of 4), when asked for or autotuned.
+// 3D: two steps per launch for FP32 / BF16 Allen-Cahn, Gray-Scott and Model C
+// (plane rings, grids with nx a multiple of 4), when asked for or autotuned.
 inline int steps_per_launch_3d(int dtype, int model, int nx, int requested) {
-    const bool ok = dtype != SP_F64 && (model == SP_ALLEN_CAHN || model == SP_GRAY_SCOTT) && nx % 4 == 0;
+    const bool ok = dtype != SP_F64 && (model == SP_ALLEN_CAHN || model == SP_GRAY_SCOTT || model == SP_MODEL_C) &&
+                    nx % 4 == 0;
     return (ok && requested >= 2) ? 2 : 1;
 }
 

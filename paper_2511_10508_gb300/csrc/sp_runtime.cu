@@ -471,6 +471,10 @@ static std::vector<TuneChoice> tune_candidates(const sp_sim *s) {
         if (s->dims == 3 && steps_per_launch_3d(s->dtype, s->model, s->nx, 2) == 2) {
             c.push_back({2, 0});  // two steps per pass, 8 rows
             c.push_back({2, 1});  // 16 rows
+            if (s->model == SP_MODEL_C) {  // one step in the plane rings (else the box kernel)
+                c.push_back({1, 4});
+                c.push_back({1, 5});
+            }
         }
         if (s->dims == 2 && s->dtype == SP_F64) {
             if (s->N <= (size_t)kSmallGrid2d) {  // small grids: steps fused per launch

@@ -15,8 +15,8 @@
 //   step3d_kernel        3D, FP64: shared-memory plane rings
 //   step3d_zreg_kernel   3D, FP64, 27-point: z-streaming with register queues
 //   step3d_wr_kernel     3D, FP32/BF16: warp per tile row, z in register queues
-//   step3d_tbs_kernel    3D, FP32/BF16 Allen-Cahn / Gray-Scott: 2 steps per pass
-//                        (warp rows, a plane ring per time level)
+//   step3d_tbs_kernel    3D, FP32/BF16 Allen-Cahn / Gray-Scott / Model C: 2 steps
+//                        per pass (Model C also 1), warp rows, a plane ring per level
 //   step3d_async_kernel  3D, FP32/BF16: cp.async plane ring, planes in flight
 //   step3d_vec_kernel    3D, FP32/BF16: plane rings of 16-byte chunks (any nx)
 //   step3d_box_kernel    3D, FP32/BF16 Model C: one CTA per box
@@ -1534,8 +1534,8 @@ __device__ __forceinline__ void ring_stencil(const RowFn &row, const ExtFn &exte
 
 // ====================================== 3D, plane rings, K steps per pass ==
 //
-// Temporal blocking in 3D: K forward-Euler steps of Allen-Cahn or Gray-Scott
-// per HBM round trip, with
+// Temporal blocking in 3D: K forward-Euler steps (K = 1: the plain step) of
+// Allen-Cahn, Gray-Scott or Model C per HBM round trip, with
 // every time level kept as a ring of planes in shared memory instead of
 // register queues, so that a thread holds no per-level state and more warps fit
 // on an SM.  Warp w owns row w of a tile (TY output rows plus K*r halo rows on
@@ -1576,9 +1576,10 @@ struct Step3dTbsShape {
 template <int MODEL, int ST, typename T, int TY, int K>
 __global__ void __launch_bounds__(Step3dTbsShape<MODEL, ST, T, TY, K>::NT)
     step3d_tbs_kernel(StepArgs a, int tiles_x, int tiles_y, int segs) {
-    static_assert(MODEL == AC || MODEL == GS, "temporal blocking in 3D covers Allen-Cahn and Gray-Scott");
+    static_assert(MODEL == AC || MODEL == GS || MODEL == MC, "Allen-Cahn, Gray-Scott and Model C");
     typedef Step3dTbsShape<MODEL, ST, T, TY, K> Sh;
     constexpr int V = Sh::V, r = Sh::r, HIN = Sh::HIN, NF = Sh::NF, CB = Sh::CB, V2 = V / 2;
+    const ConstsC<float> kc(a.k, a.kf);
     constexpr int D0 = Sh::D0, DL = Sh::DL, P = Sh::P;
     constexpr unsigned FULL = 0xffffffffu;
     typedef typename VecT<CB>::type W;
@@ -1665,6 +1666,25 @@ __global__ void __launch_bounds__(Step3dTbsShape<MODEL, ST, T, TY, K>::NT)
                 const int t = j - (s - 1) - s * r;                 // plane of level s produced now
                 if (w >= s * r && w < HIN - s * r && t >= s * r && t < n - s * r) {
                     float S[NF][V], cen[NF][V], res[NF][V];
+                    if constexpr (MODEL == MC) {
+                        // phi's stencil, and that of the density's chemical potential
+                        // m = mc_mu(phi, rho) formed at every tap (per lane, then shuffled)
+                        auto row0 = [&](int dz, int dy, float *dst) { chunk(s - 1, t + dz, 0, dy, dst); };
+                        ring_stencil<ST>(row0, extend, S[0], cen[0]);
+                        auto rowm = [&](int dz, int dy, float *dst) {
+                            float u4[V], v4[V];
+                            chunk(s - 1, t + dz, 0, dy, u4);
+                            chunk(s - 1, t + dz, 1, dy, v4);
+#pragma unroll
+                            for (int c = 0; c < V; ++c) dst[c] = mc_mu<float>(u4[c], v4[c], kc);
+                        };
+                        ring_stencil<ST>(rowm, extend, S[1], cen[1]);
+                        float vc[V];
+                        chunk(s - 1, t, 1, 0, vc);
+#pragma unroll
+                        for (int c = 0; c < V; ++c)
+                            mc_update<float>(cen[0][c], vc[c], S[0][c], S[1][c], kc, res[0][c], res[1][c]);
+                    } else {
 #pragma unroll
                     for (int f = 0; f < NF; ++f) {
                         auto row = [&](int dz, int dy, float *dst) { chunk(s - 1, t + dz, f, dy, dst); };
@@ -1681,6 +1701,7 @@ __global__ void __launch_bounds__(Step3dTbsShape<MODEL, ST, T, TY, K>::NT)
                         res[0][c0 + 1] = a0.y;
                         res[NF - 1][c0] = NF == 2 ? a1.x : a0.x;
                         res[NF - 1][c0 + 1] = NF == 2 ? a1.y : a0.y;
+                    }
                     }
                     if (s < K) {
 #pragma unroll

@@ -212,7 +212,17 @@ cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
         dim3 grid((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY);
         kern<<<grid, NT, Sh::smem_bytes, s>>>(a);
     } else if constexpr (!std::is_same<T, double>::value && MODEL == MC) {
-        // Model C, FP32 / BF16 3D: one CTA per box (the accessor-based box code)
+        // Model C, FP32 / BF16 3D: plane rings (two steps per launch: families 0 and 1,
+        // tiles of 8 and 16 rows; one step: families 4 and 5) where nx and the
+        // alignment allow, else one CTA per box (the accessor-based box code)
+        const bool al = ((uintptr_t)a.in0 | (uintptr_t)a.in1 | (uintptr_t)a.out0 | (uintptr_t)a.out1) % 16 == 0;
+        if (a.nx % 4 == 0 && al) {
+            constexpr bool tall2 = Step3dTbsShape<MODEL, ST, T, 16, 2>::smem_bytes <= kMaxSmemPerCta;
+            if (k == 2 && g_step_variant == 1 && tall2) return launch_tbs<MODEL, ST, T, (tall2 ? 16 : 8), 2>(a, s, n_sm);
+            if (k == 2) return launch_tbs<MODEL, ST, T, 8, 2>(a, s, n_sm);
+            if (g_step_variant == 5) return launch_tbs<MODEL, ST, T, 16, 1>(a, s, n_sm);
+            if (g_step_variant == 4) return launch_tbs<MODEL, ST, T, 8, 1>(a, s, n_sm);
+        }
         constexpr int BX = 32, BY = 8, BZ = 8, NT = 256;
         typedef Step3dBoxShape<MODEL, ST, T, BX, BY, BZ> Sh;
         auto kern = step3d_box_kernel<MODEL, ST, T, BX, BY, BZ, NT>;

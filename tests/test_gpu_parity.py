@@ -365,16 +365,18 @@ def test_temporal_blocking_equals_single_steps(sp, dtype, model, st):
 
 
 @pytest.mark.parametrize("dtype", [1, 2])
-@pytest.mark.parametrize("model,st", [(m, s) for m in (0, 2) for s in (3, 4, 5)])
+@pytest.mark.parametrize("model,st", [(m, s) for m in (0, 2, 3) for s in (3, 4, 5)])
 @pytest.mark.parametrize("shape", [(37, 45, 124), (6, 5, 8), (20, 17, 244)])
 def test_temporal_blocking_3d_equals_single_steps(sp, dtype, model, st, shape):
-    """3D FP32 / BF16 Allen-Cahn and Gray-Scott with two steps per launch (the
-    warp-row plane queues, intermediate planes rounded to the storage type) equal
-    single-step launches bit for bit: two tiles in x (one ragged), ragged y tiles,
+    """3D FP32 / BF16 Allen-Cahn, Gray-Scott and Model C with two steps per launch
+    (plane rings, intermediate planes rounded to the storage type), and Model C's
+    one-step plane rings, equal single-step launches bit for bit: two tiles in x (one ragged), ragged y tiles,
     z segments, a grid smaller than the two-step halo in every direction, and
     graph replays (45 steps)."""
     outs = []
     configs = [(1, 0), (2, 0), (2, 1)]  # family 1: taller tiles
+    if model == 3:
+        configs += [(1, 4), (1, 5)]  # Model C: one step in the plane rings
     for spl, fam in configs:
         sim, dt = make(sp, model, shape, st, dtype=dtype, steps_per_launch=spl)
         with sim:
