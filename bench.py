@@ -79,6 +79,8 @@ WORKLOADS = {
     "mh2d-8192-f32-lap5": (4, 2, (8192, 8192), 0.01, 0, 1, 20),
     "mh3d-256-f64-lap7": (4, 3, (256, 256, 256), 0.005, 3, 0, 10),
     "mh3d-256-f32-lap7": (4, 3, (256, 256, 256), 0.005, 3, 1, 20),
+    "mh3d-256-f32-lap27": (4, 3, (256, 256, 256), 0.005, 4, 1, 20),
+    "mh3d-256-f32-lap13x4": (4, 3, (256, 256, 256), 0.005, 5, 1, 20),
     # generated cross Laplacians (accuracy order in the name), stencil entry 6
     "ch2d-4096-f64-gen8": (1, 2, (4096, 4096), 0.002, 6, 0, 50),
     "ac2d-4096-f64-gen6": (0, 2, (4096, 4096), 0.05, 6, 0, 50),

@@ -287,7 +287,15 @@ __device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;
 // Two cells per instruction (f32x2 arithmetic of sm_100 and later): each lane
 // of __fadd2_rn / __fmul2_rn / __ffma2_rn rounds like the scalar operation, so
 // the pair forms below give the scalar helpers' results bit for bit (a negated
-// operand is exact, so -(a*b) == (-a)*b and x - y == x + (-y)).
+// operand is exact, so -(a*b) == (-a)*b and x - y == x + (-y)).  Unlike the
+// scalar __fmul_rn / __fadd_rn, a packed product that feeds a packed sum or
+// difference may be contracted into one fused multiply-add by the code
+// generator (measured on sm_103a, with --fmad=false, both for these
+// intrinsics and for the PTX add/sub/mul.rn.f32x2 forms: m1*j1 - m2*j2 on
+// pairs differed from the scalar result in the last bit).  So no pair product
+// here ever feeds a pair addition or subtraction: products enter only as
+// multiplicands or as the addend of an explicit fma2, where nothing can be
+// contracted.
 __device__ __forceinline__ float2 splat2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }

@@ -244,7 +244,7 @@ template <int ST, typename T, int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT) mh_ring3d_kernel(MhArgs a, float c3g, int tiles_x, int tiles_y, int segs) {
     typedef float C;
     typedef MhRing3dShape<ST, T, TX, TY> Sh;
-    constexpr int R = Sh::R, RIN = Sh::RIN, WIN = Sh::WIN, HIN = Sh::HIN, AIN = Sh::AIN, D = Sh::D, NF = Sh::NF;
+    constexpr int R = Sh::R, RIN = Sh::RIN, WIN = Sh::WIN, AIN = Sh::AIN, D = Sh::D, NF = Sh::NF;
     constexpr int WMU = Sh::WMU, AMU = Sh::AMU, DMU = Sh::DMU;
     constexpr int EPT = (AIN + NT - 1) / NT;  // loaded cells per thread per field
     extern __shared__ __align__(16) unsigned char smem_raw[];

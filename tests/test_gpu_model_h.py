@@ -113,14 +113,16 @@ def test_model_h_2d_tiles_equal_per_point(sp, dtype, st, shape):
         assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("shape", [(20, 24, 36), (9, 17, 70), (3, 5, 6), (40, 18, 33)])
+@pytest.mark.parametrize("shape", [(20, 24, 36), (9, 17, 70), (3, 5, 6), (40, 18, 33), (9, 17, 68), (3, 5, 8),
+                                   (40, 18, 4), (6, 40, 96)])
 @pytest.mark.parametrize("st", [3, 4, 5])
 @pytest.mark.parametrize("dtype", [1, 2])
 def test_model_h_3d_ring_equals_per_point(sp, dtype, st, shape):
     """3D FP32 / BF16: the z-streaming plane-ring kernel (family 0) and the two
     per-point passes (family 1) agree bit for bit, including a graph replay
     (33 steps).  Shapes: ragged tiles, a grid smaller than the halo in every
-    axis, several tiles with a long z axis split across CTAs."""
+    axis, several tiles with a long z axis split across CTAs, rows of 4 cells
+    (the x halo wraps the period twice) and three whole tiles in x."""
     outs = []
     for fam in (0, 1):
         with make(sp, shape, st, dtype=dtype) as s:
