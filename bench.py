@@ -54,6 +54,9 @@ WORKLOADS = {
     "ch3d-1024-f64-lap7": (1, 3, (1024, 1024, 1024), 0.005, 3, 0, 2),
     "ch3d-1024-f32-lap27": (1, 3, (1024, 1024, 1024), 0.005, 4, 1, 5),
     "ch3d-1024-f64-lap27": (1, 3, (1024, 1024, 1024), 0.005, 4, 0, 2),
+    "ch3d-1024-f64-lap27-zreg": (1, 3, (1024, 1024, 1024), 0.005, 4, 0, 2, 1, 2),
+    "ac3d-512-f64-lap27": (0, 3, (512, 512, 512), 0.05, 4, 0, 10),
+    "gs3d-512-f64-lap27": (2, 3, (512, 512, 512), 0.5, 4, 0, 5),
     "ch3d-1024-f32-lap13x4": (1, 3, (1024, 1024, 1024), 0.005, 5, 1, 5),
     "gs3d-512-f32-lap7": (2, 3, (512, 512, 512), 0.5, 3, 1, 10),
     "ac3d-1024-f32-lap27": (0, 3, (1024, 1024, 1024), 0.05, 4, 1, 5),

@@ -87,6 +87,18 @@ inline int steps_per_launch(int dims, int dtype, int model, int requested) {
     return 1;
 }
 
+// 3D FP64 27-point Allen-Cahn, Cahn-Hilliard (two passes through `mu`, N
+// doubles) and Gray-Scott with x-pair sums shared between y neighbours: kernel
+// family 0 of these grids.  Family 2 is then the z-streaming kernel with plane
+// sums in registers (step3d_zreg_kernel, family 0 of launch_step_f64), family 1
+// the accessor-based plane ring.
+constexpr int kZregFamily = 2;
+cudaError_t launch_planes27_f64(int model, const StepArgs &a, void *mu, cudaStream_t s, int n_sm);
+inline bool planes27_applies(int dims, int dtype, int stencil, int model) {
+    return dims == 3 && dtype == SP_F64 && stencil == SP_LAP_27 &&
+           (model == SP_ALLEN_CAHN || model == SP_CAHN_HILLIARD || model == SP_GRAY_SCOTT);
+}
+
 // Generated cross stencils (sp_generated.cu), radius up to kMaxGenRadius.
 constexpr int kMaxGenRadius = 4;
 int generated_weights(int order, int dims, double *wk, double *lambda_max);

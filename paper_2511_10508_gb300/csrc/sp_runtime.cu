@@ -345,13 +345,14 @@ extern "C" int sp_create(int model, int dims, const int64_t shape[3], double h, 
         release(s);
         return fail(SP_ENOMEM, "scratch allocation failed: %s", cudaGetErrorString(e));
     }
-    if (model == SP_MODEL_H || (st == SP_LAP_GENERATED && model == SP_CAHN_HILLIARD)) {
+    if (model == SP_MODEL_H || (st == SP_LAP_GENERATED && model == SP_CAHN_HILLIARD) ||
+        (planes27_applies(dims, prm.dtype, st, model) && model == SP_CAHN_HILLIARD && prm.scheme == SP_SCHEME_FD)) {
         e = cudaMalloc(&s->mu_tmp, s->N * (s->dtype == SP_F64 ? sizeof(double) : sizeof(float)));
         if (e != cudaSuccess) {
             cudaGetLastError();
             s->mu_tmp = nullptr;
             release(s);
-            return fail(SP_ENOMEM, "Model H mu buffer: %s", cudaGetErrorString(e));
+            return fail(SP_ENOMEM, "mu buffer: %s", cudaGetErrorString(e));
         }
     }
     e = launch_ic(s->dtype, s->f[0][0], (s->nf > 1 && model != SP_MODEL_H) ? s->f[0][1] : nullptr, model, dims, s->nx,
@@ -413,6 +414,10 @@ static cudaError_t launch_one_step_impl(sp_sim *s, cudaStream_t st, int k) {
         const double c3g = s->p.c3 * (stencil_radius(s->stencil) == 1 ? 1.0 / (2.0 * s->h) : 1.0 / (12.0 * s->h));
         return launch_model_h(s->dtype, s->stencil, in, out, s->mu_tmp, s->nx, s->ny, s->nz, s->k, c3g, st, s->n_sm);
     }
+    if (planes27_applies(s->dims, s->dtype, s->stencil, s->model) && s->variant != 1) {
+        if (s->variant == 0) return launch_planes27_f64(s->model, a, s->mu_tmp, st, s->n_sm);
+        g_step_variant = 0;  // kZregFamily: the z-streaming kernel is launch_step_f64's family 0
+    }
     switch (s->dtype) {
     case SP_F64: return launch_step_f64(s->model, s->stencil, a, st, s->n_sm, k);
     case SP_F32: return launch_step_f32(s->model, s->stencil, a, st, s->n_sm, k);
@@ -468,6 +473,7 @@ static std::vector<TuneChoice> tune_candidates(const sp_sim *s) {
         c.push_back({1, 0});
         c.push_back({1, 1});
         if (s->dims == 3 && s->dtype != SP_F64) c.push_back({1, 2});
+        if (planes27_applies(s->dims, s->dtype, s->stencil, s->model)) c.push_back({1, kZregFamily});
         if (s->dims == 3 && steps_per_launch_3d(s->dtype, s->model, s->nx, 2) == 2) {
             c.push_back({2, 0});  // two steps per pass, 8 rows
             c.push_back({2, 1});  // 16 rows

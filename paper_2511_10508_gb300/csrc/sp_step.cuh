@@ -1121,6 +1121,151 @@ __global__ void __launch_bounds__(NT) step3d_zreg_kernel(StepArgs a, int tiles_x
     }  // segments
 }
 
+// ------------------------------------- 3D, 27-point, FP64, shared pair sums --
+//
+// The same fixed order with the x-pair sums shared between y neighbours: in
+// row y, P(y) = f(x-1, y) + f(x+1, y); the in-plane sums are then
+// C = P(y) + (f(y-1) + f(y+1)) and D = P(y-1) + P(y+1) (exactly the groupings
+// of plane_sums27).  Each plane's P is formed once per point in shared memory
+// (rows -1 .. TY of the tile), so a stencil application costs 12 FP64
+// operations (P 1, C 2, D 1, combine 8) instead of 14; value, C and D of the
+// two previous planes stay in registers as in step3d_zreg_kernel.
+//
+// Cahn-Hilliard runs as two passes through a mu buffer (mode 0: mu of every
+// point; mode 1: the update from mu and the centre phi), so mu is evaluated
+// once per point rather than on a halo ring as well; the buffer's HBM traffic
+// (16 bytes per point) is cheap next to the FP64 work on this part.  Allen-Cahn
+// (mode 2) and Gray-Scott (mode 3) take one pass.  Same operations in the same
+// order as every other family, so the results are identical bit for bit.
+// The default for these grids; measured on GB300 against step3d_zreg_kernel:
+// Cahn-Hilliard 1024^3 17.5 vs 13.6 GLUPS, Allen-Cahn 512^3 29.6 vs 27.0,
+// Gray-Scott 512^3 14.9 vs 13.3.
+struct Planes27Args {
+    const double *in[2];   // streamed fields (mode 1: mu)
+    const double *centre;  // mode 1: phi at the output points
+    double *out[2];        // mode 0: mu
+    int nx, ny, nz;
+    StepConsts k;
+};
+
+template <int MODE>
+struct Planes27Shape {
+    static constexpr int NF = (MODE == 3) ? 2 : 1;
+    static constexpr int TX = 32, TY = 32, NT = 256;
+    static constexpr int WIN = TX + 2, HIN = TY + 2, AIN = WIN * HIN;
+    static constexpr int AP = HIN * TX;                // pair sums of rows -1 .. TY
+    static constexpr int EPT = (AIN + NT - 1) / NT;    // loaded cells per thread per field
+    static constexpr int EOUT = TX * TY / NT, OSTEP = NT / TX;
+    static constexpr size_t smem_bytes = sizeof(double) * ((size_t)2 * NF * AIN + (size_t)NF * AP);
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(256, MODE == 3 ? 1 : 2)
+    planes27_kernel(Planes27Args a, int tiles_x, long long planes_per_cta, long long total) {
+    typedef Planes27Shape<MODE> Sh;
+    constexpr int NF = Sh::NF, TX = Sh::TX, TY = Sh::TY, NT = Sh::NT, WIN = Sh::WIN, AIN = Sh::AIN, AP = Sh::AP;
+    constexpr int EPT = Sh::EPT, EOUT = Sh::EOUT, OSTEP = Sh::OSTEP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *s_in = reinterpret_cast<double *>(smem_raw);  // [2][NF][AIN]
+    double *s_P = s_in + (size_t)2 * NF * AIN;            // [NF][AP]
+    const ConstsC<double> k(a.k, StepConstsF{});
+    const int nx = a.nx, ny = a.ny, nz = a.nz, t = threadIdx.x;
+    const size_t plane = (size_t)nx * (size_t)ny;
+    const int ox = t % TX, oy = t / TX;  // output points (ox, oy + e OSTEP)
+
+    long long g0 = (long long)blockIdx.x * planes_per_cta;
+    const long long gend = min(g0 + planes_per_cta, total);
+    while (g0 < gend) {
+        const int tile = (int)(g0 / nz);
+        const int z0 = (int)(g0 - (long long)tile * nz);
+        const int z1 = (int)min((long long)nz, (long long)z0 + (gend - g0));
+        g0 += z1 - z0;
+        const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+        const int nplanes = (z1 - z0) + 2;  // loaded plane j is z = z0 - 1 + j
+
+        int loff[EPT];
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            const int c = t + e * NT;
+            if (c < AIN) {
+                const int yi = c / WIN, xi = c - yi * WIN;
+                loff[e] = wrap_idx(y0 - 1 + yi, ny) * nx + wrap_idx(x0 - 1 + xi, nx);
+            } else {
+                loff[e] = -1;
+            }
+        }
+        double pf[NF][EPT];
+        auto fetch = [&](int z) {
+            const size_t zoff = (size_t)wrap_idx(z, nz) * plane;
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+#pragma unroll
+                for (int e = 0; e < EPT; ++e)
+                    if (loff[e] >= 0) pf[f][e] = load_one(a.in[f] + zoff + loff[e]);
+        };
+        // register queues: index 0 = plane j-2, 1 = plane j-1
+        double qf[NF][EOUT][2], qC[NF][EOUT][2], qD[NF][EOUT][2];
+
+        fetch(z0 - 1);
+        for (int j = 0; j < nplanes; ++j) {
+            double *buf = s_in + (size_t)(j & 1) * NF * AIN;
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+#pragma unroll
+                for (int e = 0; e < EPT; ++e)
+                    if (loff[e] >= 0) buf[(size_t)f * AIN + t + e * NT] = pf[f][e];
+            if (j + 1 < nplanes) fetch(z0 + j);
+            __syncthreads();
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+                for (int q = t; q < AP; q += NT) {
+                    const int r = q / TX, c = q - r * TX;
+                    const double *row = buf + (size_t)f * AIN + r * WIN + c;
+                    s_P[(size_t)f * AP + q] = row[0] + row[2];
+                }
+            __syncthreads();
+            const int zo = z0 - 2 + j;  // output plane (j >= 2)
+#pragma unroll
+            for (int e = 0; e < EOUT; ++e) {
+                const int yy = oy + e * OSTEP;
+                double S[NF], fc[NF];
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    const double *p = buf + (size_t)f * AIN + (yy + 1) * WIN + (ox + 1);
+                    const double *P = s_P + (size_t)f * AP + (yy + 1) * TX + ox;
+                    const double Cz = P[0] + (p[-WIN] + p[WIN]);
+                    const double Dz = P[-TX] + P[TX];
+                    const double f0 = p[0];
+                    S[f] = (j >= 2) ? combine27(qf[f][e][0], qf[f][e][1], f0, qC[f][e][0], qC[f][e][1], Cz,
+                                                qD[f][e][0], qD[f][e][1], Dz)
+                                    : 0.0;
+                    fc[f] = qf[f][e][1];
+                    qf[f][e][0] = qf[f][e][1], qf[f][e][1] = f0;
+                    qC[f][e][0] = qC[f][e][1], qC[f][e][1] = Cz;
+                    qD[f][e][0] = qD[f][e][1], qD[f][e][1] = Dz;
+                }
+                const int x = x0 + ox, y = y0 + yy;
+                if (j >= 2 && x < nx && y < ny) {
+                    const size_t o = (size_t)zo * plane + (size_t)y * nx + x;
+                    if constexpr (MODE == 0) {
+                        a.out[0][o] = ch_mu<double>(fc[0], S[0], k);
+                    } else if constexpr (MODE == 1) {
+                        a.out[0][o] = ch_update<double>(a.centre[o], S[0], k);
+                    } else if constexpr (MODE == 2) {
+                        a.out[0][o] = ac_update<double>(fc[0], S[0], k);
+                    } else {
+                        double un, vn;
+                        gs_update<double>(fc[0], fc[1], S[0], S[1], k, un, vn);
+                        a.out[0][o] = un;
+                        a.out[1][o] = vn;
+                    }
+                }
+            }
+        }
+        __syncthreads();  // the buffers are reused by the next tile
+    }
+}
+
 // ===================================================== 3D, warp rows ==
 //
 // FP32 / BF16-storage 3D kernel built like the 2D warp-strip kernel.  Warp w

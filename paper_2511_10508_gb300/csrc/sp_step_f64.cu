@@ -7,4 +7,40 @@ cudaError_t launch_step_f64(int model, int stencil, const StepArgs &a, cudaStrea
     return launch_step_dispatch<double>(model, stencil, a, s, n_sm, k);
 }
 
+cudaError_t launch_planes27_f64(int model, const StepArgs &a, void *mu, cudaStream_t s, int n_sm) {
+    Planes27Args p;
+    p.nx = a.nx;
+    p.ny = a.ny;
+    p.nz = a.nz;
+    p.k = a.k;
+    p.centre = nullptr;
+    const double *in0 = static_cast<const double *>(a.in0), *in1 = static_cast<const double *>(a.in1);
+    double *out0 = static_cast<double *>(a.out0), *out1 = static_cast<double *>(a.out1);
+    switch (model) {
+    case CH: {
+        if (!mu) return cudaErrorInvalidValue;
+        p.in[0] = p.in[1] = in0;
+        p.out[0] = p.out[1] = static_cast<double *>(mu);
+        const cudaError_t e = launch_planes27_mode<0>(p, s, n_sm);
+        if (e != cudaSuccess) return e;
+        p.in[0] = p.in[1] = static_cast<const double *>(mu);
+        p.centre = in0;
+        p.out[0] = p.out[1] = out0;
+        return launch_planes27_mode<1>(p, s, n_sm);
+    }
+    case AC:
+        p.in[0] = p.in[1] = in0;
+        p.out[0] = p.out[1] = out0;
+        return launch_planes27_mode<2>(p, s, n_sm);
+    case GS:
+        p.in[0] = in0;
+        p.in[1] = in1;
+        p.out[0] = out0;
+        p.out[1] = out1;
+        return launch_planes27_mode<3>(p, s, n_sm);
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace sp

@@ -437,7 +437,7 @@ def test_autotune_keeps_results(sp, model, shape, dtype, st):
         spl, var = c.launch_config
         assert b.launch_config == c.launch_config  # the second tuning came from the cache
         if len(shape) == 3:
-            assert spl == 1 and var in ((0, 1, 2) if dtype != 0 else (0, 1) if st == 4 else (0,))
+            assert spl == 1 and var in ((0, 1, 2) if (dtype != 0 or st == 4) else (0,))
         elif dtype == 0 and shape[0] * shape[1] <= 1 << 20:
             assert (spl, var) in ((1, 0), (1, 1), (2, 0), (4, 0))
         elif dtype == 0:
@@ -507,6 +507,55 @@ def test_2d_fp64_families_equal_oracle(sp, model, st, shape):
             else:
                 ref = O.step(model, st, ic, dt=dt, prm=oparams(sim.prm), nsteps=11)
         assert np.array_equal(got, ref), f"family {variant}"
+
+
+@pytest.mark.parametrize("shape", [(37, 45, 70), (2, 3, 5), (3, 1, 4), (1, 1, 1), (40, 33, 65), (70, 20, 64)])
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_fp64_27point_families_equal_oracle(sp, model, shape):
+    """3D FP64 27-point: the kernel that shares the x-pair sums between y
+    neighbours (family 0; Cahn-Hilliard in two passes through the mu buffer),
+    the accessor-based plane ring (family 1) and z-streaming with plane sums in
+    registers (family 2) all equal the oracle bit for bit, through a graph
+    replay (33 steps, checked after 9 and 42).  Shapes: ragged tiles, sides
+    below the stencil radius, a single point, a long z axis split across
+    CTAs."""
+    kw = dict(gs_patches=1, gs_patch=1) if model == 2 and min(shape) < 8 else {}
+    refs = {}
+    for fam in (0, 1, 2):
+        sim, dt = make(sp, model, shape, 4, **kw)
+        with sim:
+            sim.launch_config = (1, fam)
+            assert sim.launch_config == (1, fam)
+            ic = oracle_ic(model, shape, sim.prm)
+            for n in (9, 33):
+                sim.step(n)
+                total = sim.steps_taken
+                if total not in refs:
+                    prev = refs.get(9) if total == 42 else None
+                    if model in TWO:
+                        start = prev if prev is not None else ic
+                        refs[total] = O.step(model, 4, start[0], start[1], dt=dt, prm=oparams(sim.prm),
+                                             nsteps=n)
+                    else:
+                        start = prev if prev is not None else ic
+                        refs[total] = O.step(model, 4, start, dt=dt, prm=oparams(sim.prm), nsteps=n)
+                ref = refs[total]
+                if model in TWO:
+                    assert np.array_equal(sim.read(0), ref[0]), f"family {fam}, {total} steps"
+                    assert np.array_equal(sim.read(1), ref[1]), f"family {fam}, {total} steps"
+                else:
+                    assert np.array_equal(sim.read(0), ref), f"family {fam}, {total} steps"
+
+
+def test_fp64_27point_family_2_models(sp):
+    """3D FP64 has a third kernel family only for Allen-Cahn, Cahn-Hilliard and
+    Gray-Scott with the 27-point stencil (not Model C, not the 7- or 13-point
+    stencils)."""
+    for model, st, dtype in ((3, 4, 0), (1, 3, 0), (1, 5, 0)):
+        sim, _ = make(sp, model, (8, 8, 8), st, dtype=dtype)
+        with sim:
+            with pytest.raises(sp.SpError):
+                sim.launch_config = (1, 2)
 
 
 def test_set_launch_config_rejects_unavailable(sp):
