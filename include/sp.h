@@ -199,9 +199,10 @@ typedef struct sp_sim sp_sim;
  * reduction scratch, and writes the seeded initial condition on the device.
  * Three cases also hold a chemical-potential buffer of N compute-precision
  * values (the paper's one temporary): Model H, Cahn-Hilliard with a generated
- * stencil, and 3D FP64 Cahn-Hilliard with the 27-point stencil (whose default
- * kernel takes two passes through it: on this part FP64 is bound by the FP64
- * pipe, where re-evaluating mu on tile halos costs more than the buffer).
+ * stencil, and 3D FP64 Cahn-Hilliard with the 7-, 27- or 13-point stencil
+ * (whose default kernels take two passes through it: on this part FP64 is
+ * bound by the FP64 pipe, where re-evaluating mu on tile halos costs more than
+ * the buffer's traffic).
  * Synchronises before returning.  *out receives the handle.
  */
 int sp_create(int model, int dims, const int64_t shape[3], double h, double dt,
@@ -313,11 +314,12 @@ int sp_binary_version(int *version);
 
 /* Launch configuration in use: steps fused per launch and kernel family
  * (0 = the default for the grid; alternatives the autotuner may pick: 1 for
- * every grid of the finite-difference scheme except 3D FP64 with the 7/13/
- * 19-point stencils; 2 for 3D FP32/BF16 and for 3D FP64 27-point Allen-Cahn,
- * Cahn-Hilliard and Gray-Scott (there: plane sums in registers instead of x-pair
- * sums shared between rows); 2 and 4 for 2D FP64, the strip kernel with 64
- * threads per CTA and with half the rows per batch). */
+ * every grid of the finite-difference scheme except 3D FP64 with the 7- and
+ * 13-point stencils; 2 for 3D FP32/BF16, for 3D FP64 27-point Allen-Cahn,
+ * Cahn-Hilliard and Gray-Scott (plane sums in registers instead of x-pair sums
+ * shared between rows) and for 3D FP64 7- and 13-point Cahn-Hilliard (one fused
+ * pass instead of two through the mu buffer); 2 and 4 for 2D FP64, the strip
+ * kernel with 64 threads per CTA and with half the rows per batch). */
 int sp_launch_config(const sp_sim *sim, int *steps_per_launch, int *variant);
 
 /* Number of time steps taken since creation. */

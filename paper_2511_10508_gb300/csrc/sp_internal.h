@@ -94,6 +94,14 @@ inline int steps_per_launch(int dims, int dtype, int model, int requested) {
 // the accessor-based plane ring.
 constexpr int kZregFamily = 2;
 cudaError_t launch_planes27_f64(int model, const StepArgs &a, void *mu, cudaStream_t s, int n_sm);
+// 3D FP64 Cahn-Hilliard with the 7- and 13-point stencils in two passes through
+// `mu` (N doubles): kernel family 0 of these grids; family kFusedFamily is the
+// one-pass plane ring with mu on a halo ring (launch_step_f64's family 0).
+constexpr int kFusedFamily = 2;
+cudaError_t launch_ch_twopass_f64(int stencil, const StepArgs &a, void *mu, cudaStream_t s, int n_sm);
+inline bool twopass_applies(int dims, int dtype, int stencil, int model) {
+    return dims == 3 && dtype == SP_F64 && (stencil == SP_LAP_7 || stencil == SP_LAP_13CROSS4) && model == SP_CAHN_HILLIARD;
+}
 inline bool planes27_applies(int dims, int dtype, int stencil, int model) {
     return dims == 3 && dtype == SP_F64 && stencil == SP_LAP_27 &&
            (model == SP_ALLEN_CAHN || model == SP_CAHN_HILLIARD || model == SP_GRAY_SCOTT);

@@ -346,7 +346,8 @@ extern "C" int sp_create(int model, int dims, const int64_t shape[3], double h, 
         return fail(SP_ENOMEM, "scratch allocation failed: %s", cudaGetErrorString(e));
     }
     if (model == SP_MODEL_H || (st == SP_LAP_GENERATED && model == SP_CAHN_HILLIARD) ||
-        (planes27_applies(dims, prm.dtype, st, model) && model == SP_CAHN_HILLIARD && prm.scheme == SP_SCHEME_FD)) {
+        (prm.scheme == SP_SCHEME_FD && (twopass_applies(dims, prm.dtype, st, model) ||
+                                        (planes27_applies(dims, prm.dtype, st, model) && model == SP_CAHN_HILLIARD)))) {
         e = cudaMalloc(&s->mu_tmp, s->N * (s->dtype == SP_F64 ? sizeof(double) : sizeof(float)));
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -413,6 +414,10 @@ static cudaError_t launch_one_step_impl(sp_sim *s, cudaStream_t st, int k) {
         }
         const double c3g = s->p.c3 * (stencil_radius(s->stencil) == 1 ? 1.0 / (2.0 * s->h) : 1.0 / (12.0 * s->h));
         return launch_model_h(s->dtype, s->stencil, in, out, s->mu_tmp, s->nx, s->ny, s->nz, s->k, c3g, st, s->n_sm);
+    }
+    if (twopass_applies(s->dims, s->dtype, s->stencil, s->model)) {
+        if (s->variant == 0) return launch_ch_twopass_f64(s->stencil, a, s->mu_tmp, st, s->n_sm);
+        g_step_variant = 0;  // kFusedFamily: launch_step_f64's family 0
     }
     if (planes27_applies(s->dims, s->dtype, s->stencil, s->model) && s->variant != 1) {
         if (s->variant == 0) return launch_planes27_f64(s->model, a, s->mu_tmp, st, s->n_sm);
@@ -493,6 +498,7 @@ static std::vector<TuneChoice> tune_candidates(const sp_sim *s) {
         }
     } else {
         c.push_back({1, 0});
+        if (twopass_applies(s->dims, s->dtype, s->stencil, s->model)) c.push_back({1, kFusedFamily});
     }
     return c;
 }

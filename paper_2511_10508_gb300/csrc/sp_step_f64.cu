@@ -43,4 +43,30 @@ cudaError_t launch_planes27_f64(int model, const StepArgs &a, void *mu, cudaStre
     }
 }
 
+cudaError_t launch_ch_twopass_f64(int stencil, const StepArgs &a, void *mu, cudaStream_t s, int n_sm) {
+    if (!mu) return cudaErrorInvalidValue;
+    Planes27Args p;
+    p.nx = a.nx;
+    p.ny = a.ny;
+    p.nz = a.nz;
+    p.k = a.k;
+    const double *phi = static_cast<const double *>(a.in0);
+    p.in[0] = p.in[1] = phi;
+    p.centre = nullptr;
+    p.out[0] = p.out[1] = static_cast<double *>(mu);
+    auto run = [&](auto mu_pass, auto update_pass) -> cudaError_t {
+        cudaError_t e = mu_pass(p, s, n_sm);
+        if (e != cudaSuccess) return e;
+        p.in[0] = p.in[1] = static_cast<const double *>(mu);
+        p.centre = phi;
+        p.out[0] = p.out[1] = static_cast<double *>(a.out0);
+        return update_pass(p, s, n_sm);
+    };
+    switch (stencil) {
+    case L7: return run(launch_ring2pass_mode<L7, 0>, launch_ring2pass_mode<L7, 1>);
+    case L13X4: return run(launch_ring2pass_mode<L13X4, 0>, launch_ring2pass_mode<L13X4, 1>);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace sp

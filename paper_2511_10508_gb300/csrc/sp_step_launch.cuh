@@ -164,6 +164,24 @@ cudaError_t launch_planes27_mode(const Planes27Args &a, cudaStream_t s, int n_sm
     return cudaGetLastError();
 }
 
+template <int ST, int MODE>
+cudaError_t launch_ring2pass_mode(const Planes27Args &a, cudaStream_t s, int n_sm) {
+    typedef Ring2PassShape<ST> Sh;
+    auto kern = ring2pass_kernel<ST, MODE>;
+    static const int occ = [&] {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem_bytes);
+        int o = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, Sh::NT, Sh::smem_bytes);
+        return o;
+    }();
+    const int tx = (a.nx + Sh::TX - 1) / Sh::TX, ty = (a.ny + Sh::TY - 1) / Sh::TY;
+    const long long total = (long long)tx * ty * a.nz;
+    const long long ctas = persistent_ctas(total, occ, n_sm);
+    const long long planes = (total + ctas - 1) / ctas;
+    kern<<<(unsigned)((total + planes - 1) / planes), Sh::NT, Sh::smem_bytes, s>>>(a, tx, planes, total);
+    return cudaGetLastError();
+}
+
 template <int MODEL, int ST, typename T>
 cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
     if constexpr (StencilInfo<ST>::dims == 2) {

@@ -437,7 +437,7 @@ def test_autotune_keeps_results(sp, model, shape, dtype, st):
         spl, var = c.launch_config
         assert b.launch_config == c.launch_config  # the second tuning came from the cache
         if len(shape) == 3:
-            assert spl == 1 and var in ((0, 1, 2) if (dtype != 0 or st == 4) else (0,))
+            assert spl == 1 and var in ((0, 1, 2) if (dtype != 0 or st == 4) else (0, 2) if model == 1 else (0,))
         elif dtype == 0 and shape[0] * shape[1] <= 1 << 20:
             assert (spl, var) in ((1, 0), (1, 1), (2, 0), (4, 0))
         elif dtype == 0:
@@ -547,11 +547,33 @@ def test_fp64_27point_families_equal_oracle(sp, model, shape):
                     assert np.array_equal(sim.read(0), ref), f"family {fam}, {total} steps"
 
 
+@pytest.mark.parametrize("shape", [(37, 45, 70), (2, 3, 5), (3, 1, 4), (1, 1, 1), (40, 33, 65), (70, 20, 64)])
+@pytest.mark.parametrize("st", [3, 5])
+def test_fp64_cahn_hilliard_two_pass_equals_oracle(sp, st, shape):
+    """3D FP64 Cahn-Hilliard, 7- and 13-point: the two passes through the mu
+    buffer (family 0) and the fused kernel (family 2) equal the oracle bit for
+    bit, through a graph replay (42 steps)."""
+    sim0, dt = make(sp, 1, shape, st)
+    with sim0:
+        ic = oracle_ic(1, shape, sim0.prm)
+        ref9 = O.step(1, st, ic, dt=dt, prm=oparams(sim0.prm), nsteps=9)
+        ref42 = O.step(1, st, ref9, dt=dt, prm=oparams(sim0.prm), nsteps=33)
+    for fam in (0, 2):
+        sim, _ = make(sp, 1, shape, st)
+        with sim:
+            sim.launch_config = (1, fam)
+            assert sim.launch_config == (1, fam)
+            sim.step(9)
+            assert np.array_equal(sim.read(0), ref9), f"family {fam}"
+            sim.step(33)
+            assert np.array_equal(sim.read(0), ref42), f"family {fam}"
+
+
 def test_fp64_27point_family_2_models(sp):
     """3D FP64 has a third kernel family only for Allen-Cahn, Cahn-Hilliard and
-    Gray-Scott with the 27-point stencil (not Model C, not the 7- or 13-point
-    stencils)."""
-    for model, st, dtype in ((3, 4, 0), (1, 3, 0), (1, 5, 0)):
+    Gray-Scott with the 27-point stencil and for Cahn-Hilliard with the 7- and
+    13-point stencils (not Model C, not Allen-Cahn or Gray-Scott with those)."""
+    for model, st, dtype in ((3, 4, 0), (0, 3, 0), (2, 5, 0), (3, 3, 0)):
         sim, _ = make(sp, model, (8, 8, 8), st, dtype=dtype)
         with sim:
             with pytest.raises(sp.SpError):
@@ -574,7 +596,7 @@ def test_set_launch_config_rejects_unavailable(sp):
     sim, _ = make(sp, 1, (20, 24, 28), 3, dtype=0)
     with sim:
         with pytest.raises(sp.SpError):
-            sim.launch_config = (1, 1)  # 3D FP64 7-point has one family
+            sim.launch_config = (1, 1)  # 3D FP64 7-point: families 0 and 2 only
 
 
 @pytest.mark.parametrize("shape", [(40, 33, 64), (20, 18, 136), (5, 7, 8), (70, 40, 256)])
