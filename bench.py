@@ -46,6 +46,7 @@ WORKLOADS = {
     "ch2d-8192-f32-lap5": (1, 2, (8192, 8192), 0.01, 0, 1, 10),
     "ch3d-384-f32-lap7": (1, 3, (384, 384, 384), 0.005, 3, 1, 10),
     "ch3d-384-f64-lap27": (1, 3, (384, 384, 384), 0.005, 4, 0, 4),
+    "ch3d-384-f64-lap7": (1, 3, (384, 384, 384), 0.005, 3, 0, 4),
     "ac2d-256-f64-lap5": (0, 2, (256, 256), 0.05, 0, 0, 1000),
     "gs2d-32768-f32-lap5": (2, 2, (32768, 32768), 1.0, 0, 1, 10),
     "gs2d-32768-f64-lap5": (2, 2, (32768, 32768), 1.0, 0, 0, 2),

@@ -150,6 +150,15 @@ template <int RAD, int DIR, typename C> __device__ __forceinline__ void dft(C (&
 
 // ------------------------------------------------- Stockham in shared memory --
 
+// Shared-memory slot of complex entry i of a CTA's lines: FP32 lines are padded
+// with one empty slot after every 16 entries, so that the first radix-8 stage's
+// stores (stride 8 entries, 8-way bank conflicts unpadded) and the loads of every
+// stage (16 consecutive entries per half-warp) are conflict-free.
+template <bool PAD> __device__ __forceinline__ int slot(int i) { return PAD ? i + (i >> 4) : i; }
+// entries of shared memory that e padded entries span
+template <bool PAD> __host__ __device__ __forceinline__ int padded(int e) { return PAD ? e + (e >> 4) + 1 : e; }
+
+
 // One radix-RAD stage on G lines of n points in buf (line l at buf + l*n); p is
 // the product of the radices of the earlier stages.  Butterfly b of a line
 // (b < n/RAD) reads its inputs at stride n/RAD and writes them at stride p
@@ -159,7 +168,7 @@ template <int RAD, int DIR, typename C> __device__ __forceinline__ void dft(C (&
 // memory (lo, hi), one extra complex product each (FP32, where the kernels are
 // latency-bound); otherwise from the full table in global memory (FP64, where
 // the FP64 pipe is the bound and the table stays in L1/L2).
-template <int RAD, int QMAX, int DIR, bool POW2, bool TWS, typename C>
+template <int RAD, int QMAX, int DIR, bool POW2, bool TWS, bool PAD, typename C>
 __device__ __forceinline__ void fft_stage(C *buf, int n, int G, int p, const C *tw, const C *roots, const C *lo,
                                           const C *hi, int lg_m, int lg_p, int ls) {
     const int m = n / RAD, step = n / (p * RAD), total = G * m;
@@ -180,15 +189,15 @@ __device__ __forceinline__ void fft_stage(C *buf, int n, int G, int p, const C *
                 i = b - line * m;
                 k = i % p;
             }
-            const C *src = buf + (size_t)line * n + i;
+            const int src = line * n + i;
 #pragma unroll
-            for (int j = 0; j < RAD; ++j) u[q][j] = src[j * m];
+            for (int j = 0; j < RAD; ++j) u[q][j] = buf[slot<PAD>(src + j * m)];
             if (p > 1) {
 #pragma unroll
                 for (int j = 1; j < RAD; ++j) {
                     const int t = j * k * step;
                     C w;
-                    if constexpr (TWS) w = cmul(lo[t & ((1 << ls) - 1)], hi[t >> ls]);
+                    if constexpr (TWS) w = cmul(lo[slot<true>(t & ((1 << ls) - 1))], hi[slot<true>(t >> ls)]);
                     else w = __ldg(tw + t);
                     if (DIR > 0) w.y = -w.y;
                     u[q][j] = cmul(u[q][j], w);
@@ -204,7 +213,7 @@ __device__ __forceinline__ void fft_stage(C *buf, int n, int G, int p, const C *
     for (int q = 0; q < QMAX; ++q)
         if (ob[q] >= 0) {
 #pragma unroll
-            for (int j = 0; j < RAD; ++j) buf[ob[q] + j * p] = u[q][j];
+            for (int j = 0; j < RAD; ++j) buf[slot<PAD>(ob[q] + j * p)] = u[q][j];
         }
     __syncthreads();
 }
@@ -220,6 +229,7 @@ template <typename R, bool POW2> struct FftCfg {
     static constexpr int NT = f64 ? 512 : 1024, MINB = 1;
     static constexpr int VPT = POW2 ? 8 : 4;
     static constexpr bool TWS = POW2 && !f64;
+    static constexpr bool PAD = !f64;  // padded shared-memory lines (slot)
 };
 
 // Transform G lines of L.n points in place (DIR = -1 forward, +1 inverse,
@@ -229,24 +239,24 @@ template <int DIR, bool POW2, typename R, typename C>
 __device__ __forceinline__ void fft_lines_t(C *buf, const FftLen &L, int G, const C *tw_all, const C *roots, const C *lo, const C *hi) {
     typedef FftCfg<R, POW2> Cf;
     constexpr int V = Cf::VPT;
-    constexpr bool T = Cf::TWS;
+    constexpr bool T = Cf::TWS, PD = Cf::PAD;
     const C *tw = tw_all + L.tw_off;
     int p = 1, lg_p = 0, lg_m = L.log2n;
     for (int s = 0; s < L.nst; ++s) {
         const int R_ = L.rad[s];
         if constexpr (POW2) {
-            if (R_ == 8) fft_stage<8, V / 8, DIR, true, T>(buf, L.n, G, p, tw, roots, lo, hi, lg_m - 3, lg_p, L.ls);
-            else if (R_ == 4) fft_stage<4, V / 4, DIR, true, T>(buf, L.n, G, p, tw, roots, lo, hi, lg_m - 2, lg_p, L.ls);
-            else fft_stage<2, V / 2, DIR, true, T>(buf, L.n, G, p, tw, roots, lo, hi, lg_m - 1, lg_p, L.ls);
+            if (R_ == 8) fft_stage<8, V / 8, DIR, true, T, PD>(buf, L.n, G, p, tw, roots, lo, hi, lg_m - 3, lg_p, L.ls);
+            else if (R_ == 4) fft_stage<4, V / 4, DIR, true, T, PD>(buf, L.n, G, p, tw, roots, lo, hi, lg_m - 2, lg_p, L.ls);
+            else fft_stage<2, V / 2, DIR, true, T, PD>(buf, L.n, G, p, tw, roots, lo, hi, lg_m - 1, lg_p, L.ls);
             lg_p += R_ == 8 ? 3 : R_ == 4 ? 2 : 1;
         } else {
             switch (R_) {
-            case 8: fft_stage<8, 1, DIR, false, false>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
-            case 4: fft_stage<4, 1, DIR, false, false>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
-            case 2: fft_stage<2, 2, DIR, false, false>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
-            case 3: fft_stage<3, 2, DIR, false, false>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
-            case 5: fft_stage<5, 1, DIR, false, false>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
-            default: fft_stage<7, 1, DIR, false, false>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
+            case 8: fft_stage<8, 1, DIR, false, false, PD>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
+            case 4: fft_stage<4, 1, DIR, false, false, PD>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
+            case 2: fft_stage<2, 2, DIR, false, false, PD>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
+            case 3: fft_stage<3, 2, DIR, false, false, PD>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
+            case 5: fft_stage<5, 1, DIR, false, false, PD>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
+            default: fft_stage<7, 1, DIR, false, false, PD>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
             }
         }
         p *= R_;
@@ -263,14 +273,19 @@ __device__ __forceinline__ void fft_lines(C *buf, const FftLen &L, int G, const 
 // Copy the two-level twiddle table of L into shared memory at dst (when the
 // transforms use it); returns the (lo, hi) pointers.  The caller's next barrier
 // publishes it.
+// Both tables are stored padded (slot), like the lines: a stage reads lo at
+// strides of up to 16 entries.
 template <bool TWS, typename C>
 __device__ __forceinline__ void load_twiddles(const FftLen &L, const C *tw_all, C *dst, const C **lo, const C **hi) {
     if constexpr (TWS) {
         const int nlo = 1 << L.ls, nhi = L.n >> L.ls;
-        for (int t = threadIdx.x; t < nlo + nhi; t += blockDim.x)
-            dst[t] = t < nlo ? tw_all[L.lo_off + t] : tw_all[L.hi_off + (t - nlo)];
+        C *h = dst + padded<true>(nlo);
+        for (int t = threadIdx.x; t < nlo + nhi; t += blockDim.x) {
+            if (t < nlo) dst[slot<true>(t)] = tw_all[L.lo_off + t];
+            else h[slot<true>(t - nlo)] = tw_all[L.hi_off + (t - nlo)];
+        }
         *lo = dst;
-        *hi = dst + nlo;
+        *hi = h;
     } else {
         *lo = *hi = nullptr;
     }
@@ -278,7 +293,7 @@ __device__ __forceinline__ void load_twiddles(const FftLen &L, const C *tw_all, 
 
 // complex entries of shared memory the two-level table of a length needs
 __host__ __device__ __forceinline__ int twiddle_smem(const FftLen &L, bool tws) {
-    return tws ? (1 << L.ls) + (L.n >> L.ls) : 0;
+    return tws ? padded<true>(1 << L.ls) + padded<true>(L.n >> L.ls) : 0;
 }
 
 // ------------------------------------------------------------ row passes --
@@ -291,6 +306,7 @@ __device__ void rows_forward_body(typename Cplx<R>::type *buf, const R *f, typen
                                   const typename Cplx<R>::type *roots, const typename Cplx<R>::type *lo,
                                   const typename Cplx<R>::type *hi, bool load) {
     typedef typename Cplx<R>::type C;
+    constexpr bool PD = FftCfg<R, POW2>::PAD;
     const int rb = ra + 1;
     const bool has_b = rb < nrows;
     if (load) {
@@ -300,14 +316,14 @@ __device__ void rows_forward_body(typename Cplx<R>::type *buf, const R *f, typen
                 a = coef * ((a * a) * a);
                 b = coef * ((b * b) * b);
             }
-            buf[i] = C{a, b};
+            buf[slot<PD>(i)] = C{a, b};
         }
     }
     __syncthreads();
     fft_lines<-1, POW2>(buf, L, 1, tw, roots, lo, hi);
     const int nxh = nx / 2 + 1;
     for (int k = threadIdx.x; k < nxh; k += blockDim.x) {
-        const C zk = buf[k], zc = buf[k == 0 ? 0 : nx - k];
+        const C zk = buf[slot<PD>(k)], zc = buf[slot<PD>(k == 0 ? 0 : nx - k)];
         // A = (z_k + conj z_{n-k}) / 2, B = -i (z_k - conj z_{n-k}) / 2
         const C A{R(0.5) * (zk.x + zc.x), R(0.5) * (zk.y - zc.y)};
         const C B{R(0.5) * (zk.y + zc.y), R(0.5) * (zc.x - zk.x)};
@@ -324,7 +340,7 @@ __global__ void __launch_bounds__(FftCfg<R, POW2>::NT, FftCfg<R, POW2>::MINB)
     typedef typename Cplx<R>::type C;
     C *buf = reinterpret_cast<C *>(smem_raw);
     const C *lo, *hi;
-    load_twiddles<FftCfg<R, POW2>::TWS>(L, tw, buf + nx, &lo, &hi);
+    load_twiddles<FftCfg<R, POW2>::TWS>(L, tw, buf + padded<FftCfg<R, POW2>::PAD>(nx), &lo, &hi);
     rows_forward_body<R, CUBE, POW2>(buf, f, Z, nx, nrows, 2 * blockIdx.x, coef, L, tw, roots, lo, hi, true);
 }
 
@@ -335,9 +351,10 @@ __global__ void __launch_bounds__(FftCfg<R, POW2>::NT, FftCfg<R, POW2>::MINB) ro
                                     const typename Cplx<R>::type *tw, const typename Cplx<R>::type *roots) {
     typedef typename Cplx<R>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr bool PD = FftCfg<R, POW2>::PAD;
     C *buf = reinterpret_cast<C *>(smem_raw);
     const C *lo, *hi;
-    load_twiddles<FftCfg<R, POW2>::TWS>(L, tw, buf + nx, &lo, &hi);
+    load_twiddles<FftCfg<R, POW2>::TWS>(L, tw, buf + padded<PD>(nx), &lo, &hi);
     const int ra = 2 * blockIdx.x, rb = ra + 1;
     const bool has_b = rb < nrows;
     const int half = nx / 2;
@@ -354,15 +371,15 @@ __global__ void __launch_bounds__(FftCfg<R, POW2>::NT, FftCfg<R, POW2>::MINB) ro
             A.y = -A.y;
             B.y = -B.y;
         }
-        buf[k] = C{A.x - B.y, A.y + B.x};  // A + i B
+        buf[slot<PD>(k)] = C{A.x - B.y, A.y + B.x};  // A + i B
     }
     __syncthreads();
     fft_lines<1, POW2>(buf, L, 1, tw, roots, lo, hi);
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        const C v = buf[i];
+        const C v = buf[slot<PD>(i)];
         phi[(size_t)ra * nx + i] = v.x;
         if (has_b) phi[(size_t)rb * nx + i] = v.y;
-        if (NEXT) buf[i] = C{coef * ((v.x * v.x) * v.x), has_b ? coef * ((v.y * v.y) * v.y) : R(0)};
+        if (NEXT) buf[slot<PD>(i)] = C{coef * ((v.x * v.x) * v.x), has_b ? coef * ((v.y * v.y) * v.y) : R(0)};
     }
     if (NEXT) rows_forward_body<R, false, POW2>(buf, nullptr, Z, nx, nrows, ra, coef, L, tw, roots, lo, hi, false);
 }
@@ -409,9 +426,10 @@ __global__ void __launch_bounds__(FftCfg<R, POW2>::NT, FftCfg<R, POW2>::MINB) li
                              R c1, R kappa, R dt, R inv_n) {
     typedef typename Cplx<R>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr bool PD = FftCfg<R, POW2>::PAD;
     C *buf = reinterpret_cast<C *>(smem_raw);
     const C *lo, *hi;
-    load_twiddles<FftCfg<R, POW2>::TWS>(L, tw, buf + (size_t)g.G * g.n, &lo, &hi);
+    load_twiddles<FftCfg<R, POW2>::TWS>(L, tw, buf + padded<PD>(g.G * g.n), &lo, &hi);
     const int n = g.n;
     // first line of this CTA's group and its line count
     const int gi = blockIdx.x;
@@ -435,7 +453,7 @@ __global__ void __launch_bounds__(FftCfg<R, POW2>::NT, FftCfg<R, POW2>::MINB) li
             else { l = e / n; i = e - l * n; }
         }
         else { i = e / nl; l = e - i * nl; }   // adjacent lines first: coalesced
-        buf[l * n + i] = Z[base + (size_t)l * g.lstride + (size_t)i * g.estride];
+        buf[slot<PD>(l * n + i)] = Z[base + (size_t)l * g.lstride + (size_t)i * g.estride];
     }
     __syncthreads();
     if (MODE == kLineInverse) fft_lines<1, POW2>(buf, L, nl, tw, roots, lo, hi);
@@ -459,7 +477,7 @@ __global__ void __launch_bounds__(FftCfg<R, POW2>::NT, FftCfg<R, POW2>::MINB) li
                 my = freq_of(line0 + l, g.ny);
                 mz = freq_of(i, g.nz);
             }
-            buf[l * n + i] = update_mode<R, MODEL>(uh + at, buf[l * n + i], mx, my, mz, tx, ty, tz, c1, kappa, dt,
+            buf[slot<PD>(l * n + i)] = update_mode<R, MODEL>(uh + at, buf[slot<PD>(l * n + i)], mx, my, mz, tx, ty, tz, c1, kappa, dt,
                                                    inv_n);
         }
         __syncthreads();
@@ -472,7 +490,7 @@ __global__ void __launch_bounds__(FftCfg<R, POW2>::NT, FftCfg<R, POW2>::MINB) li
             else { l = e / n; i = e - l * n; }
         }
         else { i = e / nl; l = e - i * nl; }
-        Z[base + (size_t)l * g.lstride + (size_t)i * g.estride] = buf[l * n + i];
+        Z[base + (size_t)l * g.lstride + (size_t)i * g.estride] = buf[slot<PD>(l * n + i)];
     }
 }
 
@@ -663,7 +681,8 @@ static cudaError_t run_lines_t(SpectralPlan *P, int axis, cudaStream_t s, R tx, 
     const FftLen &L = axis == 1 ? P->ly : P->lz;
     const unsigned blocks = axis == 1 ? (unsigned)((P->nxh * P->nz + g.G - 1) / g.G)
                                       : (unsigned)(P->nxh * g.groups_per_kx);
-    const size_t smem = ((size_t)g.G * g.n + twiddle_smem(L, FftCfg<R, POW2>::TWS)) * csize<R>();
+    const size_t smem = ((size_t)padded<FftCfg<R, POW2>::PAD>(g.G * g.n) + twiddle_smem(L, FftCfg<R, POW2>::TWS)) *
+                        csize<R>();
     auto kern = lines_kernel<R, MODE, MODEL, POW2>;
     cudaError_t e = prepare(kern, smem);
     if (e != cudaSuccess) return e;
@@ -684,7 +703,8 @@ template <typename R, bool CUBE, bool POW2>
 static cudaError_t run_rows_forward_t(SpectralPlan *P, const R *f, typename Cplx<R>::type *Z, R coef, cudaStream_t s) {
     typedef typename Cplx<R>::type C;
     const int nrows = P->ny * P->nz;
-    const size_t smem = ((size_t)P->nx + twiddle_smem(P->lx, FftCfg<R, POW2>::TWS)) * csize<R>();
+    const size_t smem = ((size_t)padded<FftCfg<R, POW2>::PAD>(P->nx) + twiddle_smem(P->lx, FftCfg<R, POW2>::TWS)) *
+                        csize<R>();
     auto kern = rows_forward_kernel<R, CUBE, POW2>;
     cudaError_t e = prepare(kern, smem);
     if (e != cudaSuccess) return e;
@@ -704,7 +724,8 @@ template <typename R, bool NEXT, bool POW2>
 static cudaError_t run_rows_inverse_t(SpectralPlan *P, R *phi, R coef, cudaStream_t s) {
     typedef typename Cplx<R>::type C;
     const int nrows = P->ny * P->nz;
-    const size_t smem = ((size_t)P->nx + twiddle_smem(P->lx, FftCfg<R, POW2>::TWS)) * csize<R>();
+    const size_t smem = ((size_t)padded<FftCfg<R, POW2>::PAD>(P->nx) + twiddle_smem(P->lx, FftCfg<R, POW2>::TWS)) *
+                        csize<R>();
     auto kern = rows_inverse_kernel<R, NEXT, POW2>;
     cudaError_t e = prepare(kern, smem);
     if (e != cudaSuccess) return e;
