@@ -193,14 +193,26 @@ __device__ __forceinline__ void fft_stage(C *buf, int n, int G, int p, const C *
 #pragma unroll
             for (int j = 0; j < RAD; ++j) u[q][j] = buf[slot<PAD>(src + j * m)];
             if (p > 1) {
+                if constexpr (TWS) {
+                    // w^j for j = 1 .. RAD-1 from one table look-up of w = exp(-2 pi i k step / n)
+                    // by repeated products (FP32: at most RAD-2 roundings more than a look-up
+                    // per power, well inside the FP32 tolerance)
+                    const int t = k * step;
+                    C w1 = cmul(lo[slot<true>(t & ((1 << ls) - 1))], hi[slot<true>(t >> ls)]);
+                    if (DIR > 0) w1.y = -w1.y;
+                    C wj = w1;
 #pragma unroll
-                for (int j = 1; j < RAD; ++j) {
-                    const int t = j * k * step;
-                    C w;
-                    if constexpr (TWS) w = cmul(lo[slot<true>(t & ((1 << ls) - 1))], hi[slot<true>(t >> ls)]);
-                    else w = __ldg(tw + t);
-                    if (DIR > 0) w.y = -w.y;
-                    u[q][j] = cmul(u[q][j], w);
+                    for (int j = 1; j < RAD; ++j) {
+                        u[q][j] = cmul(u[q][j], wj);
+                        if (j + 1 < RAD) wj = cmul(wj, w1);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 1; j < RAD; ++j) {
+                        C w = __ldg(tw + j * k * step);
+                        if (DIR > 0) w.y = -w.y;
+                        u[q][j] = cmul(u[q][j], w);
+                    }
                 }
             }
             dft<RAD, DIR>(u[q], roots);
@@ -414,8 +426,14 @@ __device__ __forceinline__ typename Cplx<R>::type update_mode(typename Cplx<R>::
     const R denom = R(1) - dt * L;
     const C a = *uh;
     C v;
-    v.x = (a.x + dt * (w * nh.x)) / denom;
-    v.y = (a.y + dt * (w * nh.y)) / denom;
+    if constexpr (sizeof(R) == 8) {
+        v.x = (a.x + dt * (w * nh.x)) / denom;
+        v.y = (a.y + dt * (w * nh.y)) / denom;
+    } else {  // FP32: one correctly rounded reciprocal for both parts (within an ulp of the quotients)
+        const R rd = __frcp_rn(denom);
+        v.x = (a.x + dt * (w * nh.x)) * rd;
+        v.y = (a.y + dt * (w * nh.y)) * rd;
+    }
     *uh = v;
     return C{v.x * inv_n, v.y * inv_n};
 }
