@@ -159,7 +159,8 @@ template <bool PAD> __device__ __forceinline__ int slot(int i) { return PAD ? i 
 template <bool PAD> __host__ __device__ __forceinline__ int padded(int e) { return PAD ? e + (e >> 4) + 1 : e; }
 
 
-// One radix-RAD stage on G lines of n points in buf (line l at buf + l*n); p is
+// One radix-RAD stage on G lines of n points from buf into out (line l at
+// offset l*n of each, both padded alike; one barrier, after the stores); p is
 // the product of the radices of the earlier stages.  Butterfly b of a line
 // (b < n/RAD) reads its inputs at stride n/RAD and writes them at stride p
 // from ((b - k) * RAD + k), k = b mod p.  Each thread keeps at most QMAX
@@ -169,8 +170,8 @@ template <bool PAD> __host__ __device__ __forceinline__ int padded(int e) { retu
 // latency-bound); otherwise from the full table in global memory (FP64, where
 // the FP64 pipe is the bound and the table stays in L1/L2).
 template <int RAD, int QMAX, int DIR, bool POW2, bool TWS, bool PAD, typename C>
-__device__ __forceinline__ void fft_stage(C *buf, int n, int G, int p, const C *tw, const C *roots, const C *lo,
-                                          const C *hi, int lg_m, int lg_p, int ls) {
+__device__ __forceinline__ void fft_stage(const C *buf, C *out, int n, int G, int p, const C *tw, const C *roots,
+                                          const C *lo, const C *hi, int lg_m, int lg_p, int ls) {
     const int m = n / RAD, step = n / (p * RAD), total = G * m;
     C u[QMAX][RAD];
     int ob[QMAX];
@@ -220,12 +221,11 @@ __device__ __forceinline__ void fft_stage(C *buf, int n, int G, int p, const C *
         }
     }
     (void)lg_p;
-    __syncthreads();
 #pragma unroll
     for (int q = 0; q < QMAX; ++q)
         if (ob[q] >= 0) {
 #pragma unroll
-            for (int j = 0; j < RAD; ++j) buf[slot<PAD>(ob[q] + j * p)] = u[q][j];
+            for (int j = 0; j < RAD; ++j) out[slot<PAD>(ob[q] + j * p)] = u[q][j];
         }
     __syncthreads();
 }
@@ -244,11 +244,13 @@ template <typename R, bool POW2> struct FftCfg {
     static constexpr bool PAD = !f64;  // padded shared-memory lines (slot)
 };
 
-// Transform G lines of L.n points in place (DIR = -1 forward, +1 inverse,
-// unnormalised).  Call with every thread of the CTA (at least G*n/VPT), after
-// a barrier.
+// Transform G lines of L.n points (DIR = -1 forward, +1 inverse, unnormalised),
+// alternating between the buffers buf and alt stage by stage; returns the one
+// that holds the result (the other is scratch).  Call with every thread of the
+// CTA (at least G*n/VPT), after a barrier.
 template <int DIR, bool POW2, typename R, typename C>
-__device__ __forceinline__ void fft_lines_t(C *buf, const FftLen &L, int G, const C *tw_all, const C *roots, const C *lo, const C *hi) {
+__device__ __forceinline__ C *fft_lines_t(C *buf, C *alt, const FftLen &L, int G, const C *tw_all, const C *roots,
+                                          const C *lo, const C *hi) {
     typedef FftCfg<R, POW2> Cf;
     constexpr int V = Cf::VPT;
     constexpr bool T = Cf::TWS, PD = Cf::PAD;
@@ -257,29 +259,33 @@ __device__ __forceinline__ void fft_lines_t(C *buf, const FftLen &L, int G, cons
     for (int s = 0; s < L.nst; ++s) {
         const int R_ = L.rad[s];
         if constexpr (POW2) {
-            if (R_ == 8) fft_stage<8, V / 8, DIR, true, T, PD>(buf, L.n, G, p, tw, roots, lo, hi, lg_m - 3, lg_p, L.ls);
-            else if (R_ == 4) fft_stage<4, V / 4, DIR, true, T, PD>(buf, L.n, G, p, tw, roots, lo, hi, lg_m - 2, lg_p, L.ls);
-            else fft_stage<2, V / 2, DIR, true, T, PD>(buf, L.n, G, p, tw, roots, lo, hi, lg_m - 1, lg_p, L.ls);
+            if (R_ == 8) fft_stage<8, V / 8, DIR, true, T, PD>(buf, alt, L.n, G, p, tw, roots, lo, hi, lg_m - 3, lg_p, L.ls);
+            else if (R_ == 4) fft_stage<4, V / 4, DIR, true, T, PD>(buf, alt, L.n, G, p, tw, roots, lo, hi, lg_m - 2, lg_p, L.ls);
+            else fft_stage<2, V / 2, DIR, true, T, PD>(buf, alt, L.n, G, p, tw, roots, lo, hi, lg_m - 1, lg_p, L.ls);
             lg_p += R_ == 8 ? 3 : R_ == 4 ? 2 : 1;
         } else {
             switch (R_) {
-            case 8: fft_stage<8, 1, DIR, false, false, PD>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
-            case 4: fft_stage<4, 1, DIR, false, false, PD>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
-            case 2: fft_stage<2, 2, DIR, false, false, PD>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
-            case 3: fft_stage<3, 2, DIR, false, false, PD>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
-            case 5: fft_stage<5, 1, DIR, false, false, PD>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
-            default: fft_stage<7, 1, DIR, false, false, PD>(buf, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
+            case 8: fft_stage<8, 1, DIR, false, false, PD>(buf, alt, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
+            case 4: fft_stage<4, 1, DIR, false, false, PD>(buf, alt, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
+            case 2: fft_stage<2, 2, DIR, false, false, PD>(buf, alt, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
+            case 3: fft_stage<3, 2, DIR, false, false, PD>(buf, alt, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
+            case 5: fft_stage<5, 1, DIR, false, false, PD>(buf, alt, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
+            default: fft_stage<7, 1, DIR, false, false, PD>(buf, alt, L.n, G, p, tw, roots, lo, hi, 0, 0, 0); break;
             }
         }
         p *= R_;
+        C *t = buf;
+        buf = alt;
+        alt = t;
     }
+    return buf;
 }
 
 template <int DIR, bool POW2, typename C>
-__device__ __forceinline__ void fft_lines(C *buf, const FftLen &L, int G, const C *tw_all, const C *roots,
-                                          const C *lo, const C *hi) {
+__device__ __forceinline__ C *fft_lines(C *buf, C *alt, const FftLen &L, int G, const C *tw_all, const C *roots,
+                                        const C *lo, const C *hi) {
     typedef decltype(C{}.x) R;
-    fft_lines_t<DIR, POW2, R>(buf, L, G, tw_all, roots, lo, hi);
+    return fft_lines_t<DIR, POW2, R>(buf, alt, L, G, tw_all, roots, lo, hi);
 }
 
 // Copy the two-level twiddle table of L into shared memory at dst (when the
@@ -313,7 +319,8 @@ __host__ __device__ __forceinline__ int twiddle_smem(const FftLen &L, bool tws) 
 // Forward x transforms of rows 2c and 2c+1 (the second may not exist) of a real
 // field f (cubed and scaled by coef when CUBE), written to Z[kx][row].
 template <typename R, bool CUBE, bool POW2>
-__device__ void rows_forward_body(typename Cplx<R>::type *buf, const R *f, typename Cplx<R>::type *Z, int nx,
+__device__ void rows_forward_body(typename Cplx<R>::type *buf, typename Cplx<R>::type *alt, const R *f,
+                                  typename Cplx<R>::type *Z, int nx,
                                   int nrows, int ra, R coef, const FftLen &L, const typename Cplx<R>::type *tw,
                                   const typename Cplx<R>::type *roots, const typename Cplx<R>::type *lo,
                                   const typename Cplx<R>::type *hi, bool load) {
@@ -332,10 +339,10 @@ __device__ void rows_forward_body(typename Cplx<R>::type *buf, const R *f, typen
         }
     }
     __syncthreads();
-    fft_lines<-1, POW2>(buf, L, 1, tw, roots, lo, hi);
+    const C *res = fft_lines<-1, POW2>(buf, alt, L, 1, tw, roots, lo, hi);
     const int nxh = nx / 2 + 1;
     for (int k = threadIdx.x; k < nxh; k += blockDim.x) {
-        const C zk = buf[slot<PD>(k)], zc = buf[slot<PD>(k == 0 ? 0 : nx - k)];
+        const C zk = res[slot<PD>(k)], zc = res[slot<PD>(k == 0 ? 0 : nx - k)];
         // A = (z_k + conj z_{n-k}) / 2, B = -i (z_k - conj z_{n-k}) / 2
         const C A{R(0.5) * (zk.x + zc.x), R(0.5) * (zk.y - zc.y)};
         const C B{R(0.5) * (zk.y + zc.y), R(0.5) * (zc.x - zk.x)};
@@ -351,9 +358,10 @@ __global__ void __launch_bounds__(FftCfg<R, POW2>::NT, FftCfg<R, POW2>::MINB)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     typedef typename Cplx<R>::type C;
     C *buf = reinterpret_cast<C *>(smem_raw);
+    C *alt = buf + padded<FftCfg<R, POW2>::PAD>(nx);
     const C *lo, *hi;
-    load_twiddles<FftCfg<R, POW2>::TWS>(L, tw, buf + padded<FftCfg<R, POW2>::PAD>(nx), &lo, &hi);
-    rows_forward_body<R, CUBE, POW2>(buf, f, Z, nx, nrows, 2 * blockIdx.x, coef, L, tw, roots, lo, hi, true);
+    load_twiddles<FftCfg<R, POW2>::TWS>(L, tw, alt + padded<FftCfg<R, POW2>::PAD>(nx), &lo, &hi);
+    rows_forward_body<R, CUBE, POW2>(buf, alt, f, Z, nx, nrows, 2 * blockIdx.x, coef, L, tw, roots, lo, hi, true);
 }
 
 // Inverse x transforms of rows 2c, 2c+1 from Z into phi; with NEXT, the cubic
@@ -365,8 +373,9 @@ __global__ void __launch_bounds__(FftCfg<R, POW2>::NT, FftCfg<R, POW2>::MINB) ro
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool PD = FftCfg<R, POW2>::PAD;
     C *buf = reinterpret_cast<C *>(smem_raw);
+    C *alt = buf + padded<PD>(nx);
     const C *lo, *hi;
-    load_twiddles<FftCfg<R, POW2>::TWS>(L, tw, buf + padded<PD>(nx), &lo, &hi);
+    load_twiddles<FftCfg<R, POW2>::TWS>(L, tw, alt + padded<PD>(nx), &lo, &hi);
     const int ra = 2 * blockIdx.x, rb = ra + 1;
     const bool has_b = rb < nrows;
     const int half = nx / 2;
@@ -386,14 +395,14 @@ __global__ void __launch_bounds__(FftCfg<R, POW2>::NT, FftCfg<R, POW2>::MINB) ro
         buf[slot<PD>(k)] = C{A.x - B.y, A.y + B.x};  // A + i B
     }
     __syncthreads();
-    fft_lines<1, POW2>(buf, L, 1, tw, roots, lo, hi);
+    C *res = fft_lines<1, POW2>(buf, alt, L, 1, tw, roots, lo, hi);
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        const C v = buf[slot<PD>(i)];
+        const C v = res[slot<PD>(i)];
         phi[(size_t)ra * nx + i] = v.x;
         if (has_b) phi[(size_t)rb * nx + i] = v.y;
-        if (NEXT) buf[slot<PD>(i)] = C{coef * ((v.x * v.x) * v.x), has_b ? coef * ((v.y * v.y) * v.y) : R(0)};
+        if (NEXT) res[slot<PD>(i)] = C{coef * ((v.x * v.x) * v.x), has_b ? coef * ((v.y * v.y) * v.y) : R(0)};
     }
-    if (NEXT) rows_forward_body<R, false, POW2>(buf, nullptr, Z, nx, nrows, ra, coef, L, tw, roots, lo, hi, false);
+    if (NEXT) rows_forward_body<R, false, POW2>(res, res == buf ? alt : buf, nullptr, Z, nx, nrows, ra, coef, L, tw, roots, lo, hi, false);
 }
 
 // ----------------------------------------------------------- line passes --
@@ -446,8 +455,9 @@ __global__ void __launch_bounds__(FftCfg<R, POW2>::NT, FftCfg<R, POW2>::MINB) li
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool PD = FftCfg<R, POW2>::PAD;
     C *buf = reinterpret_cast<C *>(smem_raw);
+    C *alt = buf + padded<PD>(g.G * g.n);
     const C *lo, *hi;
-    load_twiddles<FftCfg<R, POW2>::TWS>(L, tw, buf + padded<PD>(g.G * g.n), &lo, &hi);
+    load_twiddles<FftCfg<R, POW2>::TWS>(L, tw, alt + padded<PD>(g.G * g.n), &lo, &hi);
     const int n = g.n;
     // first line of this CTA's group and its line count
     const int gi = blockIdx.x;
@@ -474,8 +484,8 @@ __global__ void __launch_bounds__(FftCfg<R, POW2>::NT, FftCfg<R, POW2>::MINB) li
         buf[slot<PD>(l * n + i)] = Z[base + (size_t)l * g.lstride + (size_t)i * g.estride];
     }
     __syncthreads();
-    if (MODE == kLineInverse) fft_lines<1, POW2>(buf, L, nl, tw, roots, lo, hi);
-    else fft_lines<-1, POW2>(buf, L, nl, tw, roots, lo, hi);
+    C *res = (MODE == kLineInverse) ? fft_lines<1, POW2>(buf, alt, L, nl, tw, roots, lo, hi)
+                                    : fft_lines<-1, POW2>(buf, alt, L, nl, tw, roots, lo, hi);
     if (MODE == kLineUpdate) {
         for (int e = threadIdx.x; e < nl * n; e += blockDim.x) {
             int l, i;
@@ -495,11 +505,11 @@ __global__ void __launch_bounds__(FftCfg<R, POW2>::NT, FftCfg<R, POW2>::MINB) li
                 my = freq_of(line0 + l, g.ny);
                 mz = freq_of(i, g.nz);
             }
-            buf[slot<PD>(l * n + i)] = update_mode<R, MODEL>(uh + at, buf[slot<PD>(l * n + i)], mx, my, mz, tx, ty, tz, c1, kappa, dt,
+            res[slot<PD>(l * n + i)] = update_mode<R, MODEL>(uh + at, res[slot<PD>(l * n + i)], mx, my, mz, tx, ty, tz, c1, kappa, dt,
                                                    inv_n);
         }
         __syncthreads();
-        fft_lines<1, POW2>(buf, L, nl, tw, roots, lo, hi);
+        res = fft_lines<1, POW2>(res, res == buf ? alt : buf, L, nl, tw, roots, lo, hi);
     }
     for (int e = threadIdx.x; e < nl * n; e += blockDim.x) {
         int l, i;
@@ -508,7 +518,7 @@ __global__ void __launch_bounds__(FftCfg<R, POW2>::NT, FftCfg<R, POW2>::MINB) li
             else { l = e / n; i = e - l * n; }
         }
         else { i = e / nl; l = e - i * nl; }
-        Z[base + (size_t)l * g.lstride + (size_t)i * g.estride] = buf[slot<PD>(l * n + i)];
+        Z[base + (size_t)l * g.lstride + (size_t)i * g.estride] = res[slot<PD>(l * n + i)];
     }
 }
 
@@ -699,8 +709,8 @@ static cudaError_t run_lines_t(SpectralPlan *P, int axis, cudaStream_t s, R tx, 
     const FftLen &L = axis == 1 ? P->ly : P->lz;
     const unsigned blocks = axis == 1 ? (unsigned)((P->nxh * P->nz + g.G - 1) / g.G)
                                       : (unsigned)(P->nxh * g.groups_per_kx);
-    const size_t smem = ((size_t)padded<FftCfg<R, POW2>::PAD>(g.G * g.n) + twiddle_smem(L, FftCfg<R, POW2>::TWS)) *
-                        csize<R>();
+    const size_t smem =
+        ((size_t)2 * padded<FftCfg<R, POW2>::PAD>(g.G * g.n) + twiddle_smem(L, FftCfg<R, POW2>::TWS)) * csize<R>();
     auto kern = lines_kernel<R, MODE, MODEL, POW2>;
     cudaError_t e = prepare(kern, smem);
     if (e != cudaSuccess) return e;
@@ -721,8 +731,8 @@ template <typename R, bool CUBE, bool POW2>
 static cudaError_t run_rows_forward_t(SpectralPlan *P, const R *f, typename Cplx<R>::type *Z, R coef, cudaStream_t s) {
     typedef typename Cplx<R>::type C;
     const int nrows = P->ny * P->nz;
-    const size_t smem = ((size_t)padded<FftCfg<R, POW2>::PAD>(P->nx) + twiddle_smem(P->lx, FftCfg<R, POW2>::TWS)) *
-                        csize<R>();
+    const size_t smem =
+        ((size_t)2 * padded<FftCfg<R, POW2>::PAD>(P->nx) + twiddle_smem(P->lx, FftCfg<R, POW2>::TWS)) * csize<R>();
     auto kern = rows_forward_kernel<R, CUBE, POW2>;
     cudaError_t e = prepare(kern, smem);
     if (e != cudaSuccess) return e;
@@ -742,8 +752,8 @@ template <typename R, bool NEXT, bool POW2>
 static cudaError_t run_rows_inverse_t(SpectralPlan *P, R *phi, R coef, cudaStream_t s) {
     typedef typename Cplx<R>::type C;
     const int nrows = P->ny * P->nz;
-    const size_t smem = ((size_t)padded<FftCfg<R, POW2>::PAD>(P->nx) + twiddle_smem(P->lx, FftCfg<R, POW2>::TWS)) *
-                        csize<R>();
+    const size_t smem =
+        ((size_t)2 * padded<FftCfg<R, POW2>::PAD>(P->nx) + twiddle_smem(P->lx, FftCfg<R, POW2>::TWS)) * csize<R>();
     auto kern = rows_inverse_kernel<R, NEXT, POW2>;
     cudaError_t e = prepare(kern, smem);
     if (e != cudaSuccess) return e;
