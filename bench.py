@@ -65,6 +65,12 @@ WORKLOADS = {
     # 3D temporal blocking: one step per launch against two (warp-row plane queues)
     "gs3d-512-f32-lap7-k1": (2, 3, (512, 512, 512), 0.5, 3, 1, 10, 1, 0),
     "gs3d-512-f32-lap7-k2": (2, 3, (512, 512, 512), 0.5, 3, 1, 10, 2),
+    "gs3d-512-f32-lap7-async": (2, 3, (512, 512, 512), 0.5, 3, 1, 10, 1, 1),
+    "gs3d-512-f32-lap7-tma": (2, 3, (512, 512, 512), 0.5, 3, 1, 10, 1, 6),
+    "ch3d-1024-f32-lap7-async": (1, 3, (1024, 1024, 1024), 0.005, 3, 1, 5, 1, 1),
+    "ch3d-1024-f32-lap7-tma": (1, 3, (1024, 1024, 1024), 0.005, 3, 1, 5, 1, 6),
+    "ac3d-1024-f32-lap27-async": (0, 3, (1024, 1024, 1024), 0.05, 4, 1, 6, 1, 1),
+    "ac3d-1024-f32-lap27-tma": (0, 3, (1024, 1024, 1024), 0.05, 4, 1, 6, 1, 6),
     "ac3d-1024-f32-lap27-k1": (0, 3, (1024, 1024, 1024), 0.05, 4, 1, 6, 1, 0),
     "ac3d-1024-f32-lap27-k2": (0, 3, (1024, 1024, 1024), 0.05, 4, 1, 6, 2),
     "ac3d-1024-f32-lap7-k2": (0, 3, (1024, 1024, 1024), 0.05, 3, 1, 6, 2),

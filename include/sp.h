@@ -312,6 +312,17 @@ int sp_probe_fp64_rate(void *stream, double *gops);
  * runs on the current device. */
 int sp_binary_version(int *version);
 
+/* Test hook (no counterpart in the paper): the number of polls after which the
+ * kernels' bounded device waits (the mbarrier waits of the tensor-map plane
+ * ring, kernel family 6) give up; 0 restores the default (about 4 million polls,
+ * far beyond any transfer) and a negative value makes every wait give up at
+ * once (the copies in flight still land before the kernel returns).  A wait
+ * that gives up leaves the step's output
+ * invalid, and the next sp_read or sp_reduce of that simulation returns
+ * SP_ETIMEOUT.  Process-wide; launches captured in CUDA graphs keep the value
+ * they were captured with.  Always returns SP_OK. */
+int sp_set_wait_polls(long long polls);
+
 /* Launch configuration in use: steps fused per launch and kernel family
  * (0 = the default for the grid; alternatives the autotuner may pick: 1 for
  * every grid of the finite-difference scheme except 3D FP64 with the 7- and
@@ -319,7 +330,9 @@ int sp_binary_version(int *version);
  * Cahn-Hilliard and Gray-Scott (plane sums in registers instead of x-pair sums
  * shared between rows) and for 3D FP64 7- and 13-point Cahn-Hilliard (one fused
  * pass instead of two through the mu buffer); 2 and 4 for 2D FP64, the strip
- * kernel with 64 threads per CTA and with half the rows per batch). */
+ * kernel with 64 threads per CTA and with half the rows per batch; 6 for 3D
+ * FP32/BF16 Allen-Cahn, Cahn-Hilliard and Gray-Scott with nx a multiple of 4
+ * (FP32) or 8 (BF16): the plane ring with tensor-map (TMA) plane loads). */
 int sp_launch_config(const sp_sim *sim, int *steps_per_launch, int *variant);
 
 /* Number of time steps taken since creation. */

@@ -211,6 +211,13 @@ class Result:
         return self.t_finish - self.t_submit
 
 
+def set_wait_polls(polls: int) -> None:
+    """Test hook: polls before the kernels' bounded device waits give up (0 the
+    default, negative: give up at once); a step whose wait gave up makes the next
+    read or reduction of that simulation raise SpError(SP_ETIMEOUT)."""
+    N.lib().sp_set_wait_polls(int(polls))
+
+
 def admission_order(bytes_, priorities, free_bytes: int, free_slots: int) -> list[int]:
     """The server's admission rule (sp_admission_order): indices of the pending
     requests admitted now, in admission order."""

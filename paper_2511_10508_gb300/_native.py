@@ -83,6 +83,7 @@ _SIGS = {
     "sp_launch_config": (ctypes.c_int, [_vp, _P(ctypes.c_int), _P(ctypes.c_int)]),
     "sp_probe_fp64_rate": (ctypes.c_int, [_vp, _P(ctypes.c_double)]),
     "sp_binary_version": (ctypes.c_int, [_P(ctypes.c_int)]),
+    "sp_set_wait_polls": (ctypes.c_int, [ctypes.c_longlong]),
     "sp_destroy": (ctypes.c_int, [_vp]),
     "sp_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, _P(_vp)]),
     "sp_submit": (ctypes.c_int, [_vp, _P(sp_request), _P(ctypes.c_uint64)]),

@@ -30,6 +30,7 @@
 //                    u' = fma(dt, fma(u, g, (1/q_h2)*S(u)), u);  v' = fma(dt/q_h2, S(m), v)
 #pragma once
 
+#include <cuda.h>  // CUtensorMap
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -360,6 +361,61 @@ struct StepArgs {
     int nx, ny, nz;
     StepConsts k;            // FP64 coefficients
     StepConstsF kf;          // the same, rounded to FP32
+    int *flag = nullptr;     // set to 1 by a kernel whose bounded wait expired (else untouched)
+    long long wait_polls = 0;  // polls before a wait gives up (0: the default; < 0: none, a test hook)
 };
+
+// ------------------------------------------------------- tensor-map loads --
+//
+// Tiles moved by the Tensor Memory Accelerator (cp.async.bulk.tensor) into
+// shared memory, completion tracked by an mbarrier with a transaction count.
+// The tensor maps describe this GPU's own fields only; no multicast.
+
+struct TmaMaps {
+    CUtensorMap m[2];  // field 0, field 1
+};
+
+// default bound on mbarrier polls (each may sleep up to about 1 us): a few
+// seconds, far beyond any transfer
+constexpr long long kDefaultWaitPolls = 1LL << 22;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// make barrier initialisation visible to the async proxy (TMA)
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// order this thread's earlier shared-memory accesses before later async-proxy ones
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// one poll: the thread may sleep up to about 1 us unless the phase completes first
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(1000u)
+        : "memory");
+    return ok != 0;
+}
+// wait for the phase of the given parity to complete, at most `polls` polls
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, long long polls) {
+    for (long long i = 0; i < polls; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+// box of a rank-3 tensor map at (x, y, z) (x a multiple of 16 bytes) into dst,
+// completing `bar`'s transaction count
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
 
 }  // namespace sp

@@ -107,6 +107,15 @@ inline bool planes27_applies(int dims, int dtype, int stencil, int model) {
            (model == SP_ALLEN_CAHN || model == SP_CAHN_HILLIARD || model == SP_GRAY_SCOTT);
 }
 
+// Tensor-map (TMA) plane loads (sp_tma.cu): kernel family kTmaFamily of 3D
+// FP32/BF16 Allen-Cahn, Cahn-Hilliard and Gray-Scott grids with nx a multiple of
+// 16 bytes' worth of cells.  encode_plane_maps describes fields f0 and f1 (f1 may
+// equal f0) as nx x ny x nz tensors with box_x x box_y x 1 boxes.
+constexpr int kTmaFamily = 6;
+bool tma_available();
+cudaError_t encode_plane_maps(TmaMaps *maps, bool bf16, const void *f0, const void *f1, int nx, int ny, int nz,
+                              int box_x, int box_y);
+
 // Generated cross stencils (sp_generated.cu), radius up to kMaxGenRadius.
 constexpr int kMaxGenRadius = 4;
 int generated_weights(int order, int dims, double *wk, double *lambda_max);

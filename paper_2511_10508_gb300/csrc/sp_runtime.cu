@@ -1,6 +1,7 @@
 // sp_runtime.cu -- the C ABI of include/sp.h: simulation handles, argument
 // validation, the forward-Euler stability check, device buffers, initial
 // conditions, stepping, host transfers and reductions.
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
@@ -19,6 +20,15 @@ using namespace sp;
 
 namespace sp {
 thread_local int g_step_variant = 0;
+}
+
+// Polls before the kernels' bounded device waits give up (0: their default);
+// sp_set_wait_polls, a test hook.
+static std::atomic<long long> g_wait_polls{0};
+
+extern "C" int sp_set_wait_polls(long long polls) {
+    g_wait_polls.store(polls < 0 ? -1 : polls, std::memory_order_relaxed);
+    return 0;
 }
 
 // --------------------------------------------------------------- errors --
@@ -212,7 +222,9 @@ struct sp_sim {
     int cur;              // current level
     int64_t steps;
     cudaStream_t stream;  // library-owned stream
-    double *d_partials;   // reduction scratch: 2 doubles per block, then the result
+    double *d_partials;   // reduction scratch: 2 doubles per block, the result, then the wait flag
+    int *d_flag;          // set by a kernel whose bounded wait expired (inside d_partials)
+    bool waits_used;      // a kernel with bounded waits has run (the flag is checked)
     int nred;
     double *h_out;        // pinned host scalar
     double *d_stage;      // FP64 staging for converted transfers (lazy)
@@ -338,7 +350,11 @@ extern "C" int sp_create(int model, int dims, const int64_t shape[3], double h, 
             }
         }
     s->nred = reduce_blocks(s->N, s->n_sm);
-    e = cudaMalloc(&s->d_partials, sizeof(double) * (2 * (size_t)s->nred + 1));
+    e = cudaMalloc(&s->d_partials, sizeof(double) * (2 * (size_t)s->nred + 2));
+    if (e == cudaSuccess) {
+        s->d_flag = reinterpret_cast<int *>(s->d_partials + 2 * (size_t)s->nred + 1);
+        e = cudaMemset(s->d_flag, 0, sizeof(int));
+    }
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_out, sizeof(double));
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -403,6 +419,9 @@ static cudaError_t launch_one_step_impl(sp_sim *s, cudaStream_t st, int k) {
     a.nz = s->nz;
     a.k = s->k;
     a.kf = to_float(s->k);
+    a.flag = s->d_flag;
+    a.wait_polls = g_wait_polls.load(std::memory_order_relaxed);
+    if (s->variant == kTmaFamily) s->waits_used = true;
     if (s->stencil == SP_LAP_GENERATED)
         return launch_generated(s->model, s->dtype, s->p.stencil_order, s->dims, s->genw, a, s->mu_tmp, st, s->n_sm);
     if (s->variant == kUnfusedFamily) return launch_unfused_ch(s->dtype, s->stencil, a, s->mu_tmp, st, s->n_sm);
@@ -478,6 +497,9 @@ static std::vector<TuneChoice> tune_candidates(const sp_sim *s) {
         c.push_back({1, 0});
         c.push_back({1, 1});
         if (s->dims == 3 && s->dtype != SP_F64) c.push_back({1, 2});
+        if (s->dims == 3 && s->dtype != SP_F64 && s->model != SP_MODEL_C && s->nx % (int)(16 / s->esize) == 0 &&
+            tma_available())
+            c.push_back({1, kTmaFamily});
         if (planes27_applies(s->dims, s->dtype, s->stencil, s->model)) c.push_back({1, kZregFamily});
         if (s->dims == 3 && steps_per_launch_3d(s->dtype, s->model, s->nx, 2) == 2) {
             c.push_back({2, 0});  // two steps per pass, 8 rows
@@ -651,6 +673,17 @@ static int ensure_stage(sp_sim *s) {
     return SP_OK;
 }
 
+// After a synchronisation: SP_ETIMEOUT (and the flag cleared) if a kernel's
+// bounded wait expired since the last check.
+static int check_wait_flag(sp_sim *s) {
+    if (!s->waits_used) return SP_OK;
+    int v = 0;
+    SP_CUDA(cudaMemcpy(&v, s->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!v) return SP_OK;
+    SP_CUDA(cudaMemset(s->d_flag, 0, sizeof(int)));
+    return fail(SP_ETIMEOUT, "a bounded wait in the tensor-map plane ring expired: the fields are not valid");
+}
+
 extern "C" int sp_read(sp_sim *s, int field, void *host_dst, size_t bytes, int as_f64, void *stream) {
     if (!s || !host_dst) return fail(SP_EINVAL, "NULL argument");
     if (int rc = check_field(s, field)) return rc;
@@ -671,7 +704,7 @@ extern "C" int sp_read(sp_sim *s, int field, void *host_dst, size_t bytes, int a
         }
     }
     SP_CUDA(cudaStreamSynchronize(st));
-    return SP_OK;
+    return check_wait_flag(s);
 }
 
 extern "C" int sp_write(sp_sim *s, int field, const void *host_src, size_t bytes, int is_f64, void *stream) {
@@ -726,7 +759,7 @@ extern "C" int sp_reduce(sp_sim *s, int what, double *out, void *stream) {
     SP_CUDA(cudaMemcpyAsync(s->h_out, d_out, sizeof(double), cudaMemcpyDeviceToHost, st));
     SP_CUDA(cudaStreamSynchronize(st));
     *out = *s->h_out;
-    return SP_OK;
+    return check_wait_flag(s);
 }
 
 extern "C" int sp_field_devptr(sp_sim *s, int field, void **dptr) {

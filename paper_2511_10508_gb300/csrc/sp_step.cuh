@@ -2005,10 +2005,15 @@ struct Step3dAsyncShape {
     static constexpr int DMU = (MODEL == CH) ? 2 * r + 1 : 0;
     static constexpr int NF = num_fields<MODEL>();
     static constexpr int EPT = (HIN * NCH + NT - 1) / NT;  // chunk copies per thread per field
-    static constexpr int GUARD = 16;                 // bytes before and after each region
-    static constexpr size_t in_bytes = sizeof(T) * (size_t)NF * D * PIN;
+    // plane slots start on 128-byte boundaries (tensor-map destinations)
+    static constexpr int PINS = (int)(((size_t)PIN * sizeof(T) + 127) / 128 * 128 / sizeof(T));
+    static constexpr int GUARD = 128;                // bytes before and after each region
+    static constexpr size_t in_bytes = sizeof(T) * (size_t)NF * D * PINS;
     static constexpr size_t mu_off = GUARD + in_bytes + GUARD;
-    static constexpr size_t smem_bytes = mu_off + sizeof(C) * (size_t)DMU * PMU + GUARD;
+    static constexpr size_t bar_off = (mu_off + sizeof(C) * (size_t)DMU * PMU + GUARD + 7) / 8 * 8;
+    // + D mbarriers + slack to align the dynamic shared memory base to 128 bytes
+    static constexpr size_t smem_bytes = bar_off + 8 * (size_t)D + 128;
+    static constexpr unsigned box_bytes = (unsigned)(sizeof(T) * (size_t)PIN);  // one field's plane box
 };
 
 // The V cells at p (16-byte aligned, a multiple of 16 bytes), widened to float.
@@ -2060,17 +2065,38 @@ __device__ __forceinline__ void async_chunk_sums(const T *const (&pl)[2 * Stenci
     }
 }
 
-template <int MODEL, int ST, typename T, int TXT, int TY>
-__global__ void __launch_bounds__(TXT * TY) step3d_async_kernel(StepArgs a, int tiles_x, int tiles_y, int segs) {
+// TMA (family 6): the same kernel with each input plane box (tile + halo, all
+// in-grid columns and rows) moved by one tensor-map load per field, issued by
+// one thread into the ring slot and completed on the slot's mbarrier; chunks of
+// the box outside the grid (periodic wrap, zero-filled by the load) are copied
+// from their wrapped positions with plain loads, fetched one plane ahead, once
+// the box has landed.  Waits are bounded: if one expires, every thread leaves
+// together after the copies in flight have landed (again bounded), and the
+// kernel sets *a.flag.
+template <int MODEL, int ST, typename T, int TXT, int TY, bool TMA>
+__global__ void __launch_bounds__(TXT * TY) step3d_async_kernel(StepArgs a, int tiles_x, int tiles_y, int segs,
+                                                                const __grid_constant__ TmaMaps maps) {
     static_assert(MODEL != MC, "Model C runs on the accessor-based kernels");
     typedef Step3dAsyncShape<MODEL, ST, T, TXT, TY> Sh;
     typedef typename Sh::C C;
     constexpr int V = Sh::V, r = Sh::r, R = Sh::R, TX = Sh::TX, NT = Sh::NT, NCH = Sh::NCH, SW = Sh::SW;
-    constexpr int HIN = Sh::HIN, PIN = Sh::PIN, P = Sh::P, D = Sh::D, HMU = Sh::HMU, PMU = Sh::PMU;
+    constexpr int HIN = Sh::HIN, PIN = Sh::PINS, P = Sh::P, D = Sh::D, HMU = Sh::HMU, PMU = Sh::PMU;
     constexpr int DMU = Sh::DMU, NF = Sh::NF, EPT = Sh::EPT;
+    static_assert(D <= 32, "one phase bit per slot");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *s_in = reinterpret_cast<T *>(smem_raw + Sh::GUARD);      // [NF][D][PIN]
-    C *s_mu = reinterpret_cast<C *>(smem_raw + Sh::mu_off);     // [DMU][PMU]
+    unsigned char *sbase = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    T *s_in = reinterpret_cast<T *>(sbase + Sh::GUARD);      // [NF][D][PIN]
+    C *s_mu = reinterpret_cast<C *>(sbase + Sh::mu_off);     // [DMU][PMU]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sbase + Sh::bar_off);  // [D] (TMA)
+    const long long polls = a.wait_polls == 0 ? kDefaultWaitPolls : (a.wait_polls < 0 ? 0 : a.wait_polls);
+    unsigned phase = 0;  // TMA: parity of the next completion of each slot's barrier
+    if constexpr (TMA) {
+        if (threadIdx.x == 0) {
+            for (int i = 0; i < D; ++i) mbar_init(&bars[i], 1);
+            mbar_init_fence();
+        }
+        __syncthreads();
+    }
 
     const ConstsC<C> k(a.k, a.kf);
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -2090,7 +2116,8 @@ __global__ void __launch_bounds__(TXT * TY) step3d_async_kernel(StepArgs a, int 
         const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
         const int nplanes = (z1 - z0) + 2 * R;
 
-        // global (plane-relative) offsets of this thread's chunk copies, or -1
+        // global (plane-relative) offsets of this thread's chunk copies, or -1; TMA:
+        // only chunks outside the grid (the box's zero fill) are copied by threads
         int goff[EPT];
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
@@ -2098,10 +2125,47 @@ __global__ void __launch_bounds__(TXT * TY) step3d_async_kernel(StepArgs a, int 
             goff[e] = -1;
             if (q < HIN * NCH) {
                 const int yi = q / NCH, ci = q - yi * NCH;
-                goff[e] = wrap_idx(y0 - R + yi, ny) * nx + wrap_idx(x0 - V + ci * V, nx);
+                const int y = y0 - R + yi, x = x0 - V + ci * V;
+                if (!TMA || y < 0 || y >= ny || x < 0 || x + V > nx)
+                    goff[e] = wrap_idx(y, ny) * nx + wrap_idx(x, nx);
             }
         }
+        uint4 fx[NF][EPT];  // TMA: wrapped chunks of the next plane
+        auto fetch_fix = [&](int j) {
+            if (TMA && j < nplanes) {
+                const size_t zoff = (size_t)wrap_idx(z0 - R + j, nz) * plane;
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+#pragma unroll
+                    for (int e = 0; e < EPT; ++e)
+                        if (goff[e] >= 0) fx[f][e] = __ldg(reinterpret_cast<const uint4 *>(in[f] + zoff + goff[e]));
+            }
+        };
+        auto put_fix = [&](int j) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                T *slot = s_in + ((size_t)f * D + j % D) * PIN;
+#pragma unroll
+                for (int e = 0; e < EPT; ++e)
+                    if (goff[e] >= 0) *reinterpret_cast<uint4 *>(slot + (t + e * NT) * V) = fx[f][e];
+            }
+        };
+        auto issue_tma = [&](int j) {
+            if (t == 0 && j < nplanes) {
+                fence_proxy_async_smem();  // the slot's earlier reads and writes come first
+                const int sl = j % D;
+                mbar_arrive_expect_tx(&bars[sl], NF * Sh::box_bytes);
+                const int zc = wrap_idx(z0 - R + j, nz);
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+                    tma_load_3d(s_in + ((size_t)f * D + sl) * PIN, &maps.m[f], x0 - V, y0 - R, zc, &bars[sl]);
+            }
+        };
         auto issue = [&](int j) {
+            if (TMA) {
+                issue_tma(j);
+                return;
+            }
             if (j < nplanes) {
                 const size_t zoff = (size_t)wrap_idx(z0 - R + j, nz) * plane;
 #pragma unroll
@@ -2118,9 +2182,26 @@ __global__ void __launch_bounds__(TXT * TY) step3d_async_kernel(StepArgs a, int 
 
 #pragma unroll
         for (int j = 0; j < P; ++j) issue(j);
+        fetch_fix(0);
         for (int j = 0; j < nplanes; ++j) {
-            cp_async_wait<P - 1>();
-            __syncthreads();  // plane j complete for every thread; planes <= j-1 no longer read
+            if constexpr (TMA) {
+                const int sl = j % D;
+                const bool ok = mbar_wait_bounded(&bars[sl], (phase >> sl) & 1u, polls);
+                if (ok) put_fix(j);
+                if (__syncthreads_or(!ok)) {  // plane j complete for every thread, or give up together
+                    if (t == 0 && a.flag) atomicExch(a.flag, 1);
+                    if (t == 0)
+                        for (int g = j; g < j + P && g < nplanes; ++g)  // copies still in flight
+                            mbar_wait_bounded(&bars[g % D], (phase >> (g % D)) & 1u, kDefaultWaitPolls);
+                    __syncthreads();
+                    return;
+                }
+                phase ^= 1u << sl;
+                fetch_fix(j + 1);
+            } else {
+                cp_async_wait<P - 1>();
+                __syncthreads();  // plane j complete for every thread; planes <= j-1 no longer read
+            }
             issue(j + P);
             if constexpr (MODEL == CH) {
                 if (j >= 2 * r) {
@@ -2189,7 +2270,7 @@ __global__ void __launch_bounds__(TXT * TY) step3d_async_kernel(StepArgs a, int 
                 }
             }
         }
-        cp_async_wait<0>();
+        if constexpr (!TMA) cp_async_wait<0>();
         __syncthreads();  // the rings are reused by the next segment
     }  // segments
 }

@@ -308,9 +308,13 @@ cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
             kern<<<(unsigned)std::min(items, wave), WS::NT, WS::smem_bytes, s>>>(a, tx, ty, segs);
             return cudaGetLastError();
         }
-        if (fam != 2 && a.nx % AS::V == 0 && aligned) {
-            // FP32 / BF16 3D: cp.async plane ring with planes in flight
-            auto kern = step3d_async_kernel<MODEL, ST, T, ATX, ATY>;
+        if (fam == kTmaFamily && a.nx % AS::V == 0 && aligned) {
+            // FP32 / BF16 3D: the plane ring with tensor-map plane loads
+            TmaMaps maps;
+            const cudaError_t e = encode_plane_maps(&maps, sizeof(T) == 2, a.in0, a.in1, a.nx, a.ny, a.nz, AS::SW,
+                                                    AS::HIN);
+            if (e != cudaSuccess) return e;
+            auto kern = step3d_async_kernel<MODEL, ST, T, ATX, ATY, true>;
             static const int occ = [&] {
                 cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AS::smem_bytes);
                 int o = 1;
@@ -321,7 +325,23 @@ cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s, int n_sm, int k) {
             const long long wave = (long long)n_sm * std::max(occ, 1);
             const int segs = lockstep_segments((long long)tx * ty, a.nz, 2 * AS::R, wave);
             const long long items = (long long)tx * ty * segs;
-            kern<<<(unsigned)std::min(items, wave), AS::NT, AS::smem_bytes, s>>>(a, tx, ty, segs);
+            kern<<<(unsigned)std::min(items, wave), AS::NT, AS::smem_bytes, s>>>(a, tx, ty, segs, maps);
+            return cudaGetLastError();
+        }
+        if (fam != 2 && a.nx % AS::V == 0 && aligned) {
+            // FP32 / BF16 3D: cp.async plane ring with planes in flight
+            auto kern = step3d_async_kernel<MODEL, ST, T, ATX, ATY, false>;
+            static const int occ = [&] {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AS::smem_bytes);
+                int o = 1;
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, AS::NT, AS::smem_bytes);
+                return o;
+            }();
+            const int tx = (a.nx + AS::TX - 1) / AS::TX, ty = (a.ny + ATY - 1) / ATY;
+            const long long wave = (long long)n_sm * std::max(occ, 1);
+            const int segs = lockstep_segments((long long)tx * ty, a.nz, 2 * AS::R, wave);
+            const long long items = (long long)tx * ty * segs;
+            kern<<<(unsigned)std::min(items, wave), AS::NT, AS::smem_bytes, s>>>(a, tx, ty, segs, TmaMaps{});
             return cudaGetLastError();
         }
         // FP32 / BF16 3D, any nx: vectorised plane kernel, 64 x 32 tiles

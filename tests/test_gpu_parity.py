@@ -627,6 +627,75 @@ def test_3d_kernel_families_agree(sp, dtype, model, st, shape):
         assert O.rel_l2(outs[0][0].astype(np.float64), ref) < TOL[1]
 
 
+TMA_SHAPES = {1: [(40, 33, 64), (5, 7, 8), (70, 40, 256), (9, 17, 68), (3, 2, 4), (6, 40, 192)],
+              2: [(40, 33, 64), (5, 7, 8), (70, 40, 256), (9, 17, 136), (6, 40, 256)]}
+
+
+@pytest.mark.parametrize("case", range(6))
+@pytest.mark.parametrize("model,st", [(m, s) for m in (0, 1, 2) for s in (3, 4, 5)])
+@pytest.mark.parametrize("dtype", [1, 2])
+def test_3d_tma_family_equals_cp_async_family(sp, dtype, model, st, case):
+    """3D FP32 / BF16: the plane ring with tensor-map (TMA) plane loads (family 6)
+    equals the cp.async plane ring (family 1) bit for bit, through a graph replay
+    (40 steps).  Shapes: ragged tiles in x, y and z, a grid smaller than one tile
+    in every axis (the box's out-of-grid chunks are all wrapped copies, several
+    periods for nx = 4), several x tiles, and long z axes split across CTAs."""
+    shapes = TMA_SHAPES[dtype]
+    if case >= len(shapes):
+        pytest.skip("fewer BF16 shapes (nx a multiple of 8)")
+    shape = shapes[case]
+    kw = dict(gs_patches=1, gs_patch=1) if model == 2 and min(shape) < 8 else {}
+    outs = []
+    for variant in (1, 6):
+        sim, dt = make(sp, model, shape, st, dtype=dtype, **kw)
+        with sim:
+            sim.launch_config = (1, variant)
+            assert sim.launch_config == (1, variant)
+            sim.step(40)
+            outs.append([sim.read(f, as_f64=False) for f in range(2 if model in TWO else 1)])
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+def test_3d_tma_family_availability(sp):
+    """Family 6 needs 3D FP32 / BF16, nx a multiple of 16 bytes of cells, and not
+    Model C."""
+    for model, shape, st, dtype in ((3, (8, 8, 8), 3, 1), (1, (8, 8, 10), 3, 1), (1, (8, 8, 12), 3, 2),
+                                    (1, (8, 8, 8), 3, 0), (1, (64, 64), 0, 1)):
+        sim, _ = make(sp, model, shape, st, dtype=dtype)
+        with sim:
+            with pytest.raises(sp.SpError):
+                sim.launch_config = (1, 6)
+
+
+def test_3d_tma_wait_timeout_reports_and_recovers(sp):
+    """A bounded mbarrier wait that gives up (forced with the test hook: no polls)
+    ends the kernel with the copies in flight drained and sets the simulation's
+    flag: the next read raises SP_ETIMEOUT once, the context stays usable, and a
+    later run with the default bound equals the cp.async family bit for bit."""
+    shape = (20, 33, 64)
+    sim, _ = make(sp, 1, shape, 3, dtype=1)
+    with sim:
+        sim.launch_config = (1, 6)
+        try:
+            sp.set_wait_polls(-1)
+            sim.step(2)
+        finally:
+            sp.set_wait_polls(0)
+        with pytest.raises(sp.SpError) as ei:
+            sim.read(0)
+        assert ei.value.code == 6  # SP_ETIMEOUT
+        sim.read(0)  # the flag was cleared
+    outs = []
+    for variant in (6, 1):
+        sim, _ = make(sp, 1, shape, 3, dtype=1)
+        with sim:
+            sim.launch_config = (1, variant)
+            sim.step(5)
+            outs.append(sim.read(0, as_f64=False))
+    assert np.array_equal(outs[0], outs[1])
+
+
 def test_two_host_threads_step_independent_grids(sp):
     """Two simulations stepped (and autotuned) concurrently from two host threads
     give the same fields as when run one after the other: the launch
