@@ -215,7 +215,9 @@ int sp_step(sp_sim *sim, int64_t nsteps, void *stream);
  * Copy field `field` (0 = phi/u, 1 = v) of the current time level to host
  * memory.  as_f64 != 0 converts to FP64 (exact widening for FP32/BF16);
  * otherwise the storage type is copied.  `bytes` must equal N * element size.
- * Synchronises `stream` before returning.
+ * Synchronises `stream` before returning.  SP_ETIMEOUT (once, after copying) if
+ * a bounded device wait of a step since the last check expired (the field is
+ * then not a valid time level; see sp_set_wait_polls).
  */
 int sp_read(sp_sim *sim, int field, void *host_dst, size_t bytes, int as_f64, void *stream);
 
@@ -226,7 +228,8 @@ int sp_read(sp_sim *sim, int field, void *host_dst, size_t bytes, int as_f64, vo
  */
 int sp_write(sp_sim *sim, int field, const void *host_src, size_t bytes, int is_f64, void *stream);
 
-/* Reduce the current time level (sp_reduce_what) into *out (FP64).  Synchronises. */
+/* Reduce the current time level (sp_reduce_what) into *out (FP64).  Synchronises.
+ * SP_ETIMEOUT as for sp_read. */
 int sp_reduce(sp_sim *sim, int what, double *out, void *stream);
 
 /*

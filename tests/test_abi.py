@@ -215,3 +215,12 @@ def test_admission_order_by_priority(sp):
     assert order([], [], 100, 4) == []
     # negative priorities come after the default 0
     assert order([1, 1, 1], [-1, 0, -5], 100, 10) == [1, 0, 2]
+
+
+def test_wait_poll_hook_needs_no_device():
+    """The bounded-wait test hook only sets a process-wide value: callable
+    without a GPU, every value accepted, 0 restores the default."""
+    import paper_2511_10508_gb300._native as N
+
+    for v in (5, -1, 0):
+        assert N.lib().sp_set_wait_polls(v) == 0
