@@ -127,3 +127,25 @@ def test_reference_arm_line():
     assert line["e2e"] == {"value": line["value"], "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+
+
+def test_workload_table_is_well_formed():
+    """Every bench workload names a model, dims and stencil that fit together,
+    a storage type, a positive step count, and (where given) a steps-per-launch
+    and kernel-family pair from the library's documented values; the per-config
+    entries name existing workloads."""
+    models = {0, 1, 2, 3, 4}
+    for name, spec in bench.WORKLOADS.items():
+        assert 7 <= len(spec) <= 9, name
+        model, dims, shape, dt, st, dtype, sub = spec[:7]
+        assert model in models and dims in (2, 3) and len(shape) == dims, name
+        assert all(int(n) >= 1 for n in shape) and dt > 0 and sub >= 1, name
+        assert dtype in (0, 1, 2), name
+        if st != 6:  # fixed stencils: 0-2 are 2D, 3-5 are 3D
+            assert (st < 3) == (dims == 2), name
+        if len(spec) > 7:
+            assert spec[7] in (1, 2, 4), name
+        if len(spec) > 8:
+            assert spec[8] in (0, 1, 2, 3, 4, 5, 6), name
+    for entry in bench.PER_CONFIG:
+        assert entry[1] in bench.WORKLOADS, entry
